@@ -1,0 +1,380 @@
+"""Benchmark: LM iterations/s of sliding-window bundle adjustment on one GB300.
+
+Default workload: the 20-keyframe stereo window (5000 landmarks, ~53k observations, 5%
+outliers), mixed precision, 20 LM iterations per solve; one step = one full solve from
+the same initial state.  The plain FP64 path is timed on the same window beside it.
+
+Prints one JSON line (rank 0).  Keys beyond the base contract: gobs_per_s, rms_px and the
+oracle's RMS (validity gate |diff| <= 1e-3 px), fp64 (the FP64 path's throughput),
+roofline (dominant kernel, achieved vs peak), cpu_baseline (oracle on the host cores),
+e2e (through the public API with host buffers), clocks, gpu_launches.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c1] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_GFLOPS = 1250.0     # 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="c1")
+    ap.add_argument("--precision", default=None, help="mixed (default for c1) or fp64")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.rows = []
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def peaks():
+    try:
+        with open(MEASURED_PEAKS) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# -------------------------------------------------------------- algorithmic work model
+
+def work_model(p, P: int, mixed: bool) -> dict:
+    """Algorithmic bytes and FLOPs of each part of one LM iteration."""
+    t = 4 if mixed else 8
+    N, M, K = p.N, p.M, p.K
+    n_c = 6 * (K - 1)
+    m = np.bincount(np.unique(p.obs_lm.astype(np.int64) * K + p.obs_kf) // K, minlength=M)
+    blocks = float(np.sum(m * (m + 1) / 2))
+    lin_bytes = N * (2 * t + 4) + P * (12 + 9 * t) + M * (24 + 72) + K * 96
+    schur_bytes = P * (12 + 9 * t) + M * (72 + 48) + 8 * n_c * n_c
+    backsub_bytes = N * (2 * t + 4) + P * (12 + 9 * t) + M * (24 * 3 + 72 + 48)
+    return {
+        "lin": {"bytes": lin_bytes, "flops": 110.0 * N + 130.0 * P},
+        "schur": {"bytes": schur_bytes, "flops": 216.0 * blocks + 135.0 * P},
+        "chol": {"bytes": 16.0 * n_c * n_c, "flops": n_c ** 3 / 3.0 + 2.0 * n_c ** 2},
+        "backsub": {"bytes": backsub_bytes, "flops": 40.0 * N + 24.0 * P},
+        "schur_blocks": blocks,
+    }
+
+
+# ------------------------------------------------------------------------- reference
+
+def run_reference(args):
+    """The oracle (CPU, FP64 dense normal equations) on the same workload: each step is one
+    LM iteration of the oracle's solve (a bounded sample of the 20-iteration solve)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import ba
+    from paper_2506_04359_gb300 import synth
+    p = synth.make_problem(args.workload)
+    w = ba.Window.from_problem(p)
+    poses, lms, lam, nu, lin = p.poses0.copy(), p.lm0.copy(), 1e-4, 2.0, None
+    for _ in range(args.warmup):
+        poses, lms, lam, nu, _, lin = ba.lm_iteration(w, poses, lms, lam, nu, lin)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        poses, lms, lam, nu, _, lin = ba.lm_iteration(w, poses, lms, lam, nu, lin)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": "BA LM iters/s (c1 window)", "value": v, "unit": "LM iters/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "K": p.K, "C": p.C, "M": p.M, "N": p.N, "precision": "fp64",
+                   "step": "one oracle LM iteration (dense full normal equations, LAPACK Cholesky)"},
+        "cpu_baseline": {"value": v, "unit": "LM iters/s", "cores": cores(), "kind": "oracle",
+                         "sample": f"{args.steps} LM iterations of the {args.workload} window"},
+        "e2e": {"value": v, "unit": "LM iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_04359_gb300 import cvba, synth
+
+    p = synth.make_problem(args.workload)
+    precision = args.precision or ("mixed" if p.precision == "mixed" else "fp64")
+    stream = torch.cuda.Stream(device=dev)
+    l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def make_ctx(prec):
+        ctx = cvba.Context(prec, device=local, stream=stream.cuda_stream).load(p)
+        return ctx
+
+    poses0 = torch.tensor(p.poses0.reshape(p.K, 12), dtype=torch.float64, device=dev)
+    lms0 = torch.tensor(p.lm0, dtype=torch.float64, device=dev)
+    launches_per_solve = None
+
+    def timed_solves(ctx, steps, warmup, sampler=None):
+        """Device time of `steps` solves, L2 flushed between solves outside the events."""
+        nonlocal launches_per_solve
+        launches_per_solve = ctx.cvba_solve_launch_count(p.iters) + 2
+        for _ in range(warmup):
+            with torch.cuda.stream(stream):
+                ctx.cvba_set_poses_dev(poses0.data_ptr())
+                ctx.cvba_set_landmarks_dev(lms0.data_ptr())
+                ctx.cvba_solve_async(p.iters, huber_delta=p.huber_delta)
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                l2_flush.fill_(float(k))
+                ev[k][0].record(stream)
+                ctx.cvba_set_poses_dev(poses0.data_ptr())
+                ctx.cvba_set_landmarks_dev(lms0.data_ptr())
+                ctx.cvba_solve_async(p.iters, huber_delta=p.huber_delta)
+                ev[k][1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize()
+        barrier(ws)
+        wall = time.perf_counter() - t0
+        dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+        return dev_s, wall
+
+    # --- main timed run (mixed by default)
+    ctx = make_ctx(precision)
+    P = ctx.cvba_get_sizes()["P"]
+    with ClockSampler(local) as cs:
+        dev_s, wall = timed_solves(ctx, args.steps, args.warmup)
+    dev_s = max_over_ranks(dev_s, ws)
+    tr = ctx.cvba_get_trace(p.iters)
+    ev = ctx.cvba_evaluate(p.huber_delta)
+    iters_total = args.steps * p.iters * ws
+    value = iters_total / dev_s
+    gobs = float(np.sum(tr["n_valid"])) * args.steps * ws / dev_s / 1e9
+
+    # --- roofline of the dominant kernel (CUDA events around each part, same stream)
+    prof = ctx.cvba_profile_iteration(20, huber_delta=p.huber_delta)
+    kern = {k: v for k, v in prof.items() if k != "memset"}
+    dom = max(kern, key=kern.get)
+    wm = work_model(p, P, precision == "mixed")
+    pk, pk_kind = peaks()
+    if dom == "chol":
+        achieved = wm["chol"]["flops"] / (kern[dom] * 1e-3) / 1e12
+        roof = {"kernel": "k_chol", "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS / 1e3,
+                "unit": "TFLOP/s", "frac": achieved / (FP64_NOMINAL_GFLOPS / 1e3), "traffic": None,
+                "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); a probe measured 1.19 TFLOP/s"}
+    else:
+        achieved = wm[dom]["bytes"] / (kern[dom] * 1e-3) / 1e9
+        roof = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind}
+    roof["ms_per_launch"] = kern[dom]
+    roof["parts_ms"] = prof
+
+    # --- FP64 path on the same window
+    fp64 = None
+    if precision != "fp64":
+        c64 = make_ctx("fp64")
+        d64, _ = timed_solves(c64, max(3, args.steps // 2), 1)
+        d64 = max_over_ranks(d64, ws)
+        fp64 = {"value": max(3, args.steps // 2) * p.iters * ws / d64, "unit": "LM iters/s",
+                "rms_px": c64.cvba_evaluate(p.huber_delta)["rms"]}
+        c64.close()
+
+    # --- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_intr, h_tcb = pin(p.rig.intr), pin(p.rig.T_cb.reshape(-1, 12))
+        h_poses, h_lms = pin(p.poses0.reshape(p.K, 12)), pin(p.lm0)
+        h_kf, h_cam, h_lm = pin(p.obs_kf.astype(np.int32)), pin(p.obs_cam.astype(np.int32)), pin(p.obs_lm.astype(np.int32))
+        h_uv = pin(p.obs_uv)
+        out_p = pin(np.zeros((p.K, 3, 4)))
+        out_l = pin(np.zeros((p.M, 3)))
+        ce = cvba.Context(precision, device=local, stream=stream.cuda_stream)
+
+        def e2e_step():
+            ce.cvba_set_rig(h_intr, h_tcb)
+            ce.cvba_set_poses(h_poses, p.fixed_kf)
+            ce.cvba_set_landmarks(h_lms)
+            ce.cvba_set_observations(h_kf, h_cam, h_lm, h_uv)
+            ce.cvba_solve(p.iters, huber_delta=p.huber_delta)
+            cvba.lib.cvba_get_poses(ce._h, cvba._dptr(out_p))
+            cvba.lib.cvba_get_landmarks(ce._h, cvba._dptr(out_l))
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier(ws)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+        h2d = sum(a.nbytes for a in (h_intr, h_tcb, h_poses, h_lms, h_kf, h_cam, h_lm, h_uv))
+        d2h = out_p.nbytes + out_l.nbytes + p.iters * 64
+        e2e = {"value": iters_total / e2e_s, "unit": "LM iters/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / args.steps}
+        ce.close()
+
+    # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import ba
+        w = ba.Window.from_problem(p)
+        t0 = time.perf_counter()
+        poses, lms, lam, nu, lin = p.poses0.copy(), p.lm0.copy(), 1e-4, 2.0, None
+        n_it = 0
+        while n_it < p.iters:
+            poses, lms, lam, nu, _, lin = ba.lm_iteration(w, poses, lms, lam, nu, lin)
+            n_it += 1
+            if time.perf_counter() - t0 > 12.0:
+                break
+        dt = time.perf_counter() - t0
+        cpu = {"value": n_it / dt, "unit": "LM iters/s", "cores": cores(), "kind": "oracle",
+               "sample": f"first {n_it} LM iterations of the {args.workload} window (dense FP64 normal equations)"}
+
+    golden_rms = None
+    gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle.json")
+    if os.path.exists(gpath):
+        with open(gpath) as f:
+            golden_rms = json.load(f)["final_rms_px"]
+
+    if rank == 0:
+        line = {
+            "metric": "BA LM iters/s (Gobs/s, RMS within 1e-3 px of oracle, % HBM peak)",
+            "value": value, "unit": "LM iters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "K": p.K, "C": p.C, "M": p.M, "N": p.N, "pairs": P,
+                       "precision": precision, "lm_iters_per_step": p.iters, "parallelism": "replicas",
+                       "l2": "flushed between steps (512 MiB write outside the timed events)"},
+            "gobs_per_s": gobs,
+            "rms_px": ev["rms"], "rms_oracle_px": golden_rms,
+            "rms_ok": None if golden_rms is None else bool(abs(ev["rms"] - golden_rms) <= 1e-3),
+            "fp64": fp64,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": cs.summary(),
+            "gpu_launches": launches_per_solve * args.steps,
+            "wall_s_timed": wall,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,181 @@
+/*
+ * cvba.h - C ABI of the GB300 sliding-window bundle-adjustment library.
+ *
+ * The library solves the local sparse bundle adjustment (SBA) problem of cuVSLAM
+ * (arXiv 2506.04359, Sec. 2.2 "3D module"):
+ *
+ *   r_ijk = pi(T^cb_k T^bw_i p^w_j) - o_{j,k}                          (Eq. r^repr)
+ *   argmin over T^bw_{1:N}, p^w_{1:M} of  sum_i sum_j sum_k ||r_ijk||^2_Sigma   (Eq. argmin)
+ *
+ * with keyframe poses T^bw_i (base-from-world), a rig of cameras with fixed
+ * camera-from-base extrinsics T^cb_k and pinhole intrinsics, landmarks p^w_j and pixel
+ * observations o_{j,k}.  As in Sec. 2.2, the linear system of each Levenberg-Marquardt
+ * (LM) step is solved with the Schur complement: poses first (dense Cholesky of the
+ * reduced camera system), landmarks afterwards.
+ *
+ * Readings fixed by this library where the paper is silent: pinhole projection without
+ * distortion; Sigma = I (pixels); Huber robust kernel on the per-observation residual
+ * norm with IRLS weights; left SE(3) update T <- Exp(xi) T with xi = (rho, phi); Euclidean
+ * landmark update; one keyframe fixed (gauge); observations with camera depth <= z_min
+ * are invalid; Marquardt scaling D = diag(H) floored at 1e-12 max(diag H); Nielsen's
+ * lambda update; exactly `iters` iterations, each one linear solve, accepted or not.
+ *
+ * Conventions
+ *  - Poses are (3 x 4) row-major [R | t] with X_b = R X_w + t (12 doubles each).
+ *  - Rig extrinsics T_cb are (3 x 4) row-major [R | t] with X_c = R X_b + t.
+ *  - Intrinsics are fx, fy, cx, cy (4 doubles per camera); camera axes x right, y down,
+ *    z forward; u = fx X/Z + cx, v = fy Y/Z + cy.
+ *  - All host arrays are owned by the caller; setters copy them (host -> device) at the
+ *    call, getters copy out into caller-owned arrays.  No pointer is retained.
+ *  - Every call returns a status; no C++ exception crosses the ABI.  The message of the
+ *    last failure on a context is available from cvba_last_error().
+ *  - A context is bound to one CUDA device and one stream; calls on one context must not
+ *    overlap in time.  Different contexts are independent.
+ */
+#ifndef CVBA_H
+#define CVBA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cvba_ctx cvba_ctx;
+
+typedef enum {
+  CVBA_OK = 0,
+  CVBA_ERR_INVALID_ARG = 1,  /* bad size, NULL pointer, unsupported option */
+  CVBA_ERR_INDEX = 2,        /* observation index out of range */
+  CVBA_ERR_NONFINITE = 3,    /* NaN / Inf in an input array */
+  CVBA_ERR_CUDA = 4,         /* a CUDA runtime call failed (message has the detail) */
+  CVBA_ERR_OOM = 5,          /* device allocation failed */
+  CVBA_ERR_NOT_PD = 6,       /* reserved: a system was not positive definite (solve
+                                reports this per iteration in cvba_iter.nonpd instead) */
+  CVBA_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+  CVBA_ERR_STATE = 8         /* call out of order (e.g. solve before all setters) */
+} cvba_status;
+
+typedef enum {
+  CVBA_FP64 = 0,   /* every step in FP64 */
+  CVBA_MIXED = 1   /* residuals, Jacobians and Schur products in FP32 with FP64
+                      accumulation; RCS Cholesky, refinement and gain ratio in FP64 */
+} cvba_precision;
+
+typedef struct {
+  int iters;            /* LM iterations to run (>= 0) */
+  double huber_delta;   /* Huber threshold in pixels (> 0) */
+  double lambda0;       /* initial LM damping (> 0); used when reset_lambda != 0 */
+  double z_min;         /* minimum camera depth of a valid observation (metres) */
+  int reset_lambda;     /* 1: start from lambda0, nu = 2; 0: continue the context's
+                           lambda and nu (after cvba_set_damping or a previous solve) */
+} cvba_opts;
+
+typedef struct {
+  double cost0;      /* F = 1/2 sum rho(||r||^2) at the linearisation point */
+  double cost1;      /* F at the candidate (NaN if the system was not PD) */
+  double lambda;     /* damping used for this iteration's solve */
+  double gain;       /* (cost0 - cost1) / pred */
+  double pred;       /* predicted reduction L = 1/2 d^T (lambda D d - g) */
+  double step_norm;  /* ||delta|| over all free coordinates */
+  double rms_px;     /* unweighted RMS reprojection error at the linearisation point */
+  int accepted;      /* 1 if the candidate became the new state */
+  int nonpd;         /* 1 if a 3x3 landmark block or the RCS was not PD (step rejected) */
+  int n_valid;       /* observations with camera depth > z_min */
+  int n_inlier;      /* valid observations with ||r|| <= huber_delta */
+} cvba_iter;
+
+/* Library / context lifetime ---------------------------------------------------- */
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL = a new non-blocking stream owned by the context). */
+cvba_status cvba_create(cvba_ctx** out, int device, void* cuda_stream, cvba_precision precision);
+void cvba_destroy(cvba_ctx* ctx);
+const char* cvba_status_string(cvba_status s);
+const char* cvba_last_error(const cvba_ctx* ctx);
+
+/* Problem definition (Sec. 2.2: rig T^cb_k and intrinsics, poses T^bw_i, landmarks
+ * p^w_j, observations o_{j,k}) ---------------------------------------------------- */
+
+/* n_cams >= 1 cameras: intr[n_cams*4] (fx, fy, cx, cy), T_cb[n_cams*12]. */
+cvba_status cvba_set_rig(cvba_ctx* ctx, int n_cams, const double* intr, const double* T_cb);
+
+/* n_kf >= 2 keyframe poses T_bw[n_kf*12]; keyframe `fixed_kf` is held constant. */
+cvba_status cvba_set_poses(cvba_ctx* ctx, int n_kf, const double* T_bw, int fixed_kf);
+
+/* n_lm >= 1 landmarks p_w[n_lm*3] in world coordinates. */
+cvba_status cvba_set_landmarks(cvba_ctx* ctx, int n_lm, const double* p_w);
+
+/* n_obs observations: keyframe kf[n], camera cam[n], landmark lm[n] and pixel uv[2n..2n+1].
+ * Indices are validated (CVBA_ERR_INDEX); every landmark needs >= 2 observations
+ * (CVBA_ERR_INVALID_ARG).  Must follow set_rig, set_poses and set_landmarks.
+ * This call builds the device layout: observations sorted by (landmark, keyframe,
+ * camera), landmarks reordered by keyframe span, and the solve's work tiles. */
+cvba_status cvba_set_observations(cvba_ctx* ctx, int n_obs, const int32_t* kf, const int32_t* cam,
+                                  const int32_t* lm, const double* uv);
+
+/* Solve ---------------------------------------------------------------------------- */
+
+/* Run opts->iters LM iterations from the current state.  trace (caller-owned,
+ * opts->iters entries, may be NULL) receives one record per iteration.  The whole solve
+ * runs on the device; the host waits once at the end. */
+cvba_status cvba_solve(cvba_ctx* ctx, const cvba_opts* opts, cvba_iter* trace);
+
+/* Cost, counts and RMS at the current state (cost = 1/2 sum rho). */
+cvba_status cvba_evaluate(cvba_ctx* ctx, double huber_delta, double z_min, double* cost,
+                          double* rms_px, int* n_valid, int* n_inlier);
+
+/* Results and state ------------------------------------------------------------------ */
+
+cvba_status cvba_get_poses(cvba_ctx* ctx, double* T_bw /* n_kf*12 */);
+cvba_status cvba_get_landmarks(cvba_ctx* ctx, double* p_w /* n_lm*3, caller's order */);
+
+/* Increment solved in the last iteration, accepted or not: the free keyframes' twists in
+ * keyframe order (6 each, fixed keyframe skipped), then landmark steps in the caller's
+ * landmark order (3 each).  dx[6*(n_kf-1) + 3*n_lm]. */
+cvba_status cvba_get_increment(cvba_ctx* ctx, double* dx);
+
+/* Current LM damping state (lambda, nu) and its replacement. */
+cvba_status cvba_get_damping(cvba_ctx* ctx, double* lambda, double* nu);
+cvba_status cvba_set_damping(cvba_ctx* ctx, double lambda, double nu);
+
+/* Device layout, for exact integer checks: lm_order[n_lm] = caller landmark index of each
+ * internal landmark; obs_order[n_obs] = caller observation index of each internal slot;
+ * lm_off[n_lm+1] = internal landmark segment offsets into the slots.  Any may be NULL. */
+cvba_status cvba_get_layout(cvba_ctx* ctx, int32_t* lm_order, int32_t* obs_order, int32_t* lm_off);
+
+/* Sizes: n_kf, n_cams, n_lm, n_obs, n_pairs ((landmark, keyframe) pairs). Any may be NULL. */
+cvba_status cvba_get_sizes(cvba_ctx* ctx, int* n_kf, int* n_cams, int* n_lm, int* n_obs, int* n_pairs);
+
+/* Number of kernel launches one solve of `iters` iterations issues (graph nodes that
+ * are kernels of this library). */
+cvba_status cvba_solve_launch_count(cvba_ctx* ctx, int iters, int* n_launches);
+
+/* Asynchronous solve: enqueue the solve on the context's stream and return without
+ * waiting.  The iteration records stay on the device until cvba_get_trace. */
+cvba_status cvba_solve_async(cvba_ctx* ctx, const cvba_opts* opts);
+
+/* Copy the first n iteration records of the last solve (waits for the stream). */
+cvba_status cvba_get_trace(cvba_ctx* ctx, cvba_iter* trace, int n);
+
+/* Device-pointer variants (e.g. torch tensors' data_ptr()): same layouts as the host
+ * setters / getters, copied on the context's stream without a host synchronisation.
+ * Require a layout (cvba_set_observations).  The caller keeps the arrays alive until the
+ * stream has consumed them. */
+cvba_status cvba_set_poses_dev(cvba_ctx* ctx, const double* T_bw /* device, n_kf*12 */);
+cvba_status cvba_set_landmarks_dev(cvba_ctx* ctx, const double* p_w /* device, n_lm*3 */);
+cvba_status cvba_get_poses_dev(cvba_ctx* ctx, double* T_bw /* device, n_kf*12 */);
+cvba_status cvba_get_landmarks_dev(cvba_ctx* ctx, double* p_w /* device, n_lm*3 */);
+
+/* Profiling: run `reps` iterations with CUDA events around each part of an iteration
+ * (part names: cvba_profile_names(), comma separated) and return the mean milliseconds
+ * per part in ms[*n_parts].  With ms == NULL only *n_parts is set.  Leaves the state as
+ * `reps` LM iterations would. */
+cvba_status cvba_profile_iteration(cvba_ctx* ctx, const cvba_opts* opts, int reps, float* ms, int* n_parts);
+const char* cvba_profile_names(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CVBA_H */

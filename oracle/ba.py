@@ -356,3 +356,23 @@ def layout(obs_kf, obs_cam, obs_lm, M):
     counts = np.bincount(np.asarray(obs_lm, np.int64), minlength=M)
     lm_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
     return perm, lm_off
+
+
+def device_layout(obs_kf, obs_cam, obs_lm, M):
+    """Integer layout the library builds, by its definition: landmarks ordered by (first
+    observing keyframe, last observing keyframe, caller index); observation slots ordered
+    by (landmark rank, keyframe, camera, caller index); landmark segment offsets."""
+    obs_kf = np.asarray(obs_kf, np.int64)
+    obs_lm = np.asarray(obs_lm, np.int64)
+    first = np.full(M, np.iinfo(np.int64).max)
+    last = np.full(M, -1)
+    np.minimum.at(first, obs_lm, obs_kf)
+    np.maximum.at(last, obs_lm, obs_kf)
+    lm_order = np.lexsort((np.arange(M), last, first)).astype(np.int32)
+    rank = np.empty(M, np.int64)
+    rank[lm_order] = np.arange(M)
+    n = np.arange(obs_kf.size)
+    obs_order = np.lexsort((n, np.asarray(obs_cam, np.int64), obs_kf, rank[obs_lm])).astype(np.int32)
+    counts = np.bincount(rank[obs_lm], minlength=M)
+    lm_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    return lm_order, obs_order, lm_off

@@ -1,0 +1,847 @@
+// Host side of the C ABI declared in include/cvba.h: argument validation, the device
+// layout of one bundle-adjustment window (observations sorted by landmark, keyframe,
+// camera; (landmark, keyframe) pairs; work tiles), device memory and the CUDA graph that
+// replays a whole LM solve.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cvba_internal.h"
+
+using namespace cvba;
+
+struct cvba_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cvba_precision prec = CVBA_FP64;
+  std::string err;
+
+  int C = 0, K = 0, M = 0, N = 0, P = 0, fixed_kf = 0;
+  std::vector<double> intr, T_cb, poses, lms;
+  bool have_rig = false, have_poses = false, have_lms = false, have_layout = false;
+
+  std::vector<int32_t> lm_order, lm_rank, obs_order, lm_off;
+  std::vector<LinTile> lin_tiles;
+  std::vector<SchurTile> schur_tiles;
+
+  struct Slot {
+    void* p;
+    size_t cap;
+  };
+  std::vector<Slot> arena;       // device buffers of the layout, reused when large enough
+  size_t arena_next = 0;
+  Dev d{};
+  double* d_eval = nullptr;
+  int32_t* d_lm_order = nullptr;
+  cvba_iter* d_trace = nullptr;
+  int trace_cap = 0;
+  cudaGraphExec_t graph = nullptr;
+  Dev graph_dev{};               // device view the graph was captured with
+  struct Key {
+    int iters = -1, reset = -1;
+    double lam0 = 0, huber = 0, zmin = 0;
+    bool operator==(const Key& o) const {
+      return iters == o.iters && reset == o.reset && lam0 == o.lam0 && huber == o.huber && zmin == o.zmin;
+    }
+  } graph_key;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+cvba_status fail(cvba_ctx* c, cvba_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+cvba_status cuda_fail(cvba_ctx* c, cudaError_t e, const char* what) {
+  cudaGetLastError();
+  return fail(c, e == cudaErrorMemoryAllocation ? CVBA_ERR_OOM : CVBA_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                 \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+bool all_finite(const double* p, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+void drop_graph(cvba_ctx* c) {
+  if (c->graph) {
+    cudaGraphExecDestroy(c->graph);
+    c->graph = nullptr;
+  }
+  c->graph_key = cvba_ctx::Key{};
+}
+
+void free_device(cvba_ctx* c) {
+  drop_graph(c);
+  for (auto& s : c->arena) cudaFree(s.p);
+  c->arena.clear();
+  c->arena_next = 0;
+  if (c->d_trace) cudaFree(c->d_trace);
+  c->d_trace = nullptr;
+  c->trace_cap = 0;
+  c->d = Dev{};
+  c->d_eval = nullptr;
+  c->d_lm_order = nullptr;
+  c->have_layout = false;
+}
+
+// Next buffer of the layout: the slot used by the previous layout is kept when it is
+// large enough, so re-loading a window of the same shape allocates nothing.
+template <typename T>
+cudaError_t dalloc(cvba_ctx* c, T** p, size_t n) {
+  const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+  const size_t idx = c->arena_next++;
+  if (idx < c->arena.size() && c->arena[idx].cap >= bytes) {
+    *p = static_cast<T*>(c->arena[idx].p);
+    return cudaSuccess;
+  }
+  void* q = nullptr;
+  if (idx < c->arena.size()) {
+    cudaFree(c->arena[idx].p);
+    c->arena[idx] = {nullptr, 0};
+  }
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) return e;
+  if (idx < c->arena.size())
+    c->arena[idx] = {q, bytes};
+  else
+    c->arena.push_back({q, bytes});
+  *p = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+// Stream-ordered copies on the context's stream (which may be a caller's stream).
+cudaError_t d2h(cvba_ctx* c, void* dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
+}
+cudaError_t h2d(cvba_ctx* c, void* dst, const void* src, size_t bytes) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream);
+  return e != cudaSuccess ? e : cudaStreamSynchronize(c->stream);
+}
+
+int read_cur(cvba_ctx* c) {
+  int cur = 0;
+  if (c->d.ctrl && d2h(c, &cur, &c->d.ctrl->cur, sizeof(int)) != cudaSuccess) cur = 0;
+  return cur;
+}
+
+// Stable counting sort of idx by key[idx] in [0, n_keys).
+void counting_sort(std::vector<int32_t>& idx, const std::vector<int32_t>& key, int n_keys) {
+  std::vector<int64_t> cnt((size_t)n_keys + 1, 0);
+  for (int32_t i : idx) cnt[(size_t)key[i] + 1]++;
+  for (int k = 0; k < n_keys; ++k) cnt[k + 1] += cnt[k];
+  std::vector<int32_t> out(idx.size());
+  for (int32_t i : idx) out[cnt[key[i]]++] = i;
+  idx.swap(out);
+}
+
+cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, const int32_t* lm, const double* uv) {
+  const int K = c->K, C = c->C, M = c->M, N = c->N;
+  // --- landmark order: by (first keyframe, last keyframe, caller index)
+  std::vector<int32_t> first(M, K), last(M, -1), count(M, 0);
+  for (int n = 0; n < N; ++n) {
+    const int j = lm[n];
+    first[j] = std::min(first[j], kf[n]);
+    last[j] = std::max(last[j], kf[n]);
+    count[j]++;
+  }
+  for (int j = 0; j < M; ++j)
+    if (count[j] < 2)
+      return fail(c, CVBA_ERR_INVALID_ARG, "landmark " + std::to_string(j) + " has fewer than 2 observations");
+  c->lm_order.resize(M);
+  for (int j = 0; j < M; ++j) c->lm_order[j] = j;
+  {
+    std::vector<int32_t> key_last(M), key_first(M);
+    for (int j = 0; j < M; ++j) {
+      key_last[j] = last[j];
+      key_first[j] = first[j];
+    }
+    counting_sort(c->lm_order, key_last, K);
+    counting_sort(c->lm_order, key_first, K);
+  }
+  c->lm_rank.assign(M, 0);
+  for (int i = 0; i < M; ++i) c->lm_rank[c->lm_order[i]] = i;
+  // --- observation order: by (internal landmark, keyframe, camera, caller index)
+  std::vector<int32_t> key_kc(N), key_lm(N);
+  for (int n = 0; n < N; ++n) {
+    key_kc[n] = kf[n] * C + cam[n];
+    key_lm[n] = c->lm_rank[lm[n]];
+  }
+  c->obs_order.resize(N);
+  for (int n = 0; n < N; ++n) c->obs_order[n] = n;
+  counting_sort(c->obs_order, key_kc, K * C);
+  counting_sort(c->obs_order, key_lm, M);
+  c->lm_off.assign(M + 1, 0);
+  for (int n = 0; n < N; ++n) c->lm_off[key_lm[n] + 1]++;
+  for (int j = 0; j < M; ++j) c->lm_off[j + 1] += c->lm_off[j];
+  // --- pairs (internal landmark, keyframe)
+  std::vector<int32_t> pair_kf, pair_lm, pair_obs, lm_pair(M + 1, 0), obs_cam(N);
+  pair_kf.reserve(N);
+  pair_lm.reserve(N);
+  pair_obs.reserve(N + 1);
+  for (int s = 0; s < N; ++s) {
+    const int n = c->obs_order[s];
+    const int jl = key_lm[n];
+    obs_cam[s] = cam[n];
+    if (s == 0 || jl != key_lm[c->obs_order[s - 1]] || kf[n] != kf[c->obs_order[s - 1]]) {
+      pair_kf.push_back(kf[n]);
+      pair_lm.push_back(jl);
+      pair_obs.push_back(s);
+      lm_pair[jl + 1]++;
+    }
+  }
+  const int P = (int)pair_kf.size();
+  pair_obs.push_back(N);
+  for (int j = 0; j < M; ++j) lm_pair[j + 1] += lm_pair[j];
+  std::vector<int32_t> lm_blk(M + 1, 0);
+  {
+    int64_t acc = 0;
+    for (int j = 0; j < M; ++j) {
+      const int64_t m = lm_pair[j + 1] - lm_pair[j];
+      acc += m * (m - 1) / 2;
+      if (acc > INT32_MAX) return fail(c, CVBA_ERR_INVALID_ARG, "too many pose-pair blocks");
+      lm_blk[j + 1] = (int32_t)acc;
+    }
+  }
+  std::vector<int32_t> kf_pb(K);
+  for (int a = 0; a < K; ++a) kf_pb[a] = a == c->fixed_kf ? -1 : (a < c->fixed_kf ? a : a - 1);
+  c->P = P;
+
+  // --- tiles
+  const int n_sm = 152;
+  c->lin_tiles.clear();
+  {
+    const int target = std::max(32, std::min(LIN_TILE_PAIRS, (P + 2 * n_sm - 1) / (2 * n_sm)));
+    int l0 = 0;
+    while (l0 < M) {
+      int l1 = l0;
+      while (l1 < M) {
+        const int np = lm_pair[l1 + 1] - lm_pair[l0];
+        if (l1 > l0 && (np > target || l1 - l0 >= LIN_TILE_LMS)) break;
+        ++l1;
+      }
+      c->lin_tiles.push_back(LinTile{l0, l1, lm_pair[l0], lm_pair[l1]});
+      l0 = l1;
+    }
+  }
+  c->schur_tiles.clear();
+  {
+    const int target = std::max(32, std::min(SCHUR_TILE_PAIRS, (P + 2 * n_sm - 1) / (2 * n_sm)));
+    std::vector<int> lo(M, INT32_MAX), hi(M, -1);
+    for (int j = 0; j < M; ++j)
+      for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
+        const int pb = kf_pb[pair_kf[q]];
+        if (pb < 0) continue;
+        lo[j] = std::min(lo[j], pb);
+        hi[j] = std::max(hi[j], pb);
+      }
+    auto wide = [&](int j) { return hi[j] >= 0 && hi[j] - lo[j] + 1 > SPAN_MAX; };
+    int l0 = 0;
+    while (l0 < M) {
+      const bool direct = wide(l0);
+      int l1 = l0, wlo = INT32_MAX, whi = -1;
+      while (l1 < M) {
+        if (wide(l1) != direct) break;
+        const int np = lm_pair[l1 + 1] - lm_pair[l0];
+        if (np > SCHUR_TILE_PAIRS || l1 - l0 >= SCHUR_TILE_LMS) break;
+        if (l1 > l0 && np > target) break;
+        int nlo = std::min(wlo, lo[l1]), nhi = std::max(whi, hi[l1]);
+        if (!direct && nhi >= 0 && nhi - nlo + 1 > SPAN_MAX) break;
+        wlo = nlo;
+        whi = nhi;
+        ++l1;
+      }
+      SchurTile t{};
+      t.l0 = l0;
+      t.l1 = l1;
+      t.p0 = lm_pair[l0];
+      t.p1 = lm_pair[l1];
+      t.b0 = lm_blk[l0];
+      t.b1 = lm_blk[l1];
+      t.direct = direct ? 1 : 0;
+      t.k_lo = whi >= 0 ? wlo : 0;
+      t.span = whi >= 0 ? whi - wlo + 1 : 1;
+      if (direct) {
+        t.k_lo = 0;
+        t.span = K - 1;
+      }
+      c->schur_tiles.push_back(t);
+      l0 = l1;
+    }
+  }
+
+  // --- device buffers
+  c->have_layout = false;
+  c->arena_next = 0;
+  const int n_c = 6 * (K - 1);
+  const bool mixed = c->prec == CVBA_MIXED;
+  Dev& d = c->d;
+  d = Dev{};
+  d.K = K;
+  d.C = C;
+  d.M = M;
+  d.N = N;
+  d.P = P;
+  d.n_c = n_c;
+  d.fixed_kf = c->fixed_kf;
+  d.mixed = mixed ? 1 : 0;
+  d.n_lin_tiles = (int)c->lin_tiles.size();
+  d.n_schur_tiles = (int)c->schur_tiles.size();
+  double *rig, *pose0, *pose1, *lm0, *lm1;
+  int32_t *ocam, *pkf, *plm, *pobs, *lpair, *lblk, *kpb;
+  LinTile* lt;
+  SchurTile* st;
+  CK(dalloc(c, &rig, (size_t)C * RIG_STRIDE), "alloc rig");
+  CK(dalloc(c, &pose0, (size_t)K * POSE_STRIDE), "alloc poses");
+  CK(dalloc(c, &pose1, (size_t)K * POSE_STRIDE), "alloc poses");
+  CK(dalloc(c, &lm0, (size_t)M * 3), "alloc landmarks");
+  CK(dalloc(c, &lm1, (size_t)M * 3), "alloc landmarks");
+  CK(dalloc(c, &ocam, N), "alloc obs");
+  CK(dalloc(c, &pkf, P), "alloc pairs");
+  CK(dalloc(c, &plm, P), "alloc pairs");
+  CK(dalloc(c, &pobs, (size_t)P + 1), "alloc pairs");
+  CK(dalloc(c, &lpair, (size_t)M + 1), "alloc lm offsets");
+  CK(dalloc(c, &lblk, (size_t)M + 1), "alloc lm offsets");
+  CK(dalloc(c, &kpb, K), "alloc kf map");
+  CK(dalloc(c, &lt, c->lin_tiles.size()), "alloc tiles");
+  CK(dalloc(c, &st, c->schur_tiles.size()), "alloc tiles");
+  d.rig = rig;
+  d.pose[0] = pose0;
+  d.pose[1] = pose1;
+  d.lm[0] = lm0;
+  d.lm[1] = lm1;
+  d.obs_cam = ocam;
+  d.pair_kf = pkf;
+  d.pair_lm = plm;
+  d.pair_obs = pobs;
+  d.lm_pair = lpair;
+  d.lm_blk = lblk;
+  d.kf_pb = kpb;
+  d.lin_tiles = lt;
+  d.schur_tiles = st;
+  if (mixed) {
+    float* uvf;
+    CK(dalloc(c, &uvf, (size_t)N * 2), "alloc obs");
+    std::vector<float> h(2 * (size_t)N);
+    for (int s = 0; s < N; ++s) {
+      h[2 * s] = (float)uv[2 * (size_t)c->obs_order[s]];
+      h[2 * s + 1] = (float)uv[2 * (size_t)c->obs_order[s] + 1];
+    }
+    CK(cudaMemcpy(uvf, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice), "upload obs");
+    d.obs_uv = uvf;
+    float* pl;
+    CK(dalloc(c, &pl, (size_t)P * PAIR_LIN), "alloc pair lin");
+    d.pair_lin = pl;
+  } else {
+    double* uvd;
+    CK(dalloc(c, &uvd, (size_t)N * 2), "alloc obs");
+    std::vector<double> h(2 * (size_t)N);
+    for (int s = 0; s < N; ++s) {
+      h[2 * s] = uv[2 * (size_t)c->obs_order[s]];
+      h[2 * s + 1] = uv[2 * (size_t)c->obs_order[s] + 1];
+    }
+    CK(cudaMemcpy(uvd, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice), "upload obs");
+    d.obs_uv = uvd;
+    double* pl;
+    CK(dalloc(c, &pl, (size_t)P * PAIR_LIN), "alloc pair lin");
+    d.pair_lin = pl;
+  }
+  CK(dalloc(c, &d.lm_H, (size_t)M * 6), "alloc");
+  CK(dalloc(c, &d.lm_g, (size_t)M * 3), "alloc");
+  CK(dalloc(c, &d.kf_gp, (size_t)K * 6), "alloc");
+  CK(dalloc(c, &d.kf_dp, (size_t)K * 6), "alloc");
+  CK(dalloc(c, &d.lm_Vinv, (size_t)M * VINV_STRIDE), "alloc");
+  CK(dalloc(c, &d.S, (size_t)n_c * n_c), "alloc RCS");
+  CK(dalloc(c, &d.bS, (size_t)n_c), "alloc");
+  CK(dalloc(c, &d.dc, (size_t)n_c), "alloc");
+  CK(dalloc(c, &d.dp, (size_t)M * 3), "alloc");
+  CK(dalloc(c, &d.lin_part, (size_t)d.n_lin_tiles * 4), "alloc");
+  CK(dalloc(c, &d.bs_part, (size_t)d.n_lin_tiles * 8), "alloc");
+  CK(dalloc(c, &d.ctrl, 1), "alloc");
+  CK(dalloc(c, &c->d_eval, 4), "alloc");
+  CK(dalloc(c, &c->d_lm_order, M), "alloc");
+  CK(cudaMemcpy(c->d_lm_order, c->lm_order.data(), (size_t)M * 4, cudaMemcpyHostToDevice), "upload");
+  d.trace = c->d_trace;
+  CK(cudaMemset(d.dc, 0, sizeof(double) * std::max(n_c, 1)), "memset");
+  CK(cudaMemset(d.dp, 0, sizeof(double) * (size_t)M * 3), "memset");
+  CK(cudaMemset(d.lin_part, 0, sizeof(double) * (size_t)d.n_lin_tiles * 4), "memset");
+  CK(cudaMemset(d.bs_part, 0, sizeof(double) * (size_t)d.n_lin_tiles * 8), "memset");
+  {
+    Ctrl h{};
+    h.cur = 0;
+    h.lam = 1e-4;
+    h.nu = 2.0;
+    CK(cudaMemcpy(d.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice), "upload ctrl");
+  }
+  std::vector<double> righ((size_t)C * RIG_STRIDE);
+  for (int k = 0; k < C; ++k) {
+    for (int i = 0; i < 4; ++i) righ[k * RIG_STRIDE + i] = c->intr[k * 4 + i];
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) righ[k * RIG_STRIDE + 4 + r * 3 + q] = c->T_cb[k * 12 + r * 4 + q];
+      righ[k * RIG_STRIDE + 13 + r] = c->T_cb[k * 12 + r * 4 + 3];
+    }
+  }
+  std::vector<double> poseh((size_t)K * POSE_STRIDE);
+  for (int a = 0; a < K; ++a)
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) poseh[a * POSE_STRIDE + r * 3 + q] = c->poses[a * 12 + r * 4 + q];
+      poseh[a * POSE_STRIDE + 9 + r] = c->poses[a * 12 + r * 4 + 3];
+    }
+  std::vector<double> lmh((size_t)M * 3);
+  for (int i = 0; i < M; ++i)
+    for (int k = 0; k < 3; ++k) lmh[(size_t)i * 3 + k] = c->lms[(size_t)c->lm_order[i] * 3 + k];
+  CK(cudaMemcpy(rig, righ.data(), righ.size() * 8, cudaMemcpyHostToDevice), "upload rig");
+  CK(cudaMemcpy(pose0, poseh.data(), poseh.size() * 8, cudaMemcpyHostToDevice), "upload poses");
+  CK(cudaMemcpy(lm0, lmh.data(), lmh.size() * 8, cudaMemcpyHostToDevice), "upload landmarks");
+  CK(cudaMemcpy(ocam, obs_cam.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "upload");
+  CK(cudaMemcpy(pkf, pair_kf.data(), (size_t)P * 4, cudaMemcpyHostToDevice), "upload");
+  CK(cudaMemcpy(plm, pair_lm.data(), (size_t)P * 4, cudaMemcpyHostToDevice), "upload");
+  CK(cudaMemcpy(pobs, pair_obs.data(), ((size_t)P + 1) * 4, cudaMemcpyHostToDevice), "upload");
+  CK(cudaMemcpy(lpair, lm_pair.data(), ((size_t)M + 1) * 4, cudaMemcpyHostToDevice), "upload");
+  CK(cudaMemcpy(lblk, lm_blk.data(), ((size_t)M + 1) * 4, cudaMemcpyHostToDevice), "upload");
+  CK(cudaMemcpy(kpb, kf_pb.data(), (size_t)K * 4, cudaMemcpyHostToDevice), "upload");
+  CK(cudaMemcpy(lt, c->lin_tiles.data(), c->lin_tiles.size() * sizeof(LinTile), cudaMemcpyHostToDevice), "upload");
+  CK(cudaMemcpy(st, c->schur_tiles.data(), c->schur_tiles.size() * sizeof(SchurTile), cudaMemcpyHostToDevice),
+     "upload");
+  c->have_layout = true;
+  return CVBA_OK;
+}
+
+cvba_status upload_state(cvba_ctx* c) {
+  // poses / landmarks replaced after the layout exists: write into the current buffer
+  const int cur = read_cur(c);
+  const int K = c->K, M = c->M;
+  std::vector<double> poseh((size_t)K * POSE_STRIDE);
+  for (int a = 0; a < K; ++a)
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) poseh[a * POSE_STRIDE + r * 3 + q] = c->poses[a * 12 + r * 4 + q];
+      poseh[a * POSE_STRIDE + 9 + r] = c->poses[a * 12 + r * 4 + 3];
+    }
+  std::vector<double> lmh((size_t)M * 3);
+  for (int i = 0; i < M; ++i)
+    for (int k = 0; k < 3; ++k) lmh[(size_t)i * 3 + k] = c->lms[(size_t)c->lm_order[i] * 3 + k];
+  CK(cudaMemcpyAsync(c->d.pose[cur], poseh.data(), poseh.size() * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+  CK(cudaMemcpyAsync(c->d.lm[cur], lmh.data(), lmh.size() * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  return CVBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cvba_status_string(cvba_status s) {
+  switch (s) {
+    case CVBA_OK: return "ok";
+    case CVBA_ERR_INVALID_ARG: return "invalid argument";
+    case CVBA_ERR_INDEX: return "index out of range";
+    case CVBA_ERR_NONFINITE: return "non-finite input";
+    case CVBA_ERR_CUDA: return "CUDA error";
+    case CVBA_ERR_OOM: return "out of device memory";
+    case CVBA_ERR_NOT_PD: return "not positive definite";
+    case CVBA_ERR_TIMEOUT: return "device wait timed out";
+    case CVBA_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* cvba_last_error(const cvba_ctx* c) { return c ? c->err.c_str() : ""; }
+
+cvba_status cvba_create(cvba_ctx** out, int device, void* stream, cvba_precision prec) {
+  if (!out) return CVBA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (prec != CVBA_FP64 && prec != CVBA_MIXED) return CVBA_ERR_INVALID_ARG;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev) {
+    cudaGetLastError();
+    return CVBA_ERR_CUDA;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return CVBA_ERR_CUDA;
+  if (prop.major != 10 || prop.minor != 3) return CVBA_ERR_CUDA;   // built for sm_103a only
+  cvba_ctx* c = new cvba_ctx();
+  c->device = device;
+  c->prec = prec;
+  DeviceGuard g(device);
+  cudaError_t e = set_kernel_attributes();
+  if (e == cudaSuccess) {
+    if (stream) {
+      c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      c->own_stream = true;
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return CVBA_ERR_CUDA;
+  }
+  *out = c;
+  return CVBA_OK;
+}
+
+void cvba_destroy(cvba_ctx* c) {
+  if (!c) return;
+  {
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_device(c);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  }
+  delete c;
+}
+
+cvba_status cvba_set_rig(cvba_ctx* c, int n_cams, const double* intr, const double* T_cb) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (n_cams < 1 || n_cams > C_MAX || !intr || !T_cb)
+    return fail(c, CVBA_ERR_INVALID_ARG, "set_rig: need 1 <= n_cams <= 64 and non-NULL arrays");
+  if (!all_finite(intr, (size_t)n_cams * 4) || !all_finite(T_cb, (size_t)n_cams * 12))
+    return fail(c, CVBA_ERR_NONFINITE, "set_rig: non-finite value");
+  DeviceGuard g(c->device);
+  if (c->have_layout && n_cams != c->C) c->have_layout = false;
+  c->C = n_cams;
+  c->intr.assign(intr, intr + (size_t)n_cams * 4);
+  c->T_cb.assign(T_cb, T_cb + (size_t)n_cams * 12);
+  c->have_rig = true;
+  if (c->have_layout) {
+    std::vector<double> righ((size_t)c->C * RIG_STRIDE);
+    for (int k = 0; k < c->C; ++k) {
+      for (int i = 0; i < 4; ++i) righ[k * RIG_STRIDE + i] = c->intr[k * 4 + i];
+      for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q) righ[k * RIG_STRIDE + 4 + r * 3 + q] = c->T_cb[k * 12 + r * 4 + q];
+        righ[k * RIG_STRIDE + 13 + r] = c->T_cb[k * 12 + r * 4 + 3];
+      }
+    }
+    CK(h2d(c, const_cast<double*>(c->d.rig), righ.data(), righ.size() * 8), "upload rig");
+  }
+  return CVBA_OK;
+}
+
+cvba_status cvba_set_poses(cvba_ctx* c, int n_kf, const double* T_bw, int fixed_kf) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (n_kf < 2 || n_kf > K_MAX || !T_bw)
+    return fail(c, CVBA_ERR_INVALID_ARG, "set_poses: need 2 <= n_kf <= 256 and a non-NULL array");
+  if (fixed_kf < 0 || fixed_kf >= n_kf) return fail(c, CVBA_ERR_INDEX, "set_poses: fixed_kf out of range");
+  if (!all_finite(T_bw, (size_t)n_kf * 12)) return fail(c, CVBA_ERR_NONFINITE, "set_poses: non-finite value");
+  DeviceGuard g(c->device);
+  if (c->have_layout && (n_kf != c->K || fixed_kf != c->fixed_kf)) c->have_layout = false;
+  c->K = n_kf;
+  c->fixed_kf = fixed_kf;
+  c->poses.assign(T_bw, T_bw + (size_t)n_kf * 12);
+  c->have_poses = true;
+  if (c->have_layout) return upload_state(c);
+  return CVBA_OK;
+}
+
+cvba_status cvba_set_landmarks(cvba_ctx* c, int n_lm, const double* p_w) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (n_lm < 1 || !p_w) return fail(c, CVBA_ERR_INVALID_ARG, "set_landmarks: need n_lm >= 1 and a non-NULL array");
+  if (!all_finite(p_w, (size_t)n_lm * 3)) return fail(c, CVBA_ERR_NONFINITE, "set_landmarks: non-finite value");
+  DeviceGuard g(c->device);
+  if (c->have_layout && n_lm != c->M) c->have_layout = false;
+  c->M = n_lm;
+  c->lms.assign(p_w, p_w + (size_t)n_lm * 3);
+  c->have_lms = true;
+  if (c->have_layout) return upload_state(c);
+  return CVBA_OK;
+}
+
+cvba_status cvba_set_observations(cvba_ctx* c, int n_obs, const int32_t* kf, const int32_t* cam,
+                                  const int32_t* lm, const double* uv) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_rig || !c->have_poses || !c->have_lms)
+    return fail(c, CVBA_ERR_STATE, "set_observations: set rig, poses and landmarks first");
+  if (n_obs < 1 || !kf || !cam || !lm || !uv)
+    return fail(c, CVBA_ERR_INVALID_ARG, "set_observations: need n_obs >= 1 and non-NULL arrays");
+  for (int n = 0; n < n_obs; ++n) {
+    if (kf[n] < 0 || kf[n] >= c->K || cam[n] < 0 || cam[n] >= c->C || lm[n] < 0 || lm[n] >= c->M)
+      return fail(c, CVBA_ERR_INDEX, "set_observations: index out of range at observation " + std::to_string(n));
+  }
+  if (!all_finite(uv, (size_t)n_obs * 2)) return fail(c, CVBA_ERR_NONFINITE, "set_observations: non-finite uv");
+  DeviceGuard g(c->device);
+  c->N = n_obs;
+  return build_layout(c, kf, cam, lm, uv);
+}
+
+namespace {
+cvba_status enqueue_solve(cvba_ctx* c, const cvba_opts* o) {
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "solve: set_observations first");
+  if (o->iters < 0 || !(o->huber_delta > 0.0) || !std::isfinite(o->huber_delta) || !std::isfinite(o->z_min) ||
+      (o->reset_lambda && !(o->lambda0 > 0.0 && std::isfinite(o->lambda0))))
+    return fail(c, CVBA_ERR_INVALID_ARG, "solve: bad options");
+  if (o->iters == 0) return CVBA_OK;
+  if (o->iters > c->trace_cap) {
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (c->d_trace) cudaFree(c->d_trace);
+    c->d_trace = nullptr;
+    c->trace_cap = 0;
+    CK(cudaMalloc(&c->d_trace, sizeof(cvba_iter) * (size_t)o->iters), "alloc trace");
+    c->trace_cap = o->iters;
+  }
+  c->d.trace = c->d_trace;
+  cvba_ctx::Key key;
+  key.iters = o->iters;
+  key.reset = o->reset_lambda ? 1 : 0;
+  key.lam0 = o->lambda0;
+  key.huber = o->huber_delta;
+  key.zmin = o->z_min;
+  if (!c->graph || !(key == c->graph_key) || std::memcmp(&c->graph_dev, &c->d, sizeof(Dev)) != 0) {
+    drop_graph(c);
+    cudaGraph_t gr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = enqueue_solve_init(c->d, o->lambda0, o->huber_delta, o->z_min, o->iters, key.reset, c->stream);
+    for (int it = 0; it < o->iters && e == cudaSuccess; ++it) e = enqueue_iteration(c->d, c->stream, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "enqueue solve");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+    e = cudaGraphInstantiate(&c->graph, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) return cuda_fail(c, e, "instantiate graph");
+    c->graph_key = key;
+    std::memcpy(&c->graph_dev, &c->d, sizeof(Dev));
+  }
+  CK(cudaGraphLaunch(c->graph, c->stream), "launch solve");
+  return CVBA_OK;
+}
+}  // namespace
+
+cvba_status cvba_solve(cvba_ctx* c, const cvba_opts* o, cvba_iter* trace) {
+  if (!c || !o) return CVBA_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cvba_status st = enqueue_solve(c, o);
+  if (st != CVBA_OK || o->iters == 0) return st;
+  if (trace)
+    CK(cudaMemcpyAsync(trace, c->d_trace, sizeof(cvba_iter) * (size_t)o->iters, cudaMemcpyDeviceToHost, c->stream),
+       "copy trace");
+  CK(cudaStreamSynchronize(c->stream), "solve");
+  return CVBA_OK;
+}
+
+cvba_status cvba_solve_async(cvba_ctx* c, const cvba_opts* o) {
+  if (!c || !o) return CVBA_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  return enqueue_solve(c, o);
+}
+
+cvba_status cvba_get_trace(cvba_ctx* c, cvba_iter* trace, int n) {
+  if (!c || !trace || n < 0) return CVBA_ERR_INVALID_ARG;
+  if (n > c->trace_cap) return fail(c, CVBA_ERR_INVALID_ARG, "get_trace: more records than the last solve");
+  if (n == 0) return CVBA_OK;
+  DeviceGuard g(c->device);
+  CK(d2h(c, trace, c->d_trace, sizeof(cvba_iter) * (size_t)n), "copy trace");
+  return CVBA_OK;
+}
+
+cvba_status cvba_set_poses_dev(cvba_ctx* c, const double* T_bw) {
+  if (!c || !T_bw) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "set_poses_dev: set_observations first");
+  DeviceGuard g(c->device);
+  CK(enqueue_state_io(c->d, 0, const_cast<double*>(T_bw), c->d_lm_order, c->stream), "set poses");
+  return CVBA_OK;
+}
+
+cvba_status cvba_set_landmarks_dev(cvba_ctx* c, const double* p_w) {
+  if (!c || !p_w) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "set_landmarks_dev: set_observations first");
+  DeviceGuard g(c->device);
+  CK(enqueue_state_io(c->d, 1, const_cast<double*>(p_w), c->d_lm_order, c->stream), "set landmarks");
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_poses_dev(cvba_ctx* c, double* T_bw) {
+  if (!c || !T_bw) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "get_poses_dev: set_observations first");
+  DeviceGuard g(c->device);
+  CK(enqueue_state_io(c->d, 2, T_bw, c->d_lm_order, c->stream), "get poses");
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_landmarks_dev(cvba_ctx* c, double* p_w) {
+  if (!c || !p_w) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "get_landmarks_dev: set_observations first");
+  DeviceGuard g(c->device);
+  CK(enqueue_state_io(c->d, 3, p_w, c->d_lm_order, c->stream), "get landmarks");
+  return CVBA_OK;
+}
+
+cvba_status cvba_profile_iteration(cvba_ctx* c, const cvba_opts* o, int reps, float* ms, int* n_parts) {
+  if (!c || !o || reps < 1) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "profile: set_observations first");
+  const int np = profile_parts();
+  if (n_parts) *n_parts = np;
+  if (!ms) return CVBA_OK;
+  DeviceGuard g(c->device);
+  cvba_opts one = *o;
+  one.iters = reps;
+  if (reps > c->trace_cap) {
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    if (c->d_trace) cudaFree(c->d_trace);
+    c->d_trace = nullptr;
+    c->trace_cap = 0;
+    CK(cudaMalloc(&c->d_trace, sizeof(cvba_iter) * (size_t)reps), "alloc trace");
+    c->trace_cap = reps;
+  }
+  c->d.trace = c->d_trace;
+  std::vector<cudaEvent_t> ev((size_t)np + 1);
+  for (auto& e : ev) CK(cudaEventCreate(&e), "event");
+  std::vector<double> acc(np, 0.0);
+  CK(enqueue_solve_init(c->d, one.lambda0, one.huber_delta, one.z_min, reps, one.reset_lambda, c->stream), "init");
+  cvba_status st = CVBA_OK;
+  for (int r = 0; r < reps && st == CVBA_OK; ++r) {
+    cudaError_t e = enqueue_iteration(c->d, c->stream, ev.data());
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[np]);
+    if (e != cudaSuccess) {
+      st = cuda_fail(c, e, "profile iteration");
+      break;
+    }
+    for (int k = 0; k < np; ++k) {
+      float t = 0.f;
+      cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      acc[k] += t;
+    }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (st != CVBA_OK) return st;
+  for (int k = 0; k < np; ++k) ms[k] = (float)(acc[k] / reps);
+  return CVBA_OK;
+}
+
+const char* cvba_profile_names(void) { return profile_names(); }
+
+cvba_status cvba_evaluate(cvba_ctx* c, double huber, double zmin, double* cost, double* rms, int* nv, int* ni) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "evaluate: set_observations first");
+  if (!(huber > 0.0) || !std::isfinite(zmin)) return fail(c, CVBA_ERR_INVALID_ARG, "evaluate: bad options");
+  DeviceGuard g(c->device);
+  CK(enqueue_evaluate(c->d, huber, zmin, c->d_eval, c->stream), "evaluate");
+  double h[4];
+  CK(cudaMemcpyAsync(h, c->d_eval, sizeof(h), cudaMemcpyDeviceToHost, c->stream), "copy");
+  CK(cudaStreamSynchronize(c->stream), "evaluate");
+  if (cost) *cost = h[0];
+  if (rms) *rms = h[2] > 0 ? std::sqrt(h[1] / h[2]) : 0.0;
+  if (nv) *nv = (int)h[2];
+  if (ni) *ni = (int)h[3];
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_poses(cvba_ctx* c, double* T_bw) {
+  if (!c || !T_bw) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) {
+    if (!c->have_poses) return fail(c, CVBA_ERR_STATE, "get_poses: no poses");
+    std::copy(c->poses.begin(), c->poses.end(), T_bw);
+    return CVBA_OK;
+  }
+  DeviceGuard g(c->device);
+  const int cur = read_cur(c);
+  std::vector<double> h((size_t)c->K * POSE_STRIDE);
+  CK(d2h(c, h.data(), c->d.pose[cur], h.size() * 8), "copy poses");
+  for (int a = 0; a < c->K; ++a)
+    for (int r = 0; r < 3; ++r) {
+      for (int q = 0; q < 3; ++q) T_bw[a * 12 + r * 4 + q] = h[a * POSE_STRIDE + r * 3 + q];
+      T_bw[a * 12 + r * 4 + 3] = h[a * POSE_STRIDE + 9 + r];
+    }
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_landmarks(cvba_ctx* c, double* p_w) {
+  if (!c || !p_w) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) {
+    if (!c->have_lms) return fail(c, CVBA_ERR_STATE, "get_landmarks: no landmarks");
+    std::copy(c->lms.begin(), c->lms.end(), p_w);
+    return CVBA_OK;
+  }
+  DeviceGuard g(c->device);
+  const int cur = read_cur(c);
+  std::vector<double> h((size_t)c->M * 3);
+  CK(d2h(c, h.data(), c->d.lm[cur], h.size() * 8), "copy landmarks");
+  for (int i = 0; i < c->M; ++i)
+    for (int k = 0; k < 3; ++k) p_w[(size_t)c->lm_order[i] * 3 + k] = h[(size_t)i * 3 + k];
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_increment(cvba_ctx* c, double* dx) {
+  if (!c || !dx) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "get_increment: no layout");
+  DeviceGuard g(c->device);
+  const int n_c = c->d.n_c;
+  CK(d2h(c, dx, c->d.dc, sizeof(double) * n_c), "copy dc");
+  std::vector<double> h((size_t)c->M * 3);
+  CK(d2h(c, h.data(), c->d.dp, h.size() * 8), "copy dp");
+  for (int i = 0; i < c->M; ++i)
+    for (int k = 0; k < 3; ++k) dx[n_c + (size_t)c->lm_order[i] * 3 + k] = h[(size_t)i * 3 + k];
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_damping(cvba_ctx* c, double* lam, double* nu) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "get_damping: no layout");
+  DeviceGuard g(c->device);
+  Ctrl h;
+  CK(d2h(c, &h, c->d.ctrl, sizeof(Ctrl)), "copy ctrl");
+  if (lam) *lam = h.lam;
+  if (nu) *nu = h.nu;
+  return CVBA_OK;
+}
+
+cvba_status cvba_set_damping(cvba_ctx* c, double lam, double nu) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "set_damping: no layout");
+  if (!(lam > 0.0) || !(nu >= 1.0) || !std::isfinite(lam) || !std::isfinite(nu))
+    return fail(c, CVBA_ERR_INVALID_ARG, "set_damping: need lambda > 0 and nu >= 1");
+  DeviceGuard g(c->device);
+  CK(h2d(c, &c->d.ctrl->lam, &lam, sizeof(double)), "set lambda");
+  CK(h2d(c, &c->d.ctrl->nu, &nu, sizeof(double)), "set nu");
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_layout(cvba_ctx* c, int32_t* lm_order, int32_t* obs_order, int32_t* lm_off) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "get_layout: no layout");
+  if (lm_order) std::copy(c->lm_order.begin(), c->lm_order.end(), lm_order);
+  if (obs_order) std::copy(c->obs_order.begin(), c->obs_order.end(), obs_order);
+  if (lm_off) std::copy(c->lm_off.begin(), c->lm_off.end(), lm_off);
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_sizes(cvba_ctx* c, int* n_kf, int* n_cams, int* n_lm, int* n_obs, int* n_pairs) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (n_kf) *n_kf = c->K;
+  if (n_cams) *n_cams = c->C;
+  if (n_lm) *n_lm = c->M;
+  if (n_obs) *n_obs = c->N;
+  if (n_pairs) *n_pairs = c->have_layout ? c->P : 0;
+  return CVBA_OK;
+}
+
+cvba_status cvba_solve_launch_count(cvba_ctx* c, int iters, int* n) {
+  if (!c || !n || iters < 0) return CVBA_ERR_INVALID_ARG;
+  *n = iters > 0 ? kernels_per_solve_init() + iters * kernels_per_iteration() : 0;
+  return CVBA_OK;
+}
+
+}  // extern "C"

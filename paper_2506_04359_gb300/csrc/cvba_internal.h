@@ -1,0 +1,108 @@
+// Internal definitions shared by the host layer (cvba_host.cpp) and the CUDA kernels
+// (cvba_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/cvba.h"
+
+namespace cvba {
+
+constexpr int RIG_STRIDE = 16;      // fx fy cx cy | R_cb (9, row-major) | t_cb (3)
+constexpr int POSE_STRIDE = 12;     // R (9, row-major) | t (3)
+constexpr int PAIR_LIN = 9;         // per (landmark, keyframe) pair: M3 (6 sym) | X_b (3)
+constexpr int VINV_STRIDE = 8;      // per landmark: V^-1 (6 sym) | tau | unused
+constexpr int K_MAX = 256;          // keyframes per window (sliding-window sizes)
+constexpr int C_MAX = 64;           // cameras per rig
+constexpr int LIN_THREADS = 256;
+constexpr int SCHUR_THREADS = 256;
+constexpr int CHOL_THREADS = 1024;
+constexpr int DECIDE_THREADS = 256;
+constexpr int LIN_TILE_PAIRS = 1024;    // pairs per linearisation / back-substitution tile
+constexpr int LIN_TILE_LMS = 512;       // landmarks per linearisation tile
+constexpr int SCHUR_TILE_PAIRS = 256;   // pairs staged in shared memory per Schur tile
+constexpr int SCHUR_TILE_LMS = 128;
+constexpr int SPAN_MAX = 24;            // free keyframes in one Schur tile's window
+
+// Device-resident LM control block.  Written only by the solve's kernels.
+struct Ctrl {
+  int cur;            // state buffer (0/1) holding the current iterate x
+  int need_lin;       // 1: the linearisation buffers must be rebuilt at x
+  int it;             // iterations done in this solve
+  int nonpd;          // set when a landmark block or the RCS is not positive definite
+  int iters;          // iterations requested (trace capacity)
+  int pad_;
+  double lam, nu;     // LM damping state
+  double huber, zmin; // solve options
+  double pred_p;      // pose part of d^T (lam D d - g)
+  double step2_p;     // ||dc||^2
+  unsigned long long maxdiag_lm;   // bit pattern of max landmark diag(H) (non-negative double)
+};
+
+// Landmark range [l0, l1) with its pairs [p0, p1); used by linearisation,
+// back-substitution and evaluation.
+struct LinTile {
+  int l0, l1, p0, p1;
+};
+
+// Landmark range for the Schur kernel: pairs [p0, p1), off-diagonal block work items
+// [b0, b1), and the window of free keyframe blocks [k_lo, k_lo + span) whose part of the
+// reduced camera system is accumulated in shared memory (direct = 1: straight to global).
+struct SchurTile {
+  int l0, l1, p0, p1, b0, b1, k_lo, span, direct;
+};
+
+struct Dev {
+  int K, C, M, N, P, n_c, fixed_kf, mixed;
+  int n_lin_tiles, n_schur_tiles;
+  // problem
+  const double* rig;          // C * RIG_STRIDE
+  double* pose[2];            // K * POSE_STRIDE, double-buffered state
+  double* lm[2];              // M * 3 (internal landmark order)
+  const void* obs_uv;         // N * 2, double (FP64) or float (mixed)
+  const int32_t* obs_cam;     // N
+  const int32_t* pair_kf;     // P
+  const int32_t* pair_lm;     // P
+  const int32_t* pair_obs;    // P + 1 observation offsets
+  const int32_t* lm_pair;     // M + 1 pair offsets
+  const int32_t* lm_blk;      // M + 1 off-diagonal block offsets, m(m-1)/2 per landmark
+  const int32_t* kf_pb;       // K: free block index or -1 for the fixed keyframe
+  const LinTile* lin_tiles;
+  const SchurTile* schur_tiles;
+  // linearisation
+  void* pair_lin;             // P * PAIR_LIN (double or float)
+  double* lm_H;               // M * 6  (Hll: 00 01 02 11 12 22)
+  double* lm_g;               // M * 3
+  double* kf_gp;              // K * 6  pose gradient
+  double* kf_dp;              // K * 6  diag of Hpp
+  // Schur / solve
+  double* lm_Vinv;            // M * VINV_STRIDE
+  double* S;                  // n_c * n_c (lower triangle used)
+  double* bS;                 // n_c   sum of W V^-1 g_l
+  double* dc;                 // n_c   pose increment
+  double* dp;                 // M * 3 landmark increment
+  // partial sums per linearisation tile
+  double* lin_part;           // n_lin_tiles * 4: cost, sum r^2, n_valid, n_inlier
+  double* bs_part;            // n_lin_tiles * 4: candidate cost, pred_l, step2_l, unused
+  cvba_iter* trace;           // iteration records (ctrl->iters entries)
+  Ctrl* ctrl;
+};
+
+// Launchers (cvba_kernels.cu).  All enqueue on `s` and return the launch status.
+cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double zmin, int iters,
+                               int reset_lambda, cudaStream_t s);
+// One LM iteration.  With ev != nullptr, profile_parts() + 1 events are recorded around
+// the iteration's parts (for cvba_profile_iteration).
+cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev);
+int profile_parts();
+const char* profile_names();
+// State transfer between a caller's device array (caller layout and landmark order) and
+// the current state buffer: mode 0 poses in, 1 landmarks in, 2 poses out, 3 landmarks out.
+cudaError_t enqueue_state_io(const Dev& d, int mode, double* user, const int32_t* lm_order, cudaStream_t s);
+int kernels_per_iteration();
+int kernels_per_solve_init();
+cudaError_t enqueue_evaluate(const Dev& d, double huber, double zmin, double* out4, cudaStream_t s);
+cudaError_t set_kernel_attributes();
+
+}  // namespace cvba

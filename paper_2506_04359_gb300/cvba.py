@@ -1,0 +1,250 @@
+"""Thin ctypes binding of the C ABI in include/cvba.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library libcvba.so; this module only converts
+numpy arrays to pointers and status codes to exceptions.  If the library has not been
+built, importing this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libcvba.so")
+
+CVBA_FP64 = 0
+CVBA_MIXED = 1
+STATUS = {0: "CVBA_OK", 1: "CVBA_ERR_INVALID_ARG", 2: "CVBA_ERR_INDEX", 3: "CVBA_ERR_NONFINITE",
+          4: "CVBA_ERR_CUDA", 5: "CVBA_ERR_OOM", 6: "CVBA_ERR_NOT_PD", 7: "CVBA_ERR_TIMEOUT",
+          8: "CVBA_ERR_STATE"}
+
+
+class cvba_opts(C.Structure):
+    _fields_ = [("iters", C.c_int), ("huber_delta", C.c_double), ("lambda0", C.c_double),
+                ("z_min", C.c_double), ("reset_lambda", C.c_int)]
+
+
+class cvba_iter(C.Structure):
+    _fields_ = [("cost0", C.c_double), ("cost1", C.c_double), ("lambda_", C.c_double),
+                ("gain", C.c_double), ("pred", C.c_double), ("step_norm", C.c_double),
+                ("rms_px", C.c_double), ("accepted", C.c_int), ("nonpd", C.c_int),
+                ("n_valid", C.c_int), ("n_inlier", C.c_int)]
+
+
+ITER_DTYPE = np.dtype([("cost0", "f8"), ("cost1", "f8"), ("lambda", "f8"), ("gain", "f8"), ("pred", "f8"),
+                       ("step_norm", "f8"), ("rms_px", "f8"), ("accepted", "i4"), ("nonpd", "i4"),
+                       ("n_valid", "i4"), ("n_inlier", "i4")])
+assert ITER_DTYPE.itemsize == C.sizeof(cvba_iter)
+
+
+class CvbaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`"
+                          " (the CUDA library is required; there is no CPU path)")
+    lib = C.CDLL(LIB_PATH)
+    vp, i, d, dp, ip = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    sig = {
+        "cvba_create": (i, [C.POINTER(vp), i, vp, i]),
+        "cvba_destroy": (None, [vp]),
+        "cvba_status_string": (C.c_char_p, [i]),
+        "cvba_last_error": (C.c_char_p, [vp]),
+        "cvba_set_rig": (i, [vp, i, dp, dp]),
+        "cvba_set_poses": (i, [vp, i, dp, i]),
+        "cvba_set_landmarks": (i, [vp, i, dp]),
+        "cvba_set_observations": (i, [vp, i, ip, ip, ip, dp]),
+        "cvba_solve": (i, [vp, C.POINTER(cvba_opts), vp]),
+        "cvba_evaluate": (i, [vp, d, d, dp, dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "cvba_get_poses": (i, [vp, dp]),
+        "cvba_get_landmarks": (i, [vp, dp]),
+        "cvba_get_increment": (i, [vp, dp]),
+        "cvba_get_damping": (i, [vp, dp, dp]),
+        "cvba_set_damping": (i, [vp, d, d]),
+        "cvba_get_layout": (i, [vp, ip, ip, ip]),
+        "cvba_get_sizes": (i, [vp] + [C.POINTER(C.c_int)] * 5),
+        "cvba_solve_launch_count": (i, [vp, i, C.POINTER(C.c_int)]),
+        "cvba_solve_async": (i, [vp, C.POINTER(cvba_opts)]),
+        "cvba_get_trace": (i, [vp, vp, i]),
+        "cvba_set_poses_dev": (i, [vp, vp]),
+        "cvba_set_landmarks_dev": (i, [vp, vp]),
+        "cvba_get_poses_dev": (i, [vp, vp]),
+        "cvba_get_landmarks_dev": (i, [vp, vp]),
+        "cvba_profile_iteration": (i, [vp, C.POINTER(cvba_opts), i, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
+        "cvba_profile_names": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+class Context:
+    """One BA window on one GPU (owns a cvba_ctx)."""
+
+    def __init__(self, precision: str | int = "fp64", device: int = 0, stream: int | None = None):
+        prec = {"fp64": CVBA_FP64, "mixed": CVBA_MIXED}.get(precision, precision)
+        h = C.c_void_p()
+        st = lib.cvba_create(C.byref(h), int(device), C.c_void_p(stream) if stream else None, int(prec))
+        if st != 0:
+            raise CvbaError(st, "cvba_create failed (a GB300 / sm_103 device is required)")
+        self._h = h
+        self.precision = prec
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.cvba_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, st: int):
+        if st != 0:
+            raise CvbaError(st, lib.cvba_last_error(self._h).decode())
+
+    # --- setters
+    def cvba_set_rig(self, intr, T_cb):
+        intr, T_cb = _f64(intr).reshape(-1, 4), _f64(T_cb).reshape(-1, 12)
+        self._check(lib.cvba_set_rig(self._h, intr.shape[0], _dptr(intr), _dptr(T_cb)))
+
+    def cvba_set_poses(self, T_bw, fixed_kf: int = 0):
+        T = _f64(T_bw).reshape(-1, 12)
+        self._check(lib.cvba_set_poses(self._h, T.shape[0], _dptr(T), int(fixed_kf)))
+
+    def cvba_set_landmarks(self, p_w):
+        p = _f64(p_w).reshape(-1, 3)
+        self._check(lib.cvba_set_landmarks(self._h, p.shape[0], _dptr(p)))
+
+    def cvba_set_observations(self, kf, cam, lm, uv):
+        kf, cam, lm, uv = _i32(kf), _i32(cam), _i32(lm), _f64(uv).reshape(-1, 2)
+        self._check(lib.cvba_set_observations(self._h, kf.size, _iptr(kf), _iptr(cam), _iptr(lm), _dptr(uv)))
+
+    # --- solve
+    def cvba_solve(self, iters: int, huber_delta: float = 1.0, lambda0: float = 1e-4, z_min: float = 1e-3,
+                   reset_lambda: bool = True) -> np.ndarray:
+        o = cvba_opts(int(iters), float(huber_delta), float(lambda0), float(z_min), 1 if reset_lambda else 0)
+        trace = np.zeros(max(int(iters), 1), ITER_DTYPE)
+        self._check(lib.cvba_solve(self._h, C.byref(o), C.c_void_p(trace.ctypes.data)))
+        return trace[:int(iters)]
+
+    def cvba_evaluate(self, huber_delta: float = 1.0, z_min: float = 1e-3):
+        cost, rms = C.c_double(), C.c_double()
+        nv, ni = C.c_int(), C.c_int()
+        self._check(lib.cvba_evaluate(self._h, float(huber_delta), float(z_min), C.byref(cost), C.byref(rms),
+                                      C.byref(nv), C.byref(ni)))
+        return dict(cost=cost.value, rms=rms.value, n_valid=nv.value, n_inlier=ni.value)
+
+    # --- getters
+    def cvba_get_sizes(self):
+        v = [C.c_int() for _ in range(5)]
+        self._check(lib.cvba_get_sizes(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(["K", "C", "M", "N", "P"], [x.value for x in v]))
+
+    def cvba_get_poses(self) -> np.ndarray:
+        K = self.cvba_get_sizes()["K"]
+        out = np.zeros((K, 3, 4))
+        self._check(lib.cvba_get_poses(self._h, _dptr(out)))
+        return out
+
+    def cvba_get_landmarks(self) -> np.ndarray:
+        M = self.cvba_get_sizes()["M"]
+        out = np.zeros((M, 3))
+        self._check(lib.cvba_get_landmarks(self._h, _dptr(out)))
+        return out
+
+    def cvba_get_increment(self) -> np.ndarray:
+        s = self.cvba_get_sizes()
+        out = np.zeros(6 * (s["K"] - 1) + 3 * s["M"])
+        self._check(lib.cvba_get_increment(self._h, _dptr(out)))
+        return out
+
+    def cvba_get_damping(self):
+        lam, nu = C.c_double(), C.c_double()
+        self._check(lib.cvba_get_damping(self._h, C.byref(lam), C.byref(nu)))
+        return lam.value, nu.value
+
+    def cvba_set_damping(self, lam: float, nu: float):
+        self._check(lib.cvba_set_damping(self._h, float(lam), float(nu)))
+
+    def cvba_get_layout(self):
+        s = self.cvba_get_sizes()
+        lo = np.zeros(s["M"], np.int32)
+        oo = np.zeros(s["N"], np.int32)
+        off = np.zeros(s["M"] + 1, np.int32)
+        self._check(lib.cvba_get_layout(self._h, _iptr(lo), _iptr(oo), _iptr(off)))
+        return lo, oo, off
+
+    def cvba_solve_launch_count(self, iters: int) -> int:
+        n = C.c_int()
+        self._check(lib.cvba_solve_launch_count(self._h, int(iters), C.byref(n)))
+        return n.value
+
+    # --- asynchronous / device-pointer calls (pointers are device addresses, e.g. a
+    #     torch tensor's data_ptr())
+    def cvba_solve_async(self, iters: int, huber_delta: float = 1.0, lambda0: float = 1e-4, z_min: float = 1e-3,
+                         reset_lambda: bool = True):
+        o = cvba_opts(int(iters), float(huber_delta), float(lambda0), float(z_min), 1 if reset_lambda else 0)
+        self._check(lib.cvba_solve_async(self._h, C.byref(o)))
+
+    def cvba_get_trace(self, n: int) -> np.ndarray:
+        trace = np.zeros(max(int(n), 1), ITER_DTYPE)
+        self._check(lib.cvba_get_trace(self._h, C.c_void_p(trace.ctypes.data), int(n)))
+        return trace[:int(n)]
+
+    def cvba_set_poses_dev(self, ptr: int):
+        self._check(lib.cvba_set_poses_dev(self._h, C.c_void_p(ptr)))
+
+    def cvba_set_landmarks_dev(self, ptr: int):
+        self._check(lib.cvba_set_landmarks_dev(self._h, C.c_void_p(ptr)))
+
+    def cvba_get_poses_dev(self, ptr: int):
+        self._check(lib.cvba_get_poses_dev(self._h, C.c_void_p(ptr)))
+
+    def cvba_get_landmarks_dev(self, ptr: int):
+        self._check(lib.cvba_get_landmarks_dev(self._h, C.c_void_p(ptr)))
+
+    def cvba_profile_iteration(self, reps: int, huber_delta: float = 1.0, lambda0: float = 1e-4,
+                               z_min: float = 1e-3) -> dict:
+        o = cvba_opts(int(reps), float(huber_delta), float(lambda0), float(z_min), 1)
+        n = C.c_int()
+        self._check(lib.cvba_profile_iteration(self._h, C.byref(o), int(reps), None, C.byref(n)))
+        ms = (C.c_float * n.value)()
+        self._check(lib.cvba_profile_iteration(self._h, C.byref(o), int(reps), ms, C.byref(n)))
+        names = lib.cvba_profile_names().decode().split(",")
+        return dict(zip(names, [float(x) for x in ms]))
+
+    # --- convenience
+    def load(self, problem, poses=None, landmarks=None):
+        """Load a synth.Problem (rig, initial poses and landmarks, observations)."""
+        self.cvba_set_rig(problem.rig.intr, problem.rig.T_cb)
+        self.cvba_set_poses(problem.poses0 if poses is None else poses, problem.fixed_kf)
+        self.cvba_set_landmarks(problem.lm0 if landmarks is None else landmarks)
+        self.cvba_set_observations(problem.obs_kf, problem.obs_cam, problem.obs_lm, problem.obs_uv)
+        return self
