@@ -139,7 +139,7 @@ def cores() -> int:
 # -------------------------------------------------------------- algorithmic work model
 
 def work_model(p, P: int, mixed: bool) -> dict:
-    """Algorithmic bytes and FLOPs of each part of one LM iteration."""
+    """Algorithmic bytes and FLOPs of each part of one LM iteration (per-unit figures x units)."""
     t = 4 if mixed else 8
     N, M, K = p.N, p.M, p.K
     n_c = 6 * (K - 1)
