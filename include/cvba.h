@@ -175,6 +175,34 @@ cvba_status cvba_get_landmarks_dev(cvba_ctx* ctx, double* p_w /* device, n_lm*3 
 cvba_status cvba_profile_iteration(cvba_ctx* ctx, const cvba_opts* opts, int reps, float* ms, int* n_parts);
 const char* cvba_profile_names(void);
 
+/* Allocation-free evaluation ----------------------------------------------------------
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot allocate
+ * device memory while running (a tracking thread whose GPU memory is fixed at start-up,
+ * where an allocation could block or fail and may be forbidden after initialisation, or
+ * a program whose GPU memory belongs to another allocator).  Such callers cannot create a
+ * cvba_ctx, so this call needs none.
+ *
+ * Computes, on the calling thread's current device and on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream), the same quantities as cvba_evaluate for a window
+ * given as plain DEVICE arrays in the caller's layouts and order: intr[n_cams*4],
+ * T_cb[n_cams*12], T_bw[n_kf*12], p_w[n_lm*3], kf/cam/lm[n_obs] (int32), uv[n_obs*2].
+ * Writes out[5] (device doubles): cost = 1/2 sum rho(|r|^2) over valid observations,
+ * sum |r|^2, n_valid, n_inlier, and the number of observations skipped because an index
+ * was out of range.  The call is asynchronous: out is ready when the stream reaches it.
+ *
+ * It allocates nothing: its scratch (per-block partial sums) is a fixed 640 KB device
+ * array inside the library, held by every GPU that loads it until the process exits.
+ * n_obs is limited to 4,194,304 (CVBA_ERR_INVALID_ARG beyond).  The first call on each
+ * device looks up the array's device address; make that first call before capturing any
+ * stream.  All calls on a device share the array: calls whose kernels overlap on the GPU
+ * race on it and must be serialised by the caller. */
+cvba_status cvba_evaluate_noalloc(int n_obs, int n_kf, int n_cams, int n_lm, const double* intr,
+                                  const double* T_cb, const double* T_bw, const double* p_w,
+                                  const int32_t* kf, const int32_t* cam, const int32_t* lm,
+                                  const double* uv, double huber_delta, double z_min, double* out,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

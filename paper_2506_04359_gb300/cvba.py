@@ -78,6 +78,7 @@ def _load() -> C.CDLL:
         "cvba_get_landmarks_dev": (i, [vp, vp]),
         "cvba_profile_iteration": (i, [vp, C.POINTER(cvba_opts), i, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
         "cvba_profile_names": (C.c_char_p, []),
+        "cvba_evaluate_noalloc": (i, [i, i, i, i] + [vp] * 8 + [d, d, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -248,3 +249,16 @@ class Context:
         self.cvba_set_landmarks(problem.lm0 if landmarks is None else landmarks)
         self.cvba_set_observations(problem.obs_kf, problem.obs_cam, problem.obs_lm, problem.obs_uv)
         return self
+
+
+def cvba_evaluate_noalloc(n_obs: int, n_kf: int, n_cams: int, n_lm: int, intr: int, T_cb: int, T_bw: int, p_w: int,
+                          kf: int, cam: int, lm: int, uv: int, huber_delta: float, z_min: float, out: int,
+                          stream: int = 0) -> None:
+    """Allocation-free cost evaluation from device pointers (see include/cvba.h); raises on a
+    non-OK status.  `out` receives 5 doubles on the device, asynchronously on `stream`."""
+    st = lib.cvba_evaluate_noalloc(int(n_obs), int(n_kf), int(n_cams), int(n_lm), C.c_void_p(intr),
+                                   C.c_void_p(T_cb), C.c_void_p(T_bw), C.c_void_p(p_w), C.c_void_p(kf),
+                                   C.c_void_p(cam), C.c_void_p(lm), C.c_void_p(uv), float(huber_delta),
+                                   float(z_min), C.c_void_p(out), C.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise CvbaError(st, "cvba_evaluate_noalloc failed")
