@@ -26,7 +26,7 @@ struct cvba_ctx {
 
   std::vector<int32_t> lm_order, lm_rank, obs_order, lm_off;
   std::vector<LinTile> lin_tiles;
-  std::vector<SchurTile> schur_tiles;
+  std::vector<SchurTile> schur_tiles, direct_tiles;
 
   struct Slot {
     void* p;
@@ -244,13 +244,43 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
         if (l1 > l0 && (np > target || l1 - l0 >= LIN_TILE_LMS)) break;
         ++l1;
       }
-      c->lin_tiles.push_back(LinTile{l0, l1, lm_pair[l0], lm_pair[l1]});
+      LinTile t{l0, l1, lm_pair[l0], lm_pair[l1], 0, 0, 0};
+      int lo = K, hi = -1;
+      for (int q = t.p0; q < t.p1; ++q) {
+        lo = std::min(lo, pair_kf[q]);
+        hi = std::max(hi, pair_kf[q]);
+      }
+      t.kf_lo = hi >= 0 ? lo : 0;
+      t.kf_n = hi >= 0 ? hi - lo + 1 : 0;
+      c->lin_tiles.push_back(t);
       l0 = l1;
     }
   }
-  c->schur_tiles.clear();
+  // offsets of the per-keyframe partials and, per keyframe, the tiles covering it
+  std::vector<int32_t> kf_tiles_off(K + 1, 0), kf_tiles;
+  size_t kf_part_len = 0;
   {
-    const int target = std::max(32, std::min(SCHUR_TILE_PAIRS, (P + 2 * n_sm - 1) / (2 * n_sm)));
+    for (auto& t : c->lin_tiles) {
+      t.part_off = (int)kf_part_len;
+      kf_part_len += (size_t)t.kf_n * 12;
+      for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) kf_tiles_off[a + 1]++;
+    }
+    for (int a = 0; a < K; ++a) kf_tiles_off[a + 1] += kf_tiles_off[a];
+    kf_tiles.resize(kf_tiles_off[K]);
+    std::vector<int32_t> fill(kf_tiles_off.begin(), kf_tiles_off.end() - 1);
+    for (int ti = 0; ti < (int)c->lin_tiles.size(); ++ti) {
+      const auto& t = c->lin_tiles[ti];
+      for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) kf_tiles[fill[a]++] = ti;
+    }
+  }
+  // Schur tiles: runs of landmarks (in internal order) with the same window [lo, hi] of
+  // free keyframes, at most `target` landmarks; landmarks spanning more than SPAN_MAX free
+  // keyframes go to direct tiles (<= SCHUR_TILE_PAIRS pairs, <= SCHUR_TILE_LMS landmarks).
+  c->schur_tiles.clear();
+  c->direct_tiles.clear();
+  int max_span = 1;
+  {
+    const int target = std::max(8, std::min(SCHUR_TILE_LMS, (M + n_sm - 1) / n_sm));
     std::vector<int> lo(M, INT32_MAX), hi(M, -1);
     for (int j = 0; j < M; ++j)
       for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
@@ -262,35 +292,55 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     auto wide = [&](int j) { return hi[j] >= 0 && hi[j] - lo[j] + 1 > SPAN_MAX; };
     int l0 = 0;
     while (l0 < M) {
-      const bool direct = wide(l0);
-      int l1 = l0, wlo = INT32_MAX, whi = -1;
-      while (l1 < M) {
-        if (wide(l1) != direct) break;
-        const int np = lm_pair[l1 + 1] - lm_pair[l0];
-        if (np > SCHUR_TILE_PAIRS || l1 - l0 >= SCHUR_TILE_LMS) break;
-        if (l1 > l0 && np > target) break;
-        int nlo = std::min(wlo, lo[l1]), nhi = std::max(whi, hi[l1]);
-        if (!direct && nhi >= 0 && nhi - nlo + 1 > SPAN_MAX) break;
-        wlo = nlo;
-        whi = nhi;
-        ++l1;
-      }
+      int l1 = l0 + 1;
       SchurTile t{};
+      if (wide(l0)) {
+        while (l1 < M && wide(l1) && l1 - l0 < SCHUR_TILE_LMS &&
+               lm_pair[l1 + 1] - lm_pair[l0] <= SCHUR_TILE_PAIRS)
+          ++l1;
+        t.direct = 1;
+        t.k_lo = 0;
+        t.span = K - 1;
+      } else {
+        while (l1 < M && l1 - l0 < target && !wide(l1) && lo[l1] == lo[l0] && hi[l1] == hi[l0]) ++l1;
+        t.direct = 0;
+        t.k_lo = hi[l0] >= 0 ? lo[l0] : 0;
+        t.span = hi[l0] >= 0 ? hi[l0] - lo[l0] + 1 : 0;
+        max_span = std::max(max_span, t.span);
+      }
       t.l0 = l0;
       t.l1 = l1;
       t.p0 = lm_pair[l0];
       t.p1 = lm_pair[l1];
       t.b0 = lm_blk[l0];
       t.b1 = lm_blk[l1];
-      t.direct = direct ? 1 : 0;
-      t.k_lo = whi >= 0 ? wlo : 0;
-      t.span = whi >= 0 ? whi - wlo + 1 : 1;
-      if (direct) {
-        t.k_lo = 0;
-        t.span = K - 1;
-      }
-      c->schur_tiles.push_back(t);
+      t.part_off = -1;
+      (t.direct ? c->direct_tiles : c->schur_tiles).push_back(t);
       l0 = l1;
+    }
+  }
+  // window partial offsets and, per block (a >= b) of free keyframes, the covering tiles
+  const int nfb = K - 1;
+  const int n_blk = nfb * (nfb + 1) / 2;
+  std::vector<int32_t> blk_tiles_off(n_blk + 1, 0), blk_tiles;
+  size_t schur_part_len = 0;
+  {
+    for (auto& t : c->schur_tiles) {
+      const size_t rows = 6 * (size_t)t.span;
+      if (schur_part_len + rows * (rows + 1) / 2 + rows > (size_t)INT32_MAX)
+        return fail(c, CVBA_ERR_INVALID_ARG, "Schur partials exceed 2^31 entries");
+      t.part_off = (int)schur_part_len;
+      schur_part_len += rows * (rows + 1) / 2 + rows;
+      for (int a = t.k_lo; a < t.k_lo + t.span; ++a)
+        for (int b = t.k_lo; b <= a; ++b) blk_tiles_off[a * (a + 1) / 2 + b + 1]++;
+    }
+    for (int i = 0; i < n_blk; ++i) blk_tiles_off[i + 1] += blk_tiles_off[i];
+    blk_tiles.resize(blk_tiles_off[n_blk]);
+    std::vector<int32_t> fill(blk_tiles_off.begin(), blk_tiles_off.end() - 1);
+    for (int ti = 0; ti < (int)c->schur_tiles.size(); ++ti) {
+      const auto& t = c->schur_tiles[ti];
+      for (int a = t.k_lo; a < t.k_lo + t.span; ++a)
+        for (int b = t.k_lo; b <= a; ++b) blk_tiles[fill[a * (a + 1) / 2 + b]++] = ti;
     }
   }
 
@@ -311,6 +361,8 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   d.mixed = mixed ? 1 : 0;
   d.n_lin_tiles = (int)c->lin_tiles.size();
   d.n_schur_tiles = (int)c->schur_tiles.size();
+  d.n_direct_tiles = (int)c->direct_tiles.size();
+  d.max_span = max_span;
   double *rig, *pose0, *pose1, *lm0, *lm1;
   int32_t *ocam, *pkf, *plm, *pobs, *lpair, *lblk, *kpb;
   LinTile* lt;
@@ -329,6 +381,9 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   CK(dalloc(c, &kpb, K), "alloc kf map");
   CK(dalloc(c, &lt, c->lin_tiles.size()), "alloc tiles");
   CK(dalloc(c, &st, c->schur_tiles.size()), "alloc tiles");
+  SchurTile* dtl;
+  CK(dalloc(c, &dtl, c->direct_tiles.size()), "alloc tiles");
+  d.direct_tiles = dtl;
   d.rig = rig;
   d.pose[0] = pose0;
   d.pose[1] = pose1;
@@ -379,6 +434,29 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   CK(dalloc(c, &d.bS, (size_t)n_c), "alloc");
   CK(dalloc(c, &d.dc, (size_t)n_c), "alloc");
   CK(dalloc(c, &d.dp, (size_t)M * 3), "alloc");
+  {
+    double *kp, *sp;
+    int32_t *kto, *kt, *bto, *bt;
+    CK(dalloc(c, &kp, kf_part_len), "alloc");
+    CK(dalloc(c, &sp, schur_part_len), "alloc");
+    CK(dalloc(c, &kto, (size_t)K + 1), "alloc");
+    CK(dalloc(c, &kt, kf_tiles.size()), "alloc");
+    CK(dalloc(c, &bto, (size_t)n_blk + 1), "alloc");
+    CK(dalloc(c, &bt, blk_tiles.size()), "alloc");
+    CK(cudaMemcpy(kto, kf_tiles_off.data(), kf_tiles_off.size() * 4, cudaMemcpyHostToDevice), "upload");
+    if (!kf_tiles.empty())
+      CK(cudaMemcpy(kt, kf_tiles.data(), kf_tiles.size() * 4, cudaMemcpyHostToDevice), "upload");
+    CK(cudaMemcpy(bto, blk_tiles_off.data(), blk_tiles_off.size() * 4, cudaMemcpyHostToDevice), "upload");
+    if (!blk_tiles.empty())
+      CK(cudaMemcpy(bt, blk_tiles.data(), blk_tiles.size() * 4, cudaMemcpyHostToDevice), "upload");
+    d.kf_part = kp;
+    d.schur_part = sp;
+    d.kf_tiles_off = kto;
+    d.kf_tiles = kt;
+    d.blk_tiles_off = bto;
+    d.blk_tiles = bt;
+    d.n_blk = n_blk;
+  }
   CK(dalloc(c, &d.lin_part, (size_t)d.n_lin_tiles * 4), "alloc");
   CK(dalloc(c, &d.bs_part, (size_t)d.n_lin_tiles * 8), "alloc");
   CK(dalloc(c, &d.ctrl, 1), "alloc");
@@ -425,8 +503,12 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   CK(cudaMemcpy(lblk, lm_blk.data(), ((size_t)M + 1) * 4, cudaMemcpyHostToDevice), "upload");
   CK(cudaMemcpy(kpb, kf_pb.data(), (size_t)K * 4, cudaMemcpyHostToDevice), "upload");
   CK(cudaMemcpy(lt, c->lin_tiles.data(), c->lin_tiles.size() * sizeof(LinTile), cudaMemcpyHostToDevice), "upload");
-  CK(cudaMemcpy(st, c->schur_tiles.data(), c->schur_tiles.size() * sizeof(SchurTile), cudaMemcpyHostToDevice),
-     "upload");
+  if (!c->schur_tiles.empty())
+    CK(cudaMemcpy(st, c->schur_tiles.data(), c->schur_tiles.size() * sizeof(SchurTile), cudaMemcpyHostToDevice),
+       "upload");
+  if (!c->direct_tiles.empty())
+    CK(cudaMemcpy(dtl, c->direct_tiles.data(), c->direct_tiles.size() * sizeof(SchurTile), cudaMemcpyHostToDevice),
+       "upload");
   c->have_layout = true;
   return CVBA_OK;
 }

@@ -19,8 +19,8 @@ constexpr int LIN_THREADS = 256;
 constexpr int SCHUR_THREADS = 256;
 constexpr int CHOL_THREADS = 1024;
 constexpr int DECIDE_THREADS = 256;
-constexpr int LIN_TILE_PAIRS = 1024;    // pairs per linearisation / back-substitution tile
-constexpr int LIN_TILE_LMS = 512;       // landmarks per linearisation tile
+constexpr int LIN_TILE_PAIRS = 256;     // pairs per linearisation / back-substitution tile
+constexpr int LIN_TILE_LMS = 256;       // landmarks per linearisation tile
 constexpr int SCHUR_TILE_PAIRS = 256;   // pairs staged in shared memory per Schur tile
 constexpr int SCHUR_TILE_LMS = 128;
 constexpr int SPAN_MAX = 24;            // free keyframes in one Schur tile's window
@@ -44,6 +44,7 @@ struct Ctrl {
 // back-substitution and evaluation.
 struct LinTile {
   int l0, l1, p0, p1;
+  int kf_lo, kf_n, part_off;   // keyframes [kf_lo, kf_lo + kf_n) touched; offset in kf_part
 };
 
 // Landmark range for the Schur kernel: pairs [p0, p1), off-diagonal block work items
@@ -51,6 +52,7 @@ struct LinTile {
 // reduced camera system is accumulated in shared memory (direct = 1: straight to global).
 struct SchurTile {
   int l0, l1, p0, p1, b0, b1, k_lo, span, direct;
+  int part_off;                // offset of the window partial in schur_part (-1: direct)
 };
 
 struct Dev {
@@ -69,7 +71,9 @@ struct Dev {
   const int32_t* lm_blk;      // M + 1 off-diagonal block offsets, m(m-1)/2 per landmark
   const int32_t* kf_pb;       // K: free block index or -1 for the fixed keyframe
   const LinTile* lin_tiles;
-  const SchurTile* schur_tiles;
+  const SchurTile* schur_tiles;    // landmarks sharing one window of <= SPAN_MAX free keyframes
+  const SchurTile* direct_tiles;   // landmarks spanning more (atomics into S)
+  int n_direct_tiles, max_span;
   // linearisation
   void* pair_lin;             // P * PAIR_LIN (double or float)
   double* lm_H;               // M * 6  (Hll: 00 01 02 11 12 22)
@@ -82,6 +86,14 @@ struct Dev {
   double* bS;                 // n_c   sum of W V^-1 g_l
   double* dc;                 // n_c   pose increment
   double* dp;                 // M * 3 landmark increment
+  // per-tile partials and the lists of tiles covering each keyframe / RCS block
+  double* kf_part;            // per lin tile: kf_n * 12 (g_p 6, diag Hpp 6)
+  double* schur_part;         // per Schur tile: window (rows (rows + 1) / 2) then b (rows)
+  const int32_t* kf_tiles_off;   // K + 1
+  const int32_t* kf_tiles;       // lin tiles covering each keyframe
+  const int32_t* blk_tiles_off;  // n_blk + 1, blocks (a >= b) of free keyframes
+  const int32_t* blk_tiles;      // Schur tiles (non-direct) covering each block
+  int n_blk;
   // partial sums per linearisation tile
   double* lin_part;           // n_lin_tiles * 4: cost, sum r^2, n_valid, n_inlier
   double* bs_part;            // n_lin_tiles * 4: candidate cost, pred_l, step2_l, unused

@@ -18,8 +18,10 @@
 //
 // Compute type T: double (FP64 path) or float (mixed path).  All sums of the normal
 // equations, the Schur window and the costs are accumulated in double.
-#include <cfloat>
+#include <cooperative_groups.h>
 #include <math_constants.h>
+
+#include <cfloat>
 #include <cmath>
 
 #include "cvba_internal.h"
@@ -270,29 +272,25 @@ __global__ void k_solve_init(Dev d, double lam0, double huber, double zmin, int 
     c->step2_p = 0.0;
     c->maxdiag_lm = 0ull;
   }
-  for (int i = threadIdx.x; i < d.K * 6; i += blockDim.x) {
-    d.kf_gp[i] = 0.0;
-    d.kf_dp[i] = 0.0;
-  }
 }
 
 // ----------------------------------------------------------------- k_lin
+// Thread per (landmark, keyframe) pair; each pair writes its contributions to its own
+// shared-memory slot, then owner threads sum them in pair order (per landmark: its
+// contiguous pairs; per keyframe and component: the tile's pairs of that keyframe), so
+// there are no atomics and the sums are reproducible.
 template <typename T>
 __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
   Ctrl* ctrl = d.ctrl;
   if (!ctrl->need_lin) return;
   extern __shared__ __align__(16) double smem[];
   const LinTile tile = d.lin_tiles[blockIdx.x];
-  const int nl = tile.l1 - tile.l0;
+  const int nl = tile.l1 - tile.l0, np = tile.p1 - tile.p0;
   double* s_rig = smem;                                // C * 16
-  double* s_lm = s_rig + d.C * RIG_STRIDE;             // LIN_TILE_LMS * 9
-  double* s_kf = s_lm + LIN_TILE_LMS * 9;              // K * 12
-  double* s_red = s_kf + d.K * 12;                     // 128
-  int* s_flag = reinterpret_cast<int*>(s_red + 128);   // K
+  double* s_pair = s_rig + d.C * RIG_STRIDE;           // LIN_TILE_PAIRS * 21
+  double* s_red = s_pair + LIN_TILE_PAIRS * 21;        // 128
+  int* s_kf = reinterpret_cast<int*>(s_red + 128);     // LIN_TILE_PAIRS
   for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = d.rig[i];
-  for (int i = threadIdx.x; i < nl * 9; i += blockDim.x) s_lm[i] = 0.0;
-  for (int i = threadIdx.x; i < d.K * 12; i += blockDim.x) s_kf[i] = 0.0;
-  for (int i = threadIdx.x; i < d.K; i += blockDim.x) s_flag[i] = 0;
   __syncthreads();
 
   const int cur = ctrl->cur;
@@ -300,7 +298,8 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
   const double* lmp = d.lm[cur];
   const T hub = (T)ctrl->huber, zmin = (T)ctrl->zmin;
   PairStats st;
-  for (int q = tile.p0 + threadIdx.x; q < tile.p1; q += blockDim.x) {
+  for (int qi = threadIdx.x; qi < np; qi += blockDim.x) {
+    const int q = tile.p0 + qi;
     const int a = d.pair_kf[q], j = d.pair_lm[q];
     T X[3], M3[6], a3[3];
     eval_pair<T, true>(pose + a * POSE_STRIDE, lmp + 3 * j, d.pair_obs[q], d.pair_obs[q + 1], d.obs_cam,
@@ -319,61 +318,168 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int c = 0; c < 3; ++c) G[r * 3 + c] = M[r * 3] * R[c] + M[r * 3 + 1] * R[3 + c] + M[r * 3 + 2] * R[6 + c];
-    double* L = s_lm + (j - tile.l0) * 9;
+    double* sl = s_pair + qi * 21;
     const int si[6] = {0, 0, 0, 1, 1, 2}, sj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const int r = si[k], c = sj[k];
-      const T h = R[r] * G[c] + R[3 + r] * G[3 + c] + R[6 + r] * G[6 + c];
-      atomicAdd(L + k, (double)h);
+      sl[k] = (double)(R[r] * G[c] + R[3 + r] * G[3 + c] + R[6 + r] * G[6 + c]);
     }
 #pragma unroll
-    for (int r = 0; r < 3; ++r) atomicAdd(L + 6 + r, (double)(R[r] * a3[0] + R[3 + r] * a3[1] + R[6 + r] * a3[2]));
-    if (d.kf_pb[a] >= 0) {
-      // pose gradient B^T a3 = (a3, X x a3); diag of B^T M3 B
-      double* Kf = s_kf + a * 12;
-      atomicAdd(Kf + 0, (double)a3[0]);
-      atomicAdd(Kf + 1, (double)a3[1]);
-      atomicAdd(Kf + 2, (double)a3[2]);
-      atomicAdd(Kf + 3, (double)(X[1] * a3[2] - X[2] * a3[1]));
-      atomicAdd(Kf + 4, (double)(X[2] * a3[0] - X[0] * a3[2]));
-      atomicAdd(Kf + 5, (double)(X[0] * a3[1] - X[1] * a3[0]));
-      atomicAdd(Kf + 6, (double)M3[0]);
-      atomicAdd(Kf + 7, (double)M3[3]);
-      atomicAdd(Kf + 8, (double)M3[5]);
-      atomicAdd(Kf + 9, (double)(M3[3] * X[2] * X[2] - 2 * M3[4] * X[1] * X[2] + M3[5] * X[1] * X[1]));
-      atomicAdd(Kf + 10, (double)(M3[0] * X[2] * X[2] - 2 * M3[2] * X[0] * X[2] + M3[5] * X[0] * X[0]));
-      atomicAdd(Kf + 11, (double)(M3[0] * X[1] * X[1] - 2 * M3[1] * X[0] * X[1] + M3[3] * X[0] * X[0]));
-      s_flag[a] = 1;
-    }
+    for (int r = 0; r < 3; ++r) sl[6 + r] = (double)(R[r] * a3[0] + R[3 + r] * a3[1] + R[6 + r] * a3[2]);
+    // pose gradient B^T a3 = (a3, X x a3) and diag of B^T M3 B (fixed keyframe: unused)
+    sl[9] = (double)a3[0];
+    sl[10] = (double)a3[1];
+    sl[11] = (double)a3[2];
+    sl[12] = (double)(X[1] * a3[2] - X[2] * a3[1]);
+    sl[13] = (double)(X[2] * a3[0] - X[0] * a3[2]);
+    sl[14] = (double)(X[0] * a3[1] - X[1] * a3[0]);
+    sl[15] = (double)M3[0];
+    sl[16] = (double)M3[3];
+    sl[17] = (double)M3[5];
+    sl[18] = (double)(M3[3] * X[2] * X[2] - 2 * M3[4] * X[1] * X[2] + M3[5] * X[1] * X[1]);
+    sl[19] = (double)(M3[0] * X[2] * X[2] - 2 * M3[2] * X[0] * X[2] + M3[5] * X[0] * X[0]);
+    sl[20] = (double)(M3[0] * X[1] * X[1] - 2 * M3[1] * X[0] * X[1] + M3[3] * X[0] * X[0]);
+    s_kf[qi] = d.kf_pb[a] >= 0 ? a : -1;
   }
   double v[4] = {st.cost, st.sq, (double)st.nv, (double)st.ni};
-  block_sum4(v, s_red);
+  block_sum4(v, s_red);                              // contains barriers: slots complete
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) d.lin_part[blockIdx.x * 4 + k] = v[k];
   }
-  __syncthreads();
+  // per landmark: sum of its pairs (contiguous, in order)
   double mx = 0.0;
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     const int j = tile.l0 + l;
+    double h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int q = d.lm_pair[j]; q < d.lm_pair[j + 1]; ++q)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = s_lm[l * 9 + k];
+      for (int k = 0; k < 9; ++k) h[k] += s_pair[(q - tile.p0) * 21 + k];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = s_lm[l * 9 + 6 + k];
-    mx = fmax(mx, fmax(s_lm[l * 9], fmax(s_lm[l * 9 + 3], s_lm[l * 9 + 5])));
+    for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = h[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = h[6 + k];
+    mx = fmax(mx, fmax(h[0], fmax(h[3], h[5])));
+  }
+  // per keyframe and component: sum over this tile's pairs of that keyframe, in order
+  for (int e = threadIdx.x; e < tile.kf_n * 12; e += blockDim.x) {
+    const int a = tile.kf_lo + e / 12, comp = e % 12;
+    double sum = 0.0;
+    for (int qi = 0; qi < np; ++qi)
+      if (s_kf[qi] == a) sum += s_pair[qi * 21 + 9 + comp];
+    d.kf_part[tile.part_off + e] = sum;
   }
   mx = block_max(mx, s_red);
   if (threadIdx.x == 0 && mx > 0.0)
     atomicMax(&ctrl->maxdiag_lm, (unsigned long long)__double_as_longlong(mx));
-  for (int a = threadIdx.x; a < d.K; a += blockDim.x) {
-    if (!s_flag[a]) continue;
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      atomicAdd(d.kf_gp + a * 6 + k, s_kf[a * 12 + k]);
-      atomicAdd(d.kf_dp + a * 6 + k, s_kf[a * 12 + 6 + k]);
+}
+
+// g_p and diag(Hpp) of keyframe blockIdx.x: fixed-order sum of the covering tiles'
+// partials (lane l takes tiles l, l+32, ...; then a butterfly over the warp).
+__global__ void __launch_bounds__(384) k_kf_reduce(Dev d) {
+  const int a = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;   // warp = component (12)
+  const int t0 = d.kf_tiles_off[a], t1 = d.kf_tiles_off[a + 1];
+  double v = 0.0;
+  for (int t = t0 + lane; t < t1; t += 32) {
+    const LinTile tl = d.lin_tiles[d.kf_tiles[t]];
+    v += d.kf_part[tl.part_off + (a - tl.kf_lo) * 12 + warp];
+  }
+  v = warp_sum(v);
+  if (lane == 0) {
+    if (warp < 6) d.kf_gp[a * 6 + warp] = v; else d.kf_dp[a * 6 + warp - 6] = v;
+  }
+}
+
+// Closed-form inverse of V_j = Hll_j + lam D_l,j (adjugate / determinant), stored with tau
+// in lm_Vinv.  Mixed path only: Hll_j is summed from FP32 products, so information below
+// ~2^-23 of its trace is rounding noise (a landmark drifting to infinity along its ray has
+// an eigenvalue ~1e-15 of the others).  If V_j then fails the positive-definite test, the
+// block is retried with tau = 2^-20 tr(Hll_j) added to its diagonal; tau enters the
+// predicted reduction in k_backsub.  The FP64 path never adds tau.
+template <typename T>
+__device__ void landmark_vinv(const Dev& d, int j, double lam, double floor_, double inv[6]) {
+  const double* H = d.lm_H + 6 * j;
+  double tau = 0.0;
+  bool ok = false;
+  for (int attempt = 0; attempt < (sizeof(T) == 4 ? 2 : 1) && !ok; ++attempt) {
+    if (attempt == 1) tau = 0x1p-20 * (H[0] + H[3] + H[5]);
+    const double a = H[0] + lam * fmax(H[0], floor_) + tau;
+    const double b = H[1], c = H[2];
+    const double dd = H[3] + lam * fmax(H[3], floor_) + tau;
+    const double e = H[4];
+    const double f = H[5] + lam * fmax(H[5], floor_) + tau;
+    const double A = dd * f - e * e, Bc = c * e - b * f, Cc = b * e - c * dd;
+    const double det = a * A + b * Bc + c * Cc;
+    const double m2 = a * dd - b * b;
+    if (a > 0.0 && m2 > 0.0 && det > 0.0 && isfinite(det)) {
+      const double id = 1.0 / det;
+      inv[0] = A * id;
+      inv[1] = Bc * id;
+      inv[2] = Cc * id;
+      inv[3] = (a * f - c * c) * id;
+      inv[4] = (b * c - a * e) * id;
+      inv[5] = m2 * id;
+      ok = true;
     }
   }
+  if (!ok) {
+    for (int k = 0; k < 6; ++k) inv[k] = 0.0;
+    tau = 0.0;
+    d.ctrl->nonpd = 1;
+  }
+  for (int k = 0; k < 6; ++k) d.lm_Vinv[j * VINV_STRIDE + k] = inv[k];
+  d.lm_Vinv[j * VINV_STRIDE + 6] = tau;
+}
+
+// Per pair: W = J_pose^T W J_lm = [G; [X]x G] with G = M3 R (6 x 3), Y = W V^-1, the pair's
+// diagonal-block term U - Y W^T (U = B^T M3 B, lower 21) and Y g_l.
+template <typename T>
+__device__ __forceinline__ void pair_schur_terms(const T* pl, const double* R_pose, const double* vinv6,
+                                                 const double* gl3, T W[18], T Y[18], T Dg[21], T bY[6]) {
+  T M3[6], X[3], M[9], R[9], G[9];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) M3[k] = pl[k];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) X[k] = pl[6 + k];
+  sym3_full(M3, M);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) R[k] = (T)R_pose[k];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) G[r * 3 + c] = M[r * 3] * R[c] + M[r * 3 + 1] * R[3 + c] + M[r * 3 + 2] * R[6 + c];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) W[k] = G[k];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    W[9 + c] = X[1] * G[6 + c] - X[2] * G[3 + c];
+    W[12 + c] = X[2] * G[c] - X[0] * G[6 + c];
+    W[15 + c] = X[0] * G[3 + c] - X[1] * G[c];
+  }
+  T Vi[9];
+  {
+    T s6[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s6[k] = (T)vinv6[k];
+    sym3_full(s6, Vi);
+  }
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Y[r * 3 + c] = W[r * 3] * Vi[c] + W[r * 3 + 1] * Vi[3 + c] + W[r * 3 + 2] * Vi[6 + c];
+  T U[36];
+  pose_info(M, X, U);
+  int k = 0;
+#pragma unroll
+  for (int r = 0; r < 6; ++r)
+#pragma unroll
+    for (int c = 0; c <= r; ++c, ++k)
+      Dg[k] = U[r * 6 + c] - (Y[r * 3] * W[c * 3] + Y[r * 3 + 1] * W[c * 3 + 1] + Y[r * 3 + 2] * W[c * 3 + 2]);
+  const T g0 = (T)gl3[0], g1 = (T)gl3[1], g2 = (T)gl3[2];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) bY[r] = Y[r * 3] * g0 + Y[r * 3 + 1] * g1 + Y[r * 3 + 2] * g2;
 }
 
 // ---------------------------------------------------------------- k_schur
@@ -387,8 +493,11 @@ struct SchurSmem {
   }
 };
 
+// Tiles whose landmarks span more than SPAN_MAX free keyframes: every block product is
+// added straight into the global reduced camera system with atomics (rare in sliding
+// windows; not bit-reproducible).
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS) k_schur(Dev d) {
+__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct(Dev d) {
   using SM = SchurSmem<T>;
   extern __shared__ __align__(16) double smem[];
   double* s_win = smem;                               // WIN_ENTRIES
@@ -401,7 +510,7 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur(Dev d) {
   int* s_blk = reinterpret_cast<int*>(s_Y + SCHUR_TILE_PAIRS * 18);  // SCHUR_TILE_LMS + 1
 
   Ctrl* ctrl = d.ctrl;
-  const SchurTile tile = d.schur_tiles[blockIdx.x];
+  const SchurTile tile = d.direct_tiles[blockIdx.x];
   const int nl = tile.l1 - tile.l0;
   const int n_c = d.n_c;
   const double lam = ctrl->lam;
@@ -411,49 +520,11 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur(Dev d) {
     for (int i = threadIdx.x; i < rows * (rows + 1) / 2; i += blockDim.x) s_win[i] = 0.0;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) s_b[i] = 0.0;
   }
-  // phase 1: closed-form inverse of V_j = Hll_j + lam D_l,j (adjugate / determinant).
-  // Mixed path only: Hll_j is summed from FP32 products, so information below ~2^-23 of
-  // its trace is rounding noise (a landmark drifting to infinity along its ray has an
-  // eigenvalue ~1e-15 of the others).  If V_j then fails the positive-definite test, the
-  // block is retried with tau = 2^-20 tr(Hll_j) added to its diagonal; tau enters the
-  // predicted reduction in k_backsub.  The FP64 path never adds tau.
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     const int j = tile.l0 + l;
-    const double* H = d.lm_H + 6 * j;
     double inv[6];
-    double tau = 0.0;
-    bool ok = false;
-    for (int attempt = 0; attempt < (sizeof(T) == 4 ? 2 : 1) && !ok; ++attempt) {
-      if (attempt == 1) tau = 0x1p-20 * (H[0] + H[3] + H[5]);
-      const double a = H[0] + lam * fmax(H[0], floor_) + tau;
-      const double b = H[1], c = H[2];
-      const double dd = H[3] + lam * fmax(H[3], floor_) + tau;
-      const double e = H[4];
-      const double f = H[5] + lam * fmax(H[5], floor_) + tau;
-      const double A = dd * f - e * e, Bc = c * e - b * f, Cc = b * e - c * dd;
-      const double det = a * A + b * Bc + c * Cc;
-      const double m2 = a * dd - b * b;
-      if (a > 0.0 && m2 > 0.0 && det > 0.0 && isfinite(det)) {
-        const double id = 1.0 / det;
-        inv[0] = A * id;
-        inv[1] = Bc * id;
-        inv[2] = Cc * id;
-        inv[3] = (a * f - c * c) * id;
-        inv[4] = (b * c - a * e) * id;
-        inv[5] = m2 * id;
-        ok = true;
-      }
-    }
-    if (!ok) {
-      for (int k = 0; k < 6; ++k) inv[k] = 0.0;
-      tau = 0.0;
-      ctrl->nonpd = 1;
-    }
-    for (int k = 0; k < 6; ++k) {
-      s_vinv[l * 6 + k] = inv[k];
-      d.lm_Vinv[j * VINV_STRIDE + k] = inv[k];
-    }
-    d.lm_Vinv[j * VINV_STRIDE + 6] = tau;
+    landmark_vinv<T>(d, j, lam, floor_, inv);
+    for (int k = 0; k < 6; ++k) s_vinv[l * 6 + k] = inv[k];
     for (int k = 0; k < 3; ++k) s_gl[l * 3 + k] = d.lm_g[j * 3 + k];
   }
   for (int l = threadIdx.x; l <= nl; l += blockDim.x) s_blk[l] = d.lm_blk[tile.l0 + l] - tile.b0;
@@ -574,18 +645,194 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur(Dev d) {
   }
   __syncthreads();
 
-  // phase 4: flush the window into the global reduced camera system
+  // phase 4: the window (and its part of b) as this tile's partial, summed per RCS block
+  // in a fixed order by k_rcs_reduce
   if (!tile.direct) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int base = 6 * tile.k_lo;
-    for (int wr = warp; wr < rows; wr += nw) {
-      for (int wc = lane; wc <= wr; wc += 32) {
-        const double v = s_win[wr * (wr + 1) / 2 + wc];
-        if (v != 0.0) atomicAdd(d.S + (size_t)(base + wr) * n_c + base + wc, v);
+    const int nw_ = rows * (rows + 1) / 2;
+    double* out = d.schur_part + tile.part_off;
+    for (int i = threadIdx.x; i < nw_; i += blockDim.x) out[i] = s_win[i];
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) out[nw_ + i] = s_b[i];
+  }
+}
+
+// ------------------------------------------------------------ k_schur_group
+// Reduced camera system from a tile of landmarks that share the same window of free
+// keyframes [k_lo, k_lo + span): their contributions to that window of S,
+//   S_ab += sum_j (U_ja - Y_ja W_ja^T) (a = b),   S_ab -= sum_j Y_ja W_jb^T (a > b),
+//   b_a  += sum_j Y_ja g_l,j,
+// form a dense product over the tile's landmarks (a keyframe of the window that does not
+// observe a landmark contributes zero blocks).  Landmarks are staged in chunks; each
+// thread owns fixed entries of the window and accumulates them in registers over the
+// landmarks in order: FP64 on the FP64 path, Kahan-compensated FP32 on the mixed path.
+// The window is written as the tile's partial, summed over tiles by k_rcs_reduce.
+constexpr int kGroupOwn = 16;      // window entries per thread and pass (passes cover E + rows)
+constexpr int kStage = 76;         // per (landmark, block): Y[6][4] W[6][4] Dg[21] bY[6] pad
+template <typename T>
+struct GroupChunk {
+  static constexpr int value = sizeof(T) == 4 ? 16 : 8;
+};
+
+size_t group_smem_bytes(int max_span, bool mixed) {
+  const size_t t = mixed ? 4 : 8;
+  const int ch = mixed ? 16 : 8;
+  return sizeof(double) * (SCHUR_TILE_LMS * 9 + 64) + t * (size_t)ch * max_span * kStage;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group(Dev d) {
+  constexpr int CH = GroupChunk<T>::value;
+  extern __shared__ __align__(16) double smem[];
+  double* s_vinv = smem;                              // SCHUR_TILE_LMS * 6
+  double* s_gl = s_vinv + SCHUR_TILE_LMS * 6;         // SCHUR_TILE_LMS * 3
+  double* s_red = s_gl + SCHUR_TILE_LMS * 3;          // 64
+  T* s_stg = reinterpret_cast<T*>(s_red + 64);        // CH * max_span * kStage
+  const SchurTile tile = d.schur_tiles[blockIdx.x];
+  const int nl = tile.l1 - tile.l0;
+  const int span = tile.span, rows = 6 * span, E = rows * (rows + 1) / 2, NE = E + rows;
+  const double lam = d.ctrl->lam;
+  const double floor_ = diag_floor(d, s_red);
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    const int j = tile.l0 + l;
+    double inv[6];
+    landmark_vinv<T>(d, j, lam, floor_, inv);
+    for (int k = 0; k < 6; ++k) s_vinv[l * 6 + k] = inv[k];
+    for (int k = 0; k < 3; ++k) s_gl[l * 3 + k] = d.lm_g[j * 3 + k];
+  }
+  if (span == 0) return;                             // landmarks seen only by the fixed keyframe
+  // Passes over the window's entries (kGroupOwn per thread each).  Owned entries are
+  // offsets into one landmark's staging: bit 31 set = a dot product of a Y row and a W row
+  // (offsets in bits 0-14 and 15-29); otherwise a staged scalar.
+  const int stg_len = CH * span * kStage;
+  const double* pose = d.pose[d.ctrl->cur];
+  for (int e0 = 0; e0 < NE; e0 += kGroupOwn * SCHUR_THREADS) {
+    int off[kGroupOwn];
+    T acc[kGroupOwn], cmp[kGroupOwn];
+#pragma unroll
+    for (int i = 0; i < kGroupOwn; ++i) {
+      const int e = e0 + threadIdx.x + i * SCHUR_THREADS;
+      acc[i] = 0;
+      cmp[i] = 0;
+      off[i] = 0;
+      if (e < E) {
+        int wr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (wr * (wr + 1) / 2 > e) --wr;
+        while ((wr + 1) * (wr + 2) / 2 <= e) ++wr;
+        const int wc = e - wr * (wr + 1) / 2;
+        const int ya = wr / 6, r = wr % 6, wb = wc / 6, c = wc % 6;
+        if (ya == wb)
+          off[i] = ya * kStage + 48 + r * (r + 1) / 2 + c;
+        else
+          off[i] = (int)(0x80000000u | (unsigned)(ya * kStage + r * 4) | ((unsigned)(wb * kStage + 24 + c * 4) << 15));
+      } else if (e < NE) {
+        const int wr = e - E;
+        off[i] = (wr / 6) * kStage + 69 + wr % 6;
       }
     }
-    for (int r = threadIdx.x; r < rows; r += blockDim.x)
-      if (s_b[r] != 0.0) atomicAdd(d.bS + base + r, s_b[r]);
+    for (int c0 = 0; c0 < nl; c0 += CH) {
+      const int nc = min(CH, nl - c0);
+      __syncthreads();                               // previous chunk consumed
+      for (int i = threadIdx.x; i < stg_len; i += blockDim.x) s_stg[i] = 0;
+      __syncthreads();
+      const int q0 = d.lm_pair[tile.l0 + c0], q1 = d.lm_pair[tile.l0 + c0 + nc];
+      for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        const int a = d.pair_kf[q];
+        const int pb = d.kf_pb[a];
+        if (pb < 0) continue;
+        const int l = d.pair_lm[q] - tile.l0;        // index in the tile
+        T W[18], Y[18], Dg[21], bY[6];
+        pair_schur_terms<T>(reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN, pose + a * POSE_STRIDE,
+                            s_vinv + l * 6, s_gl + l * 3, W, Y, Dg, bY);
+        T* st = s_stg + ((l - c0) * span + (pb - tile.k_lo)) * kStage;
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            st[r * 4 + k] = Y[r * 3 + k];
+            st[24 + r * 4 + k] = W[r * 3 + k];
+          }
+#pragma unroll
+        for (int k = 0; k < 21; ++k) st[48 + k] = Dg[k];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
+      }
+      __syncthreads();
+      for (int lr = 0; lr < nc; ++lr) {
+        const T* base = s_stg + lr * span * kStage;
+#pragma unroll
+        for (int i = 0; i < kGroupOwn; ++i) {
+          if (e0 + threadIdx.x + i * SCHUR_THREADS >= NE) break;
+          T v;
+          if (off[i] < 0) {
+            const T* y = base + (off[i] & 0x7fff);
+            const T* w = base + ((off[i] >> 15) & 0x7fff);
+            v = -(y[0] * w[0] + y[1] * w[1] + y[2] * w[2]);
+          } else {
+            v = base[off[i]];
+          }
+          if (sizeof(T) == 4) {                      // Kahan: acc - cmp is the running sum
+            const T yk = v - cmp[i];
+            const T t = acc[i] + yk;
+            cmp[i] = (t - acc[i]) - yk;
+            acc[i] = t;
+          } else {
+            acc[i] += v;
+          }
+        }
+      }
+    }
+    double* out = d.schur_part + tile.part_off;
+#pragma unroll
+    for (int i = 0; i < kGroupOwn; ++i) {
+      const int e = e0 + threadIdx.x + i * SCHUR_THREADS;
+      if (e < NE) out[e] = (double)acc[i] - (double)cmp[i];
+    }
+  }
+}
+
+// Block (a, b), a >= b, of the reduced camera system (and b_a when a == b): fixed-order sum
+// of the window partials of the Schur tiles covering it, added to what direct tiles wrote.
+__global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) {
+  const int blk = blockIdx.x;
+  const int t0 = d.blk_tiles_off[blk], t1 = d.blk_tiles_off[blk + 1];
+  if (t0 == t1) return;
+  int a = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+  while (a * (a + 1) / 2 > blk) --a;
+  while ((a + 1) * (a + 2) / 2 <= blk) ++a;
+  const int b = blk - a * (a + 1) / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int n_ent = a == b ? 27 : 36;              // 21 lower entries + 6 of b, or 36
+  for (int e = warp; e < n_ent; e += nw) {
+    int r, c;
+    bool is_b = false;
+    if (a != b) {
+      r = e / 6;
+      c = e % 6;
+    } else if (e < 21) {
+      r = 0;
+      while ((r + 1) * (r + 2) / 2 <= e) ++r;
+      c = e - r * (r + 1) / 2;
+    } else {
+      r = e - 21;
+      c = 0;
+      is_b = true;
+    }
+    double v = 0.0;
+    for (int t = t0 + lane; t < t1; t += 32) {
+      const SchurTile st = d.schur_tiles[d.blk_tiles[t]];
+      const int rows = 6 * st.span;
+      const int wr = 6 * (a - st.k_lo) + r;
+      if (is_b) {
+        v += d.schur_part[st.part_off + rows * (rows + 1) / 2 + wr];
+      } else {
+        const int wc = 6 * (b - st.k_lo) + c;
+        v += d.schur_part[st.part_off + wr * (wr + 1) / 2 + wc];
+      }
+    }
+    v = warp_sum(v);
+    if (lane == 0) {
+      if (is_b) d.bS[6 * a + r] += v;
+      else d.S[(size_t)(6 * a + r) * d.n_c + 6 * b + c] += v;
+    }
   }
 }
 
@@ -699,6 +946,332 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(Dev d) {
   }
 }
 
+// ---------------------------------------------------------- k_chol_cluster
+// The damped reduced camera system A = S + lam D_p (n_c x n_c, FP64) factored A = L L^T
+// by a thread-block cluster of CS CTAs, then dc = A^-1 (b - g_p).
+//
+// Layout: A is padded to NP = 8 * NB rows (identity in the padding) and split into 8-row
+// block rows; block row r lives in the shared memory of CTA r % CS.  Right-looking by
+// 8-column panels.  Step k (the diagonal block L_kk already factored and pushed, with the
+// reciprocals of its diagonal, to every CTA):
+//   1. every CTA solves its block rows r > k against L_kk (L_rk = A_rk L_kk^-T); CTA 0
+//      does the same for the right-hand side, carried as an extra row, which fuses the
+//      forward substitution L y = rhs into the factorisation; each CTA pushes its new
+//      panel blocks L_rk to every CTA;                                   cluster barrier
+//   2. look-ahead: the owner of block k+1 first updates and factors its diagonal block and
+//      pushes it; then every CTA applies A_rc -= L_rk L_ck^T to its block rows (c in
+//      (k, r]) and CTA 0 updates the right-hand side;                    cluster barrier
+// On GB300 a dependent FP64 FMA takes ~64 cycles, a divide ~430 and a square root ~680,
+// so the pivot chain uses rsqrt and multiplications, and the diagonal blocks' inverses
+// are formed once, in parallel, after the factorisation.
+// Backward substitution L^T x = y runs from the last block: the owner of block k sums the
+// contributions other CTAs pushed into its slots (fixed order), multiplies by L_kk^-T,
+// writes x_k, and pushes the running contributions of block row k to the owners of blocks
+// < k.  All pushes are plain DSMEM stores made visible by the next cluster barrier.
+constexpr int kCB = 8;
+
+struct CholSmem {
+  int NP, NB, nlb, CS;
+  __host__ __device__ size_t rows_off() const { return 0; }
+  __host__ __device__ size_t panel_off() const { return rows_off() + (size_t)nlb * kCB * NP; }
+  __host__ __device__ size_t lkk_off() const { return panel_off() + (size_t)NB * kCB * kCB; }
+  __host__ __device__ size_t y_off() const { return lkk_off() + kCB * kCB + kCB; }
+  __host__ __device__ size_t acc_off() const { return y_off() + NP; }
+  __host__ __device__ size_t contrib_off() const { return acc_off() + NP; }
+  __host__ __device__ size_t linv_off() const { return contrib_off() + (size_t)nlb * CS * kCB; }
+  __host__ __device__ size_t red_off() const { return linv_off() + (size_t)nlb * kCB * kCB; }
+  __host__ __device__ size_t flag_off() const { return red_off() + 128; }
+  __host__ __device__ size_t doubles() const { return flag_off() + 8; }
+};
+
+__host__ __device__ inline CholSmem chol_layout(int n_c, int CS) {
+  CholSmem L;
+  L.NB = (n_c + kCB - 1) / kCB;
+  L.NP = L.NB * kCB;
+  L.nlb = (L.NB + CS - 1) / CS;
+  L.CS = CS;
+  return L;
+}
+
+// Factor the 8x8 block D (row stride NP) in place with warp 0 and push it, with the
+// reciprocals of its diagonal and a non-PD flag, to every CTA of the cluster.
+__device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk, int* flag,
+                                                 cooperative_groups::cluster_group& cluster, int CS) {
+  const int tid = threadIdx.x;
+  if (tid < 32) {
+    const int i = tid;
+    bool bad = false;
+    for (int c = 0; c < kCB; ++c) {
+      __syncwarp();
+      const double piv = D[c * NP + c];
+      if (!(piv > 0.0) || !isfinite(piv)) bad = true;
+      const double rs = rsqrt(fmax(piv, 1e-300));
+      __syncwarp();
+      if (i == c) D[c * NP + c] = piv * rs;
+      if (i > c && i < kCB) D[i * NP + c] *= rs;
+      __syncwarp();
+      if (i > c && i < kCB)
+        for (int j = c + 1; j <= i; ++j) D[i * NP + j] = fma(-D[i * NP + c], D[j * NP + c], D[i * NP + j]);
+    }
+    __syncwarp();
+    if (i == 0 && bad) *flag = 1;
+  }
+  __syncthreads();
+  const int bad = *flag;
+  constexpr int W = kCB * kCB + kCB + 1;           // block, reciprocals, flag
+  for (int e = tid; e < CS * W; e += blockDim.x) {
+    const int dst = e / W, t = e % W;
+    if (t < kCB * kCB) {
+      const int i = t / kCB, m = t % kCB;
+      cluster.map_shared_rank(lkk, dst)[t] = m <= i ? D[i * NP + m] : 0.0;
+    } else if (t < kCB * kCB + kCB) {
+      const int c = t - kCB * kCB;
+      cluster.map_shared_rank(lkk, dst)[t] = 1.0 / D[c * NP + c];
+    } else if (bad) {
+      *cluster.map_shared_rank(flag, dst) = 1;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_chol_cluster(Dev d) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) double smem[];
+  Ctrl* ctrl = d.ctrl;
+  if (ctrl->nonpd) return;                         // uniform: a landmark block failed
+  const int CS = (int)cluster.num_blocks();
+  const int q = (int)cluster.block_rank();
+  const int n = d.n_c;
+  const CholSmem Ls = chol_layout(n, CS);
+  const int NP = Ls.NP, NB = Ls.NB;
+  double* rows = smem + Ls.rows_off();             // [lb][i][col]
+  double* panel = smem + Ls.panel_off();           // [c][i][m] = L[8c+i][8k+m]
+  double* lkk = smem + Ls.lkk_off();               // [i][m], then 8 reciprocals of the diagonal
+  double* ybuf = smem + Ls.y_off();                // right-hand side row / y
+  double* acc = smem + Ls.acc_off();               // backward contributions of own rows
+  double* contrib = smem + Ls.contrib_off();       // [lb][from CTA][8]
+  double* linv = smem + Ls.linv_off();             // [lb][i][m] inverse of own diagonal blocks
+  double* red = smem + Ls.red_off();
+  int* flag = reinterpret_cast<int*>(smem + Ls.flag_off());
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double lam = ctrl->lam;
+  const double floor_ = diag_floor(d, red);        // block-level, contains barriers
+
+  // ---- load own block rows (damped, padded), rhs on CTA 0
+  for (int lb = 0; lb < Ls.nlb; ++lb) {
+    const int r = q + lb * CS;
+    if (r >= NB) break;
+    for (int e = tid; e < kCB * NP; e += nt) {
+      const int i = e / NP, c = e % NP, gi = kCB * r + i;
+      double v = 0.0;
+      if (gi < n && c < n) {
+        if (c <= gi) v = d.S[(size_t)gi * n + c];
+        if (c == gi) {
+          const int pb = gi / 6, comp = gi % 6;
+          const int kf = pb < d.fixed_kf ? pb : pb + 1;
+          v += lam * fmax(d.kf_dp[kf * 6 + comp], floor_);
+        }
+      } else if (gi >= n && c == gi) {
+        v = 1.0;
+      }
+      rows[(size_t)(lb * kCB + i) * NP + c] = v;
+    }
+  }
+  for (int c = tid; c < NP; c += nt) {
+    double v = 0.0;
+    if (q == 0 && c < n) {
+      const int pb = c / 6, comp = c % 6;
+      const int kf = pb < d.fixed_kf ? pb : pb + 1;
+      v = d.bS[c] - d.kf_gp[kf * 6 + comp];
+    }
+    ybuf[c] = v;
+    acc[c] = 0.0;
+  }
+  for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
+  if (tid == 0) *flag = 0;
+  cluster.sync();
+  if (q == 0) chol_factor_push(rows, NP, lkk, flag, cluster, CS);   // block 0 is CTA 0's first row block
+
+  // ---- factorisation with the forward substitution fused
+  for (int k = 0; k < NB; ++k) {
+    cluster.sync();                                // L_kk (and flag) visible everywhere
+    if (*flag) break;
+    // 1. TRSM of own block rows below k, and of the right-hand side on CTA 0
+    const double* linvd = lkk + kCB * kCB;
+    for (int e = tid; e < (Ls.nlb + 1) * kCB; e += nt) {
+      const int lb = e / kCB, i = e % kCB;
+      double* a;
+      if (lb < Ls.nlb) {
+        const int r = q + lb * CS;
+        if (r <= k || r >= NB) continue;
+        a = rows + (size_t)(lb * kCB + i) * NP + kCB * k;
+      } else {
+        if (q != 0 || i > 0) continue;
+        a = ybuf + kCB * k;
+      }
+      double t[kCB];
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) t[c] = a[c];
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) {
+        const double x = t[c] * linvd[c];
+        t[c] = x;
+#pragma unroll
+        for (int m = c + 1; m < kCB; ++m) t[m] = fma(-x, lkk[m * kCB + c], t[m]);
+      }
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) a[c] = t[c];
+    }
+    __syncthreads();
+    for (int lb = 0; lb < Ls.nlb; ++lb) {          // push panel blocks L_rk to every CTA
+      const int r = q + lb * CS;
+      if (r <= k || r >= NB) continue;
+      for (int e = tid; e < CS * kCB * kCB; e += nt) {
+        const int dst = e / (kCB * kCB), t = e % (kCB * kCB), i = t / kCB, m = t % kCB;
+        cluster.map_shared_rank(panel, dst)[(size_t)r * kCB * kCB + t] =
+            rows[(size_t)(lb * kCB + i) * NP + kCB * k + m];
+      }
+    }
+    cluster.sync();                                // panel k visible everywhere
+    // 2a. look-ahead: owner of block k+1 updates and factors its diagonal block first
+    if (k + 1 < NB && q == (k + 1) % CS) {
+      const int lb = (k + 1) / CS;
+      const double* Lr = panel + (size_t)(k + 1) * kCB * kCB;
+      for (int e = tid; e < kCB * kCB; e += nt) {
+        const int i = e / kCB, j = e % kCB;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < kCB; ++m) s = fma(Lr[i * kCB + m], Lr[j * kCB + m], s);
+        rows[(size_t)(lb * kCB + i) * NP + kCB * (k + 1) + j] -= s;
+      }
+      __syncthreads();
+      chol_factor_push(rows + (size_t)(lb * kCB) * NP + kCB * (k + 1), NP, lkk, flag, cluster, CS);
+    }
+    // 2b. trailing update of own block rows: A_rc -= L_rk L_ck^T, c in (k, r]
+    for (int lb = 0; lb < Ls.nlb; ++lb) {
+      const int r = q + lb * CS;
+      if (r <= k + 1 || r >= NB) continue;
+      const double* Lr = panel + (size_t)r * kCB * kCB;
+      const int cnt = (r - k) * kCB * kCB;
+      for (int e = tid; e < cnt; e += nt) {
+        const int c = k + 1 + e / (kCB * kCB), t = e % (kCB * kCB), i = t / kCB, j = t % kCB;
+        const double* Lc = panel + (size_t)c * kCB * kCB + j * kCB;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < kCB; ++m) s = fma(Lr[i * kCB + m], Lc[m], s);
+        rows[(size_t)(lb * kCB + i) * NP + kCB * c + j] -= s;
+      }
+    }
+    if (q == 0) {
+      const double* y = ybuf + kCB * k;
+      for (int e = tid; e < NP - kCB * (k + 1); e += nt) {
+        const int g = kCB * (k + 1) + e, c = g / kCB, j = g % kCB;
+        const double* Lc = panel + (size_t)c * kCB * kCB + j * kCB;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < kCB; ++m) s = fma(y[m], Lc[m], s);
+        ybuf[g] -= s;
+      }
+    }
+    __syncthreads();
+  }
+  cluster.sync();
+  if (*flag) {
+    if (q == 0 && tid == 0) ctrl->nonpd = 1;
+    return;
+  }
+  // inverses of own diagonal blocks (thread per (block, column)), y to every CTA
+  for (int e = tid; e < Ls.nlb * kCB; e += nt) {
+    const int lb = e / kCB, j = e % kCB, r = q + lb * CS;
+    if (r >= NB) continue;
+    const double* D = rows + (size_t)(lb * kCB) * NP + kCB * r;
+    double z[kCB];
+#pragma unroll
+    for (int i = 0; i < kCB; ++i) {
+      double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+      for (int m = 0; m < i; ++m) s = fma(-D[i * NP + m], z[m], s);
+      z[i] = i < j ? 0.0 : s / D[i * NP + i];
+    }
+#pragma unroll
+    for (int i = 0; i < kCB; ++i) linv[(lb * kCB + i) * kCB + j] = z[i];
+  }
+  if (q == 0) {
+    for (int e = tid; e < CS * NP; e += nt) {
+      const int dst = e / NP, c = e % NP;
+      if (dst != 0) cluster.map_shared_rank(ybuf, dst)[c] = ybuf[c];
+    }
+  }
+  cluster.sync();
+
+  // ---- backward substitution L^T x = y
+  for (int k = NB - 1; k >= 0; --k) {
+    if (q == k % CS) {
+      const int lb = k / CS;
+      double* xk = red;                            // 8 values, CTA-local
+      double* tk = red + 16;
+      if (tid < kCB * 16) {                        // t_i = y_i - acc_i - sum over CTAs (fixed order)
+        const int i = tid / 16, src = tid % 16;
+        double v = src < CS ? contrib[(lb * CS + src) * kCB + i] : 0.0;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
+        if (src == 0) tk[i] = ybuf[kCB * k + i] - acc[kCB * k + i] - v;
+      }
+      __syncthreads();
+      if (tid < kCB * kCB) {                       // x = L_kk^-T t
+        const int i = tid / kCB, c = tid % kCB;
+        double v = linv[(lb * kCB + c) * kCB + i] * tk[c];
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 8);
+        if (c == 0) {
+          xk[i] = v;
+          if (kCB * k + i < n) d.dc[kCB * k + i] = v;
+        }
+      }
+      __syncthreads();
+      for (int g = tid; g < kCB * k; g += nt) {    // acc[k'] += L_kk'^T x_k, pushed to owners
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < kCB; ++i) s = fma(rows[(size_t)(lb * kCB + i) * NP + g], xk[i], s);
+        const double a = acc[g] + s;
+        acc[g] = a;
+        const int kp = g / kCB, dst = kp % CS;
+        if (dst != q) cluster.map_shared_rank(contrib, dst)[((kp / CS) * CS + q) * kCB + (g % kCB)] = a;
+      }
+    }
+    cluster.sync();
+  }
+
+  // ---- epilogue: predicted-reduction part, step norm, candidate poses
+  if (q == 0) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = tid; i < n; i += nt) {
+      const int pb = i / 6, comp = i % 6;
+      const int kf = pb < d.fixed_kf ? pb : pb + 1;
+      const double D = fmax(d.kf_dp[kf * 6 + comp], floor_);
+      const double xi = d.dc[i];
+      v[0] += xi * (lam * D * xi - d.kf_gp[kf * 6 + comp]);
+      v[1] += xi * xi;
+    }
+    block_sum4(v, red);
+    if (tid == 0) {
+      ctrl->pred_p = v[0];
+      ctrl->step2_p = v[1];
+    }
+  }
+  const int cur = ctrl->cur;
+  for (int a = q * nt + tid; a < d.K; a += CS * nt) {
+    const double* T0 = d.pose[cur] + a * POSE_STRIDE;
+    double* T1 = d.pose[cur ^ 1] + a * POSE_STRIDE;
+    const int pb = d.kf_pb[a];
+    if (pb < 0) {
+      for (int k = 0; k < POSE_STRIDE; ++k) T1[k] = T0[k];
+    } else {
+      pose_plus(T0, d.dc + 6 * pb, T1);
+    }
+  }
+}
+
 // --------------------------------------------------------------- k_backsub
 template <typename T>
 __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
@@ -711,11 +1284,10 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
   }
   const int nl = tile.l1 - tile.l0;
   double* s_rig = smem;                              // C * 16
-  double* s_acc = s_rig + d.C * RIG_STRIDE;          // LIN_TILE_LMS * 3
-  double* s_new = s_acc + LIN_TILE_LMS * 3;          // LIN_TILE_LMS * 3
+  double* s_acc = s_rig + d.C * RIG_STRIDE;          // LIN_TILE_PAIRS * 3 (per pair slots)
+  double* s_new = s_acc + LIN_TILE_PAIRS * 3;        // LIN_TILE_LMS * 3
   double* s_red = s_new + LIN_TILE_LMS * 3;          // 128
   for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = d.rig[i];
-  for (int i = threadIdx.x; i < nl * 3; i += blockDim.x) s_acc[i] = 0.0;
   const double lam = ctrl->lam;
   const double floor_ = diag_floor(d, s_red);   // contains __syncthreads
   const int cur = ctrl->cur;
@@ -724,7 +1296,11 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
   for (int q = tile.p0 + threadIdx.x; q < tile.p1; q += blockDim.x) {
     const int a = d.pair_kf[q];
     const int pb = d.kf_pb[a];
-    if (pb < 0) continue;
+    double* acc = s_acc + (q - tile.p0) * 3;
+    if (pb < 0) {
+      acc[0] = acc[1] = acc[2] = 0.0;
+      continue;
+    }
     const T* pl = reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN;
     const double* xi = d.dc + 6 * pb;
     T X[3] = {pl[6], pl[7], pl[8]};
@@ -743,10 +1319,8 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
 #pragma unroll
     for (int r = 0; r < 3; ++r) w3[r] = M[r * 3] * u[0] + M[r * 3 + 1] * u[1] + M[r * 3 + 2] * u[2];
     const double* R = pose + a * POSE_STRIDE;
-    double* acc = s_acc + (d.pair_lm[q] - tile.l0) * 3;
 #pragma unroll
-    for (int c = 0; c < 3; ++c)
-      atomicAdd(acc + c, (double)((T)R[c] * w3[0] + (T)R[3 + c] * w3[1] + (T)R[6 + c] * w3[2]));
+    for (int c = 0; c < 3; ++c) acc[c] = (double)((T)R[c] * w3[0] + (T)R[3 + c] * w3[1] + (T)R[6 + c] * w3[2]);
   }
   __syncthreads();
   // phase 2: dp_j = -V_j^-1 (g_l + acc); candidate landmark; predicted-reduction part
@@ -756,7 +1330,13 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
     const double* Vi = d.lm_Vinv + VINV_STRIDE * j;
     const double tau = Vi[6];
     const double* g = d.lm_g + 3 * j;
-    const double t0 = g[0] + s_acc[l * 3], t1 = g[1] + s_acc[l * 3 + 1], t2 = g[2] + s_acc[l * 3 + 2];
+    double t0 = g[0], t1 = g[1], t2 = g[2];
+    for (int q = d.lm_pair[j]; q < d.lm_pair[j + 1]; ++q) {
+      const double* acc = s_acc + (q - tile.p0) * 3;
+      t0 += acc[0];
+      t1 += acc[1];
+      t2 += acc[2];
+    }
     const double dp0 = -(Vi[0] * t0 + Vi[1] * t1 + Vi[2] * t2);
     const double dp1 = -(Vi[1] * t0 + Vi[3] * t1 + Vi[4] * t2);
     const double dp2 = -(Vi[2] * t0 + Vi[4] * t1 + Vi[5] * t2);
@@ -855,14 +1435,6 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d) {
       ctrl->need_lin = 0;
     }
     ctrl->nonpd = 0;
-    s_red[0] = acc ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  if (s_red[0] != 0.0) {
-    for (int i = threadIdx.x; i < d.K * 6; i += blockDim.x) {
-      d.kf_gp[i] = 0.0;
-      d.kf_dp[i] = 0.0;
-    }
   }
 }
 
@@ -925,12 +1497,26 @@ __global__ void k_state_io(Dev d, int mode, double* user, const int32_t* lm_orde
 }
 
 size_t lin_smem(const Dev& d) {
-  return sizeof(double) * (d.C * RIG_STRIDE + LIN_TILE_LMS * 9 + d.K * 12 + 128) + sizeof(int) * d.K;
+  return sizeof(double) * (d.C * RIG_STRIDE + LIN_TILE_PAIRS * 21 + 128) + sizeof(int) * LIN_TILE_PAIRS;
 }
-size_t backsub_smem(const Dev& d) { return sizeof(double) * (d.C * RIG_STRIDE + LIN_TILE_LMS * 6 + 128); }
+size_t backsub_smem(const Dev& d) {
+  return sizeof(double) * (d.C * RIG_STRIDE + LIN_TILE_PAIRS * 3 + LIN_TILE_LMS * 3 + 128);
+}
 size_t eval_smem(const Dev& d) { return sizeof(double) * (d.C * RIG_STRIDE + 128); }
 constexpr int kCholSmemMaxN = 160;
 size_t chol_smem(int n) { return sizeof(double) * ((size_t)n * n + n); }
+constexpr size_t kClusterSmemMax = 220 * 1024;
+int g_cluster_max = 16;                         // largest cluster size the device launches
+
+// Cluster size for the distributed Cholesky, or 0 when the system is too large for the
+// cluster's shared memory (then the single-CTA global-memory kernel runs).
+int chol_cluster_size(int n_c) {
+  for (int cs : {16, 8}) {
+    if (cs > g_cluster_max) continue;
+    if (chol_layout(n_c, cs).doubles() * sizeof(double) <= kClusterSmemMax) return cs;
+  }
+  return 0;
+}
 
 }  // namespace
 
@@ -943,18 +1529,47 @@ cudaError_t set_kernel_attributes() {
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_lin<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_schur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_schur_direct<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)SchurSmem<double>::bytes());
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_schur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(k_schur_direct<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)SchurSmem<float>::bytes());
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_schur_group<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)group_smem_bytes(SPAN_MAX, false));
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_schur_group<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)group_smem_bytes(SPAN_MAX, true));
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)chol_smem(kCholSmemMaxN));
-  return e;
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  {
+    // largest cluster of 256-thread CTAs with the maximum shared memory that fits
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = kClusterSmemMax;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int n_clusters = 0;
+    g_cluster_max = (cudaOccupancyMaxActiveClusters(&n_clusters, k_chol_cluster, &cfg) == cudaSuccess &&
+                     n_clusters > 0) ? 16 : 8;
+    cudaGetLastError();
+  }
+  return cudaSuccess;
 }
 
-int kernels_per_iteration() { return 5; }
+int kernels_per_iteration() { return 7; }
 int kernels_per_solve_init() { return 1; }
 
 cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double zmin, int iters, int reset,
@@ -975,20 +1590,50 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   else
     k_lin<double><<<d.n_lin_tiles, LIN_THREADS, lin_smem(d), s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_kf_reduce<<<d.K, 384, 0, s>>>(d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(1)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(d.S, 0, sizeof(double) * (size_t)d.n_c * d.n_c, s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(d.bS, 0, sizeof(double) * (size_t)d.n_c, s)) != cudaSuccess) return e;
   if ((e = mark(2)) != cudaSuccess) return e;
-  if (d.mixed)
-    k_schur<float><<<d.n_schur_tiles, SCHUR_THREADS, SchurSmem<float>::bytes(), s>>>(d);
-  else
-    k_schur<double><<<d.n_schur_tiles, SCHUR_THREADS, SchurSmem<double>::bytes(), s>>>(d);
+  if (d.n_schur_tiles > 0) {
+    const size_t sm = group_smem_bytes(d.max_span, d.mixed != 0);
+    if (d.mixed)
+      k_schur_group<float><<<d.n_schur_tiles, SCHUR_THREADS, sm, s>>>(d);
+    else
+      k_schur_group<double><<<d.n_schur_tiles, SCHUR_THREADS, sm, s>>>(d);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (d.n_direct_tiles > 0) {
+    if (d.mixed)
+      k_schur_direct<float><<<d.n_direct_tiles, SCHUR_THREADS, SchurSmem<float>::bytes(), s>>>(d);
+    else
+      k_schur_direct<double><<<d.n_direct_tiles, SCHUR_THREADS, SchurSmem<double>::bytes(), s>>>(d);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_rcs_reduce<<<d.n_blk, 256, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(3)) != cudaSuccess) return e;
-  if (d.n_c <= kCholSmemMaxN)
+  if (chol_cluster_size(d.n_c) > 0) {
+    const int CS = chol_cluster_size(d.n_c);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CS);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = chol_layout(d.n_c, CS).doubles() * sizeof(double);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, k_chol_cluster, d)) != cudaSuccess) return e;
+  } else if (d.n_c <= kCholSmemMaxN) {
     k_chol<true><<<1, CHOL_THREADS, chol_smem(d.n_c), s>>>(d);
-  else
+  } else {
     k_chol<false><<<1, CHOL_THREADS, 0, s>>>(d);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(4)) != cudaSuccess) return e;
   if (d.mixed)

@@ -154,6 +154,17 @@ def test_fp64_lockstep_multicamera(cvba):
         assert g["accepted"] == int(o.accepted)
 
 
+def test_fp64_lockstep_wide_landmarks(cvba):
+    """40 keyframes, distant points seen by every camera that sees them: most landmark
+    windows are wider than a Schur tile window (24 keyframes), exercising the direct
+    (atomic) Schur path next to the grouped one, and a 234-row reduced system."""
+    p = synth.make_problem("c0", K=40, M=300, seed=14,
+                           volume=dict(kind="box", lo=(-5.0, -2.0, 15.0), hi=(25.0, 2.0, 30.0)))
+    for d, tol, g, o in lockstep(cvba, p, 3):
+        assert d <= tol, (d, tol)
+        assert g["accepted"] == int(o.accepted)
+
+
 @pytest.fixture(scope="module")
 def c1_oracle():
     p = synth.make_problem("c1")
