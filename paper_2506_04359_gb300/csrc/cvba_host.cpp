@@ -149,6 +149,14 @@ int read_cur(cvba_ctx* c) {
   return cur;
 }
 
+// FP32 copy of `n` doubles into a device mirror (mixed path only).
+cudaError_t upload_f32(cvba_ctx* c, float* dst, const double* src, size_t n) {
+  if (!dst) return cudaSuccess;
+  std::vector<float> h(n);
+  for (size_t i = 0; i < n; ++i) h[i] = (float)src[i];
+  return h2d(c, dst, h.data(), n * sizeof(float));
+}
+
 // Stable counting sort of idx by key[idx] in [0, n_keys).
 void counting_sort(std::vector<int32_t>& idx, const std::vector<int32_t>& key, int n_keys) {
   std::vector<int64_t> cnt((size_t)n_keys + 1, 0);
@@ -389,6 +397,21 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   d.pose[1] = pose1;
   d.lm[0] = lm0;
   d.lm[1] = lm1;
+  if (mixed) {
+    float *rf, *pf0, *pf1, *lf0, *lf1, *dcf;
+    CK(dalloc(c, &rf, (size_t)C * RIG_STRIDE), "alloc mirrors");
+    CK(dalloc(c, &pf0, (size_t)K * POSE_STRIDE), "alloc mirrors");
+    CK(dalloc(c, &pf1, (size_t)K * POSE_STRIDE), "alloc mirrors");
+    CK(dalloc(c, &lf0, (size_t)M * 3), "alloc mirrors");
+    CK(dalloc(c, &lf1, (size_t)M * 3), "alloc mirrors");
+    CK(dalloc(c, &dcf, (size_t)n_c), "alloc mirrors");
+    d.rig_f = rf;
+    d.pose_f[0] = pf0;
+    d.pose_f[1] = pf1;
+    d.lm_f[0] = lf0;
+    d.lm_f[1] = lf1;
+    d.dc_f = dcf;
+  }
   d.obs_cam = ocam;
   d.pair_kf = pkf;
   d.pair_lm = plm;
@@ -495,6 +518,11 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   CK(cudaMemcpy(rig, righ.data(), righ.size() * 8, cudaMemcpyHostToDevice), "upload rig");
   CK(cudaMemcpy(pose0, poseh.data(), poseh.size() * 8, cudaMemcpyHostToDevice), "upload poses");
   CK(cudaMemcpy(lm0, lmh.data(), lmh.size() * 8, cudaMemcpyHostToDevice), "upload landmarks");
+  if (mixed) {
+    CK(upload_f32(c, const_cast<float*>(d.rig_f), righ.data(), righ.size()), "upload mirrors");
+    CK(upload_f32(c, d.pose_f[0], poseh.data(), poseh.size()), "upload mirrors");
+    CK(upload_f32(c, d.lm_f[0], lmh.data(), lmh.size()), "upload mirrors");
+  }
   CK(cudaMemcpy(ocam, obs_cam.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "upload");
   CK(cudaMemcpy(pkf, pair_kf.data(), (size_t)P * 4, cudaMemcpyHostToDevice), "upload");
   CK(cudaMemcpy(plm, pair_lm.data(), (size_t)P * 4, cudaMemcpyHostToDevice), "upload");
@@ -529,6 +557,8 @@ cvba_status upload_state(cvba_ctx* c) {
   CK(cudaMemcpyAsync(c->d.pose[cur], poseh.data(), poseh.size() * 8, cudaMemcpyHostToDevice, c->stream), "upload");
   CK(cudaMemcpyAsync(c->d.lm[cur], lmh.data(), lmh.size() * 8, cudaMemcpyHostToDevice, c->stream), "upload");
   CK(cudaStreamSynchronize(c->stream), "sync");
+  CK(upload_f32(c, c->d.pose_f[cur], poseh.data(), poseh.size()), "upload mirrors");
+  CK(upload_f32(c, c->d.lm_f[cur], lmh.data(), lmh.size()), "upload mirrors");
   return CVBA_OK;
 }
 
@@ -620,6 +650,7 @@ cvba_status cvba_set_rig(cvba_ctx* c, int n_cams, const double* intr, const doub
       }
     }
     CK(h2d(c, const_cast<double*>(c->d.rig), righ.data(), righ.size() * 8), "upload rig");
+    CK(upload_f32(c, const_cast<float*>(c->d.rig_f), righ.data(), righ.size()), "upload rig");
   }
   return CVBA_OK;
 }

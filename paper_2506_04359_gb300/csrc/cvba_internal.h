@@ -62,6 +62,12 @@ struct Dev {
   const double* rig;          // C * RIG_STRIDE
   double* pose[2];            // K * POSE_STRIDE, double-buffered state
   double* lm[2];              // M * 3 (internal landmark order)
+  // FP32 mirrors of the state for the mixed path (written wherever the FP64 state is
+  // written; FP64<->FP32 conversions run on the slow FP64 pipe, so hot loops avoid them)
+  const float* rig_f;         // C * RIG_STRIDE
+  float* pose_f[2];           // K * POSE_STRIDE
+  float* lm_f[2];             // M * 3
+  float* dc_f;                // n_c
   const void* obs_uv;         // N * 2, double (FP64) or float (mixed)
   const int32_t* obs_cam;     // N
   const int32_t* pair_kf;     // P

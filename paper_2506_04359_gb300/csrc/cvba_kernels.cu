@@ -108,19 +108,51 @@ __device__ __forceinline__ void load_uv(const float* uv, int n, float& u, float&
   v = x.y;
 }
 
+// Running sum: plain for double; Kahan-compensated for float (s - c is the sum).
+template <typename T>
+struct Acc {
+  T s = 0, c = 0;
+  __device__ __forceinline__ void add(T v) {
+    if (sizeof(T) == 4) {
+      const T y = v - c;
+      const T t = s + y;
+      c = (t - s) - y;
+      s = t;
+    } else {
+      s += v;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+template <typename T>
 struct PairStats {
-  double cost = 0.0, sq = 0.0;
+  Acc<T> cost, sq;
   int nv = 0, ni = 0;
 };
+
+// State in the compute type: the FP64 buffers, or their FP32 mirrors on the mixed path.
+template <typename T> __device__ __forceinline__ const T* st_pose(const Dev& d, int b);
+template <> __device__ __forceinline__ const double* st_pose<double>(const Dev& d, int b) { return d.pose[b]; }
+template <> __device__ __forceinline__ const float* st_pose<float>(const Dev& d, int b) { return d.pose_f[b]; }
+template <typename T> __device__ __forceinline__ const T* st_lm(const Dev& d, int b);
+template <> __device__ __forceinline__ const double* st_lm<double>(const Dev& d, int b) { return d.lm[b]; }
+template <> __device__ __forceinline__ const float* st_lm<float>(const Dev& d, int b) { return d.lm_f[b]; }
+template <typename T> __device__ __forceinline__ const T* st_rig(const Dev& d);
+template <> __device__ __forceinline__ const double* st_rig<double>(const Dev& d) { return d.rig; }
+template <> __device__ __forceinline__ const float* st_rig<float>(const Dev& d) { return d.rig_f; }
+template <typename T> __device__ __forceinline__ const T* st_dc(const Dev& d);
+template <> __device__ __forceinline__ const double* st_dc<double>(const Dev& d) { return d.dc; }
+template <> __device__ __forceinline__ const float* st_dc<float>(const Dev& d) { return d.dc_f; }
 
 // Residuals of the observations [o0, o1) of one (landmark, keyframe) pair at pose P
 // and landmark pw; with JAC also the pair's camera-frame information M3 (sym 00 01 02 11
 // 12 22) and a3 = sum w A^T r, A = d pi(X_c) / d X_b = J_pi R_cb.
 template <typename T, bool JAC>
-__device__ __forceinline__ void eval_pair(const double* __restrict__ P, const double* pw, int o0, int o1,
+__device__ __forceinline__ void eval_pair(const T* __restrict__ P, const T* pw, int o0, int o1,
                                           const int32_t* __restrict__ obs_cam, const T* __restrict__ uv,
-                                          const double* rig, T hub, T zmin, T X[3], T M3[6], T a3[3],
-                                          PairStats& st) {
+                                          const T* rig, T hub, T zmin, T X[3], T M3[6], T a3[3],
+                                          PairStats<T>& st) {
   T R[9], t[3];
 #pragma unroll
   for (int k = 0; k < 9; ++k) R[k] = (T)P[k];
@@ -136,7 +168,7 @@ __device__ __forceinline__ void eval_pair(const double* __restrict__ P, const do
     for (int k = 0; k < 3; ++k) a3[k] = 0;
   }
   for (int n = o0; n < o1; ++n) {
-    const double* rg = rig + obs_cam[n] * RIG_STRIDE;
+    const T* rg = rig + obs_cam[n] * RIG_STRIDE;
     const T fx = (T)rg[0], fy = (T)rg[1], cx = (T)rg[2], cy = (T)rg[3];
     T Rc[9];
 #pragma unroll
@@ -155,8 +187,8 @@ __device__ __forceinline__ void eval_pair(const double* __restrict__ P, const do
     const T e = sqrt(s);
     const bool inl = e <= hub;
     const T rho = inl ? s : fma((T)2 * hub, e, -hub * hub);
-    st.cost += 0.5 * (double)rho;
-    st.sq += (double)s;
+    st.cost.add((T)0.5 * rho);
+    st.sq.add(s);
     st.nv += 1;
     st.ni += inl ? 1 : 0;
     if (JAC) {
@@ -286,18 +318,19 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
   extern __shared__ __align__(16) double smem[];
   const LinTile tile = d.lin_tiles[blockIdx.x];
   const int nl = tile.l1 - tile.l0, np = tile.p1 - tile.p0;
-  double* s_rig = smem;                                // C * 16
-  double* s_pair = s_rig + d.C * RIG_STRIDE;           // LIN_TILE_PAIRS * 21
-  double* s_red = s_pair + LIN_TILE_PAIRS * 21;        // 128
-  int* s_kf = reinterpret_cast<int*>(s_red + 128);     // LIN_TILE_PAIRS
-  for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = d.rig[i];
+  double* s_red = smem;                                // 128
+  T* s_rig = reinterpret_cast<T*>(s_red + 128);        // C * 16
+  T* s_pair = s_rig + d.C * RIG_STRIDE;                // LIN_TILE_PAIRS * 21
+  int* s_kf = reinterpret_cast<int*>(s_pair + LIN_TILE_PAIRS * 21);   // LIN_TILE_PAIRS
+  const T* rig = st_rig<T>(d);
+  for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = rig[i];
   __syncthreads();
 
   const int cur = ctrl->cur;
-  const double* pose = d.pose[cur];
-  const double* lmp = d.lm[cur];
+  const T* pose = st_pose<T>(d, cur);
+  const T* lmp = st_lm<T>(d, cur);
   const T hub = (T)ctrl->huber, zmin = (T)ctrl->zmin;
-  PairStats st;
+  PairStats<T> st;
   for (int qi = threadIdx.x; qi < np; qi += blockDim.x) {
     const int q = tile.p0 + qi;
     const int a = d.pair_kf[q], j = d.pair_lm[q];
@@ -312,37 +345,37 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
     // landmark block: J_lm = A R  ->  Hll += R^T M3 R, g_l += R^T a3
     T R[9], M[9], G[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = (T)pose[a * POSE_STRIDE + k];
+    for (int k = 0; k < 9; ++k) R[k] = pose[a * POSE_STRIDE + k];
     sym3_full(M3, M);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int c = 0; c < 3; ++c) G[r * 3 + c] = M[r * 3] * R[c] + M[r * 3 + 1] * R[3 + c] + M[r * 3 + 2] * R[6 + c];
-    double* sl = s_pair + qi * 21;
+    T* sl = s_pair + qi * 21;
     const int si[6] = {0, 0, 0, 1, 1, 2}, sj[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       const int r = si[k], c = sj[k];
-      sl[k] = (double)(R[r] * G[c] + R[3 + r] * G[3 + c] + R[6 + r] * G[6 + c]);
+      sl[k] = R[r] * G[c] + R[3 + r] * G[3 + c] + R[6 + r] * G[6 + c];
     }
 #pragma unroll
-    for (int r = 0; r < 3; ++r) sl[6 + r] = (double)(R[r] * a3[0] + R[3 + r] * a3[1] + R[6 + r] * a3[2]);
+    for (int r = 0; r < 3; ++r) sl[6 + r] = R[r] * a3[0] + R[3 + r] * a3[1] + R[6 + r] * a3[2];
     // pose gradient B^T a3 = (a3, X x a3) and diag of B^T M3 B (fixed keyframe: unused)
-    sl[9] = (double)a3[0];
-    sl[10] = (double)a3[1];
-    sl[11] = (double)a3[2];
-    sl[12] = (double)(X[1] * a3[2] - X[2] * a3[1]);
-    sl[13] = (double)(X[2] * a3[0] - X[0] * a3[2]);
-    sl[14] = (double)(X[0] * a3[1] - X[1] * a3[0]);
-    sl[15] = (double)M3[0];
-    sl[16] = (double)M3[3];
-    sl[17] = (double)M3[5];
-    sl[18] = (double)(M3[3] * X[2] * X[2] - 2 * M3[4] * X[1] * X[2] + M3[5] * X[1] * X[1]);
-    sl[19] = (double)(M3[0] * X[2] * X[2] - 2 * M3[2] * X[0] * X[2] + M3[5] * X[0] * X[0]);
-    sl[20] = (double)(M3[0] * X[1] * X[1] - 2 * M3[1] * X[0] * X[1] + M3[3] * X[0] * X[0]);
+    sl[9] = a3[0];
+    sl[10] = a3[1];
+    sl[11] = a3[2];
+    sl[12] = X[1] * a3[2] - X[2] * a3[1];
+    sl[13] = X[2] * a3[0] - X[0] * a3[2];
+    sl[14] = X[0] * a3[1] - X[1] * a3[0];
+    sl[15] = M3[0];
+    sl[16] = M3[3];
+    sl[17] = M3[5];
+    sl[18] = M3[3] * X[2] * X[2] - 2 * M3[4] * X[1] * X[2] + M3[5] * X[1] * X[1];
+    sl[19] = M3[0] * X[2] * X[2] - 2 * M3[2] * X[0] * X[2] + M3[5] * X[0] * X[0];
+    sl[20] = M3[0] * X[1] * X[1] - 2 * M3[1] * X[0] * X[1] + M3[3] * X[0] * X[0];
     s_kf[qi] = d.kf_pb[a] >= 0 ? a : -1;
   }
-  double v[4] = {st.cost, st.sq, (double)st.nv, (double)st.ni};
+  double v[4] = {st.cost.value(), st.sq.value(), (double)st.nv, (double)st.ni};
   block_sum4(v, s_red);                              // contains barriers: slots complete
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -352,23 +385,23 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
   double mx = 0.0;
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     const int j = tile.l0 + l;
-    double h[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    Acc<T> h[9];
     for (int q = d.lm_pair[j]; q < d.lm_pair[j + 1]; ++q)
 #pragma unroll
-      for (int k = 0; k < 9; ++k) h[k] += s_pair[(q - tile.p0) * 21 + k];
+      for (int k = 0; k < 9; ++k) h[k].add(s_pair[(q - tile.p0) * 21 + k]);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = h[k];
+    for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = h[k].value();
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = h[6 + k];
-    mx = fmax(mx, fmax(h[0], fmax(h[3], h[5])));
+    for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = h[6 + k].value();
+    mx = fmax(mx, fmax(h[0].value(), fmax(h[3].value(), h[5].value())));
   }
   // per keyframe and component: sum over this tile's pairs of that keyframe, in order
   for (int e = threadIdx.x; e < tile.kf_n * 12; e += blockDim.x) {
     const int a = tile.kf_lo + e / 12, comp = e % 12;
-    double sum = 0.0;
+    Acc<T> sum;
     for (int qi = 0; qi < np; ++qi)
-      if (s_kf[qi] == a) sum += s_pair[qi * 21 + 9 + comp];
-    d.kf_part[tile.part_off + e] = sum;
+      if (s_kf[qi] == a) sum.add(s_pair[qi * 21 + 9 + comp]);
+    d.kf_part[tile.part_off + e] = sum.value();
   }
   mx = block_max(mx, s_red);
   if (threadIdx.x == 0 && mx > 0.0)
@@ -378,13 +411,20 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
 // g_p and diag(Hpp) of keyframe blockIdx.x: fixed-order sum of the covering tiles'
 // partials (lane l takes tiles l, l+32, ...; then a butterfly over the warp).
 __global__ void __launch_bounds__(384) k_kf_reduce(Dev d) {
+  __shared__ int s_off[384];
   const int a = blockIdx.x;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;   // warp = component (12)
   const int t0 = d.kf_tiles_off[a], t1 = d.kf_tiles_off[a + 1];
   double v = 0.0;
-  for (int t = t0 + lane; t < t1; t += 32) {
-    const LinTile tl = d.lin_tiles[d.kf_tiles[t]];
-    v += d.kf_part[tl.part_off + (a - tl.kf_lo) * 12 + warp];
+  for (int c0 = t0; c0 < t1; c0 += 384) {            // stage offsets of a chunk of tiles
+    const int nc = min(384, t1 - c0);
+    __syncthreads();
+    if (threadIdx.x < nc) {
+      const LinTile tl = d.lin_tiles[d.kf_tiles[c0 + threadIdx.x]];
+      s_off[threadIdx.x] = tl.part_off + (a - tl.kf_lo) * 12;
+    }
+    __syncthreads();
+    for (int t = lane; t < nc; t += 32) v += d.kf_part[s_off[t] + warp];
   }
   v = warp_sum(v);
   if (lane == 0) {
@@ -436,8 +476,8 @@ __device__ void landmark_vinv(const Dev& d, int j, double lam, double floor_, do
 // Per pair: W = J_pose^T W J_lm = [G; [X]x G] with G = M3 R (6 x 3), Y = W V^-1, the pair's
 // diagonal-block term U - Y W^T (U = B^T M3 B, lower 21) and Y g_l.
 template <typename T>
-__device__ __forceinline__ void pair_schur_terms(const T* pl, const double* R_pose, const double* vinv6,
-                                                 const double* gl3, T W[18], T Y[18], T Dg[21], T bY[6]) {
+__device__ __forceinline__ void pair_schur_terms(const T* pl, const T* R_pose, const T* vinv6,
+                                                 const T* gl3, T W[18], T Y[18], T Dg[21], T bY[6]) {
   T M3[6], X[3], M[9], R[9], G[9];
 #pragma unroll
   for (int k = 0; k < 6; ++k) M3[k] = pl[k];
@@ -445,7 +485,7 @@ __device__ __forceinline__ void pair_schur_terms(const T* pl, const double* R_po
   for (int k = 0; k < 3; ++k) X[k] = pl[6 + k];
   sym3_full(M3, M);
 #pragma unroll
-  for (int k = 0; k < 9; ++k) R[k] = (T)R_pose[k];
+  for (int k = 0; k < 9; ++k) R[k] = R_pose[k];
 #pragma unroll
   for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -462,7 +502,7 @@ __device__ __forceinline__ void pair_schur_terms(const T* pl, const double* R_po
   {
     T s6[6];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) s6[k] = (T)vinv6[k];
+    for (int k = 0; k < 6; ++k) s6[k] = vinv6[k];
     sym3_full(s6, Vi);
   }
 #pragma unroll
@@ -477,7 +517,7 @@ __device__ __forceinline__ void pair_schur_terms(const T* pl, const double* R_po
 #pragma unroll
     for (int c = 0; c <= r; ++c, ++k)
       Dg[k] = U[r * 6 + c] - (Y[r * 3] * W[c * 3] + Y[r * 3 + 1] * W[c * 3 + 1] + Y[r * 3 + 2] * W[c * 3 + 2]);
-  const T g0 = (T)gl3[0], g1 = (T)gl3[1], g2 = (T)gl3[2];
+  const T g0 = gl3[0], g1 = gl3[1], g2 = gl3[2];
 #pragma unroll
   for (int r = 0; r < 6; ++r) bY[r] = Y[r * 3] * g0 + Y[r * 3 + 1] * g1 + Y[r * 3 + 2] * g2;
 }
@@ -675,17 +715,17 @@ struct GroupChunk {
 size_t group_smem_bytes(int max_span, bool mixed) {
   const size_t t = mixed ? 4 : 8;
   const int ch = mixed ? 16 : 8;
-  return sizeof(double) * (SCHUR_TILE_LMS * 9 + 64) + t * (size_t)ch * max_span * kStage;
+  return sizeof(double) * 64 + t * ((size_t)SCHUR_TILE_LMS * 9 + (size_t)ch * max_span * kStage);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group(Dev d) {
   constexpr int CH = GroupChunk<T>::value;
   extern __shared__ __align__(16) double smem[];
-  double* s_vinv = smem;                              // SCHUR_TILE_LMS * 6
-  double* s_gl = s_vinv + SCHUR_TILE_LMS * 6;         // SCHUR_TILE_LMS * 3
-  double* s_red = s_gl + SCHUR_TILE_LMS * 3;          // 64
-  T* s_stg = reinterpret_cast<T*>(s_red + 64);        // CH * max_span * kStage
+  double* s_red = smem;                               // 64
+  T* s_vinv = reinterpret_cast<T*>(s_red + 64);       // SCHUR_TILE_LMS * 6
+  T* s_gl = s_vinv + SCHUR_TILE_LMS * 6;              // SCHUR_TILE_LMS * 3
+  T* s_stg = s_gl + SCHUR_TILE_LMS * 3;               // CH * max_span * kStage
   const SchurTile tile = d.schur_tiles[blockIdx.x];
   const int nl = tile.l1 - tile.l0;
   const int span = tile.span, rows = 6 * span, E = rows * (rows + 1) / 2, NE = E + rows;
@@ -695,15 +735,15 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group(Dev d) {
     const int j = tile.l0 + l;
     double inv[6];
     landmark_vinv<T>(d, j, lam, floor_, inv);
-    for (int k = 0; k < 6; ++k) s_vinv[l * 6 + k] = inv[k];
-    for (int k = 0; k < 3; ++k) s_gl[l * 3 + k] = d.lm_g[j * 3 + k];
+    for (int k = 0; k < 6; ++k) s_vinv[l * 6 + k] = (T)inv[k];
+    for (int k = 0; k < 3; ++k) s_gl[l * 3 + k] = (T)d.lm_g[j * 3 + k];
   }
   if (span == 0) return;                             // landmarks seen only by the fixed keyframe
   // Passes over the window's entries (kGroupOwn per thread each).  Owned entries are
   // offsets into one landmark's staging: bit 31 set = a dot product of a Y row and a W row
   // (offsets in bits 0-14 and 15-29); otherwise a staged scalar.
   const int stg_len = CH * span * kStage;
-  const double* pose = d.pose[d.ctrl->cur];
+  const T* pose = st_pose<T>(d, d.ctrl->cur);
   for (int e0 = 0; e0 < NE; e0 += kGroupOwn * SCHUR_THREADS) {
     int off[kGroupOwn];
     T acc[kGroupOwn], cmp[kGroupOwn];
@@ -792,6 +832,7 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group(Dev d) {
 // Block (a, b), a >= b, of the reduced camera system (and b_a when a == b): fixed-order sum
 // of the window partials of the Schur tiles covering it, added to what direct tiles wrote.
 __global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) {
+  __shared__ int s_off[256], s_klo[256], s_rows[256];
   const int blk = blockIdx.x;
   const int t0 = d.blk_tiles_off[blk], t1 = d.blk_tiles_off[blk + 1];
   if (t0 == t1) return;
@@ -801,37 +842,64 @@ __global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) {
   const int b = blk - a * (a + 1) / 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int n_ent = a == b ? 27 : 36;              // 21 lower entries + 6 of b, or 36
-  for (int e = warp; e < n_ent; e += nw) {
-    int r, c;
-    bool is_b = false;
-    if (a != b) {
-      r = e / 6;
-      c = e % 6;
-    } else if (e < 21) {
-      r = 0;
-      while ((r + 1) * (r + 2) / 2 <= e) ++r;
-      c = e - r * (r + 1) / 2;
-    } else {
-      r = e - 21;
-      c = 0;
-      is_b = true;
+  constexpr int kPer = 5;                          // entries per warp (8 warps x 5 >= 36)
+  double v[kPer] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int c0 = t0; c0 < t1; c0 += 256) {          // stage a chunk of covering tiles
+    const int nc = min(256, t1 - c0);
+    __syncthreads();
+    if (threadIdx.x < nc) {
+      const SchurTile st = d.schur_tiles[d.blk_tiles[c0 + threadIdx.x]];
+      s_off[threadIdx.x] = st.part_off;
+      s_klo[threadIdx.x] = st.k_lo;
+      s_rows[threadIdx.x] = 6 * st.span;
     }
-    double v = 0.0;
-    for (int t = t0 + lane; t < t1; t += 32) {
-      const SchurTile st = d.schur_tiles[d.blk_tiles[t]];
-      const int rows = 6 * st.span;
-      const int wr = 6 * (a - st.k_lo) + r;
-      if (is_b) {
-        v += d.schur_part[st.part_off + rows * (rows + 1) / 2 + wr];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+      const int e = warp + k * nw;
+      if (e >= n_ent) break;
+      int r, c;
+      bool is_b = false;
+      if (a != b) {
+        r = e / 6;
+        c = e % 6;
+      } else if (e < 21) {
+        r = 0;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        c = e - r * (r + 1) / 2;
       } else {
-        const int wc = 6 * (b - st.k_lo) + c;
-        v += d.schur_part[st.part_off + wr * (wr + 1) / 2 + wc];
+        r = e - 21;
+        c = 0;
+        is_b = true;
+      }
+      for (int t = lane; t < nc; t += 32) {
+        const int rows = s_rows[t];
+        const int wr = 6 * (a - s_klo[t]) + r;
+        const int idx = is_b ? rows * (rows + 1) / 2 + wr : wr * (wr + 1) / 2 + 6 * (b - s_klo[t]) + c;
+        v[k] += d.schur_part[s_off[t] + idx];
       }
     }
-    v = warp_sum(v);
+  }
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) {
+    const int e = warp + k * nw;
+    if (e >= n_ent) break;
+    const double sum = warp_sum(v[k]);
     if (lane == 0) {
-      if (is_b) d.bS[6 * a + r] += v;
-      else d.S[(size_t)(6 * a + r) * d.n_c + 6 * b + c] += v;
+      if (a == b && e >= 21) {
+        d.bS[6 * a + (e - 21)] += sum;
+      } else {
+        int r, c;
+        if (a != b) {
+          r = e / 6;
+          c = e % 6;
+        } else {
+          r = 0;
+          while ((r + 1) * (r + 2) / 2 <= e) ++r;
+          c = e - r * (r + 1) / 2;
+        }
+        d.S[(size_t)(6 * a + r) * d.n_c + 6 * b + c] += sum;
+      }
     }
   }
 }
@@ -943,7 +1011,13 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(Dev d) {
     } else {
       pose_plus(T0, d.dc + 6 * pb, T1);
     }
+    if (d.mixed) {
+      float* F1 = d.pose_f[cur ^ 1] + a * POSE_STRIDE;
+      for (int k = 0; k < POSE_STRIDE; ++k) F1[k] = (float)T1[k];
+    }
   }
+  if (d.mixed)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_c; i += gridDim.x * blockDim.x) d.dc_f[i] = (float)d.dc[i];
 }
 
 // ---------------------------------------------------------- k_chol_cluster
@@ -979,7 +1053,8 @@ struct CholSmem {
   __host__ __device__ size_t acc_off() const { return y_off() + NP; }
   __host__ __device__ size_t contrib_off() const { return acc_off() + NP; }
   __host__ __device__ size_t linv_off() const { return contrib_off() + (size_t)nlb * CS * kCB; }
-  __host__ __device__ size_t red_off() const { return linv_off() + (size_t)nlb * kCB * kCB; }
+  __host__ __device__ size_t rdiag_off() const { return linv_off() + (size_t)nlb * kCB * kCB; }
+  __host__ __device__ size_t red_off() const { return rdiag_off() + (size_t)nlb * kCB; }
   __host__ __device__ size_t flag_off() const { return red_off() + 128; }
   __host__ __device__ size_t doubles() const { return flag_off() + 8; }
 };
@@ -993,30 +1068,60 @@ __host__ __device__ inline CholSmem chol_layout(int n_c, int CS) {
   return L;
 }
 
-// Factor the 8x8 block D (row stride NP) in place with warp 0 and push it, with the
-// reciprocals of its diagonal and a non-PD flag, to every CTA of the cluster.
-__device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk, int* flag,
+// x^(-1/2) for a positive FP64 pivot: Newton-Raphson on f(y) = y^-2 - x,
+// y <- y (3 - x y^2) / 2, seeded by the FP32 reciprocal square root.  Each step roughly
+// squares the relative error (2^-22 -> ~1e-13 -> below double rounding), at three
+// dependent FP64 operations per step -- shorter than a full FP64 square root and divide,
+// which on GB300 take ~680 and ~430 cycles in a dependent chain.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return rsqrt(x);
+  double y = (double)rsqrtf((float)x);
+  const double h = 0.5 * x;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double e = fma(-h * y, y, 0.5);     // 1/2 - x y^2 / 2
+    y = fma(y, e, y);
+  }
+  return y;
+}
+
+// Factor the 8x8 block D (row stride NP) in place with warp 0 (lane i holds row i in
+// registers) and push L_kk, the reciprocals of its diagonal and a non-PD flag to every
+// CTA of the cluster.  rdiag (may be null) keeps the reciprocals for the owner.
+__device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk, int* flag, double* rdiag,
                                                  cooperative_groups::cluster_group& cluster, int CS) {
   const int tid = threadIdx.x;
+  __shared__ double s_rs[kCB];
   if (tid < 32) {
     const int i = tid;
+    double a[kCB];
+#pragma unroll
+    for (int j = 0; j < kCB; ++j) a[j] = (i < kCB && j <= i) ? D[i * NP + j] : 0.0;
     bool bad = false;
+#pragma unroll
     for (int c = 0; c < kCB; ++c) {
-      __syncwarp();
-      const double piv = D[c * NP + c];
+      const double piv = __shfl_sync(0xffffffffu, a[c], c);
       if (!(piv > 0.0) || !isfinite(piv)) bad = true;
-      const double rs = rsqrt(fmax(piv, 1e-300));
-      __syncwarp();
-      if (i == c) D[c * NP + c] = piv * rs;
-      if (i > c && i < kCB) D[i * NP + c] *= rs;
-      __syncwarp();
-      if (i > c && i < kCB)
-        for (int j = c + 1; j <= i; ++j) D[i * NP + j] = fma(-D[i * NP + c], D[j * NP + c], D[i * NP + j]);
+      const double rs = rsqrt_nr(fmax(piv, 1e-300));
+      double l = 0.0;
+      if (i == c) l = piv * rs;
+      else if (i > c && i < kCB) l = a[c] * rs;
+      a[c] = (i >= c) ? l : a[c];
+      if (i == c) s_rs[c] = rs;
+#pragma unroll
+      for (int j = c + 1; j < kCB; ++j) {
+        const double ljc = __shfl_sync(0xffffffffu, l, j);
+        if (i >= j && i < kCB) a[j] = fma(-l, ljc, a[j]);
+      }
     }
-    __syncwarp();
+    if (i < kCB)
+#pragma unroll
+      for (int j = 0; j < kCB; ++j)
+        if (j <= i) D[i * NP + j] = a[j];
     if (i == 0 && bad) *flag = 1;
   }
   __syncthreads();
+  if (rdiag && tid < kCB) rdiag[tid] = s_rs[tid];
   const int bad = *flag;
   constexpr int W = kCB * kCB + kCB + 1;           // block, reciprocals, flag
   for (int e = tid; e < CS * W; e += blockDim.x) {
@@ -1025,8 +1130,7 @@ __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk,
       const int i = t / kCB, m = t % kCB;
       cluster.map_shared_rank(lkk, dst)[t] = m <= i ? D[i * NP + m] : 0.0;
     } else if (t < kCB * kCB + kCB) {
-      const int c = t - kCB * kCB;
-      cluster.map_shared_rank(lkk, dst)[t] = 1.0 / D[c * NP + c];
+      cluster.map_shared_rank(lkk, dst)[t] = s_rs[t - kCB * kCB];
     } else if (bad) {
       *cluster.map_shared_rank(flag, dst) = 1;
     }
@@ -1051,6 +1155,7 @@ __global__ void __launch_bounds__(256) k_chol_cluster(Dev d) {
   double* acc = smem + Ls.acc_off();               // backward contributions of own rows
   double* contrib = smem + Ls.contrib_off();       // [lb][from CTA][8]
   double* linv = smem + Ls.linv_off();             // [lb][i][m] inverse of own diagonal blocks
+  double* rdiag = smem + Ls.rdiag_off();           // [lb][i] reciprocals of own diagonal entries
   double* red = smem + Ls.red_off();
   int* flag = reinterpret_cast<int*>(smem + Ls.flag_off());
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -1090,7 +1195,7 @@ __global__ void __launch_bounds__(256) k_chol_cluster(Dev d) {
   for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
   if (tid == 0) *flag = 0;
   cluster.sync();
-  if (q == 0) chol_factor_push(rows, NP, lkk, flag, cluster, CS);   // block 0 is CTA 0's first row block
+  if (q == 0) chol_factor_push(rows, NP, lkk, flag, rdiag, cluster, CS);   // block 0: CTA 0's first row block
 
   // ---- factorisation with the forward substitution fused
   for (int k = 0; k < NB; ++k) {
@@ -1145,7 +1250,7 @@ __global__ void __launch_bounds__(256) k_chol_cluster(Dev d) {
         rows[(size_t)(lb * kCB + i) * NP + kCB * (k + 1) + j] -= s;
       }
       __syncthreads();
-      chol_factor_push(rows + (size_t)(lb * kCB) * NP + kCB * (k + 1), NP, lkk, flag, cluster, CS);
+      chol_factor_push(rows + (size_t)(lb * kCB) * NP + kCB * (k + 1), NP, lkk, flag, rdiag + lb * kCB, cluster, CS);
     }
     // 2b. trailing update of own block rows: A_rc -= L_rk L_ck^T, c in (k, r]
     for (int lb = 0; lb < Ls.nlb; ++lb) {
@@ -1191,7 +1296,7 @@ __global__ void __launch_bounds__(256) k_chol_cluster(Dev d) {
       double s = (i == j) ? 1.0 : 0.0;
 #pragma unroll
       for (int m = 0; m < i; ++m) s = fma(-D[i * NP + m], z[m], s);
-      z[i] = i < j ? 0.0 : s / D[i * NP + i];
+      z[i] = i < j ? 0.0 : s * rdiag[lb * kCB + i];
     }
 #pragma unroll
     for (int i = 0; i < kCB; ++i) linv[(lb * kCB + i) * kCB + j] = z[i];
@@ -1269,7 +1374,13 @@ __global__ void __launch_bounds__(256) k_chol_cluster(Dev d) {
     } else {
       pose_plus(T0, d.dc + 6 * pb, T1);
     }
+    if (d.mixed) {
+      float* F1 = d.pose_f[cur ^ 1] + a * POSE_STRIDE;
+      for (int k = 0; k < POSE_STRIDE; ++k) F1[k] = (float)T1[k];
+    }
   }
+  if (d.mixed)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_c; i += gridDim.x * blockDim.x) d.dc_f[i] = (float)d.dc[i];
 }
 
 // --------------------------------------------------------------- k_backsub
@@ -1283,31 +1394,33 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
     return;
   }
   const int nl = tile.l1 - tile.l0;
-  double* s_rig = smem;                              // C * 16
-  double* s_acc = s_rig + d.C * RIG_STRIDE;          // LIN_TILE_PAIRS * 3 (per pair slots)
-  double* s_new = s_acc + LIN_TILE_PAIRS * 3;        // LIN_TILE_LMS * 3
-  double* s_red = s_new + LIN_TILE_LMS * 3;          // 128
-  for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = d.rig[i];
+  double* s_red = smem;                              // 128
+  T* s_rig = reinterpret_cast<T*>(s_red + 128);      // C * 16
+  T* s_acc = s_rig + d.C * RIG_STRIDE;               // LIN_TILE_PAIRS * 3 (per pair slots)
+  T* s_new = s_acc + LIN_TILE_PAIRS * 3;             // LIN_TILE_LMS * 3
+  const T* rig = st_rig<T>(d);
+  for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = rig[i];
   const double lam = ctrl->lam;
   const double floor_ = diag_floor(d, s_red);   // contains __syncthreads
   const int cur = ctrl->cur;
-  const double* pose = d.pose[cur];
+  const T* pose = st_pose<T>(d, cur);
+  const T* dcT = st_dc<T>(d);
   // phase 1: W_ja^T dc_a = R_a^T M3 (rho + phi x X) accumulated per landmark
   for (int q = tile.p0 + threadIdx.x; q < tile.p1; q += blockDim.x) {
     const int a = d.pair_kf[q];
     const int pb = d.kf_pb[a];
-    double* acc = s_acc + (q - tile.p0) * 3;
+    T* acc = s_acc + (q - tile.p0) * 3;
     if (pb < 0) {
-      acc[0] = acc[1] = acc[2] = 0.0;
+      acc[0] = acc[1] = acc[2] = 0;
       continue;
     }
     const T* pl = reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN;
-    const double* xi = d.dc + 6 * pb;
+    const T* xi = dcT + 6 * pb;
     T X[3] = {pl[6], pl[7], pl[8]};
     T u[3];
-    u[0] = (T)xi[0] + ((T)xi[4] * X[2] - (T)xi[5] * X[1]);
-    u[1] = (T)xi[1] + ((T)xi[5] * X[0] - (T)xi[3] * X[2]);
-    u[2] = (T)xi[2] + ((T)xi[3] * X[1] - (T)xi[4] * X[0]);
+    u[0] = xi[0] + (xi[4] * X[2] - xi[5] * X[1]);
+    u[1] = xi[1] + (xi[5] * X[0] - xi[3] * X[2]);
+    u[2] = xi[2] + (xi[3] * X[1] - xi[4] * X[0]);
     T M[9];
     {
       T s6[6];
@@ -1318,9 +1431,9 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
     T w3[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) w3[r] = M[r * 3] * u[0] + M[r * 3 + 1] * u[1] + M[r * 3 + 2] * u[2];
-    const double* R = pose + a * POSE_STRIDE;
+    const T* R = pose + a * POSE_STRIDE;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) acc[c] = (double)((T)R[c] * w3[0] + (T)R[3 + c] * w3[1] + (T)R[6 + c] * w3[2]);
+    for (int c = 0; c < 3; ++c) acc[c] = R[c] * w3[0] + R[3 + c] * w3[1] + R[6 + c] * w3[2];
   }
   __syncthreads();
   // phase 2: dp_j = -V_j^-1 (g_l + acc); candidate landmark; predicted-reduction part
@@ -1330,13 +1443,14 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
     const double* Vi = d.lm_Vinv + VINV_STRIDE * j;
     const double tau = Vi[6];
     const double* g = d.lm_g + 3 * j;
-    double t0 = g[0], t1 = g[1], t2 = g[2];
+    Acc<T> w0, w1, w2;
     for (int q = d.lm_pair[j]; q < d.lm_pair[j + 1]; ++q) {
-      const double* acc = s_acc + (q - tile.p0) * 3;
-      t0 += acc[0];
-      t1 += acc[1];
-      t2 += acc[2];
+      const T* acc = s_acc + (q - tile.p0) * 3;
+      w0.add(acc[0]);
+      w1.add(acc[1]);
+      w2.add(acc[2]);
     }
+    const double t0 = g[0] + w0.value(), t1 = g[1] + w1.value(), t2 = g[2] + w2.value();
     const double dp0 = -(Vi[0] * t0 + Vi[1] * t1 + Vi[2] * t2);
     const double dp1 = -(Vi[1] * t0 + Vi[3] * t1 + Vi[4] * t2);
     const double dp2 = -(Vi[2] * t0 + Vi[4] * t1 + Vi[5] * t2);
@@ -1352,20 +1466,24 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
     double* pn = d.lm[cur ^ 1] + 3 * j;
     const double n0 = p[0] + dp0, n1 = p[1] + dp1, n2 = p[2] + dp2;
     pn[0] = n0; pn[1] = n1; pn[2] = n2;
-    s_new[l * 3] = n0; s_new[l * 3 + 1] = n1; s_new[l * 3 + 2] = n2;
+    s_new[l * 3] = (T)n0; s_new[l * 3 + 1] = (T)n1; s_new[l * 3 + 2] = (T)n2;
+    if (d.mixed) {
+      float* pf = d.lm_f[cur ^ 1] + 3 * j;
+      pf[0] = (float)n0; pf[1] = (float)n1; pf[2] = (float)n2;
+    }
   }
   __syncthreads();
   // phase 3: candidate cost, same arithmetic and order as k_lin's cost
-  const double* pnew = d.pose[cur ^ 1];
+  const T* pnew = st_pose<T>(d, cur ^ 1);
   const T hub = (T)ctrl->huber, zmin = (T)ctrl->zmin;
-  PairStats st;
+  PairStats<T> st;
   for (int q = tile.p0 + threadIdx.x; q < tile.p1; q += blockDim.x) {
     const int a = d.pair_kf[q], j = d.pair_lm[q];
     T X[3];
     eval_pair<T, false>(pnew + a * POSE_STRIDE, s_new + 3 * (j - tile.l0), d.pair_obs[q], d.pair_obs[q + 1],
                         d.obs_cam, reinterpret_cast<const T*>(d.obs_uv), s_rig, hub, zmin, X, nullptr, nullptr, st);
   }
-  v[0] = st.cost;
+  v[0] = st.cost.value();
   block_sum4(v, s_red);
   if (threadIdx.x == 0) {
     d.bs_part[blockIdx.x * 4 + 0] = v[0];
@@ -1443,21 +1561,22 @@ template <typename T>
 __global__ void __launch_bounds__(LIN_THREADS) k_eval(Dev d, double huber, double zmin, double* part) {
   extern __shared__ __align__(16) double smem[];
   const LinTile tile = d.lin_tiles[blockIdx.x];
-  double* s_rig = smem;
-  double* s_red = s_rig + d.C * RIG_STRIDE;
-  for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = d.rig[i];
+  double* s_red = smem;
+  T* s_rig = reinterpret_cast<T*>(s_red + 128);
+  const T* rig = st_rig<T>(d);
+  for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = rig[i];
   __syncthreads();
   const int cur = d.ctrl->cur;
-  const double* pose = d.pose[cur];
-  const double* lmp = d.lm[cur];
-  PairStats st;
+  const T* pose = st_pose<T>(d, cur);
+  const T* lmp = st_lm<T>(d, cur);
+  PairStats<T> st;
   for (int q = tile.p0 + threadIdx.x; q < tile.p1; q += blockDim.x) {
     const int a = d.pair_kf[q], j = d.pair_lm[q];
     T X[3];
     eval_pair<T, false>(pose + a * POSE_STRIDE, lmp + 3 * j, d.pair_obs[q], d.pair_obs[q + 1], d.obs_cam,
                         reinterpret_cast<const T*>(d.obs_uv), s_rig, (T)huber, (T)zmin, X, nullptr, nullptr, st);
   }
-  double v[4] = {st.cost, st.sq, (double)st.nv, (double)st.ni};
+  double v[4] = {st.cost.value(), st.sq.value(), (double)st.nv, (double)st.ni};
   block_sum4(v, s_red);
   if (threadIdx.x == 0)
     for (int k = 0; k < 4; ++k) part[blockIdx.x * 4 + k] = v[k];
@@ -1486,6 +1605,8 @@ __global__ void k_state_io(Dev d, int mode, double* user, const int32_t* lm_orde
       }
       if (mode == 0) P[9 + r] = U[r * 4 + 3]; else U[r * 4 + 3] = P[9 + r];
     }
+    if (mode == 0 && d.mixed)
+      for (int k = 0; k < POSE_STRIDE; ++k) d.pose_f[cur][i * POSE_STRIDE + k] = (float)P[k];
   } else {
     if (i >= d.M) return;
     double* L = d.lm[cur] + 3 * i;
@@ -1493,16 +1614,19 @@ __global__ void k_state_io(Dev d, int mode, double* user, const int32_t* lm_orde
     for (int k = 0; k < 3; ++k) {
       if (mode == 1) L[k] = U[k]; else U[k] = L[k];
     }
+    if (mode == 1 && d.mixed)
+      for (int k = 0; k < 3; ++k) d.lm_f[cur][3 * i + k] = (float)L[k];
   }
 }
 
+size_t tsize(const Dev& d) { return d.mixed ? sizeof(float) : sizeof(double); }
 size_t lin_smem(const Dev& d) {
-  return sizeof(double) * (d.C * RIG_STRIDE + LIN_TILE_PAIRS * 21 + 128) + sizeof(int) * LIN_TILE_PAIRS;
+  return sizeof(double) * 128 + tsize(d) * (d.C * RIG_STRIDE + LIN_TILE_PAIRS * 21) + sizeof(int) * LIN_TILE_PAIRS;
 }
 size_t backsub_smem(const Dev& d) {
-  return sizeof(double) * (d.C * RIG_STRIDE + LIN_TILE_PAIRS * 3 + LIN_TILE_LMS * 3 + 128);
+  return sizeof(double) * 128 + tsize(d) * (d.C * RIG_STRIDE + LIN_TILE_PAIRS * 3 + LIN_TILE_LMS * 3);
 }
-size_t eval_smem(const Dev& d) { return sizeof(double) * (d.C * RIG_STRIDE + 128); }
+size_t eval_smem(const Dev& d) { return sizeof(double) * 128 + tsize(d) * d.C * RIG_STRIDE; }
 constexpr int kCholSmemMaxN = 160;
 size_t chol_smem(int n) { return sizeof(double) * ((size_t)n * n + n); }
 constexpr size_t kClusterSmemMax = 220 * 1024;
