@@ -175,6 +175,40 @@ cvba_status cvba_get_landmarks_dev(cvba_ctx* ctx, double* p_w /* device, n_lm*3 
 cvba_status cvba_profile_iteration(cvba_ctx* ctx, const cvba_opts* opts, int reps, float* ms, int* n_parts);
 const char* cvba_profile_names(void);
 
+/* Differentiable cost -------------------------------------------------------------------
+ *
+ * The robust objective of Sec. 2.2 (Eq. r^repr summed with the Huber kernel) as a
+ * differentiable function of the keyframe poses, landmarks and intrinsics, for training
+ * and analysis loops (the binding wraps it as a torch.autograd.Function).  Context-free:
+ * every array is a caller-owned DEVICE array in the caller's order, all floating arrays of
+ * one type: dtype 0 = FP64, 1 = FP32 (the arithmetic runs in that type; the keyframe
+ * exponentials in FP64).  Arrays: intr[C*4], T_cb[C*12], xi[K*6] (left tangent
+ * perturbation, translation first), T_bw[K*12], p_w[M*3], kf/cam/lm[N] (int32), uv[N*2].
+ * Keyframe i is evaluated at Exp(xi_i) T_bw_i.  Observations with an index out of range
+ * or camera depth <= z_min contribute nothing.  Limits: K <= 256, C <= 64.
+ *
+ * `work` is a caller-allocated device workspace of at least
+ * cvba_cost_workspace_bytes(N, K, C) bytes (per-block partial sums).  Both calls are
+ * asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream). */
+size_t cvba_cost_workspace_bytes(int n_obs, int n_kf, int n_cams);
+
+/* cost[0] = 1/2 sum_n rho(|r_n|^2) (device scalar of the dtype). */
+cvba_status cvba_cost_forward(int dtype, int n_obs, int n_kf, int n_cams, int n_lm, const void* intr,
+                              const void* T_cb, const void* xi, const void* T_bw, const void* p_w,
+                              const int32_t* kf, const int32_t* cam, const int32_t* lm, const void* uv,
+                              double huber_delta, double z_min, void* cost, void* work, size_t work_bytes,
+                              void* stream);
+
+/* Adjoint: with g = grad_cost[0] (device scalar), writes g dF/dxi (K*6, through the left
+ * Jacobian of SE(3)), g dF/dT_bw (K*12), g dF/dp_w (M*3) and g dF/dintr (C*4); any output
+ * may be NULL.  Jacobians are recomputed, not stored by the forward call. */
+cvba_status cvba_cost_backward(int dtype, int n_obs, int n_kf, int n_cams, int n_lm, const void* intr,
+                               const void* T_cb, const void* xi, const void* T_bw, const void* p_w,
+                               const int32_t* kf, const int32_t* cam, const int32_t* lm, const void* uv,
+                               double huber_delta, double z_min, const void* grad_cost, void* g_xi,
+                               void* g_T_bw, void* g_p_w, void* g_intr, void* work, size_t work_bytes,
+                               void* stream);
+
 /* Allocation-free evaluation ----------------------------------------------------------
  *
  * The paper has no counterpart to this call; it exists for callers that cannot allocate

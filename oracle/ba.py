@@ -179,7 +179,10 @@ def jacobians(win: Window, poses: np.ndarray, lms: np.ndarray):
     Rc = win.T_cb[win.obs_cam, :, :3]
     dXb = np.zeros((N, 3, 6))
     dXb[:, :, :3] = np.eye(3)
-    dXb[:, :, 3:] = -np.stack([hat(x) for x in Xb]) if N else np.zeros((0, 3, 3))
+    # -[X_b]x, row by row
+    dXb[:, 0, 4], dXb[:, 0, 5] = Xb[:, 2], -Xb[:, 1]
+    dXb[:, 1, 3], dXb[:, 1, 5] = -Xb[:, 2], Xb[:, 0]
+    dXb[:, 2, 3], dXb[:, 2, 4] = Xb[:, 1], -Xb[:, 0]
     JpR = np.einsum("nij,njk->nik", Jpi, Rc)
     Jpose = np.einsum("nij,njk->nik", JpR, dXb)
     Jlm = np.einsum("nij,njk->nik", JpR, poses[win.obs_kf, :, :3])
@@ -376,3 +379,78 @@ def device_layout(obs_kf, obs_cam, obs_lm, M):
     counts = np.bincount(rank[obs_lm], minlength=M)
     lm_off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
     return lm_order, obs_order, lm_off
+
+
+# --------------------------------------------------------------- differentiable cost
+
+def se3_left_jacobian(xi: np.ndarray) -> np.ndarray:
+    """Left Jacobian of SE(3) at xi = (rho, phi): Exp(xi + d) ~ Exp(J_l d) Exp(xi).
+    J_l = [[J, Q], [0, J]] with J the SO(3) left Jacobian (= V of se3_exp) and Q(rho, phi)
+    the closed form of Barfoot, State Estimation for Robotics (2017), Eq. (7.86)."""
+    rho, phi = xi[:3], xi[3:]
+    t = float(np.linalg.norm(phi))
+    if t < TAYLOR_THETA:
+        B, C = 0.5 - t * t / 24.0, 1.0 / 6.0 - t * t / 120.0
+        D, E = 1.0 / 24.0 - t * t / 720.0, 1.0 / 120.0 - t * t / 2520.0
+    else:
+        B = (1.0 - math.cos(t)) / (t * t)
+        C = (t - math.sin(t)) / t ** 3
+        D = (t * t + 2.0 * math.cos(t) - 2.0) / (2.0 * t ** 4)
+        E = (2.0 * t - 3.0 * math.sin(t) + t * math.cos(t)) / (2.0 * t ** 5)
+    P, R = hat(phi), hat(rho)
+    J = np.eye(3) + B * P + C * (P @ P)
+    Q = (0.5 * R + C * (P @ R + R @ P + P @ R @ P) + D * (P @ P @ R + R @ P @ P - 3.0 * P @ R @ P)
+         + E * (P @ R @ P @ P + P @ P @ R @ P))
+    out = np.zeros((6, 6))
+    out[:3, :3] = J
+    out[:3, 3:] = Q
+    out[3:, 3:] = J
+    return out
+
+
+def cost_grad(win: Window, poses, lms, intr=None, xi=None):
+    """F = 1/2 sum rho(|r|^2) with keyframe i at Exp(xi_i) T_i, and its gradient w.r.t.
+    xi (K, 6), the pose matrices T (K, 3, 4), the landmarks (M, 3) and the intrinsics (C, 4).
+
+    dF/dxi_i = J_l(xi_i)^T sum_n J_pose,n^T w_n r_n   (J_pose: left perturbation at T')
+    dF/dT_i  = sum_n R_e^T g_X (x) [p_j; 1],  g_X = (dr/dX')^T w r
+    dF/dp_j  = sum_n J_lm,n^T w_n r_n
+    dF/dintr = sum_n w (r_u X/Z, r_v Y/Z, r_u, r_v)."""
+    K, M = win.K, win.M
+    intr = win.intr if intr is None else np.asarray(intr, float)
+    xi = np.zeros((K, 6)) if xi is None else np.asarray(xi, float)
+    Tp = np.stack([pose_plus(poses[i], xi[i]) for i in range(K)])
+    w2 = Window(intr=intr, T_cb=win.T_cb, obs_kf=win.obs_kf, obs_cam=win.obs_cam, obs_lm=win.obs_lm,
+                obs_uv=win.obs_uv, K=K, M=M, fixed_kf=-1, huber_delta=win.huber_delta, z_min=win.z_min)
+    r, valid = residuals(w2, Tp, lms)
+    s = np.einsum("ni,ni->n", r, r)
+    rho, w = huber(s, win.huber_delta)
+    w = np.where(valid, w, 0.0)
+    F = 0.5 * float(rho[valid].sum())
+    Jp, Jl = jacobians(w2, Tp, lms)
+    wr = w[:, None] * r
+    g_left = np.zeros((K, 6))
+    np.add.at(g_left, win.obs_kf, np.einsum("nai,na->ni", Jp, wr))
+    g_xi = np.stack([se3_left_jacobian(xi[i]).T @ g_left[i] for i in range(K)])
+    g_lm = np.zeros((M, 3))
+    np.add.at(g_lm, win.obs_lm, np.einsum("nai,na->ni", Jl, wr))
+    # dr/dX' = J_pi R_cb; g_X = (dr/dX')^T w r; dX'/dR_ab = R_e[:, a] p_b, dX'/dt = R_e
+    Xb, Xc = transform(w2, Tp, lms)
+    Zs = np.where(valid, Xc[:, 2], 1.0)
+    f = intr[win.obs_cam]
+    Jpi = np.zeros((r.shape[0], 2, 3))
+    Jpi[:, 0, 0] = f[:, 0] / Zs
+    Jpi[:, 0, 2] = -f[:, 0] * Xc[:, 0] / Zs ** 2
+    Jpi[:, 1, 1] = f[:, 1] / Zs
+    Jpi[:, 1, 2] = -f[:, 1] * Xc[:, 1] / Zs ** 2
+    dXc = np.einsum("nai,na->ni", Jpi, wr)
+    gX = np.einsum("nji,nj->ni", win.T_cb[win.obs_cam, :, :3], dXc)
+    Re = np.stack([Tp[i, :, :3] @ poses[i, :, :3].T for i in range(K)])
+    h = np.einsum("nji,nj->ni", Re[win.obs_kf], gX)
+    p1 = np.concatenate([lms[win.obs_lm], np.ones((r.shape[0], 1))], axis=1)
+    g_T = np.zeros((K, 3, 4))
+    np.add.at(g_T, win.obs_kf, h[:, :, None] * p1[:, None, :])
+    g_intr = np.zeros_like(intr)
+    terms = np.stack([wr[:, 0] * Xc[:, 0] / Zs, wr[:, 1] * Xc[:, 1] / Zs, wr[:, 0], wr[:, 1]], 1)
+    np.add.at(g_intr, win.obs_cam, terms)
+    return F, dict(xi=g_xi, T=g_T, lm=g_lm, intr=g_intr)

@@ -79,6 +79,9 @@ def _load() -> C.CDLL:
         "cvba_profile_iteration": (i, [vp, C.POINTER(cvba_opts), i, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
         "cvba_profile_names": (C.c_char_p, []),
         "cvba_evaluate_noalloc": (i, [i, i, i, i] + [vp] * 8 + [d, d, vp, vp]),
+        "cvba_cost_workspace_bytes": (C.c_size_t, [i, i, i]),
+        "cvba_cost_forward": (i, [i, i, i, i, i] + [vp] * 9 + [d, d, vp, vp, C.c_size_t, vp]),
+        "cvba_cost_backward": (i, [i, i, i, i, i] + [vp] * 9 + [d, d, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
