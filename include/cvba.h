@@ -175,6 +175,37 @@ cvba_status cvba_get_landmarks_dev(cvba_ctx* ctx, double* p_w /* device, n_lm*3 
 cvba_status cvba_profile_iteration(cvba_ctx* ctx, const cvba_opts* opts, int reps, float* ms, int* n_parts);
 const char* cvba_profile_names(void);
 
+/* Batched windows (independent BA problems) ---------------------------------------------
+ *
+ * Solves many independent windows together (the batched form of the hot path): every
+ * phase of an LM iteration is one kernel launch over all windows' work tiles, the
+ * reduced-system Cholesky runs one thread-block cluster per window, and the whole
+ * multi-iteration solve is one CUDA graph.  Windows keep their own state, damping and
+ * iteration records (each is an ordinary context, created with the same device and
+ * precision; the batch uses the first context's stream).  A batch holds no copy of the
+ * windows' data: a window whose observations are replaced is re-planned on the next
+ * solve. */
+typedef struct cvba_batch cvba_batch;
+cvba_status cvba_batch_create(cvba_batch** out, int n_win, cvba_ctx* const* ctxs);
+void cvba_batch_destroy(cvba_batch* batch);
+const char* cvba_batch_last_error(const cvba_batch* batch);
+
+/* opts->iters LM iterations in every window; traces (may be NULL) receives n_win * iters
+ * records, window-major.  The async form only enqueues (records stay on the device). */
+cvba_status cvba_batch_solve(cvba_batch* batch, const cvba_opts* opts, cvba_iter* traces);
+cvba_status cvba_batch_solve_async(cvba_batch* batch, const cvba_opts* opts);
+cvba_status cvba_batch_launch_count(cvba_batch* batch, const cvba_opts* opts, int* n_launches);
+
+/* Tuning.  cvba_set_tuning re-plans one window's tiles (pairs per linearisation tile,
+ * landmarks per Schur tile; 0 = size-based default) keeping its state.
+ * cvba_batch_set_chol_cluster picks the CTAs per window of the batched Cholesky (2, 4, 8
+ * or 16).  cvba_batch_autotune times short batched solves over a grid of these sizes,
+ * keeps the fastest, restores every window's state and reports the choice. */
+cvba_status cvba_set_tuning(cvba_ctx* ctx, int lin_tile_pairs, int schur_tile_landmarks);
+cvba_status cvba_batch_set_chol_cluster(cvba_batch* batch, int cluster_size);
+cvba_status cvba_batch_autotune(cvba_batch* batch, const cvba_opts* opts, int* lin_tile_pairs,
+                                int* schur_tile_landmarks, int* cluster_size);
+
 /* Differentiable cost -------------------------------------------------------------------
  *
  * The robust objective of Sec. 2.2 (Eq. r^repr summed with the Huber kernel) as a

@@ -25,6 +25,9 @@ struct cvba_ctx {
   bool have_rig = false, have_poses = false, have_lms = false, have_layout = false;
 
   std::vector<int32_t> lm_order, lm_rank, obs_order, lm_off;
+  std::vector<int32_t> h_kf, h_cam, h_lm;       // caller's observations (for re-planning)
+  std::vector<double> h_uv;
+  int tune_lin_pairs = 0, tune_schur_lms = 0;   // 0: size-based defaults
   std::vector<LinTile> lin_tiles;
   std::vector<SchurTile> schur_tiles, direct_tiles;
 
@@ -243,7 +246,8 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   const int n_sm = 152;
   c->lin_tiles.clear();
   {
-    const int target = std::max(32, std::min(LIN_TILE_PAIRS, (P + 2 * n_sm - 1) / (2 * n_sm)));
+    const int target = c->tune_lin_pairs > 0 ? std::min(LIN_TILE_PAIRS, c->tune_lin_pairs)
+                                             : std::max(32, std::min(LIN_TILE_PAIRS, (P + 2 * n_sm - 1) / (2 * n_sm)));
     int l0 = 0;
     while (l0 < M) {
       int l1 = l0;
@@ -288,7 +292,8 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   c->direct_tiles.clear();
   int max_span = 1;
   {
-    const int target = std::max(8, std::min(SCHUR_TILE_LMS, (M + n_sm - 1) / n_sm));
+    const int target = c->tune_schur_lms > 0 ? std::min(SCHUR_TILE_LMS, c->tune_schur_lms)
+                                             : std::max(8, std::min(SCHUR_TILE_LMS, (M + n_sm - 1) / n_sm));
     std::vector<int> lo(M, INT32_MAX), hi(M, -1);
     for (int j = 0; j < M; ++j)
       for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
@@ -698,7 +703,35 @@ cvba_status cvba_set_observations(cvba_ctx* c, int n_obs, const int32_t* kf, con
   if (!all_finite(uv, (size_t)n_obs * 2)) return fail(c, CVBA_ERR_NONFINITE, "set_observations: non-finite uv");
   DeviceGuard g(c->device);
   c->N = n_obs;
+  c->h_kf.assign(kf, kf + n_obs);
+  c->h_cam.assign(cam, cam + n_obs);
+  c->h_lm.assign(lm, lm + n_obs);
+  c->h_uv.assign(uv, uv + 2 * (size_t)n_obs);
   return build_layout(c, kf, cam, lm, uv);
+}
+
+cvba_status cvba_set_tuning(cvba_ctx* c, int lin_tile_pairs, int schur_tile_landmarks) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (lin_tile_pairs < 0 || schur_tile_landmarks < 0)
+    return fail(c, CVBA_ERR_INVALID_ARG, "set_tuning: sizes must be >= 0 (0 = default)");
+  c->tune_lin_pairs = lin_tile_pairs;
+  c->tune_schur_lms = schur_tile_landmarks;
+  if (!c->have_layout) return CVBA_OK;
+  DeviceGuard g(c->device);
+  // re-plan with the same observations; the state on the device is kept
+  const int cur = read_cur(c);
+  std::vector<double> poses((size_t)c->K * 12), lms((size_t)c->M * 3);
+  cvba_status st = cvba_get_poses(c, poses.data());
+  if (st == CVBA_OK) st = cvba_get_landmarks(c, lms.data());
+  if (st != CVBA_OK) return st;
+  double lam = 1e-4, nu = 2.0;
+  cvba_get_damping(c, &lam, &nu);
+  c->poses = poses;
+  c->lms = lms;
+  (void)cur;
+  st = build_layout(c, c->h_kf.data(), c->h_cam.data(), c->h_lm.data(), c->h_uv.data());
+  if (st == CVBA_OK) st = cvba_set_damping(c, lam, nu);
+  return st;
 }
 
 namespace {
@@ -953,7 +986,318 @@ cvba_status cvba_get_sizes(cvba_ctx* c, int* n_kf, int* n_cams, int* n_lm, int* 
 
 cvba_status cvba_solve_launch_count(cvba_ctx* c, int iters, int* n) {
   if (!c || !n || iters < 0) return CVBA_ERR_INVALID_ARG;
-  *n = iters > 0 ? kernels_per_solve_init() + iters * kernels_per_iteration() : 0;
+  *n = iters > 0 ? kernels_per_solve_init() + iters * (c->have_layout ? solve_kernels_per_iteration(c->d)
+                                                                    : kernels_per_iteration()) : 0;
+  return CVBA_OK;
+}
+
+}  // extern "C"
+
+// ============================================================== batched windows
+
+struct cvba_batch {
+  std::vector<cvba_ctx*> ctxs;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int mixed = 0;
+  int chol_cs = 4;
+  void* dbuf = nullptr;              // Dev array and work lists
+  size_t dbuf_bytes = 0;
+  std::vector<Dev> host_devs, fallback;
+  BatchLaunch L;
+  cudaGraphExec_t graph = nullptr;
+  cvba_ctx::Key key;
+  int key_cs = 0;
+  std::vector<Dev> snap;             // views the plan was built from
+  std::string err;
+};
+
+namespace {
+
+cvba_status bfail(cvba_batch* b, cvba_status s, const std::string& m) {
+  if (b) b->err = m;
+  return s;
+}
+
+void batch_drop_graph(cvba_batch* b) {
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  b->graph = nullptr;
+  b->key = cvba_ctx::Key{};
+}
+
+cvba_status ensure_trace(cvba_ctx* c, int iters) {
+  if (iters <= c->trace_cap) return CVBA_OK;
+  CK(cudaStreamSynchronize(c->stream), "sync");
+  if (c->d_trace) cudaFree(c->d_trace);
+  c->d_trace = nullptr;
+  c->trace_cap = 0;
+  CK(cudaMalloc(&c->d_trace, sizeof(cvba_iter) * (size_t)iters), "alloc trace");
+  c->trace_cap = iters;
+  c->d.trace = c->d_trace;
+  return CVBA_OK;
+}
+
+// (Re)build the device plan and capture the graph of `o->iters` batched iterations.
+cvba_status batch_prepare(cvba_batch* b, const cvba_opts* o) {
+  const int n = (int)b->ctxs.size();
+  for (cvba_ctx* c : b->ctxs) {
+    if (!c->have_layout) return bfail(b, CVBA_ERR_STATE, "batch: every window needs set_observations");
+    cvba_status st = ensure_trace(c, o->iters);
+    if (st != CVBA_OK) return bfail(b, st, c->err);
+    c->d.trace = c->d_trace;
+  }
+  bool same = (int)b->snap.size() == n && b->graph && b->key_cs == b->chol_cs;
+  for (int w = 0; same && w < n; ++w) same = std::memcmp(&b->snap[w], &b->ctxs[w]->d, sizeof(Dev)) == 0;
+  cvba_ctx::Key key;
+  key.iters = o->iters;
+  key.reset = o->reset_lambda ? 1 : 0;
+  key.lam0 = o->lambda0;
+  key.huber = o->huber_delta;
+  key.zmin = o->z_min;
+  if (same && key == b->key) return CVBA_OK;
+  batch_drop_graph(b);
+  // views, plan sizes, work lists
+  b->snap.clear();
+  b->host_devs.clear();
+  for (cvba_ctx* c : b->ctxs) {
+    b->snap.push_back(c->d);
+    b->host_devs.push_back(c->d);
+  }
+  BatchLaunch& L = b->L;
+  L = BatchLaunch{};
+  L.n_win = n;
+  L.mixed = b->mixed;
+  L.chol_cs = b->chol_cs;
+  batch_plan_sizes(b->host_devs.data(), n, L);
+  b->fallback.clear();
+  std::vector<int2> lin, kf, sch, blk, dir, win;
+  for (int w = 0; w < n; ++w) {
+    const Dev& d = b->host_devs[w];
+    if (d.chol_fallback) b->fallback.push_back(d);
+    for (int t = 0; t < d.n_lin_tiles; ++t) lin.push_back(make_int2(w, t));
+    for (int a = 0; a < d.K; ++a) kf.push_back(make_int2(w, a));
+    for (int t = 0; t < d.n_schur_tiles; ++t) sch.push_back(make_int2(w, t));
+    for (int t = 0; t < d.n_blk; ++t) blk.push_back(make_int2(w, t));
+    for (int t = 0; t < d.n_direct_tiles; ++t) dir.push_back(make_int2(w, t));
+    win.push_back(make_int2(w, 0));
+  }
+  const size_t n_items = lin.size() + kf.size() + sch.size() + blk.size() + dir.size() + win.size();
+  const size_t bytes = sizeof(Dev) * n + sizeof(int2) * n_items + 256;
+  cvba_ctx* c = b->ctxs[0];
+  if (bytes > b->dbuf_bytes) {
+    if (b->dbuf) cudaFree(b->dbuf);
+    b->dbuf = nullptr;
+    b->dbuf_bytes = 0;
+    CK(cudaMalloc(&b->dbuf, bytes), "alloc batch plan");
+    b->dbuf_bytes = bytes;
+  }
+  std::vector<unsigned char> h(bytes, 0);
+  std::memcpy(h.data(), b->host_devs.data(), sizeof(Dev) * n);
+  size_t off = sizeof(Dev) * n;
+  off = (off + 15) / 16 * 16;
+  auto put = [&](const std::vector<int2>& v, const int2** dst, int* cnt) {
+    *dst = reinterpret_cast<const int2*>(static_cast<unsigned char*>(b->dbuf) + off);
+    *cnt = (int)v.size();
+    if (!v.empty()) std::memcpy(h.data() + off, v.data(), v.size() * sizeof(int2));
+    off += v.size() * sizeof(int2);
+  };
+  L.wins = static_cast<const Dev*>(b->dbuf);
+  int n_win_items = 0;
+  put(lin, &L.lin_items, &L.n_lin);
+  put(kf, &L.kf_items, &L.n_kf);
+  put(sch, &L.schur_items, &L.n_schur);
+  put(blk, &L.blk_items, &L.n_blkit);
+  put(dir, &L.direct_items, &L.n_direct);
+  put(win, &L.win_items, &n_win_items);
+  L.fallback_host = b->fallback.data();
+  CK(cudaMemcpy(b->dbuf, h.data(), bytes, cudaMemcpyHostToDevice), "upload batch plan");
+  // capture
+  cudaGraph_t gr;
+  CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  cudaError_t e = enqueue_batch_init(L, o->lambda0, o->huber_delta, o->z_min, o->iters, key.reset, b->stream);
+  for (int it = 0; it < o->iters && e == cudaSuccess; ++it) e = enqueue_batch_iteration(L, b->stream);
+  cudaError_t e2 = cudaStreamEndCapture(b->stream, &gr);
+  if (e != cudaSuccess) return cuda_fail(c, e, "enqueue batch");
+  if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+  e = cudaGraphInstantiate(&b->graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) return cuda_fail(c, e, "instantiate batch graph");
+  b->key = key;
+  b->key_cs = b->chol_cs;
+  return CVBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cvba_status cvba_batch_create(cvba_batch** out, int n_win, cvba_ctx* const* ctxs) {
+  if (!out || n_win < 1 || !ctxs) return CVBA_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int w = 0; w < n_win; ++w) {
+    if (!ctxs[w]) return CVBA_ERR_INVALID_ARG;
+    if (ctxs[w]->device != ctxs[0]->device || ctxs[w]->prec != ctxs[0]->prec) return CVBA_ERR_INVALID_ARG;
+  }
+  cvba_batch* b = new cvba_batch();
+  b->ctxs.assign(ctxs, ctxs + n_win);
+  b->device = ctxs[0]->device;
+  b->stream = ctxs[0]->stream;
+  b->mixed = ctxs[0]->prec == CVBA_MIXED ? 1 : 0;
+  *out = b;
+  return CVBA_OK;
+}
+
+void cvba_batch_destroy(cvba_batch* b) {
+  if (!b) return;
+  {
+    DeviceGuard g(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    if (b->dbuf) cudaFree(b->dbuf);
+  }
+  delete b;
+}
+
+const char* cvba_batch_last_error(const cvba_batch* b) { return b ? b->err.c_str() : ""; }
+
+cvba_status cvba_batch_set_chol_cluster(cvba_batch* b, int cs) {
+  if (!b || !(cs == 2 || cs == 4 || cs == 8 || cs == 16)) return CVBA_ERR_INVALID_ARG;
+  b->chol_cs = cs;
+  return CVBA_OK;
+}
+
+cvba_status cvba_batch_solve_async(cvba_batch* b, const cvba_opts* o) {
+  if (!b || !o) return CVBA_ERR_INVALID_ARG;
+  if (o->iters < 0 || !(o->huber_delta > 0.0) || !std::isfinite(o->z_min) ||
+      (o->reset_lambda && !(o->lambda0 > 0.0)))
+    return bfail(b, CVBA_ERR_INVALID_ARG, "batch solve: bad options");
+  if (o->iters == 0) return CVBA_OK;
+  DeviceGuard g(b->device);
+  cvba_status st = batch_prepare(b, o);
+  if (st != CVBA_OK) {
+    if (b->err.empty()) b->err = b->ctxs[0]->err;
+    return st;
+  }
+  if (cudaGraphLaunch(b->graph, b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, CVBA_ERR_CUDA, "batch graph launch failed");
+  }
+  return CVBA_OK;
+}
+
+cvba_status cvba_batch_solve(cvba_batch* b, const cvba_opts* o, cvba_iter* traces) {
+  cvba_status st = cvba_batch_solve_async(b, o);
+  if (st != CVBA_OK || o->iters == 0) return st;
+  DeviceGuard g(b->device);
+  if (traces) {
+    for (size_t w = 0; w < b->ctxs.size(); ++w)
+      if (cudaMemcpyAsync(traces + w * (size_t)o->iters, b->ctxs[w]->d_trace, sizeof(cvba_iter) * (size_t)o->iters,
+                          cudaMemcpyDeviceToHost, b->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, CVBA_ERR_CUDA, "batch trace copy failed");
+      }
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return bfail(b, CVBA_ERR_CUDA, "batch solve failed");
+  }
+  return CVBA_OK;
+}
+
+cvba_status cvba_batch_launch_count(cvba_batch* b, const cvba_opts* o, int* n) {
+  if (!b || !o || !n) return CVBA_ERR_INVALID_ARG;
+  DeviceGuard g(b->device);
+  cvba_status st = batch_prepare(b, o);
+  if (st != CVBA_OK) return st;
+  *n = o->iters > 0 ? 1 + o->iters * batch_kernels_per_iteration(b->L) : 0;
+  return CVBA_OK;
+}
+
+// Autotuner: times a 2-iteration batched solve for each candidate (lin tile pairs, Schur
+// tile landmarks), then each Cholesky cluster size, keeps the fastest and restores every
+// window's state.  Writes the chosen values (any pointer may be NULL).
+cvba_status cvba_batch_autotune(cvba_batch* b, const cvba_opts* o, int* best_lin, int* best_schur, int* best_cs) {
+  if (!b || !o) return CVBA_ERR_INVALID_ARG;
+  DeviceGuard g(b->device);
+  const int n = (int)b->ctxs.size();
+  std::vector<std::vector<double>> P(n), Lm(n);
+  std::vector<double> lam(n), nu(n);
+  for (int w = 0; w < n; ++w) {
+    cvba_ctx* c = b->ctxs[w];
+    P[w].resize((size_t)c->K * 12);
+    Lm[w].resize((size_t)c->M * 3);
+    if (cvba_get_poses(c, P[w].data()) != CVBA_OK || cvba_get_landmarks(c, Lm[w].data()) != CVBA_OK ||
+        cvba_get_damping(c, &lam[w], &nu[w]) != CVBA_OK)
+      return bfail(b, CVBA_ERR_STATE, "autotune: windows need a layout");
+  }
+  auto restore = [&]() -> cvba_status {
+    for (int w = 0; w < n; ++w) {
+      cvba_ctx* c = b->ctxs[w];
+      cvba_status st = cvba_set_poses(c, c->K, P[w].data(), c->fixed_kf);
+      if (st == CVBA_OK) st = cvba_set_landmarks(c, c->M, Lm[w].data());
+      if (st == CVBA_OK) st = cvba_set_damping(c, lam[w], nu[w]);
+      if (st != CVBA_OK) return st;
+    }
+    return CVBA_OK;
+  };
+  cvba_opts t = *o;
+  t.iters = 2;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto timed = [&](float* ms) -> cvba_status {
+    cvba_status st = cvba_batch_solve(b, &t, nullptr);             // prepares + warms the graph
+    if (st == CVBA_OK) st = restore();
+    if (st != CVBA_OK) return st;
+    cudaEventRecord(e0, b->stream);
+    st = cvba_batch_solve_async(b, &t);
+    cudaEventRecord(e1, b->stream);
+    if (st == CVBA_OK && cudaEventSynchronize(e1) != cudaSuccess) st = CVBA_ERR_CUDA;
+    if (st == CVBA_OK) cudaEventElapsedTime(ms, e0, e1);
+    cvba_status st2 = restore();
+    return st != CVBA_OK ? st : st2;
+  };
+  const int lin_c[] = {64, 128, 256};
+  const int sch_c[] = {16, 32, 64, 128};
+  float best = 1e30f;
+  int bl = 0, bs = 0, bc = b->chol_cs;
+  cvba_status st = CVBA_OK;
+  for (int li : lin_c) {
+    for (int sc : sch_c) {
+      for (int w = 0; w < n && st == CVBA_OK; ++w) st = cvba_set_tuning(b->ctxs[w], li, sc);
+      float ms = 0.f;
+      if (st == CVBA_OK) st = timed(&ms);
+      if (st != CVBA_OK) break;
+      if (ms < best) {
+        best = ms;
+        bl = li;
+        bs = sc;
+      }
+    }
+    if (st != CVBA_OK) break;
+  }
+  if (st == CVBA_OK)
+    for (int w = 0; w < n && st == CVBA_OK; ++w) st = cvba_set_tuning(b->ctxs[w], bl, bs);
+  if (st == CVBA_OK) {
+    best = 1e30f;
+    for (int cs : {2, 4, 8}) {
+      b->chol_cs = cs;
+      float ms = 0.f;
+      st = timed(&ms);
+      if (st != CVBA_OK) break;
+      if (ms < best) {
+        best = ms;
+        bc = cs;
+      }
+    }
+    b->chol_cs = bc;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != CVBA_OK) return bfail(b, st, "autotune failed: " + b->ctxs[0]->err);
+  if (best_lin) *best_lin = bl;
+  if (best_schur) *best_schur = bs;
+  if (best_cs) *best_cs = bc;
   return CVBA_OK;
 }
 

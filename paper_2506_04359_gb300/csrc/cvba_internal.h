@@ -80,6 +80,7 @@ struct Dev {
   const SchurTile* schur_tiles;    // landmarks sharing one window of <= SPAN_MAX free keyframes
   const SchurTile* direct_tiles;   // landmarks spanning more (atomics into S)
   int n_direct_tiles, max_span;
+  int chol_fallback;               // batched solves: 1 = factor with the single-CTA kernel
   // linearisation
   void* pair_lin;             // P * PAIR_LIN (double or float)
   double* lm_H;               // M * 6  (Hll: 00 01 02 11 12 22)
@@ -106,6 +107,31 @@ struct Dev {
   cvba_iter* trace;           // iteration records (ctrl->iters entries)
   Ctrl* ctrl;
 };
+
+// Batched solve of independent windows: each phase is one launch over a work list of
+// (window, item) pairs; the Cholesky runs one cluster of chol_cs CTAs per window.
+struct BatchLaunch {
+  const Dev* wins = nullptr;       // device array of per-window views
+  int n_win = 0, mixed = 0;
+  const int2* lin_items = nullptr;   int n_lin = 0;      // (window, lin tile)
+  const int2* kf_items = nullptr;    int n_kf = 0;       // (window, keyframe)
+  const int2* schur_items = nullptr; int n_schur = 0;    // (window, group tile)
+  const int2* blk_items = nullptr;   int n_blkit = 0;    // (window, RCS block)
+  const int2* direct_items = nullptr; int n_direct = 0;  // (window, direct tile)
+  const int2* win_items = nullptr;                       // (window, 0)
+  size_t lin_smem = 0, backsub_smem = 0, group_smem = 0, direct_smem = 0, chol_smem = 0;
+  int chol_cs = 4;
+  int n_fallback = 0;
+  const Dev* fallback_host = nullptr;                   // host copies of windows that do not fit
+};
+// Fill the shared-memory maxima and fallback flags of `b` from host copies of the views
+// (chol_fallback is written into host_devs before they are uploaded).
+void batch_plan_sizes(Dev* host_devs, int n_win, BatchLaunch& b);
+cudaError_t enqueue_batch_init(const BatchLaunch& b, double lam0, double huber, double zmin, int iters, int reset,
+                               cudaStream_t s);
+cudaError_t enqueue_batch_iteration(const BatchLaunch& b, cudaStream_t s);
+int batch_kernels_per_iteration(const BatchLaunch& b);
+int solve_kernels_per_iteration(const Dev& d);
 
 // Launchers (cvba_kernels.cu).  All enqueue on `s` and return the launch status.
 cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double zmin, int iters,

@@ -21,6 +21,7 @@
 #include <cooperative_groups.h>
 #include <math_constants.h>
 
+#include <algorithm>
 #include <cfloat>
 #include <cmath>
 
@@ -287,9 +288,18 @@ __device__ void pose_plus(const double* T0, const double* xi, double* T1) {
 
 // =================================================================== kernels
 
-__global__ void k_solve_init(Dev d, double lam0, double huber, double zmin, int iters, int reset) {
+// Per-window device view for the batched kernels: the CTA copies its window's Dev into
+// shared memory (CTA-uniform) and runs the same body as the single-window kernel.
+__device__ __forceinline__ void load_dev(Dev& dst, const Dev* src) {
+  static_assert(sizeof(Dev) % 4 == 0, "Dev size");
+  for (int i = threadIdx.x; i < (int)(sizeof(Dev) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(&dst)[i] = reinterpret_cast<const int*>(src)[i];
+  __syncthreads();
+}
+
+__device__ __forceinline__ void solve_init_body(const Dev& d, double lam0, double huber, double zmin, int iters, int reset) {
   Ctrl* c = d.ctrl;
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
+  if (threadIdx.x == 0) {
     c->need_lin = 1;
     c->it = 0;
     c->nonpd = 0;
@@ -306,17 +316,27 @@ __global__ void k_solve_init(Dev d, double lam0, double huber, double zmin, int 
   }
 }
 
+__global__ void k_solve_init(Dev d, double lam0, double huber, double zmin, int iters, int reset) {
+  solve_init_body(d, lam0, huber, zmin, iters, reset);
+}
+__global__ void k_solve_init_b(const Dev* __restrict__ wins, double lam0, double huber, double zmin, int iters,
+                               int reset) {
+  __shared__ Dev sd;
+  load_dev(sd, wins + blockIdx.x);
+  solve_init_body(sd, lam0, huber, zmin, iters, reset);
+}
+
 // ----------------------------------------------------------------- k_lin
 // Thread per (landmark, keyframe) pair; each pair writes its contributions to its own
 // shared-memory slot, then owner threads sum them in pair order (per landmark: its
 // contiguous pairs; per keyframe and component: the tile's pairs of that keyframe), so
 // there are no atomics and the sums are reproducible.
 template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
+__device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
   Ctrl* ctrl = d.ctrl;
   if (!ctrl->need_lin) return;
   extern __shared__ __align__(16) double smem[];
-  const LinTile tile = d.lin_tiles[blockIdx.x];
+  const LinTile tile = d.lin_tiles[item];
   const int nl = tile.l1 - tile.l0, np = tile.p1 - tile.p0;
   double* s_red = smem;                                // 128
   T* s_rig = reinterpret_cast<T*>(s_red + 128);        // C * 16
@@ -379,7 +399,7 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
   block_sum4(v, s_red);                              // contains barriers: slots complete
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) d.lin_part[blockIdx.x * 4 + k] = v[k];
+    for (int k = 0; k < 4; ++k) d.lin_part[item * 4 + k] = v[k];
   }
   // per landmark: sum of its pairs (contiguous, in order)
   double mx = 0.0;
@@ -408,11 +428,21 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) {
     atomicMax(&ctrl->maxdiag_lm, (unsigned long long)__double_as_longlong(mx));
 }
 
+template <typename T>
+__global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) { k_lin_body<T>(d, blockIdx.x); }
+template <typename T>
+__global__ void __launch_bounds__(LIN_THREADS) k_lin_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+  __shared__ Dev sd;
+  const int2 it = items[blockIdx.x];
+  load_dev(sd, wins + it.x);
+  k_lin_body<T>(sd, it.y);
+}
+
 // g_p and diag(Hpp) of keyframe blockIdx.x: fixed-order sum of the covering tiles'
 // partials (lane l takes tiles l, l+32, ...; then a butterfly over the warp).
-__global__ void __launch_bounds__(384) k_kf_reduce(Dev d) {
+__device__ __forceinline__ void k_kf_reduce_body(const Dev& d, int item) {
   __shared__ int s_off[384];
-  const int a = blockIdx.x;
+  const int a = item;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;   // warp = component (12)
   const int t0 = d.kf_tiles_off[a], t1 = d.kf_tiles_off[a + 1];
   double v = 0.0;
@@ -430,6 +460,14 @@ __global__ void __launch_bounds__(384) k_kf_reduce(Dev d) {
   if (lane == 0) {
     if (warp < 6) d.kf_gp[a * 6 + warp] = v; else d.kf_dp[a * 6 + warp - 6] = v;
   }
+}
+
+__global__ void __launch_bounds__(384) k_kf_reduce(Dev d) { k_kf_reduce_body(d, blockIdx.x); }
+__global__ void __launch_bounds__(384) k_kf_reduce_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+  __shared__ Dev sd;
+  const int2 it = items[blockIdx.x];
+  load_dev(sd, wins + it.x);
+  k_kf_reduce_body(sd, it.y);
 }
 
 // Closed-form inverse of V_j = Hll_j + lam D_l,j (adjugate / determinant), stored with tau
@@ -537,7 +575,7 @@ struct SchurSmem {
 // added straight into the global reduced camera system with atomics (rare in sliding
 // windows; not bit-reproducible).
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct(Dev d) {
+__device__ __forceinline__ void k_schur_direct_body(const Dev& d, int item) {
   using SM = SchurSmem<T>;
   extern __shared__ __align__(16) double smem[];
   double* s_win = smem;                               // WIN_ENTRIES
@@ -550,7 +588,7 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct(Dev d) {
   int* s_blk = reinterpret_cast<int*>(s_Y + SCHUR_TILE_PAIRS * 18);  // SCHUR_TILE_LMS + 1
 
   Ctrl* ctrl = d.ctrl;
-  const SchurTile tile = d.direct_tiles[blockIdx.x];
+  const SchurTile tile = d.direct_tiles[item];
   const int nl = tile.l1 - tile.l0;
   const int n_c = d.n_c;
   const double lam = ctrl->lam;
@@ -695,6 +733,16 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct(Dev d) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct(Dev d) { k_schur_direct_body<T>(d, blockIdx.x); }
+template <typename T>
+__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+  __shared__ Dev sd;
+  const int2 it = items[blockIdx.x];
+  load_dev(sd, wins + it.x);
+  k_schur_direct_body<T>(sd, it.y);
+}
+
 // ------------------------------------------------------------ k_schur_group
 // Reduced camera system from a tile of landmarks that share the same window of free
 // keyframes [k_lo, k_lo + span): their contributions to that window of S,
@@ -719,14 +767,14 @@ size_t group_smem_bytes(int max_span, bool mixed) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group(Dev d) {
+__device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
   constexpr int CH = GroupChunk<T>::value;
   extern __shared__ __align__(16) double smem[];
   double* s_red = smem;                               // 64
   T* s_vinv = reinterpret_cast<T*>(s_red + 64);       // SCHUR_TILE_LMS * 6
   T* s_gl = s_vinv + SCHUR_TILE_LMS * 6;              // SCHUR_TILE_LMS * 3
   T* s_stg = s_gl + SCHUR_TILE_LMS * 3;               // CH * max_span * kStage
-  const SchurTile tile = d.schur_tiles[blockIdx.x];
+  const SchurTile tile = d.schur_tiles[item];
   const int nl = tile.l1 - tile.l0;
   const int span = tile.span, rows = 6 * span, E = rows * (rows + 1) / 2, NE = E + rows;
   const double lam = d.ctrl->lam;
@@ -829,13 +877,23 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group(Dev d) {
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group(Dev d) { k_schur_group_body<T>(d, blockIdx.x); }
+template <typename T>
+__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+  __shared__ Dev sd;
+  const int2 it = items[blockIdx.x];
+  load_dev(sd, wins + it.x);
+  k_schur_group_body<T>(sd, it.y);
+}
+
 // Block (a, b), a >= b, of the reduced camera system (and b_a when a == b): fixed-order sum
-// of the window partials of the Schur tiles covering it, added to what direct tiles wrote.
-__global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) {
+// of the window partials of the Schur tiles covering it, assigned (zero when no tile covers
+// it); the direct tiles' atomics are added after this kernel.
+__device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
   __shared__ int s_off[256], s_klo[256], s_rows[256];
-  const int blk = blockIdx.x;
+  const int blk = item;
   const int t0 = d.blk_tiles_off[blk], t1 = d.blk_tiles_off[blk + 1];
-  if (t0 == t1) return;
   int a = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
   while (a * (a + 1) / 2 > blk) --a;
   while ((a + 1) * (a + 2) / 2 <= blk) ++a;
@@ -887,7 +945,7 @@ __global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) {
     const double sum = warp_sum(v[k]);
     if (lane == 0) {
       if (a == b && e >= 21) {
-        d.bS[6 * a + (e - 21)] += sum;
+        d.bS[6 * a + (e - 21)] = sum;
       } else {
         int r, c;
         if (a != b) {
@@ -898,17 +956,25 @@ __global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) {
           while ((r + 1) * (r + 2) / 2 <= e) ++r;
           c = e - r * (r + 1) / 2;
         }
-        d.S[(size_t)(6 * a + r) * d.n_c + 6 * b + c] += sum;
+        d.S[(size_t)(6 * a + r) * d.n_c + 6 * b + c] = sum;
       }
     }
   }
+}
+
+__global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) { k_rcs_reduce_body(d, blockIdx.x); }
+__global__ void __launch_bounds__(256) k_rcs_reduce_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+  __shared__ Dev sd;
+  const int2 it = items[blockIdx.x];
+  load_dev(sd, wins + it.x);
+  k_rcs_reduce_body(sd, it.y);
 }
 
 // ----------------------------------------------------------------- k_chol
 // Dense FP64 Cholesky of the damped reduced camera system, then the two triangular
 // solves.  One CTA; the matrix lives in shared memory when it fits (SMEM) else in global.
 template <bool SMEM>
-__global__ void __launch_bounds__(CHOL_THREADS) k_chol(Dev d) {
+__device__ __forceinline__ void k_chol_body(const Dev& d, int item) {
   extern __shared__ __align__(16) double smem[];
   __shared__ double s_red[128];
   __shared__ double s_piv;
@@ -1017,7 +1083,17 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol(Dev d) {
     }
   }
   if (d.mixed)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_c; i += gridDim.x * blockDim.x) d.dc_f[i] = (float)d.dc[i];
+    for (int i = threadIdx.x; i < d.n_c; i += blockDim.x) d.dc_f[i] = (float)d.dc[i];
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol(Dev d) { k_chol_body<SMEM>(d, blockIdx.x); }
+template <bool SMEM>
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+  __shared__ Dev sd;
+  const int2 it = items[blockIdx.x];
+  load_dev(sd, wins + it.x);
+  k_chol_body<SMEM>(sd, it.y);
 }
 
 // ---------------------------------------------------------- k_chol_cluster
@@ -1137,7 +1213,7 @@ __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk,
   }
 }
 
-__global__ void __launch_bounds__(256) k_chol_cluster(Dev d) {
+__device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
   extern __shared__ __align__(16) double smem[];
@@ -1380,17 +1456,26 @@ __global__ void __launch_bounds__(256) k_chol_cluster(Dev d) {
     }
   }
   if (d.mixed)
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n_c; i += gridDim.x * blockDim.x) d.dc_f[i] = (float)d.dc[i];
+    for (int i = q * nt + tid; i < d.n_c; i += CS * nt) d.dc_f[i] = (float)d.dc[i];
+}
+
+__global__ void __launch_bounds__(256) k_chol_cluster(Dev d) { chol_cluster_body(d); }
+// Batched: one cluster per window (cluster index = window).
+__global__ void __launch_bounds__(256) k_chol_cluster_b(const Dev* __restrict__ wins) {
+  __shared__ Dev sd;
+  load_dev(sd, wins + blockIdx.x / cooperative_groups::this_cluster().dim_blocks().x);
+  if (sd.chol_fallback) return;                    // uniform over the cluster
+  chol_cluster_body(sd);
 }
 
 // --------------------------------------------------------------- k_backsub
 template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
+__device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
   extern __shared__ __align__(16) double smem[];
   Ctrl* ctrl = d.ctrl;
-  const LinTile tile = d.lin_tiles[blockIdx.x];
+  const LinTile tile = d.lin_tiles[item];
   if (ctrl->nonpd) {
-    if (threadIdx.x < 4) d.bs_part[blockIdx.x * 4 + threadIdx.x] = 0.0;
+    if (threadIdx.x < 4) d.bs_part[item * 4 + threadIdx.x] = 0.0;
     return;
   }
   const int nl = tile.l1 - tile.l0;
@@ -1486,11 +1571,21 @@ __global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) {
   v[0] = st.cost.value();
   block_sum4(v, s_red);
   if (threadIdx.x == 0) {
-    d.bs_part[blockIdx.x * 4 + 0] = v[0];
-    d.bs_part[blockIdx.x * 4 + 1] = v[1];
-    d.bs_part[blockIdx.x * 4 + 2] = v[2];
-    d.bs_part[blockIdx.x * 4 + 3] = 0.0;
+    d.bs_part[item * 4 + 0] = v[0];
+    d.bs_part[item * 4 + 1] = v[1];
+    d.bs_part[item * 4 + 2] = v[2];
+    d.bs_part[item * 4 + 3] = 0.0;
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) { k_backsub_body<T>(d, blockIdx.x); }
+template <typename T>
+__global__ void __launch_bounds__(LIN_THREADS) k_backsub_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+  __shared__ Dev sd;
+  const int2 it = items[blockIdx.x];
+  load_dev(sd, wins + it.x);
+  k_backsub_body<T>(sd, it.y);
 }
 
 // --------------------------------------------------------------- k_decide
@@ -1507,7 +1602,7 @@ __device__ void reduce_parts(const double* part, int n_tiles, double out[4], dou
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d) {
+__device__ __forceinline__ void k_decide_body(const Dev& d, int item) {
   __shared__ double s_red[128];
   Ctrl* ctrl = d.ctrl;
   double lin[4], bs[4];
@@ -1554,6 +1649,14 @@ __global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d) {
     }
     ctrl->nonpd = 0;
   }
+}
+
+__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d) { k_decide_body(d, blockIdx.x); }
+__global__ void __launch_bounds__(DECIDE_THREADS) k_decide_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+  __shared__ Dev sd;
+  const int2 it = items[blockIdx.x];
+  load_dev(sd, wins + it.x);
+  k_decide_body(sd, it.y);
 }
 
 // ------------------------------------------------------------- evaluation
@@ -1646,32 +1749,46 @@ int chol_cluster_size(int n_c) {
 
 // ================================================================ launchers
 
+// Opt a kernel into `want` bytes of dynamic shared memory, clamped to what is left of the
+// 227 KB per-CTA limit after its static shared memory (the batched kernels stage their
+// window's Dev there).  Launches request far less than the clamp except the Cholesky ones,
+// whose plans are checked against the same limit.
+template <typename F>
+cudaError_t set_dyn_smem(F* f, size_t want) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, f);
+  if (e != cudaSuccess) return e;
+  const size_t limit = 227 * 1024 - fa.sharedSizeBytes;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::min(want, limit));
+}
+
 cudaError_t set_kernel_attributes() {
   cudaError_t e;
-  const int big = 227 * 1024;
-  e = cudaFuncSetAttribute(k_lin<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_lin<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_schur_direct<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SchurSmem<double>::bytes());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_schur_direct<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)SchurSmem<float>::bytes());
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_schur_group<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)group_smem_bytes(SPAN_MAX, false));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_schur_group<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)group_smem_bytes(SPAN_MAX, true));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_chol<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)chol_smem(kCholSmemMaxN));
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterSmemMax);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e != cudaSuccess) return e;
+  const size_t big = 227 * 1024;
+  if ((e = set_dyn_smem(k_lin<double>, big)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_lin<float>, big)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_schur_direct<double>, SchurSmem<double>::bytes())) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_schur_direct<float>, SchurSmem<float>::bytes())) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_schur_group<double>, group_smem_bytes(SPAN_MAX, false))) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_schur_group<float>, group_smem_bytes(SPAN_MAX, true))) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_chol<true>, chol_smem(kCholSmemMaxN))) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_chol_cluster, kClusterSmemMax)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+    return e;
+  if ((e = set_dyn_smem(k_chol_cluster_b, kClusterSmemMax)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(k_chol_cluster_b, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
+    return e;
+  if ((e = set_dyn_smem(k_lin_b<float>, big)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_lin_b<double>, big)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_backsub_b<float>, big)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_backsub_b<double>, big)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_backsub<float>, big)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_backsub<double>, big)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_schur_group_b<float>, group_smem_bytes(SPAN_MAX, true))) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_schur_group_b<double>, group_smem_bytes(SPAN_MAX, false))) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_schur_direct_b<float>, SchurSmem<float>::bytes())) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_schur_direct_b<double>, SchurSmem<double>::bytes())) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_chol_b<true>, chol_smem(kCholSmemMaxN))) != cudaSuccess) return e;
   {
     // largest cluster of 256-thread CTAs with the maximum shared memory that fits
     cudaLaunchConfig_t cfg = {};
@@ -1717,8 +1834,6 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   k_kf_reduce<<<d.K, 384, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(1)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(d.S, 0, sizeof(double) * (size_t)d.n_c * d.n_c, s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(d.bS, 0, sizeof(double) * (size_t)d.n_c, s)) != cudaSuccess) return e;
   if ((e = mark(2)) != cudaSuccess) return e;
   if (d.n_schur_tiles > 0) {
     const size_t sm = group_smem_bytes(d.max_span, d.mixed != 0);
@@ -1728,6 +1843,8 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
       k_schur_group<double><<<d.n_schur_tiles, SCHUR_THREADS, sm, s>>>(d);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  k_rcs_reduce<<<d.n_blk, 256, 0, s>>>(d);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (d.n_direct_tiles > 0) {
     if (d.mixed)
       k_schur_direct<float><<<d.n_direct_tiles, SCHUR_THREADS, SchurSmem<float>::bytes(), s>>>(d);
@@ -1735,8 +1852,7 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
       k_schur_direct<double><<<d.n_direct_tiles, SCHUR_THREADS, SchurSmem<double>::bytes(), s>>>(d);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_rcs_reduce<<<d.n_blk, 256, 0, s>>>(d);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
   if ((e = mark(3)) != cudaSuccess) return e;
   if (chol_cluster_size(d.n_c) > 0) {
     const int CS = chol_cluster_size(d.n_c);
@@ -1769,6 +1885,95 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   k_decide<<<1, DECIDE_THREADS, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return mark(6);
+}
+
+int solve_kernels_per_iteration(const Dev& d) {
+  return 6 + (d.n_schur_tiles > 0 ? 1 : 0) + (d.n_direct_tiles > 0 ? 1 : 0);
+}
+
+void batch_plan_sizes(Dev* hd, int n_win, BatchLaunch& b) {
+  b.lin_smem = b.backsub_smem = b.group_smem = b.chol_smem = 0;
+  b.direct_smem = hd[0].mixed ? SchurSmem<float>::bytes() : SchurSmem<double>::bytes();
+  b.n_fallback = 0;
+  int max_span = 1;
+  for (int w = 0; w < n_win; ++w) {
+    const Dev& d = hd[w];
+    b.lin_smem = std::max(b.lin_smem, lin_smem(d));
+    b.backsub_smem = std::max(b.backsub_smem, backsub_smem(d));
+    max_span = std::max(max_span, d.max_span);
+    const size_t cs = chol_layout(d.n_c, b.chol_cs).doubles() * sizeof(double);
+    hd[w].chol_fallback = cs > kClusterSmemMax ? 1 : 0;
+    if (hd[w].chol_fallback) b.n_fallback++;
+    else b.chol_smem = std::max(b.chol_smem, cs);
+  }
+  b.group_smem = group_smem_bytes(max_span, hd[0].mixed != 0);
+}
+
+int batch_kernels_per_iteration(const BatchLaunch& b) {
+  return 6 + (b.n_schur > 0 ? 1 : 0) + (b.n_direct > 0 ? 1 : 0) + b.n_fallback;
+}
+
+cudaError_t enqueue_batch_init(const BatchLaunch& b, double lam0, double huber, double zmin, int iters, int reset,
+                               cudaStream_t s) {
+  k_solve_init_b<<<b.n_win, 256, 0, s>>>(b.wins, lam0, huber, zmin, iters, reset);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_batch_iteration(const BatchLaunch& b, cudaStream_t s) {
+  cudaError_t e;
+  if (b.mixed)
+    k_lin_b<float><<<b.n_lin, LIN_THREADS, b.lin_smem, s>>>(b.wins, b.lin_items);
+  else
+    k_lin_b<double><<<b.n_lin, LIN_THREADS, b.lin_smem, s>>>(b.wins, b.lin_items);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_kf_reduce_b<<<b.n_kf, 384, 0, s>>>(b.wins, b.kf_items);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (b.n_schur > 0) {
+    if (b.mixed)
+      k_schur_group_b<float><<<b.n_schur, SCHUR_THREADS, b.group_smem, s>>>(b.wins, b.schur_items);
+    else
+      k_schur_group_b<double><<<b.n_schur, SCHUR_THREADS, b.group_smem, s>>>(b.wins, b.schur_items);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_rcs_reduce_b<<<b.n_blkit, 256, 0, s>>>(b.wins, b.blk_items);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (b.n_direct > 0) {
+    if (b.mixed)
+      k_schur_direct_b<float><<<b.n_direct, SCHUR_THREADS, b.direct_smem, s>>>(b.wins, b.direct_items);
+    else
+      k_schur_direct_b<double><<<b.n_direct, SCHUR_THREADS, b.direct_smem, s>>>(b.wins, b.direct_items);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (b.n_fallback < b.n_win) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.n_win * b.chol_cs);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = b.chol_smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = b.chol_cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, k_chol_cluster_b, b.wins)) != cudaSuccess) return e;
+  }
+  for (int f = 0; f < b.n_fallback; ++f) {
+    const Dev& d = b.fallback_host[f];
+    if (d.n_c <= kCholSmemMaxN)
+      k_chol<true><<<1, CHOL_THREADS, chol_smem(d.n_c), s>>>(d);
+    else
+      k_chol<false><<<1, CHOL_THREADS, 0, s>>>(d);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (b.mixed)
+    k_backsub_b<float><<<b.n_lin, LIN_THREADS, b.backsub_smem, s>>>(b.wins, b.lin_items);
+  else
+    k_backsub_b<double><<<b.n_lin, LIN_THREADS, b.backsub_smem, s>>>(b.wins, b.lin_items);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_decide_b<<<b.n_win, DECIDE_THREADS, 0, s>>>(b.wins, b.win_items);
+  return cudaGetLastError();
 }
 
 cudaError_t enqueue_state_io(const Dev& d, int mode, double* user, const int32_t* lm_order, cudaStream_t s) {

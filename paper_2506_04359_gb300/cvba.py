@@ -79,6 +79,15 @@ def _load() -> C.CDLL:
         "cvba_profile_iteration": (i, [vp, C.POINTER(cvba_opts), i, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
         "cvba_profile_names": (C.c_char_p, []),
         "cvba_evaluate_noalloc": (i, [i, i, i, i] + [vp] * 8 + [d, d, vp, vp]),
+        "cvba_set_tuning": (i, [vp, i, i]),
+        "cvba_batch_create": (i, [C.POINTER(vp), i, C.POINTER(vp)]),
+        "cvba_batch_destroy": (None, [vp]),
+        "cvba_batch_last_error": (C.c_char_p, [vp]),
+        "cvba_batch_solve": (i, [vp, C.POINTER(cvba_opts), vp]),
+        "cvba_batch_solve_async": (i, [vp, C.POINTER(cvba_opts)]),
+        "cvba_batch_launch_count": (i, [vp, C.POINTER(cvba_opts), C.POINTER(C.c_int)]),
+        "cvba_batch_set_chol_cluster": (i, [vp, i]),
+        "cvba_batch_autotune": (i, [vp, C.POINTER(cvba_opts)] + [C.POINTER(C.c_int)] * 3),
         "cvba_cost_workspace_bytes": (C.c_size_t, [i, i, i]),
         "cvba_cost_forward": (i, [i, i, i, i, i] + [vp] * 9 + [d, d, vp, vp, C.c_size_t, vp]),
         "cvba_cost_backward": (i, [i, i, i, i, i] + [vp] * 9 + [d, d, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]),
@@ -244,6 +253,9 @@ class Context:
         names = lib.cvba_profile_names().decode().split(",")
         return dict(zip(names, [float(x) for x in ms]))
 
+    def cvba_set_tuning(self, lin_tile_pairs: int = 0, schur_tile_landmarks: int = 0):
+        self._check(lib.cvba_set_tuning(self._h, int(lin_tile_pairs), int(schur_tile_landmarks)))
+
     # --- convenience
     def load(self, problem, poses=None, landmarks=None):
         """Load a synth.Problem (rig, initial poses and landmarks, observations)."""
@@ -265,3 +277,58 @@ def cvba_evaluate_noalloc(n_obs: int, n_kf: int, n_cams: int, n_lm: int, intr: i
                                    float(z_min), C.c_void_p(out), C.c_void_p(stream) if stream else None)
     if st != 0:
         raise CvbaError(st, "cvba_evaluate_noalloc failed")
+
+
+class Batch:
+    """Independent windows solved together (cvba_batch_*): one launch per LM phase for all
+    windows, one cluster per window for the Cholesky, the whole solve one CUDA graph."""
+
+    def __init__(self, contexts):
+        self.contexts = list(contexts)
+        arr = (C.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = C.c_void_p()
+        st = lib.cvba_batch_create(C.byref(h), len(self.contexts), arr)
+        if st != 0:
+            raise CvbaError(st, "cvba_batch_create failed (same device and precision required)")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.cvba_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, st):
+        if st != 0:
+            raise CvbaError(st, lib.cvba_batch_last_error(self._h).decode())
+
+    @staticmethod
+    def _opts(iters, huber_delta, lambda0, z_min, reset_lambda):
+        return cvba_opts(int(iters), float(huber_delta), float(lambda0), float(z_min), 1 if reset_lambda else 0)
+
+    def cvba_batch_solve(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, reset_lambda=True):
+        o = self._opts(iters, huber_delta, lambda0, z_min, reset_lambda)
+        tr = np.zeros((len(self.contexts), max(int(iters), 1)), ITER_DTYPE)
+        self._check(lib.cvba_batch_solve(self._h, C.byref(o), C.c_void_p(tr.ctypes.data)))
+        return tr[:, :int(iters)]
+
+    def cvba_batch_solve_async(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, reset_lambda=True):
+        o = self._opts(iters, huber_delta, lambda0, z_min, reset_lambda)
+        self._check(lib.cvba_batch_solve_async(self._h, C.byref(o)))
+
+    def cvba_batch_launch_count(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3):
+        o = self._opts(iters, huber_delta, lambda0, z_min, True)
+        n = C.c_int()
+        self._check(lib.cvba_batch_launch_count(self._h, C.byref(o), C.byref(n)))
+        return n.value
+
+    def cvba_batch_set_chol_cluster(self, cs: int):
+        self._check(lib.cvba_batch_set_chol_cluster(self._h, int(cs)))
+
+    def cvba_batch_autotune(self, iters=2, huber_delta=1.0, lambda0=1e-4, z_min=1e-3):
+        o = self._opts(iters, huber_delta, lambda0, z_min, True)
+        v = [C.c_int() for _ in range(3)]
+        self._check(lib.cvba_batch_autotune(self._h, C.byref(o), *[C.byref(x) for x in v]))
+        return dict(lin_tile_pairs=v[0].value, schur_tile_landmarks=v[1].value, chol_cluster=v[2].value)
