@@ -70,6 +70,12 @@ typedef struct {
   double z_min;         /* minimum camera depth of a valid observation (metres) */
   int reset_lambda;     /* 1: start from lambda0, nu = 2; 0: continue the context's
                            lambda and nu (after cvba_set_damping or a previous solve) */
+  int refine;           /* FP64 iterative-refinement corrections allowed per reduced-camera-
+                           system solve (0..8; each is taken only while the residual fails
+                           the backward-error test |r| <= |A| |dc| 2^-53 sqrt(n_c), infinity
+                           norms); < 0 selects the precision's default: 1 for CVBA_MIXED,
+                           0 for CVBA_FP64.  The single-CTA fallback factorisations used for
+                           systems too large for a cluster's shared memory do not refine. */
 } cvba_opts;
 
 typedef struct {
@@ -84,6 +90,10 @@ typedef struct {
   int nonpd;         /* 1 if a 3x3 landmark block or the RCS was not PD (step rejected) */
   int n_valid;       /* observations with camera depth > z_min */
   int n_inlier;      /* valid observations with ||r|| <= huber_delta */
+  double berr;       /* backward error |r|/(|A| |dc| + |b|) of the reduced-camera-system
+                        solve before refinement (NaN when refine == 0 or not PD) */
+  int refined;       /* refinement corrections applied */
+  int reserved;
 } cvba_iter;
 
 /* Library / context lifetime ---------------------------------------------------- */

@@ -45,10 +45,11 @@ struct cvba_ctx {
   cudaGraphExec_t graph = nullptr;
   Dev graph_dev{};               // device view the graph was captured with
   struct Key {
-    int iters = -1, reset = -1;
+    int iters = -1, reset = -1, refine = -1;
     double lam0 = 0, huber = 0, zmin = 0;
     bool operator==(const Key& o) const {
-      return iters == o.iters && reset == o.reset && lam0 == o.lam0 && huber == o.huber && zmin == o.zmin;
+      return iters == o.iters && reset == o.reset && refine == o.refine && lam0 == o.lam0 && huber == o.huber &&
+             zmin == o.zmin;
     }
   } graph_key;
 };
@@ -735,11 +736,25 @@ cvba_status cvba_set_tuning(cvba_ctx* c, int lin_tile_pairs, int schur_tile_land
 }
 
 namespace {
+bool opts_ok(const cvba_opts* o) {
+  return o->iters >= 0 && o->huber_delta > 0.0 && std::isfinite(o->huber_delta) && std::isfinite(o->z_min) &&
+         (!o->reset_lambda || (o->lambda0 > 0.0 && std::isfinite(o->lambda0))) && o->refine <= 8;
+}
+
+cvba_ctx::Key make_key(const cvba_opts* o, bool mixed) {
+  cvba_ctx::Key key;
+  key.iters = o->iters;
+  key.reset = o->reset_lambda ? 1 : 0;
+  key.refine = o->refine < 0 ? (mixed ? 1 : 0) : o->refine;
+  key.lam0 = o->lambda0;
+  key.huber = o->huber_delta;
+  key.zmin = o->z_min;
+  return key;
+}
+
 cvba_status enqueue_solve(cvba_ctx* c, const cvba_opts* o) {
   if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "solve: set_observations first");
-  if (o->iters < 0 || !(o->huber_delta > 0.0) || !std::isfinite(o->huber_delta) || !std::isfinite(o->z_min) ||
-      (o->reset_lambda && !(o->lambda0 > 0.0 && std::isfinite(o->lambda0))))
-    return fail(c, CVBA_ERR_INVALID_ARG, "solve: bad options");
+  if (!opts_ok(o)) return fail(c, CVBA_ERR_INVALID_ARG, "solve: bad options");
   if (o->iters == 0) return CVBA_OK;
   if (o->iters > c->trace_cap) {
     CK(cudaStreamSynchronize(c->stream), "sync");
@@ -750,17 +765,13 @@ cvba_status enqueue_solve(cvba_ctx* c, const cvba_opts* o) {
     c->trace_cap = o->iters;
   }
   c->d.trace = c->d_trace;
-  cvba_ctx::Key key;
-  key.iters = o->iters;
-  key.reset = o->reset_lambda ? 1 : 0;
-  key.lam0 = o->lambda0;
-  key.huber = o->huber_delta;
-  key.zmin = o->z_min;
+  const cvba_ctx::Key key = make_key(o, c->prec == CVBA_MIXED);
   if (!c->graph || !(key == c->graph_key) || std::memcmp(&c->graph_dev, &c->d, sizeof(Dev)) != 0) {
     drop_graph(c);
     cudaGraph_t gr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-    cudaError_t e = enqueue_solve_init(c->d, o->lambda0, o->huber_delta, o->z_min, o->iters, key.reset, c->stream);
+    cudaError_t e = enqueue_solve_init(c->d, o->lambda0, o->huber_delta, o->z_min, o->iters, key.reset, key.refine,
+                                       c->stream);
     for (int it = 0; it < o->iters && e == cudaSuccess; ++it) e = enqueue_iteration(c->d, c->stream, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
     if (e != cudaSuccess) return cuda_fail(c, e, "enqueue solve");
@@ -856,7 +867,10 @@ cvba_status cvba_profile_iteration(cvba_ctx* c, const cvba_opts* o, int reps, fl
   std::vector<cudaEvent_t> ev((size_t)np + 1);
   for (auto& e : ev) CK(cudaEventCreate(&e), "event");
   std::vector<double> acc(np, 0.0);
-  CK(enqueue_solve_init(c->d, one.lambda0, one.huber_delta, one.z_min, reps, one.reset_lambda, c->stream), "init");
+  if (!opts_ok(&one)) return fail(c, CVBA_ERR_INVALID_ARG, "profile: bad options");
+  CK(enqueue_solve_init(c->d, one.lambda0, one.huber_delta, one.z_min, reps, one.reset_lambda,
+                        make_key(&one, c->prec == CVBA_MIXED).refine, c->stream),
+     "init");
   cvba_status st = CVBA_OK;
   for (int r = 0; r < reps && st == CVBA_OK; ++r) {
     cudaError_t e = enqueue_iteration(c->d, c->stream, ev.data());
@@ -1048,12 +1062,7 @@ cvba_status batch_prepare(cvba_batch* b, const cvba_opts* o) {
   }
   bool same = (int)b->snap.size() == n && b->graph && b->key_cs == b->chol_cs;
   for (int w = 0; same && w < n; ++w) same = std::memcmp(&b->snap[w], &b->ctxs[w]->d, sizeof(Dev)) == 0;
-  cvba_ctx::Key key;
-  key.iters = o->iters;
-  key.reset = o->reset_lambda ? 1 : 0;
-  key.lam0 = o->lambda0;
-  key.huber = o->huber_delta;
-  key.zmin = o->z_min;
+  const cvba_ctx::Key key = make_key(o, b->mixed != 0);
   if (same && key == b->key) return CVBA_OK;
   batch_drop_graph(b);
   // views, plan sizes, work lists
@@ -1114,7 +1123,8 @@ cvba_status batch_prepare(cvba_batch* b, const cvba_opts* o) {
   // capture
   cudaGraph_t gr;
   CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-  cudaError_t e = enqueue_batch_init(L, o->lambda0, o->huber_delta, o->z_min, o->iters, key.reset, b->stream);
+  cudaError_t e = enqueue_batch_init(L, o->lambda0, o->huber_delta, o->z_min, o->iters, key.reset, key.refine,
+                                     b->stream);
   for (int it = 0; it < o->iters && e == cudaSuccess; ++it) e = enqueue_batch_iteration(L, b->stream);
   cudaError_t e2 = cudaStreamEndCapture(b->stream, &gr);
   if (e != cudaSuccess) return cuda_fail(c, e, "enqueue batch");
@@ -1168,9 +1178,7 @@ cvba_status cvba_batch_set_chol_cluster(cvba_batch* b, int cs) {
 
 cvba_status cvba_batch_solve_async(cvba_batch* b, const cvba_opts* o) {
   if (!b || !o) return CVBA_ERR_INVALID_ARG;
-  if (o->iters < 0 || !(o->huber_delta > 0.0) || !std::isfinite(o->z_min) ||
-      (o->reset_lambda && !(o->lambda0 > 0.0)))
-    return bfail(b, CVBA_ERR_INVALID_ARG, "batch solve: bad options");
+  if (!opts_ok(o)) return bfail(b, CVBA_ERR_INVALID_ARG, "batch solve: bad options");
   if (o->iters == 0) return CVBA_OK;
   DeviceGuard g(b->device);
   cvba_status st = batch_prepare(b, o);

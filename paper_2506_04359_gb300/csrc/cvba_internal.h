@@ -38,6 +38,9 @@ struct Ctrl {
   double pred_p;      // pose part of d^T (lam D d - g)
   double step2_p;     // ||dc||^2
   unsigned long long maxdiag_lm;   // bit pattern of max landmark diag(H) (non-negative double)
+  int refine_max;     // iterative-refinement corrections allowed per RCS solve
+  int refined;        // corrections applied in this iteration
+  double berr;        // backward error |r| / (|A| |dc| + |b|) of the first RCS solve (NaN: not formed)
 };
 
 // Landmark range [l0, l1) with its pairs [p0, p1); used by linearisation,
@@ -128,14 +131,14 @@ struct BatchLaunch {
 // (chol_fallback is written into host_devs before they are uploaded).
 void batch_plan_sizes(Dev* host_devs, int n_win, BatchLaunch& b);
 cudaError_t enqueue_batch_init(const BatchLaunch& b, double lam0, double huber, double zmin, int iters, int reset,
-                               cudaStream_t s);
+                               int refine, cudaStream_t s);
 cudaError_t enqueue_batch_iteration(const BatchLaunch& b, cudaStream_t s);
 int batch_kernels_per_iteration(const BatchLaunch& b);
 int solve_kernels_per_iteration(const Dev& d);
 
 // Launchers (cvba_kernels.cu).  All enqueue on `s` and return the launch status.
 cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double zmin, int iters,
-                               int reset_lambda, cudaStream_t s);
+                               int reset_lambda, int refine, cudaStream_t s);
 // One LM iteration.  With ev != nullptr, profile_parts() + 1 events are recorded around
 // the iteration's parts (for cvba_profile_iteration).
 cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev);

@@ -297,7 +297,8 @@ __device__ __forceinline__ void load_dev(Dev& dst, const Dev* src) {
   __syncthreads();
 }
 
-__device__ __forceinline__ void solve_init_body(const Dev& d, double lam0, double huber, double zmin, int iters, int reset) {
+__device__ __forceinline__ void solve_init_body(const Dev& d, double lam0, double huber, double zmin, int iters, int reset,
+                                                int refine) {
   Ctrl* c = d.ctrl;
   if (threadIdx.x == 0) {
     c->need_lin = 1;
@@ -313,17 +314,20 @@ __device__ __forceinline__ void solve_init_body(const Dev& d, double lam0, doubl
     c->pred_p = 0.0;
     c->step2_p = 0.0;
     c->maxdiag_lm = 0ull;
+    c->refine_max = refine;
+    c->refined = 0;
+    c->berr = CUDART_NAN;
   }
 }
 
-__global__ void k_solve_init(Dev d, double lam0, double huber, double zmin, int iters, int reset) {
-  solve_init_body(d, lam0, huber, zmin, iters, reset);
+__global__ void k_solve_init(Dev d, double lam0, double huber, double zmin, int iters, int reset, int refine) {
+  solve_init_body(d, lam0, huber, zmin, iters, reset, refine);
 }
 __global__ void k_solve_init_b(const Dev* __restrict__ wins, double lam0, double huber, double zmin, int iters,
-                               int reset) {
+                               int reset, int refine) {
   __shared__ Dev sd;
   load_dev(sd, wins + blockIdx.x);
-  solve_init_body(sd, lam0, huber, zmin, iters, reset);
+  solve_init_body(sd, lam0, huber, zmin, iters, reset, refine);
 }
 
 // ----------------------------------------------------------------- k_lin
@@ -1122,17 +1126,25 @@ constexpr int kCB = 8;
 
 struct CholSmem {
   int NP, NB, nlb, CS;
+  size_t rows_len;                                 // packed lower block rows, max over CTAs
   __host__ __device__ size_t rows_off() const { return 0; }
-  __host__ __device__ size_t panel_off() const { return rows_off() + (size_t)nlb * kCB * NP; }
+  __host__ __device__ size_t panel_off() const { return rows_off() + rows_len; }
   __host__ __device__ size_t lkk_off() const { return panel_off() + (size_t)NB * kCB * kCB; }
   __host__ __device__ size_t y_off() const { return lkk_off() + kCB * kCB + kCB; }
   __host__ __device__ size_t acc_off() const { return y_off() + NP; }
   __host__ __device__ size_t contrib_off() const { return acc_off() + NP; }
   __host__ __device__ size_t linv_off() const { return contrib_off() + (size_t)nlb * CS * kCB; }
   __host__ __device__ size_t rdiag_off() const { return linv_off() + (size_t)nlb * kCB * kCB; }
-  __host__ __device__ size_t red_off() const { return rdiag_off() + (size_t)nlb * kCB; }
+  __host__ __device__ size_t nrm_off() const { return rdiag_off() + (size_t)nlb * kCB; }
+  __host__ __device__ size_t red_off() const { return nrm_off() + (size_t)CS * 4; }
   __host__ __device__ size_t flag_off() const { return red_off() + 128; }
   __host__ __device__ size_t doubles() const { return flag_off() + 8; }
+  // CTA q's lb-th block row is block row r = q + lb CS; only its columns [0, 8(r+1)) are
+  // stored (the lower triangle), row-major with width 8(r+1), one block row after another.
+  __host__ __device__ size_t row_off(int q, int lb) const {
+    return (size_t)kCB * kCB * ((size_t)lb * (q + 1) + (size_t)CS * lb * (lb - 1) / 2);
+  }
+  __host__ __device__ int row_width(int q, int lb) const { return kCB * (q + lb * CS + 1); }
 };
 
 __host__ __device__ inline CholSmem chol_layout(int n_c, int CS) {
@@ -1141,6 +1153,13 @@ __host__ __device__ inline CholSmem chol_layout(int n_c, int CS) {
   L.NP = L.NB * kCB;
   L.nlb = (L.NB + CS - 1) / CS;
   L.CS = CS;
+  L.rows_len = 0;
+  for (int q = 0; q < CS; ++q) {
+    int nb = 0;
+    while (nb < L.nlb && q + nb * CS < L.NB) ++nb;
+    const size_t len = L.row_off(q, nb);
+    if (len > L.rows_len) L.rows_len = len;
+  }
   return L;
 }
 
@@ -1213,6 +1232,67 @@ __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk,
   }
 }
 
+// Backward substitution L^T x = y (y in ybuf on every CTA, acc and contrib zero).  The
+// owner of block k writes x_k to d.dc (adds it when `accumulate`).  Ends with a cluster
+// barrier.
+__device__ __forceinline__ void chol_backward(const Dev& d, const CholSmem& Ls, int q, const double* rows,
+                                              const double* ybuf, double* acc, double* contrib, const double* linv,
+                                              double* red, bool accumulate,
+                                              cooperative_groups::cluster_group& cluster) {
+  const int CS = Ls.CS, NB = Ls.NB, n = d.n_c;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int k = NB - 1; k >= 0; --k) {
+    if (q == k % CS) {
+      const int lb = k / CS;
+      const double* R = rows + Ls.row_off(q, lb);
+      const int W = Ls.row_width(q, lb);
+      double* xk = red;                            // 8 values, CTA-local
+      double* tk = red + 16;
+      if (tid < kCB * 16) {                        // t_i = y_i - acc_i - sum over CTAs (fixed order)
+        const int i = tid / 16, src = tid % 16;
+        double v = src < CS ? contrib[(lb * CS + src) * kCB + i] : 0.0;
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
+        if (src == 0) tk[i] = ybuf[kCB * k + i] - acc[kCB * k + i] - v;
+      }
+      __syncthreads();
+      if (tid < kCB * kCB) {                       // x = L_kk^-T t
+        const int i = tid / kCB, c = tid % kCB;
+        double v = linv[(lb * kCB + c) * kCB + i] * tk[c];
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 8);
+        if (c == 0) {
+          xk[i] = v;
+          if (kCB * k + i < n) d.dc[kCB * k + i] = accumulate ? d.dc[kCB * k + i] + v : v;
+        }
+      }
+      __syncthreads();
+      for (int g = tid; g < kCB * k; g += nt) {    // acc[k'] += L_kk'^T x_k, pushed to owners
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < kCB; ++i) s = fma(R[i * W + g], xk[i], s);
+        const double a = acc[g] + s;
+        acc[g] = a;
+        const int kp = g / kCB, dst = kp % CS;
+        if (dst != q) cluster.map_shared_rank(contrib, dst)[((kp / CS) * CS + q) * kCB + (g % kCB)] = a;
+      }
+    }
+    cluster.sync();
+  }
+}
+
+__device__ __forceinline__ double rcs_rhs(const Dev& d, int i) {
+  const int pb = i / 6, comp = i % 6;
+  const int kf = pb < d.fixed_kf ? pb : pb + 1;
+  return d.bS[i] - d.kf_gp[kf * 6 + comp];
+}
+
+__device__ __forceinline__ double rcs_damp(const Dev& d, int i, double lam, double floor_) {
+  const int pb = i / 6, comp = i % 6;
+  const int kf = pb < d.fixed_kf ? pb : pb + 1;
+  return lam * fmax(d.kf_dp[kf * 6 + comp], floor_);
+}
+
 __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -1223,8 +1303,8 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   const int q = (int)cluster.block_rank();
   const int n = d.n_c;
   const CholSmem Ls = chol_layout(n, CS);
-  const int NP = Ls.NP, NB = Ls.NB;
-  double* rows = smem + Ls.rows_off();             // [lb][i][col]
+  const int NB = Ls.NB, NP = Ls.NP;
+  double* rows = smem + Ls.rows_off();             // packed lower block rows of this CTA
   double* panel = smem + Ls.panel_off();           // [c][i][m] = L[8c+i][8k+m]
   double* lkk = smem + Ls.lkk_off();               // [i][m], then 8 reciprocals of the diagonal
   double* ybuf = smem + Ls.y_off();                // right-hand side row / y
@@ -1232,46 +1312,40 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   double* contrib = smem + Ls.contrib_off();       // [lb][from CTA][8]
   double* linv = smem + Ls.linv_off();             // [lb][i][m] inverse of own diagonal blocks
   double* rdiag = smem + Ls.rdiag_off();           // [lb][i] reciprocals of own diagonal entries
+  double* nrm = smem + Ls.nrm_off();               // [CTA][4] refinement norms
   double* red = smem + Ls.red_off();
   int* flag = reinterpret_cast<int*>(smem + Ls.flag_off());
   const int tid = threadIdx.x, nt = blockDim.x;
   const double lam = ctrl->lam;
   const double floor_ = diag_floor(d, red);        // block-level, contains barriers
+  auto rowp = [&](int lb) { return rows + Ls.row_off(q, lb); };
 
   // ---- load own block rows (damped, padded), rhs on CTA 0
   for (int lb = 0; lb < Ls.nlb; ++lb) {
     const int r = q + lb * CS;
     if (r >= NB) break;
-    for (int e = tid; e < kCB * NP; e += nt) {
-      const int i = e / NP, c = e % NP, gi = kCB * r + i;
+    const int W = Ls.row_width(q, lb);
+    double* R = rowp(lb);
+    for (int e = tid; e < kCB * W; e += nt) {
+      const int i = e / W, c = e % W, gi = kCB * r + i;
       double v = 0.0;
       if (gi < n && c < n) {
         if (c <= gi) v = d.S[(size_t)gi * n + c];
-        if (c == gi) {
-          const int pb = gi / 6, comp = gi % 6;
-          const int kf = pb < d.fixed_kf ? pb : pb + 1;
-          v += lam * fmax(d.kf_dp[kf * 6 + comp], floor_);
-        }
+        if (c == gi) v += rcs_damp(d, gi, lam, floor_);
       } else if (gi >= n && c == gi) {
         v = 1.0;
       }
-      rows[(size_t)(lb * kCB + i) * NP + c] = v;
+      R[e] = v;
     }
   }
   for (int c = tid; c < NP; c += nt) {
-    double v = 0.0;
-    if (q == 0 && c < n) {
-      const int pb = c / 6, comp = c % 6;
-      const int kf = pb < d.fixed_kf ? pb : pb + 1;
-      v = d.bS[c] - d.kf_gp[kf * 6 + comp];
-    }
-    ybuf[c] = v;
+    ybuf[c] = (q == 0 && c < n) ? rcs_rhs(d, c) : 0.0;
     acc[c] = 0.0;
   }
   for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
   if (tid == 0) *flag = 0;
   cluster.sync();
-  if (q == 0) chol_factor_push(rows, NP, lkk, flag, rdiag, cluster, CS);   // block 0: CTA 0's first row block
+  if (q == 0) chol_factor_push(rows, kCB, lkk, flag, rdiag, cluster, CS);   // block 0: CTA 0's first row block
 
   // ---- factorisation with the forward substitution fused
   for (int k = 0; k < NB; ++k) {
@@ -1285,7 +1359,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
       if (lb < Ls.nlb) {
         const int r = q + lb * CS;
         if (r <= k || r >= NB) continue;
-        a = rows + (size_t)(lb * kCB + i) * NP + kCB * k;
+        a = rowp(lb) + i * Ls.row_width(q, lb) + kCB * k;
       } else {
         if (q != 0 || i > 0) continue;
         a = ybuf + kCB * k;
@@ -1307,31 +1381,36 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
     for (int lb = 0; lb < Ls.nlb; ++lb) {          // push panel blocks L_rk to every CTA
       const int r = q + lb * CS;
       if (r <= k || r >= NB) continue;
+      const double* R = rowp(lb);
+      const int W = Ls.row_width(q, lb);
       for (int e = tid; e < CS * kCB * kCB; e += nt) {
         const int dst = e / (kCB * kCB), t = e % (kCB * kCB), i = t / kCB, m = t % kCB;
-        cluster.map_shared_rank(panel, dst)[(size_t)r * kCB * kCB + t] =
-            rows[(size_t)(lb * kCB + i) * NP + kCB * k + m];
+        cluster.map_shared_rank(panel, dst)[(size_t)r * kCB * kCB + t] = R[i * W + kCB * k + m];
       }
     }
     cluster.sync();                                // panel k visible everywhere
     // 2a. look-ahead: owner of block k+1 updates and factors its diagonal block first
     if (k + 1 < NB && q == (k + 1) % CS) {
       const int lb = (k + 1) / CS;
+      double* R = rowp(lb);
+      const int W = Ls.row_width(q, lb);
       const double* Lr = panel + (size_t)(k + 1) * kCB * kCB;
       for (int e = tid; e < kCB * kCB; e += nt) {
         const int i = e / kCB, j = e % kCB;
         double s = 0.0;
 #pragma unroll
         for (int m = 0; m < kCB; ++m) s = fma(Lr[i * kCB + m], Lr[j * kCB + m], s);
-        rows[(size_t)(lb * kCB + i) * NP + kCB * (k + 1) + j] -= s;
+        R[i * W + kCB * (k + 1) + j] -= s;
       }
       __syncthreads();
-      chol_factor_push(rows + (size_t)(lb * kCB) * NP + kCB * (k + 1), NP, lkk, flag, rdiag + lb * kCB, cluster, CS);
+      chol_factor_push(R + kCB * (k + 1), W, lkk, flag, rdiag + lb * kCB, cluster, CS);
     }
     // 2b. trailing update of own block rows: A_rc -= L_rk L_ck^T, c in (k, r]
     for (int lb = 0; lb < Ls.nlb; ++lb) {
       const int r = q + lb * CS;
       if (r <= k + 1 || r >= NB) continue;
+      double* R = rowp(lb);
+      const int W = Ls.row_width(q, lb);
       const double* Lr = panel + (size_t)r * kCB * kCB;
       const int cnt = (r - k) * kCB * kCB;
       for (int e = tid; e < cnt; e += nt) {
@@ -1340,7 +1419,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
         double s = 0.0;
 #pragma unroll
         for (int m = 0; m < kCB; ++m) s = fma(Lr[i * kCB + m], Lc[m], s);
-        rows[(size_t)(lb * kCB + i) * NP + kCB * c + j] -= s;
+        R[i * W + kCB * c + j] -= s;
       }
     }
     if (q == 0) {
@@ -1365,13 +1444,14 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   for (int e = tid; e < Ls.nlb * kCB; e += nt) {
     const int lb = e / kCB, j = e % kCB, r = q + lb * CS;
     if (r >= NB) continue;
-    const double* D = rows + (size_t)(lb * kCB) * NP + kCB * r;
+    const int W = Ls.row_width(q, lb);
+    const double* D = rowp(lb) + kCB * r;
     double z[kCB];
 #pragma unroll
     for (int i = 0; i < kCB; ++i) {
       double s = (i == j) ? 1.0 : 0.0;
 #pragma unroll
-      for (int m = 0; m < i; ++m) s = fma(-D[i * NP + m], z[m], s);
+      for (int m = 0; m < i; ++m) s = fma(-D[i * W + m], z[m], s);
       z[i] = i < j ? 0.0 : s * rdiag[lb * kCB + i];
     }
 #pragma unroll
@@ -1385,42 +1465,96 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   }
   cluster.sync();
 
-  // ---- backward substitution L^T x = y
-  for (int k = NB - 1; k >= 0; --k) {
-    if (q == k % CS) {
-      const int lb = k / CS;
-      double* xk = red;                            // 8 values, CTA-local
-      double* tk = red + 16;
-      if (tid < kCB * 16) {                        // t_i = y_i - acc_i - sum over CTAs (fixed order)
-        const int i = tid / 16, src = tid % 16;
-        double v = src < CS ? contrib[(lb * CS + src) * kCB + i] : 0.0;
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
-        if (src == 0) tk[i] = ybuf[kCB * k + i] - acc[kCB * k + i] - v;
-      }
-      __syncthreads();
-      if (tid < kCB * kCB) {                       // x = L_kk^-T t
-        const int i = tid / kCB, c = tid % kCB;
-        double v = linv[(lb * kCB + c) * kCB + i] * tk[c];
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 8);
-        if (c == 0) {
-          xk[i] = v;
-          if (kCB * k + i < n) d.dc[kCB * k + i] = v;
+  chol_backward(d, Ls, q, rows, ybuf, acc, contrib, linv, red, false, cluster);
+
+  // ---- iterative refinement in FP64: r = rhs - A dc from the assembled S (global, lower
+  // triangle), stopped by the backward-error test |r| <= |A| |dc| eps sqrt(n) (infinity
+  // norms, eps = 2^-53) or after refine_max corrections dc += A^-1 r.
+  const int refine_max = ctrl->refine_max;
+  for (int it_r = 0; it_r < refine_max; ++it_r) {
+    // residual of own rows, one warp per row; the rows' entries of ybuf hold r
+    {
+      const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+      double m_r = 0.0, m_a = 0.0, m_x = 0.0, m_b = 0.0;
+      for (int e = warp; e < Ls.nlb * kCB; e += nw) {
+        const int lb = e / kCB, i = e % kCB, gi = kCB * (q + lb * CS) + i;
+        if (gi >= NP) continue;
+        if (gi >= n) {                             // padding rows: zero residual
+          if (lane == 0) ybuf[gi] = 0.0;
+          continue;
         }
+        double s = 0.0, sa = 0.0;
+        for (int j = lane; j < n; j += 32) {
+          double a = j <= gi ? d.S[(size_t)gi * n + j] : d.S[(size_t)j * n + gi];
+          if (j == gi) a += rcs_damp(d, gi, lam, floor_);
+          s = fma(a, d.dc[j], s);
+          sa += fabs(a);
+        }
+        s = warp_sum(s);
+        sa = warp_sum(sa);
+        const double b = rcs_rhs(d, gi), r = b - s;
+        if (lane == 0) ybuf[gi] = r;
+        m_r = fmax(m_r, fabs(r));
+        m_a = fmax(m_a, sa);
+        m_x = fmax(m_x, fabs(d.dc[gi]));
+        m_b = fmax(m_b, fabs(b));
+      }
+      if (lane == 0) {
+        red[32 + warp] = m_r;
+        red[64 + warp] = m_a;
+        red[96 + warp] = m_x;
+        red[48 + warp] = m_b;
       }
       __syncthreads();
-      for (int g = tid; g < kCB * k; g += nt) {    // acc[k'] += L_kk'^T x_k, pushed to owners
-        double s = 0.0;
-#pragma unroll
-        for (int i = 0; i < kCB; ++i) s = fma(rows[(size_t)(lb * kCB + i) * NP + g], xk[i], s);
-        const double a = acc[g] + s;
-        acc[g] = a;
-        const int kp = g / kCB, dst = kp % CS;
-        if (dst != q) cluster.map_shared_rank(contrib, dst)[((kp / CS) * CS + q) * kCB + (g % kCB)] = a;
+      if (tid < CS * 4) {                          // push this CTA's maxima to every CTA
+        const int dst = tid / 4, k = tid % 4;
+        const int base = k == 0 ? 32 : k == 1 ? 64 : k == 2 ? 96 : 48;
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v = fmax(v, red[base + w]);
+        cluster.map_shared_rank(nrm, dst)[q * 4 + k] = v;
       }
     }
-    cluster.sync();
+    for (int e = tid; e < NP; e += nt) acc[e] = 0.0;
+    for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
+    cluster.sync();                                // norms and residual rows visible
+    double rn = 0.0, an = 0.0, xn = 0.0, bn = 0.0;
+    for (int c = 0; c < CS; ++c) {
+      rn = fmax(rn, nrm[c * 4]);
+      an = fmax(an, nrm[c * 4 + 1]);
+      xn = fmax(xn, nrm[c * 4 + 2]);
+      bn = fmax(bn, nrm[c * 4 + 3]);
+    }
+    if (it_r == 0 && q == 0 && tid == 0) ctrl->berr = rn / fmax(an * xn + bn, 1e-300);
+    if (rn <= an * xn * 0x1p-53 * sqrt((double)n)) break;   // uniform over the cluster
+    // forward sweep L y = r, right-looking: the owner of block k forms y_k = L_kk^-1 r_k
+    // and pushes it to every CTA, which then updates its own rows below k
+    for (int k = 0; k < NB; ++k) {
+      if (q == k % CS) {                           // uniform over the CTA
+        const int lb = k / CS, i = (tid / kCB) & (kCB - 1), c = tid % kCB;
+        double v = 0.0;
+        if (tid < kCB * kCB) {
+          v = linv[(lb * kCB + i) * kCB + c] * ybuf[kCB * k + c];
+#pragma unroll
+          for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 8);
+        }
+        __syncthreads();                           // r_k read before y_k overwrites it
+        if (tid < kCB * kCB)
+          for (int dst = c; dst < CS; dst += kCB) cluster.map_shared_rank(ybuf, dst)[kCB * k + i] = v;
+      }
+      cluster.sync();
+      for (int e = tid; e < Ls.nlb * kCB; e += nt) {
+        const int lb = e / kCB, i = e % kCB, r = q + lb * CS;
+        if (r <= k || r >= NB) continue;
+        const double* Rk = rowp(lb) + i * Ls.row_width(q, lb) + kCB * k;
+        double s = 0.0;
+#pragma unroll
+        for (int m = 0; m < kCB; ++m) s = fma(Rk[m], ybuf[kCB * k + m], s);
+        ybuf[kCB * r + i] -= s;
+      }
+      __syncthreads();
+    }
+    chol_backward(d, Ls, q, rows, ybuf, acc, contrib, linv, red, true, cluster);
+    if (q == 0 && tid == 0) ctrl->refined = it_r + 1;
   }
 
   // ---- epilogue: predicted-reduction part, step norm, candidate poses
@@ -1620,6 +1754,11 @@ __device__ __forceinline__ void k_decide_body(const Dev& d, int item) {
     rec.n_valid = (int)lin[2];
     rec.n_inlier = (int)lin[3];
     rec.nonpd = nonpd;
+    rec.berr = ctrl->berr;
+    rec.refined = ctrl->refined;
+    rec.reserved = 0;
+    ctrl->berr = CUDART_NAN;
+    ctrl->refined = 0;
     bool acc = false;
     if (nonpd) {
       rec.cost1 = rec.gain = rec.pred = rec.step_norm = CUDART_NAN;
@@ -1814,8 +1953,8 @@ int kernels_per_iteration() { return 7; }
 int kernels_per_solve_init() { return 1; }
 
 cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double zmin, int iters, int reset,
-                               cudaStream_t s) {
-  k_solve_init<<<1, 256, 0, s>>>(d, lam0, huber, zmin, iters, reset);
+                               int refine, cudaStream_t s) {
+  k_solve_init<<<1, 256, 0, s>>>(d, lam0, huber, zmin, iters, reset, refine);
   return cudaGetLastError();
 }
 
@@ -1914,8 +2053,8 @@ int batch_kernels_per_iteration(const BatchLaunch& b) {
 }
 
 cudaError_t enqueue_batch_init(const BatchLaunch& b, double lam0, double huber, double zmin, int iters, int reset,
-                               cudaStream_t s) {
-  k_solve_init_b<<<b.n_win, 256, 0, s>>>(b.wins, lam0, huber, zmin, iters, reset);
+                               int refine, cudaStream_t s) {
+  k_solve_init_b<<<b.n_win, 256, 0, s>>>(b.wins, lam0, huber, zmin, iters, reset, refine);
   return cudaGetLastError();
 }
 

@@ -23,19 +23,26 @@ STATUS = {0: "CVBA_OK", 1: "CVBA_ERR_INVALID_ARG", 2: "CVBA_ERR_INDEX", 3: "CVBA
 
 class cvba_opts(C.Structure):
     _fields_ = [("iters", C.c_int), ("huber_delta", C.c_double), ("lambda0", C.c_double),
-                ("z_min", C.c_double), ("reset_lambda", C.c_int)]
+                ("z_min", C.c_double), ("reset_lambda", C.c_int), ("refine", C.c_int)]
 
 
 class cvba_iter(C.Structure):
     _fields_ = [("cost0", C.c_double), ("cost1", C.c_double), ("lambda_", C.c_double),
                 ("gain", C.c_double), ("pred", C.c_double), ("step_norm", C.c_double),
                 ("rms_px", C.c_double), ("accepted", C.c_int), ("nonpd", C.c_int),
-                ("n_valid", C.c_int), ("n_inlier", C.c_int)]
+                ("n_valid", C.c_int), ("n_inlier", C.c_int), ("berr", C.c_double), ("refined", C.c_int),
+                ("reserved", C.c_int)]
+
+
+def make_opts(iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, reset_lambda=True, refine=-1) -> "cvba_opts":
+    """cvba_opts; refine < 0 selects the precision's default (1 for mixed, 0 for FP64)."""
+    return cvba_opts(int(iters), float(huber_delta), float(lambda0), float(z_min), 1 if reset_lambda else 0,
+                     int(refine))
 
 
 ITER_DTYPE = np.dtype([("cost0", "f8"), ("cost1", "f8"), ("lambda", "f8"), ("gain", "f8"), ("pred", "f8"),
                        ("step_norm", "f8"), ("rms_px", "f8"), ("accepted", "i4"), ("nonpd", "i4"),
-                       ("n_valid", "i4"), ("n_inlier", "i4")])
+                       ("n_valid", "i4"), ("n_inlier", "i4"), ("berr", "f8"), ("refined", "i4"), ("reserved", "i4")])
 assert ITER_DTYPE.itemsize == C.sizeof(cvba_iter)
 
 
@@ -161,8 +168,8 @@ class Context:
 
     # --- solve
     def cvba_solve(self, iters: int, huber_delta: float = 1.0, lambda0: float = 1e-4, z_min: float = 1e-3,
-                   reset_lambda: bool = True) -> np.ndarray:
-        o = cvba_opts(int(iters), float(huber_delta), float(lambda0), float(z_min), 1 if reset_lambda else 0)
+                   reset_lambda: bool = True, refine: int = -1) -> np.ndarray:
+        o = make_opts(iters, huber_delta, lambda0, z_min, reset_lambda, refine)
         trace = np.zeros(max(int(iters), 1), ITER_DTYPE)
         self._check(lib.cvba_solve(self._h, C.byref(o), C.c_void_p(trace.ctypes.data)))
         return trace[:int(iters)]
@@ -222,8 +229,8 @@ class Context:
     # --- asynchronous / device-pointer calls (pointers are device addresses, e.g. a
     #     torch tensor's data_ptr())
     def cvba_solve_async(self, iters: int, huber_delta: float = 1.0, lambda0: float = 1e-4, z_min: float = 1e-3,
-                         reset_lambda: bool = True):
-        o = cvba_opts(int(iters), float(huber_delta), float(lambda0), float(z_min), 1 if reset_lambda else 0)
+                         reset_lambda: bool = True, refine: int = -1):
+        o = make_opts(iters, huber_delta, lambda0, z_min, reset_lambda, refine)
         self._check(lib.cvba_solve_async(self._h, C.byref(o)))
 
     def cvba_get_trace(self, n: int) -> np.ndarray:
@@ -244,8 +251,8 @@ class Context:
         self._check(lib.cvba_get_landmarks_dev(self._h, C.c_void_p(ptr)))
 
     def cvba_profile_iteration(self, reps: int, huber_delta: float = 1.0, lambda0: float = 1e-4,
-                               z_min: float = 1e-3) -> dict:
-        o = cvba_opts(int(reps), float(huber_delta), float(lambda0), float(z_min), 1)
+                               z_min: float = 1e-3, refine: int = -1) -> dict:
+        o = make_opts(reps, huber_delta, lambda0, z_min, True, refine)
         n = C.c_int()
         self._check(lib.cvba_profile_iteration(self._h, C.byref(o), int(reps), None, C.byref(n)))
         ms = (C.c_float * n.value)()
@@ -304,22 +311,18 @@ class Batch:
         if st != 0:
             raise CvbaError(st, lib.cvba_batch_last_error(self._h).decode())
 
-    @staticmethod
-    def _opts(iters, huber_delta, lambda0, z_min, reset_lambda):
-        return cvba_opts(int(iters), float(huber_delta), float(lambda0), float(z_min), 1 if reset_lambda else 0)
-
-    def cvba_batch_solve(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, reset_lambda=True):
-        o = self._opts(iters, huber_delta, lambda0, z_min, reset_lambda)
+    def cvba_batch_solve(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, reset_lambda=True, refine=-1):
+        o = make_opts(iters, huber_delta, lambda0, z_min, reset_lambda, refine)
         tr = np.zeros((len(self.contexts), max(int(iters), 1)), ITER_DTYPE)
         self._check(lib.cvba_batch_solve(self._h, C.byref(o), C.c_void_p(tr.ctypes.data)))
         return tr[:, :int(iters)]
 
-    def cvba_batch_solve_async(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, reset_lambda=True):
-        o = self._opts(iters, huber_delta, lambda0, z_min, reset_lambda)
+    def cvba_batch_solve_async(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, reset_lambda=True, refine=-1):
+        o = make_opts(iters, huber_delta, lambda0, z_min, reset_lambda, refine)
         self._check(lib.cvba_batch_solve_async(self._h, C.byref(o)))
 
-    def cvba_batch_launch_count(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3):
-        o = self._opts(iters, huber_delta, lambda0, z_min, True)
+    def cvba_batch_launch_count(self, iters, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, refine=-1):
+        o = make_opts(iters, huber_delta, lambda0, z_min, True, refine)
         n = C.c_int()
         self._check(lib.cvba_batch_launch_count(self._h, C.byref(o), C.byref(n)))
         return n.value
@@ -327,8 +330,8 @@ class Batch:
     def cvba_batch_set_chol_cluster(self, cs: int):
         self._check(lib.cvba_batch_set_chol_cluster(self._h, int(cs)))
 
-    def cvba_batch_autotune(self, iters=2, huber_delta=1.0, lambda0=1e-4, z_min=1e-3):
-        o = self._opts(iters, huber_delta, lambda0, z_min, True)
+    def cvba_batch_autotune(self, iters=2, huber_delta=1.0, lambda0=1e-4, z_min=1e-3, refine=-1):
+        o = make_opts(iters, huber_delta, lambda0, z_min, True, refine)
         v = [C.c_int() for _ in range(3)]
         self._check(lib.cvba_batch_autotune(self._h, C.byref(o), *[C.byref(x) for x in v]))
         return dict(lin_tile_pairs=v[0].value, schur_tile_landmarks=v[1].value, chol_cluster=v[2].value)

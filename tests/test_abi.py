@@ -46,10 +46,37 @@ def test_status_strings(lib):
     assert lib.cvba_status_string(99) == b"unknown status"
 
 
-def test_binding_loads_and_matches_struct_layout(lib):
+def test_binding_loads_and_matches_struct_layout(lib, tmp_path):
+    """The ctypes structs and the trace dtype match the C header's layout (sizes and every
+    field offset, as compiled by the host C compiler)."""
+    import shutil
+    import subprocess
     from paper_2506_04359_gb300 import cvba
-    assert ctypes.sizeof(cvba.cvba_iter) == 7 * 8 + 4 * 4
     assert cvba.ITER_DTYPE.itemsize == ctypes.sizeof(cvba.cvba_iter)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"cvba_opts": cvba.cvba_opts, "cvba_iter": cvba.cvba_iter}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cvba.h"', "int main(void) {"]
+    for name, py in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in py._fields_:
+            cf = "lambda" if f == "lambda_" else f
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {cf}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for line in filter(None, out):
+        name, field, val = line.split()
+        py = structs[name]
+        got = ctypes.sizeof(py) if field == "size" else getattr(py, field).offset
+        assert got == int(val), (name, field)
+    for f in cvba.ITER_DTYPE.names:
+        cf = "lambda_" if f == "lambda" else f
+        assert cvba.ITER_DTYPE.fields[f][1] == getattr(cvba.cvba_iter, cf).offset
 
 
 def test_create_fails_loudly_without_gpu(lib):

@@ -1,0 +1,153 @@
+"""Full-size multi-camera windows, too large for the oracle's dense system: the GPU's
+increments are checked against the normal equations the oracle evaluates matrix-free
+(Eq. argmin linearised, Marquardt-damped), its costs and counts against the oracle's
+evaluation, and the mixed path's final RMS against the FP64 path's.  Also the FP64
+iterative refinement of the reduced-camera-system solve."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import ba
+from paper_2506_04359_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def cvba(cuda_device):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_04359_gb300 import cvba as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def c4():
+    return synth.make_problem("c4", 0)
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return synth.make_problem("c2", 0)
+
+
+def _stepwise_normal_residuals(cvba, p, steps, precision="fp64"):
+    """Run `steps` single LM iterations, continuing lambda, and return per step the
+    normal-equation residual of the solved increment at the state it was solved at."""
+    ctx = cvba.Context(precision).load(p)
+    win = ba.Window.from_problem(p)
+    poses, lms = p.poses0.copy(), p.lm0.copy()
+    out = []
+    for t in range(steps):
+        tr = ctx.cvba_solve(1, reset_lambda=(t == 0))
+        if t == 0:
+            ev = ba.evaluate(win, poses, lms)
+            assert int(tr[0]["n_valid"]) == ev.n_valid and int(tr[0]["n_inlier"]) == ev.n_inlier
+            assert abs(tr[0]["cost0"] - ev.F) <= 1e-10 * ev.F
+        assert tr[0]["nonpd"] == 0
+        delta = ctx.cvba_get_increment()
+        out.append(ba.normal_residual(win, poses, lms, float(tr[0]["lambda"]), delta))
+        poses, lms = ctx.cvba_get_poses(), ctx.cvba_get_landmarks()
+    ctx.close()
+    return out
+
+
+def test_c4_fp64_increments_solve_the_normal_equations(cvba, c4):
+    """100 keyframes, 32 cameras, 200k landmarks: the 594-wide reduced camera system is
+    factored by one thread-block cluster."""
+    res = _stepwise_normal_residuals(cvba, c4, 3)
+    assert max(res) <= 1e-8, res
+
+
+def test_c2_fp64_increments_solve_the_normal_equations(cvba, c2):
+    res = _stepwise_normal_residuals(cvba, c2, 3)
+    assert max(res) <= 1e-8, res
+
+
+@pytest.mark.parametrize("cfg", ["c2", "c4_no_outliers"])
+def test_mixed_matches_fp64_final_rms(cvba, cfg, c2):
+    """Final RMS of the mixed path within 1e-3 px of the FP64 path.  On the 100-keyframe
+    window this runs without the 3% outliers: with them, one landmark near a camera
+    crosses the z_min cheirality boundary under the step from the mixed path's
+    iteration-3 state, so the LM path branches (the FP64 solve makes the same decision
+    from that state; see the state-matched test below)."""
+    p = c2 if cfg == "c2" else synth.make_problem("c4", 0, outlier_frac=0.0)
+    iters = 15 if cfg.startswith("c4") else 10
+    win = ba.Window.from_problem(p)
+    rms = {}
+    for prec in ("fp64", "mixed"):
+        ctx = cvba.Context(prec).load(p)
+        tr = ctx.cvba_solve(iters)
+        assert np.all(tr["nonpd"] == 0)
+        rms[prec] = ba.evaluate(win, ctx.cvba_get_poses(), ctx.cvba_get_landmarks()).rms
+        ctx.close()
+    assert abs(rms["mixed"] - rms["fp64"]) <= 1e-3, rms
+
+
+@pytest.mark.parametrize("t", [1, 4])
+def test_c4_mixed_step_matches_fp64_step_at_same_state(cvba, c4, t):
+    """From the mixed path's state after t iterations and its lambda, one mixed iteration
+    and one FP64 iteration take the same accept decision with gains within 5%, and the
+    mixed increment solves the FP64 normal equations to 2% (FP32 Jacobians and Schur
+    products; the FP64 one to 1e-8)."""
+    win = ba.Window.from_problem(c4)
+    m = cvba.Context("mixed").load(c4)
+    m.cvba_solve(t)
+    P, L = m.cvba_get_poses(), m.cvba_get_landmarks()
+    lam, nu = m.cvba_get_damping()
+    tm = m.cvba_solve(1, reset_lambda=False)[0]
+    dm = m.cvba_get_increment()
+    m.close()
+    f = cvba.Context("fp64").load(c4, poses=P, landmarks=L)
+    f.cvba_set_damping(lam, nu)
+    tf = f.cvba_solve(1, reset_lambda=False)[0]
+    df = f.cvba_get_increment()
+    f.close()
+    assert tm["accepted"] == tf["accepted"]
+    assert abs(tm["gain"] - tf["gain"]) <= 0.05 * max(1.0, abs(tf["gain"]))
+    assert ba.normal_residual(win, P, L, lam, df) <= 1e-8
+    assert ba.normal_residual(win, P, L, lam, dm) <= 2e-2
+
+
+def test_refinement_controls_and_backward_error(cvba):
+    """Mixed path: refinement on by default, at most `refine` corrections, backward error
+    of the first solve near FP64 rounding; every setting stays within 1e-3 px of the
+    oracle's final RMS.  FP64 path: off by default (berr not formed)."""
+    p = synth.make_problem("c1", 0)
+    golden = json.load(open(os.path.join(GOLDEN, "c1_oracle.json")))
+    win = ba.Window.from_problem(p)
+    for refine in (-1, 0, 3):
+        ctx = cvba.Context("mixed").load(p)
+        tr = ctx.cvba_solve(20, refine=refine)
+        eff = 1 if refine < 0 else refine
+        assert np.all(tr["refined"] <= eff)
+        if eff == 0:
+            assert np.all(np.isnan(tr["berr"]))
+        else:
+            ok = tr["nonpd"] == 0
+            assert np.all(tr["berr"][ok] < 1e-12)
+        rms = ba.evaluate(win, ctx.cvba_get_poses(), ctx.cvba_get_landmarks()).rms
+        assert abs(rms - golden["final_rms_px"]) <= 1e-3
+        ctx.close()
+    ctx = cvba.Context("fp64").load(p)
+    tr = ctx.cvba_solve(3)
+    assert np.all(np.isnan(tr["berr"])) and np.all(tr["refined"] == 0)
+    ctx.close()
+
+
+def test_fp64_with_refinement_keeps_oracle_parity(cvba):
+    """Refinement only moves the FP64 increment towards the exact solution: the accepted
+    sequence, costs and final state still match the oracle (c0, 10 iterations)."""
+    p = synth.make_problem("c0", 0)
+    win = ba.Window.from_problem(p)
+    P, L, _, _, otr = ba.lm_solve(win, p.poses0, p.lm0, 10, keep_delta=False)
+    ctx = cvba.Context("fp64").load(p)
+    tr = ctx.cvba_solve(10, refine=4)
+    assert tr["accepted"].tolist() == [int(r.accepted) for r in otr]
+    np.testing.assert_allclose(tr["cost0"], [r.cost0 for r in otr], rtol=1e-9)
+    np.testing.assert_allclose(ctx.cvba_get_poses(), P, rtol=0, atol=1e-6)
+    assert np.all(tr["berr"][tr["nonpd"] == 0] < 1e-12)
+    ctx.close()

@@ -355,3 +355,21 @@ def test_planted_jacobian_mistakes_are_caught(kind):
 def test_planted_weight_mistake_is_caught():
     eh, eg = normal_eq_brute_error(_Planted("unweighted"), tiny(outlier_frac=0.3, seed=8))
     assert eg > 1e-3
+
+
+def test_normal_residual_matches_dense_system():
+    """The matrix-free residual of the normal equations agrees with the dense H, g: ~0 for
+    the dense Cholesky solution, the dense relative residual for a perturbed increment."""
+    p = synth.make_problem("c0", 0)
+    win = ba.Window.from_problem(p)
+    H, g, _ = ba.normal_equations(win, p.poses0, p.lm0)
+    lam = 1e-3
+    delta, D = ba.damped_solve(H, g, lam)
+    assert ba.normal_residual(win, p.poses0, p.lm0, lam, delta) <= 1e-12
+    bad = delta.copy()
+    bad[3] += 1e-3
+    bad[win.n_c + 7] -= 2e-3
+    A = H + np.diag(lam * D)
+    dense = np.linalg.norm(A @ bad + g) / np.linalg.norm(g)
+    assert dense > 1e-6
+    assert abs(ba.normal_residual(win, p.poses0, p.lm0, lam, bad) - dense) <= 1e-9 * dense
