@@ -28,6 +28,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2506_04359_gb300", "csrc", "cvba_kernels.cu")
+METRIC = "BA LM iters/s & Gobs/s at RMS reproj within 1e-3 px of oracle; % HBM peak"
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_GFLOPS = 1250.0     # 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal)
 
@@ -42,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the c4 and batched c3 sections")
     return ap.parse_args()
 
 
@@ -139,22 +143,67 @@ def cores() -> int:
 # -------------------------------------------------------------- algorithmic work model
 
 def work_model(p, P: int, mixed: bool) -> dict:
-    """Algorithmic bytes and FLOPs of each part of one LM iteration (per-unit figures x units)."""
+    """Algorithmic bytes and FLOPs of each kernel of one LM iteration (per-unit figures x units).
+
+    Per observation: uv (2 values) + packed camera/keyframe index (4 B).  Per (landmark,
+    keyframe) pair: its index (4 B) and 9 values (M3 = sum w A^T A, 6; X_b, 3).  Per
+    landmark: position (3 FP64), H_ll + g_l (9 values), V^-1 (6) and dp (3).  The reduced
+    camera system is n_c^2 FP64."""
     t = 4 if mixed else 8
     N, M, K = p.N, p.M, p.K
     n_c = 6 * (K - 1)
     m = np.bincount(np.unique(p.obs_lm.astype(np.int64) * K + p.obs_kf) // K, minlength=M)
     blocks = float(np.sum(m * (m + 1) / 2))
-    lin_bytes = N * (2 * t + 4) + P * (12 + 9 * t) + M * (24 + 72) + K * 96
-    schur_bytes = P * (12 + 9 * t) + M * (72 + 48) + 8 * n_c * n_c
-    backsub_bytes = N * (2 * t + 4) + P * (12 + 9 * t) + M * (24 * 3 + 72 + 48)
     return {
-        "lin": {"bytes": lin_bytes, "flops": 110.0 * N + 130.0 * P},
-        "schur": {"bytes": schur_bytes, "flops": 216.0 * blocks + 135.0 * P},
+        "lin": {"bytes": N * (2 * t + 4) + P * (4 + 9 * t) + M * (24 + 9 * t) + K * 96,
+                "flops": 110.0 * N + 130.0 * P},
+        "schur_group": {"bytes": P * (4 + 9 * t) + M * (9 * t + 6 * t) + 8 * n_c * n_c,
+                        "flops": 216.0 * blocks + 135.0 * P},
         "chol": {"bytes": 16.0 * n_c * n_c, "flops": n_c ** 3 / 3.0 + 2.0 * n_c ** 2},
-        "backsub": {"bytes": backsub_bytes, "flops": 40.0 * N + 24.0 * P},
+        "backsub": {"bytes": N * (2 * t + 4) + P * (4 + 9 * t) + M * (24 * 2 + 9 * t),
+                    "flops": 40.0 * N + 24.0 * P},
         "schur_blocks": blocks,
     }
+
+
+def traffic_of(kernel: str, workload: str):
+    """DRAM bytes per launch from the committed ncu record, or None when the kernels' source
+    changed since the counters were taken (or no record exists)."""
+    import hashlib
+    try:
+        with open(TRAFFIC) as f:
+            rec = json.load(f).get(kernel)
+        with open(KERNEL_SOURCE, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha256") != sha or rec.get("workload") != workload:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def roofline(prof: dict, wm: dict, workload: str, only_hbm: bool = False) -> dict:
+    """Achieved vs peak for each kernel with a work model, and the dominant one."""
+    pk, pk_kind = peaks()
+    out = {}
+    for k, ms in prof.items():
+        if k not in wm or ms <= 0:
+            continue
+        if k == "chol":
+            if only_hbm:
+                continue
+            ach = wm[k]["flops"] / (ms * 1e-3) / 1e12
+            out[k] = {"kernel": "k_chol_cluster", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_GFLOPS / 1e3,
+                      "unit": "TFLOP/s", "frac": ach / (FP64_NOMINAL_GFLOPS / 1e3),
+                      "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); a probe measured 1.19 TFLOP/s",
+                      "ms_per_launch": ms}
+        else:
+            ach = wm[k]["bytes"] / (ms * 1e-3) / 1e9
+            out[k] = {"kernel": "k_" + k, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                      "frac": ach / pk["hbm_gbs"], "peak_source": pk_kind + " (copy bandwidth)",
+                      "algorithmic_bytes": wm[k]["bytes"], "ms_per_launch": ms}
+        out[k]["traffic"] = traffic_of(out[k]["kernel"], workload)
+    return out
 
 
 # ------------------------------------------------------------------------- reference
@@ -178,7 +227,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = args.steps / dt
     print(json.dumps({
-        "impl": "reference", "metric": "BA LM iters/s (c1 window)", "value": v, "unit": "LM iters/s",
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "LM iters/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "K": p.K, "C": p.C, "M": p.M, "N": p.N, "precision": "fp64",
@@ -257,23 +306,15 @@ def run_ours(args):
     value = iters_total / dev_s
     gobs = float(np.sum(tr["n_valid"])) * args.steps * ws / dev_s / 1e9
 
-    # --- roofline of the dominant kernel (CUDA events around each part, same stream)
+    # --- roofline of the dominant kernel (CUDA events around each kernel, same stream)
     prof = ctx.cvba_profile_iteration(20, huber_delta=p.huber_delta)
-    kern = {k: v for k, v in prof.items() if k != "memset"}
-    dom = max(kern, key=kern.get)
     wm = work_model(p, P, precision == "mixed")
-    pk, pk_kind = peaks()
-    if dom == "chol":
-        achieved = wm["chol"]["flops"] / (kern[dom] * 1e-3) / 1e12
-        roof = {"kernel": "k_chol", "bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_GFLOPS / 1e3,
-                "unit": "TFLOP/s", "frac": achieved / (FP64_NOMINAL_GFLOPS / 1e3), "traffic": None,
-                "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); a probe measured 1.19 TFLOP/s"}
-    else:
-        achieved = wm[dom]["bytes"] / (kern[dom] * 1e-3) / 1e9
-        roof = {"kernel": "k_" + dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_kind}
-    roof["ms_per_launch"] = kern[dom]
+    label = f"{args.workload} {precision}"
+    roofs = roofline(prof, wm, label)
+    dom = max(roofs, key=lambda k: roofs[k]["ms_per_launch"])
+    roof = dict(roofs[dom])
     roof["parts_ms"] = prof
+    roof["workload"] = label
 
     # --- FP64 path on the same window
     fp64 = None
@@ -339,6 +380,103 @@ def run_ours(args):
         cpu = {"value": n_it / dt, "unit": "LM iters/s", "cores": cores(), "kind": "oracle",
                "sample": f"first {n_it} LM iterations of the {args.workload} window (dense FP64 normal equations)"}
 
+    # --- the 100-keyframe, 32-camera window (3.75M observations): HBM fractions of the
+    #     observation-streaming kernels, mixed vs FP64 throughput
+    c4 = None
+    batched = None
+    extra_launches = 0
+    if not args.no_extras:
+        q = synth.make_problem("c4")
+        qs = {}
+        for prec in ("mixed", "fp64"):
+            cq = cvba.Context(prec, device=local, stream=stream.cuda_stream).load(q)
+            q_p = torch.tensor(q.poses0.reshape(q.K, 12), dtype=torch.float64, device=dev)
+            q_l = torch.tensor(q.lm0, dtype=torch.float64, device=dev)
+            n_steps = 3
+            with torch.cuda.stream(stream):
+                cq.cvba_set_poses_dev(q_p.data_ptr())
+                cq.cvba_set_landmarks_dev(q_l.data_ptr())
+                cq.cvba_solve_async(q.iters, huber_delta=q.huber_delta)
+            stream.synchronize()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+            with torch.cuda.stream(stream):
+                for k in range(n_steps):
+                    l2_flush.fill_(float(k))
+                    evs[k][0].record(stream)
+                    cq.cvba_set_poses_dev(q_p.data_ptr())
+                    cq.cvba_set_landmarks_dev(q_l.data_ptr())
+                    cq.cvba_solve_async(q.iters, huber_delta=q.huber_delta)
+                    evs[k][1].record(stream)
+            stream.synchronize()
+            t_q = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+            extra_launches += n_steps * (cq.cvba_solve_launch_count(q.iters) + 2)
+            trq = cq.cvba_get_trace(q.iters)
+            qs[prec] = {"value": n_steps * q.iters / t_q, "unit": "LM iters/s",
+                        "gobs_per_s": float(np.sum(trq["n_valid"])) * n_steps / t_q / 1e9,
+                        "rms_px": cq.cvba_evaluate(q.huber_delta)["rms"]}
+            if prec == "mixed":
+                pq = cq.cvba_profile_iteration(5, huber_delta=q.huber_delta)
+                wq = work_model(q, cq.cvba_get_sizes()["P"], True)
+                qs[prec]["parts_ms"] = pq
+                qs[prec]["roofline"] = roofline(pq, wq, "c4 mixed", only_hbm=True)
+            cq.close()
+        c4 = {"workload": "c4", "K": q.K, "C": q.C, "M": q.M, "N": q.N, "iters": q.iters, **qs,
+              "rms_diff_px": abs(qs["mixed"]["rms_px"] - qs["fp64"]["rms_px"]),
+              "note": "the FP64 final state is the reference here (the dense oracle does not fit); the "
+                      "paths branch at a z_min crossing of one landmark with 3% outliers"}
+
+        # --- 256 independent windows (c3): one batched graph vs the windows one by one
+        wins = synth.make_batch(256)
+        bctx = [cvba.Context("mixed", device=local, stream=stream.cuda_stream).load(w) for w in wins]
+        batch = cvba.Batch(bctx)
+        tuned = batch.cvba_batch_autotune(iters=2)
+        for c, w in zip(bctx, wins):
+            c.cvba_set_poses(w.poses0, w.fixed_kf)
+            c.cvba_set_landmarks(w.lm0)
+        it_b = wins[0].iters
+        batch.cvba_batch_solve(it_b)                       # warm-up (captures the graph)
+        n_steps = 3
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        for k in range(n_steps):
+            for c, w in zip(bctx, wins):                   # host resets, outside the events
+                c.cvba_set_poses(w.poses0, w.fixed_kf)
+                c.cvba_set_landmarks(w.lm0)
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                l2_flush.fill_(float(k))
+                evs[k][0].record(stream)
+                batch.cvba_batch_solve_async(it_b)
+                evs[k][1].record(stream)
+            stream.synchronize()
+        t_b = sum(a.elapsed_time(b) for a, b in evs) / 1e3
+        extra_launches += n_steps * batch.cvba_batch_launch_count(it_b)
+        n_obs_b = sum(w.N for w in wins)
+        # the same windows one at a time, FP64 single-window graphs
+        seq = {}
+        for prec in ("fp64", "mixed"):
+            cs_ = [cvba.Context(prec, device=local, stream=stream.cuda_stream).load(w) for w in wins]
+            for c in cs_:
+                c.cvba_solve_async(it_b)
+            stream.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                for c in cs_:
+                    c.cvba_solve_async(it_b)
+                e1.record(stream)
+            stream.synchronize()
+            seq[prec] = len(wins) * it_b / (e0.elapsed_time(e1) / 1e3)
+            extra_launches += sum(c.cvba_solve_launch_count(it_b) for c in cs_)
+            for c in cs_:
+                c.close()
+        batched = {"workload": "c3 (256 windows, K 5-30, M 300-3000, 1/2/4/8 stereo pairs)", "precision": "mixed",
+                   "iters": it_b, "value": n_steps * len(wins) * it_b / t_b, "unit": "window LM iters/s",
+                   "gobs_per_s": n_obs_b * it_b * n_steps / t_b / 1e9, "ms_per_solve": 1e3 * t_b / n_steps,
+                   "one_by_one_fp64": seq["fp64"], "one_by_one_mixed": seq["mixed"], "autotuned": tuned}
+        batch.close()
+        for c in bctx:
+            c.close()
+
     golden_rms = None
     gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle.json")
     if os.path.exists(gpath):
@@ -347,7 +485,7 @@ def run_ours(args):
 
     if rank == 0:
         line = {
-            "metric": "BA LM iters/s (Gobs/s, RMS within 1e-3 px of oracle, % HBM peak)",
+            "metric": METRIC,
             "value": value, "unit": "LM iters/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if precision == "mixed" else "f64", "data": "synthetic",
@@ -362,7 +500,10 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": cs.summary(),
+            "c4": c4,
+            "batched": batched,
             "gpu_launches": launches_per_solve * args.steps,
+            "gpu_launches_extras": extra_launches,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)

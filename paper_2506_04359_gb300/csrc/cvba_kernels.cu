@@ -1958,8 +1958,10 @@ cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double z
   return cudaGetLastError();
 }
 
-int profile_parts() { return 6; }
-const char* profile_names() { return "lin,memset,schur,chol,backsub,decide"; }
+// One part per kernel of the iteration (a part whose kernel is not launched for this
+// window's plan reads as zero).
+int profile_parts() { return 8; }
+const char* profile_names() { return "lin,kf_reduce,schur_group,rcs_reduce,schur_direct,chol,backsub,decide"; }
 
 cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   cudaError_t e;
@@ -1970,9 +1972,9 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   else
     k_lin<double><<<d.n_lin_tiles, LIN_THREADS, lin_smem(d), s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = mark(1)) != cudaSuccess) return e;
   k_kf_reduce<<<d.K, 384, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = mark(1)) != cudaSuccess) return e;
   if ((e = mark(2)) != cudaSuccess) return e;
   if (d.n_schur_tiles > 0) {
     const size_t sm = group_smem_bytes(d.max_span, d.mixed != 0);
@@ -1982,8 +1984,10 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
       k_schur_group<double><<<d.n_schur_tiles, SCHUR_THREADS, sm, s>>>(d);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  if ((e = mark(3)) != cudaSuccess) return e;
   k_rcs_reduce<<<d.n_blk, 256, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = mark(4)) != cudaSuccess) return e;
   if (d.n_direct_tiles > 0) {
     if (d.mixed)
       k_schur_direct<float><<<d.n_direct_tiles, SCHUR_THREADS, SchurSmem<float>::bytes(), s>>>(d);
@@ -1992,7 +1996,7 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
 
-  if ((e = mark(3)) != cudaSuccess) return e;
+  if ((e = mark(5)) != cudaSuccess) return e;
   if (chol_cluster_size(d.n_c) > 0) {
     const int CS = chol_cluster_size(d.n_c);
     cudaLaunchConfig_t cfg = {};
@@ -2014,16 +2018,16 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
     k_chol<false><<<1, CHOL_THREADS, 0, s>>>(d);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = mark(4)) != cudaSuccess) return e;
+  if ((e = mark(6)) != cudaSuccess) return e;
   if (d.mixed)
     k_backsub<float><<<d.n_lin_tiles, LIN_THREADS, backsub_smem(d), s>>>(d);
   else
     k_backsub<double><<<d.n_lin_tiles, LIN_THREADS, backsub_smem(d), s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = mark(5)) != cudaSuccess) return e;
+  if ((e = mark(7)) != cudaSuccess) return e;
   k_decide<<<1, DECIDE_THREADS, 0, s>>>(d);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return mark(6);
+  return mark(8);
 }
 
 int solve_kernels_per_iteration(const Dev& d) {
