@@ -286,6 +286,22 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
       for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) kf_tiles[fill[a]++] = ti;
     }
   }
+  // per tile and keyframe of its range: the tile-local indices of that keyframe's pairs
+  // (free keyframes only), in pair order
+  std::vector<int32_t> lin_kf_off, lin_kf_idx;
+  lin_kf_idx.reserve(P);
+  for (auto& t : c->lin_tiles) {
+    t.kfl_off = (int)lin_kf_off.size();
+    std::vector<int32_t> cnt((size_t)t.kf_n + 1, 0);
+    for (int q = t.p0; q < t.p1; ++q)
+      if (kf_pb[pair_kf[q]] >= 0) cnt[pair_kf[q] - t.kf_lo + 1]++;
+    const int base = (int)lin_kf_idx.size();
+    for (int k = 0; k < t.kf_n; ++k) cnt[k + 1] += cnt[k];
+    for (int k = 0; k <= t.kf_n; ++k) lin_kf_off.push_back(base + cnt[k]);
+    lin_kf_idx.resize((size_t)base + cnt[t.kf_n]);
+    for (int q = t.p0; q < t.p1; ++q)
+      if (kf_pb[pair_kf[q]] >= 0) lin_kf_idx[base + cnt[pair_kf[q] - t.kf_lo]++] = q - t.p0;
+  }
   // Schur tiles: runs of landmarks (in internal order) with the same window [lo, hi] of
   // free keyframes, at most `target` landmarks; landmarks spanning more than SPAN_MAX free
   // keyframes go to direct tiles (<= SCHUR_TILE_PAIRS pairs, <= SCHUR_TILE_LMS landmarks).
@@ -478,6 +494,15 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     CK(cudaMemcpy(bto, blk_tiles_off.data(), blk_tiles_off.size() * 4, cudaMemcpyHostToDevice), "upload");
     if (!blk_tiles.empty())
       CK(cudaMemcpy(bt, blk_tiles.data(), blk_tiles.size() * 4, cudaMemcpyHostToDevice), "upload");
+    int32_t *lko, *lki;
+    CK(dalloc(c, &lko, lin_kf_off.size()), "alloc");
+    CK(dalloc(c, &lki, std::max<size_t>(1, lin_kf_idx.size())), "alloc");
+    if (!lin_kf_off.empty())
+      CK(cudaMemcpy(lko, lin_kf_off.data(), lin_kf_off.size() * 4, cudaMemcpyHostToDevice), "upload");
+    if (!lin_kf_idx.empty())
+      CK(cudaMemcpy(lki, lin_kf_idx.data(), lin_kf_idx.size() * 4, cudaMemcpyHostToDevice), "upload");
+    d.lin_kf_off = lko;
+    d.lin_kf_idx = lki;
     d.kf_part = kp;
     d.schur_part = sp;
     d.kf_tiles_off = kto;

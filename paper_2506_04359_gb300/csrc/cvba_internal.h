@@ -23,7 +23,7 @@ constexpr int LIN_TILE_PAIRS = 256;     // pairs per linearisation / back-substi
 constexpr int LIN_TILE_LMS = 256;       // landmarks per linearisation tile
 constexpr int SCHUR_TILE_PAIRS = 256;   // pairs staged in shared memory per Schur tile
 constexpr int SCHUR_TILE_LMS = 128;
-constexpr int SPAN_MAX = 24;            // free keyframes in one Schur tile's window
+constexpr int SPAN_MAX = 22;            // free keyframes in one Schur tile's window (<= 253 blocks)
 
 // Device-resident LM control block.  Written only by the solve's kernels.
 struct Ctrl {
@@ -38,6 +38,7 @@ struct Ctrl {
   double pred_p;      // pose part of d^T (lam D d - g)
   double step2_p;     // ||dc||^2
   unsigned long long maxdiag_lm;   // bit pattern of max landmark diag(H) (non-negative double)
+  unsigned long long maxdiag_kf;   // bit pattern of max keyframe diag(H), set by k_kf_reduce
   int refine_max;     // iterative-refinement corrections allowed per RCS solve
   int refined;        // corrections applied in this iteration
   double berr;        // backward error |r| / (|A| |dc| + |b|) of the first RCS solve (NaN: not formed)
@@ -48,6 +49,7 @@ struct Ctrl {
 struct LinTile {
   int l0, l1, p0, p1;
   int kf_lo, kf_n, part_off;   // keyframes [kf_lo, kf_lo + kf_n) touched; offset in kf_part
+  int kfl_off;                 // offset in lin_kf_off of this tile's kf_n + 1 list offsets
 };
 
 // Landmark range for the Schur kernel: pairs [p0, p1), off-diagonal block work items
@@ -97,7 +99,9 @@ struct Dev {
   double* dc;                 // n_c   pose increment
   double* dp;                 // M * 3 landmark increment
   // per-tile partials and the lists of tiles covering each keyframe / RCS block
-  double* kf_part;            // per lin tile: kf_n * 12 (g_p 6, diag Hpp 6)
+  double* kf_part;            // per lin tile: kf_n * 12 (g_p 6, diag Hpp 6); mixed: float (hi, lo) pairs
+  const int32_t* lin_kf_off;  // per lin tile, per keyframe of its range: start in lin_kf_idx (kf_n + 1)
+  const int32_t* lin_kf_idx;  // tile-local indices of each keyframe's free pairs, in pair order
   double* schur_part;         // per Schur tile: window (rows (rows + 1) / 2) then b (rows)
   const int32_t* kf_tiles_off;   // K + 1
   const int32_t* kf_tiles;       // lin tiles covering each keyframe

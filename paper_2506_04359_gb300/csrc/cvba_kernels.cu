@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "cvba_internal.h"
 
@@ -69,6 +70,20 @@ __device__ void block_sum4(double v[4], double* red) {
   __syncthreads();
 }
 
+// Block maximum of non-negative floats (result in every thread).  Contains barriers.
+__device__ float block_max_f(float v, float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  float r = 0.0f;
+  for (int w = 0; w < nw; ++w) r = fmaxf(r, red[w]);
+  __syncthreads();
+  return r;
+}
+
 __device__ double block_max(double v, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   v = warp_max(v);
@@ -87,13 +102,87 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
-// Marquardt floor 1e-12 * max(diag H) over landmarks (atomic max by k_lin) and poses.
-__device__ double diag_floor(const Dev& d, double* red) {
-  double m = 0.0;
-  for (int i = threadIdx.x; i < d.K * 6; i += blockDim.x) m = fmax(m, d.kf_dp[i]);
-  m = block_max(m, red);
-  m = fmax(m, __longlong_as_double((long long)d.ctrl->maxdiag_lm));
+// Marquardt floor 1e-12 * max(diag H) over landmarks (atomic max by k_lin) and poses
+// (atomic max by k_kf_reduce).  Starts with a block barrier, which callers rely on.
+__device__ double diag_floor(const Dev& d, double* /*red*/) {
+  __syncthreads();
+  const double m = fmax(__longlong_as_double((long long)d.ctrl->maxdiag_lm),
+                        __longlong_as_double((long long)d.ctrl->maxdiag_kf));
   return kDiagFloor * m;
+}
+
+// ---------------------------------------------------------- compensated FP32 sums
+// A value hi + lo held in two floats (about 48 significant bits).  The mixed path keeps
+// its sums in this form and converts to FP64 once per tile: on GB300 every FP64
+// operation, conversions included, issues at 1/64 of the FP32 rate.
+struct DF {
+  float hi, lo;
+};
+
+// Error-free sum of the high parts (Knuth's TwoSum), low parts added, renormalised
+// (Dekker's Fast2Sum).  Symmetric in its arguments.
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  float e = (a.hi - (s - bb)) + (b.hi - bb);
+  e += a.lo + b.lo;
+  const float hi = s + e;
+  return DF{hi, e - (hi - s)};
+}
+
+__device__ __forceinline__ DF warp_sum_df(DF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const DF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = df_add(v, w);
+  }
+  return v;
+}
+
+__device__ __forceinline__ int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order block sum of NV compensated values; thread 0 gets the FP64 results.
+// `red` holds >= 2 * NV * 32 floats.  Contains barriers.
+template <int NV>
+__device__ void block_sum_df(DF v[NV], double out[NV], float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum_df(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      red[(2 * k) * 32 + warp] = v[k].hi;
+      red[(2 * k + 1) * 32 + warp] = v[k].lo;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      DF x{lane < nw ? red[(2 * k) * 32 + lane] : 0.0f, lane < nw ? red[(2 * k + 1) * 32 + lane] : 0.0f};
+      x = warp_sum_df(x);
+      out[k] = (double)x.hi + (double)x.lo;
+    }
+  }
+  __syncthreads();
+}
+
+// Fixed-order block sum of integer counts; thread 0 gets the result.  `red` >= 32 ints.
+__device__ int block_sum_i(int v, int* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum_i(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  int r = 0;
+  if (warp == 0) r = warp_sum_i(lane < nw ? red[lane] : 0);
+  __syncthreads();
+  return r;
 }
 
 // -------------------------------------------------------------- observations
@@ -124,6 +213,8 @@ struct Acc {
     }
   }
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+  __device__ __forceinline__ DF df() const { return DF{(float)s, -(float)c}; }
+  __device__ __forceinline__ T rounded() const { return s - c; }
 };
 
 template <typename T>
@@ -314,6 +405,7 @@ __device__ __forceinline__ void solve_init_body(const Dev& d, double lam0, doubl
     c->pred_p = 0.0;
     c->step2_p = 0.0;
     c->maxdiag_lm = 0ull;
+    c->maxdiag_kf = 0ull;
     c->refine_max = refine;
     c->refined = 0;
     c->berr = CUDART_NAN;
@@ -345,7 +437,6 @@ __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
   double* s_red = smem;                                // 128
   T* s_rig = reinterpret_cast<T*>(s_red + 128);        // C * 16
   T* s_pair = s_rig + d.C * RIG_STRIDE;                // LIN_TILE_PAIRS * 21
-  int* s_kf = reinterpret_cast<int*>(s_pair + LIN_TILE_PAIRS * 21);   // LIN_TILE_PAIRS
   const T* rig = st_rig<T>(d);
   for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = rig[i];
   __syncthreads();
@@ -397,39 +488,68 @@ __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
     sl[18] = M3[3] * X[2] * X[2] - 2 * M3[4] * X[1] * X[2] + M3[5] * X[1] * X[1];
     sl[19] = M3[0] * X[2] * X[2] - 2 * M3[2] * X[0] * X[2] + M3[5] * X[0] * X[0];
     sl[20] = M3[0] * X[1] * X[1] - 2 * M3[1] * X[0] * X[1] + M3[3] * X[0] * X[0];
-    s_kf[qi] = d.kf_pb[a] >= 0 ? a : -1;
   }
-  double v[4] = {st.cost.value(), st.sq.value(), (double)st.nv, (double)st.ni};
-  block_sum4(v, s_red);                              // contains barriers: slots complete
-  if (threadIdx.x == 0) {
+  if constexpr (sizeof(T) == 4) {
+    DF v[2] = {st.cost.df(), st.sq.df()};
+    double o[2];
+    block_sum_df<2>(v, o, reinterpret_cast<float*>(s_red));   // contains barriers: slots complete
+    const int nv = block_sum_i(st.nv, reinterpret_cast<int*>(s_red));
+    const int ni = block_sum_i(st.ni, reinterpret_cast<int*>(s_red));
+    if (threadIdx.x == 0) {
+      d.lin_part[item * 4 + 0] = o[0];
+      d.lin_part[item * 4 + 1] = o[1];
+      d.lin_part[item * 4 + 2] = (double)nv;
+      d.lin_part[item * 4 + 3] = (double)ni;
+    }
+  } else {
+    double v[4] = {st.cost.value(), st.sq.value(), (double)st.nv, (double)st.ni};
+    block_sum4(v, s_red);                            // contains barriers: slots complete
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) d.lin_part[item * 4 + k] = v[k];
+      for (int k = 0; k < 4; ++k) d.lin_part[item * 4 + k] = v[k];
+    }
   }
   // per landmark: sum of its pairs (contiguous, in order)
-  double mx = 0.0;
+  T mx = 0;
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     const int j = tile.l0 + l;
     Acc<T> h[9];
     for (int q = d.lm_pair[j]; q < d.lm_pair[j + 1]; ++q)
 #pragma unroll
       for (int k = 0; k < 9; ++k) h[k].add(s_pair[(q - tile.p0) * 21 + k]);
+    if constexpr (sizeof(T) == 4) {                  // FP32 inputs of the landmark blocks
 #pragma unroll
-    for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = h[k].value();
+      for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = (double)h[k].rounded();
 #pragma unroll
-    for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = h[6 + k].value();
-    mx = fmax(mx, fmax(h[0].value(), fmax(h[3].value(), h[5].value())));
+      for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = (double)h[6 + k].rounded();
+      mx = fmaxf(mx, fmaxf(h[0].rounded(), fmaxf(h[3].rounded(), h[5].rounded())));
+    } else {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = h[k].value();
+#pragma unroll
+      for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = h[6 + k].value();
+      mx = fmax(mx, fmax(h[0].value(), fmax(h[3].value(), h[5].value())));
+    }
   }
-  // per keyframe and component: sum over this tile's pairs of that keyframe, in order
+  // per keyframe and component: sum over this tile's pairs of that keyframe, in pair
+  // order (the tile's pairs of each keyframe are listed in lin_kf_idx)
+  const int* koff = d.lin_kf_off + tile.kfl_off;
   for (int e = threadIdx.x; e < tile.kf_n * 12; e += blockDim.x) {
-    const int a = tile.kf_lo + e / 12, comp = e % 12;
+    const int ka = e / 12, comp = e % 12;
     Acc<T> sum;
-    for (int qi = 0; qi < np; ++qi)
-      if (s_kf[qi] == a) sum.add(s_pair[qi * 21 + 9 + comp]);
-    d.kf_part[tile.part_off + e] = sum.value();
+    for (int i = koff[ka]; i < koff[ka + 1]; ++i) sum.add(s_pair[d.lin_kf_idx[i] * 21 + 9 + comp]);
+    if constexpr (sizeof(T) == 4)
+      reinterpret_cast<float2*>(d.kf_part)[tile.part_off + e] = make_float2(sum.s, -sum.c);
+    else
+      d.kf_part[tile.part_off + e] = sum.value();
   }
-  mx = block_max(mx, s_red);
-  if (threadIdx.x == 0 && mx > 0.0)
-    atomicMax(&ctrl->maxdiag_lm, (unsigned long long)__double_as_longlong(mx));
+  double mxd;
+  if constexpr (sizeof(T) == 4)
+    mxd = (double)block_max_f(mx, reinterpret_cast<float*>(s_red));
+  else
+    mxd = block_max(mx, s_red);
+  if (threadIdx.x == 0 && mxd > 0.0)
+    atomicMax(&ctrl->maxdiag_lm, (unsigned long long)__double_as_longlong(mxd));
 }
 
 template <typename T>
@@ -450,6 +570,8 @@ __device__ __forceinline__ void k_kf_reduce_body(const Dev& d, int item) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;   // warp = component (12)
   const int t0 = d.kf_tiles_off[a], t1 = d.kf_tiles_off[a + 1];
   double v = 0.0;
+  DF vf{0.0f, 0.0f};                                 // mixed: tile partials are (hi, lo) floats
+  const bool mixed = d.mixed != 0;
   for (int c0 = t0; c0 < t1; c0 += 384) {            // stage offsets of a chunk of tiles
     const int nc = min(384, t1 - c0);
     __syncthreads();
@@ -458,11 +580,29 @@ __device__ __forceinline__ void k_kf_reduce_body(const Dev& d, int item) {
       s_off[threadIdx.x] = tl.part_off + (a - tl.kf_lo) * 12;
     }
     __syncthreads();
-    for (int t = lane; t < nc; t += 32) v += d.kf_part[s_off[t] + warp];
+    if (mixed) {
+      const float2* kp = reinterpret_cast<const float2*>(d.kf_part);
+      for (int t = lane; t < nc; t += 32) {
+        const float2 x = kp[s_off[t] + warp];
+        vf = df_add(vf, DF{x.x, x.y});
+      }
+    } else {
+      for (int t = lane; t < nc; t += 32) v += d.kf_part[s_off[t] + warp];
+    }
   }
-  v = warp_sum(v);
+  if (mixed) {
+    vf = warp_sum_df(vf);
+    v = (double)vf.hi + (double)vf.lo;
+  } else {
+    v = warp_sum(v);
+  }
   if (lane == 0) {
-    if (warp < 6) d.kf_gp[a * 6 + warp] = v; else d.kf_dp[a * 6 + warp - 6] = v;
+    if (warp < 6) {
+      d.kf_gp[a * 6 + warp] = v;
+    } else {
+      d.kf_dp[a * 6 + warp - 6] = v;
+      if (v > 0.0) atomicMax(&d.ctrl->maxdiag_kf, (unsigned long long)__double_as_longlong(v));
+    }
   }
 }
 
@@ -511,8 +651,14 @@ __device__ void landmark_vinv(const Dev& d, int j, double lam, double floor_, do
     tau = 0.0;
     d.ctrl->nonpd = 1;
   }
-  for (int k = 0; k < 6; ++k) d.lm_Vinv[j * VINV_STRIDE + k] = inv[k];
-  d.lm_Vinv[j * VINV_STRIDE + 6] = tau;
+  if (sizeof(T) == 4) {                              // the mixed path reads V^-1 in FP32
+    float* o = reinterpret_cast<float*>(d.lm_Vinv) + j * VINV_STRIDE;
+    for (int k = 0; k < 6; ++k) o[k] = (float)inv[k];
+    o[6] = (float)tau;
+  } else {
+    for (int k = 0; k < 6; ++k) d.lm_Vinv[j * VINV_STRIDE + k] = inv[k];
+    d.lm_Vinv[j * VINV_STRIDE + 6] = tau;
+  }
 }
 
 // Per pair: W = J_pose^T W J_lm = [G; [X]x G] with G = M3 R (6 x 3), Y = W V^-1, the pair's
@@ -752,12 +898,14 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct_b(const Dev* __r
 // keyframes [k_lo, k_lo + span): their contributions to that window of S,
 //   S_ab += sum_j (U_ja - Y_ja W_ja^T) (a = b),   S_ab -= sum_j Y_ja W_jb^T (a > b),
 //   b_a  += sum_j Y_ja g_l,j,
-// form a dense product over the tile's landmarks (a keyframe of the window that does not
-// observe a landmark contributes zero blocks).  Landmarks are staged in chunks; each
-// thread owns fixed entries of the window and accumulates them in registers over the
-// landmarks in order: FP64 on the FP64 path, Kahan-compensated FP32 on the mixed path.
-// The window is written as the tile's partial, summed over tiles by k_rcs_reduce.
-constexpr int kGroupOwn = 16;      // window entries per thread and pass (passes cover E + rows)
+// (a keyframe of the window that does not observe a landmark contributes zero blocks).
+// Register-blocked: each working thread owns one 6x6 block (a, b), a >= b, of the window
+// and accumulates it over a share of the landmarks (G groups split the landmarks when the
+// window has fewer than 256 / G blocks): per landmark it reads Y_a and W_b (12 short
+// vectors) from the staged chunk and does 108 FMAs.  Sums run per chunk in T, then into
+// a compensated (Kahan) accumulator on the mixed path or a plain FP64 one; the groups are
+// combined in a fixed order, and the window is written as the tile's partial, summed over
+// tiles by k_rcs_reduce.
 constexpr int kStage = 76;         // per (landmark, block): Y[6][4] W[6][4] Dg[21] bY[6] pad
 template <typename T>
 struct GroupChunk {
@@ -771,8 +919,26 @@ size_t group_smem_bytes(int max_span, bool mixed) {
 }
 
 template <typename T>
+__device__ __forceinline__ void load_row3(const T* p, T& x, T& y, T& z);
+template <>
+__device__ __forceinline__ void load_row3<float>(const float* p, float& x, float& y, float& z) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x = v.x;
+  y = v.y;
+  z = v.z;
+}
+template <>
+__device__ __forceinline__ void load_row3<double>(const double* p, double& x, double& y, double& z) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  x = v.x;
+  y = v.y;
+  z = p[2];
+}
+
+template <typename T>
 __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
   constexpr int CH = GroupChunk<T>::value;
+  constexpr bool kKahan = sizeof(T) == 4;
   extern __shared__ __align__(16) double smem[];
   double* s_red = smem;                               // 64
   T* s_vinv = reinterpret_cast<T*>(s_red + 64);       // SCHUR_TILE_LMS * 6
@@ -780,7 +946,7 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
   T* s_stg = s_gl + SCHUR_TILE_LMS * 3;               // CH * max_span * kStage
   const SchurTile tile = d.schur_tiles[item];
   const int nl = tile.l1 - tile.l0;
-  const int span = tile.span, rows = 6 * span, E = rows * (rows + 1) / 2, NE = E + rows;
+  const int span = tile.span, rows = 6 * span, E = rows * (rows + 1) / 2;
   const double lam = d.ctrl->lam;
   const double floor_ = diag_floor(d, s_red);
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
@@ -791,93 +957,130 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
     for (int k = 0; k < 3; ++k) s_gl[l * 3 + k] = (T)d.lm_g[j * 3 + k];
   }
   if (span == 0) return;                             // landmarks seen only by the fixed keyframe
-  // Passes over the window's entries (kGroupOwn per thread each).  Owned entries are
-  // offsets into one landmark's staging: bit 31 set = a dot product of a Y row and a W row
-  // (offsets in bits 0-14 and 15-29); otherwise a staged scalar.
+  // work item: block (a, b) of the window and landmark group g
+  const int nblk = span * (span + 1) / 2;            // <= 253 (span <= SPAN_MAX)
+  const int G = max(1, min(CH, SCHUR_THREADS / nblk));
+  const int t = threadIdx.x;
+  const bool working = t < nblk * G;
+  const int blk = t % nblk, g = t / nblk;
+  int ba = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+  while (ba * (ba + 1) / 2 > blk) --ba;
+  while ((ba + 1) * (ba + 2) / 2 <= blk) ++ba;
+  const int bb = blk - ba * (ba + 1) / 2;
+  const bool diag = ba == bb;
+  T acc[36], cmp[36];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) {
+    acc[k] = 0;
+    cmp[k] = 0;
+  }
   const int stg_len = CH * span * kStage;
   const T* pose = st_pose<T>(d, d.ctrl->cur);
-  for (int e0 = 0; e0 < NE; e0 += kGroupOwn * SCHUR_THREADS) {
-    int off[kGroupOwn];
-    T acc[kGroupOwn], cmp[kGroupOwn];
+  for (int c0 = 0; c0 < nl; c0 += CH) {
+    const int nc = min(CH, nl - c0);
+    __syncthreads();                                 // previous chunk consumed
+    for (int i = threadIdx.x; i < stg_len; i += blockDim.x) s_stg[i] = 0;
+    __syncthreads();
+    const int q0 = d.lm_pair[tile.l0 + c0], q1 = d.lm_pair[tile.l0 + c0 + nc];
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+      const int a = d.pair_kf[q];
+      const int pb = d.kf_pb[a];
+      if (pb < 0) continue;
+      const int l = d.pair_lm[q] - tile.l0;          // index in the tile
+      T W[18], Y[18], Dg[21], bY[6];
+      pair_schur_terms<T>(reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN, pose + a * POSE_STRIDE,
+                          s_vinv + l * 6, s_gl + l * 3, W, Y, Dg, bY);
+      T* st = s_stg + ((l - c0) * span + (pb - tile.k_lo)) * kStage;
 #pragma unroll
-    for (int i = 0; i < kGroupOwn; ++i) {
-      const int e = e0 + threadIdx.x + i * SCHUR_THREADS;
-      acc[i] = 0;
-      cmp[i] = 0;
-      off[i] = 0;
-      if (e < E) {
-        int wr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-        while (wr * (wr + 1) / 2 > e) --wr;
-        while ((wr + 1) * (wr + 2) / 2 <= e) ++wr;
-        const int wc = e - wr * (wr + 1) / 2;
-        const int ya = wr / 6, r = wr % 6, wb = wc / 6, c = wc % 6;
-        if (ya == wb)
-          off[i] = ya * kStage + 48 + r * (r + 1) / 2 + c;
-        else
-          off[i] = (int)(0x80000000u | (unsigned)(ya * kStage + r * 4) | ((unsigned)(wb * kStage + 24 + c * 4) << 15));
-      } else if (e < NE) {
-        const int wr = e - E;
-        off[i] = (wr / 6) * kStage + 69 + wr % 6;
-      }
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          st[r * 4 + k] = Y[r * 3 + k];
+          st[24 + r * 4 + k] = W[r * 3 + k];
+        }
+#pragma unroll
+      for (int k = 0; k < 21; ++k) st[48 + k] = Dg[k];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
     }
-    for (int c0 = 0; c0 < nl; c0 += CH) {
-      const int nc = min(CH, nl - c0);
-      __syncthreads();                               // previous chunk consumed
-      for (int i = threadIdx.x; i < stg_len; i += blockDim.x) s_stg[i] = 0;
-      __syncthreads();
-      const int q0 = d.lm_pair[tile.l0 + c0], q1 = d.lm_pair[tile.l0 + c0 + nc];
-      for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        const int a = d.pair_kf[q];
-        const int pb = d.kf_pb[a];
-        if (pb < 0) continue;
-        const int l = d.pair_lm[q] - tile.l0;        // index in the tile
-        T W[18], Y[18], Dg[21], bY[6];
-        pair_schur_terms<T>(reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN, pose + a * POSE_STRIDE,
-                            s_vinv + l * 6, s_gl + l * 3, W, Y, Dg, bY);
-        T* st = s_stg + ((l - c0) * span + (pb - tile.k_lo)) * kStage;
+    __syncthreads();
+    if (working) {
+      T part[36];
 #pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            st[r * 4 + k] = Y[r * 3 + k];
-            st[24 + r * 4 + k] = W[r * 3 + k];
-          }
-#pragma unroll
-        for (int k = 0; k < 21; ++k) st[48 + k] = Dg[k];
-#pragma unroll
-        for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
-      }
-      __syncthreads();
-      for (int lr = 0; lr < nc; ++lr) {
+      for (int k = 0; k < 36; ++k) part[k] = 0;
+      for (int lr = g; lr < nc; lr += G) {
         const T* base = s_stg + lr * span * kStage;
+        if (diag) {
+          const T* st = base + ba * kStage + 48;
 #pragma unroll
-        for (int i = 0; i < kGroupOwn; ++i) {
-          if (e0 + threadIdx.x + i * SCHUR_THREADS >= NE) break;
-          T v;
-          if (off[i] < 0) {
-            const T* y = base + (off[i] & 0x7fff);
-            const T* w = base + ((off[i] >> 15) & 0x7fff);
-            v = -(y[0] * w[0] + y[1] * w[1] + y[2] * w[2]);
-          } else {
-            v = base[off[i]];
-          }
-          if (sizeof(T) == 4) {                      // Kahan: acc - cmp is the running sum
-            const T yk = v - cmp[i];
-            const T t = acc[i] + yk;
-            cmp[i] = (t - acc[i]) - yk;
-            acc[i] = t;
-          } else {
-            acc[i] += v;
+          for (int k = 0; k < 27; ++k) part[k] += st[k];
+        } else {
+          const T* Ya = base + ba * kStage;
+          const T* Wb = base + bb * kStage + 24;
+          T w[18];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) load_row3<T>(Wb + 4 * c, w[3 * c], w[3 * c + 1], w[3 * c + 2]);
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            T y0, y1, y2;
+            load_row3<T>(Ya + 4 * r, y0, y1, y2);
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+              part[r * 6 + c] = fma(-y0, w[3 * c], fma(-y1, w[3 * c + 1], fma(-y2, w[3 * c + 2], part[r * 6 + c])));
           }
         }
       }
-    }
-    double* out = d.schur_part + tile.part_off;
 #pragma unroll
-    for (int i = 0; i < kGroupOwn; ++i) {
-      const int e = e0 + threadIdx.x + i * SCHUR_THREADS;
-      if (e < NE) out[e] = (double)acc[i] - (double)cmp[i];
+      for (int k = 0; k < 36; ++k) {
+        if (kKahan) {                                // acc - cmp is the running sum
+          const T yk = part[k] - cmp[k];
+          const T s = acc[k] + yk;
+          cmp[k] = (s - acc[k]) - yk;
+          acc[k] = s;
+        } else {
+          acc[k] += part[k];
+        }
+      }
     }
+  }
+  // combine the landmark groups in a fixed order into the staging area as blocks
+  // [blk][36] (diagonal blocks: 21 lower entries of U - Y W^T, then 6 of b): FP64 on the
+  // FP64 path, compensated (hi, lo) floats on the mixed path
+  using Out = typename std::conditional<sizeof(T) == 4, DF, double>::type;
+  Out* s_out = reinterpret_cast<Out*>(s_stg);        // nblk * 36 entries of 8 bytes fit
+  for (int gg = 0; gg < G; ++gg) {
+    __syncthreads();
+    if (working && g == gg) {
+#pragma unroll
+      for (int k = 0; k < 36; ++k) {
+        if constexpr (sizeof(T) == 4) {
+          const DF v{(float)acc[k], -(float)cmp[k]};
+          s_out[blk * 36 + k] = gg == 0 ? v : df_add(s_out[blk * 36 + k], v);
+        } else {
+          const double v = (double)acc[k];
+          s_out[blk * 36 + k] = gg == 0 ? v : s_out[blk * 36 + k] + v;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // the window partial: lower triangle of the 6 span x 6 span window, row-major, then b
+  Out* out = reinterpret_cast<Out*>(d.schur_part) + tile.part_off;
+  for (int e = threadIdx.x; e < E + rows; e += blockDim.x) {
+    Out v;
+    if (e < E) {
+      int wr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while (wr * (wr + 1) / 2 > e) --wr;
+      while ((wr + 1) * (wr + 2) / 2 <= e) ++wr;
+      const int wc = e - wr * (wr + 1) / 2;
+      const int a = wr / 6, r = wr % 6, b = wc / 6, c = wc % 6;
+      const int kb = a * (a + 1) / 2 + b;
+      v = a == b ? s_out[kb * 36 + r * (r + 1) / 2 + c] : s_out[kb * 36 + r * 6 + c];
+    } else {
+      const int wr = e - E, a = wr / 6;
+      v = s_out[(a * (a + 1) / 2 + a) * 36 + 21 + wr % 6];
+    }
+    out[e] = v;
   }
 }
 
@@ -906,6 +1109,10 @@ __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
   const int n_ent = a == b ? 27 : 36;              // 21 lower entries + 6 of b, or 36
   constexpr int kPer = 5;                          // entries per warp (8 warps x 5 >= 36)
   double v[kPer] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  DF vf[kPer];                                       // mixed: partials are (hi, lo) floats
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) vf[k] = DF{0.0f, 0.0f};
+  const bool mixed = d.mixed != 0;
   for (int c0 = t0; c0 < t1; c0 += 256) {          // stage a chunk of covering tiles
     const int nc = min(256, t1 - c0);
     __syncthreads();
@@ -938,7 +1145,12 @@ __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
         const int rows = s_rows[t];
         const int wr = 6 * (a - s_klo[t]) + r;
         const int idx = is_b ? rows * (rows + 1) / 2 + wr : wr * (wr + 1) / 2 + 6 * (b - s_klo[t]) + c;
-        v[k] += d.schur_part[s_off[t] + idx];
+        if (mixed) {
+          const DF x = reinterpret_cast<const DF*>(d.schur_part)[s_off[t] + idx];
+          vf[k] = df_add(vf[k], x);
+        } else {
+          v[k] += d.schur_part[s_off[t] + idx];
+        }
       }
     }
   }
@@ -946,7 +1158,13 @@ __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
   for (int k = 0; k < kPer; ++k) {
     const int e = warp + k * nw;
     if (e >= n_ent) break;
-    const double sum = warp_sum(v[k]);
+    double sum;
+    if (mixed) {
+      const DF x = warp_sum_df(vf[k]);
+      sum = (double)x.hi + (double)x.lo;
+    } else {
+      sum = warp_sum(v[k]);
+    }
     if (lane == 0) {
       if (a == b && e >= 21) {
         d.bS[6 * a + (e - 21)] = sum;
@@ -1163,57 +1381,87 @@ __host__ __device__ inline CholSmem chol_layout(int n_c, int CS) {
   return L;
 }
 
-// x^(-1/2) for a positive FP64 pivot: Newton-Raphson on f(y) = y^-2 - x,
-// y <- y (3 - x y^2) / 2, seeded by the FP32 reciprocal square root.  Each step roughly
-// squares the relative error (2^-22 -> ~1e-13 -> below double rounding), at three
-// dependent FP64 operations per step -- shorter than a full FP64 square root and divide,
-// which on GB300 take ~680 and ~430 cycles in a dependent chain.
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return rsqrt(x);
-  double y = (double)rsqrtf((float)x);
-  const double h = 0.5 * x;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const double e = fma(-h * y, y, 0.5);     // 1/2 - x y^2 / 2
-    y = fma(y, e, y);
-  }
-  return y;
+// Reciprocal square root of a positive FP64 pivot by Halley's iteration for x^(-1/2):
+// with y0 an approximation and e = 1 - x y0^2, y = y0 (1 + e/2 + 3e^2/8) has relative
+// error O(e^3).  The seed is the FP32 hardware approximation (relative error ~2^-22), so
+// one step is below FP64 rounding.  The FP64 -> FP32 -> FP64 moves of the seed are done
+// on the bit patterns with integer operations: on GB300 every FP64-pipe instruction,
+// conversions included, costs ~64 cycles of a sub-partition's FP64 pipe whatever the
+// number of active lanes, and this leaves five on the pivot chain.  `ok` is false
+// unless x is positive and its exponent within 2^+-120 (then the result is meaningless
+// and the caller reports a non-positive-definite system).
+__device__ __forceinline__ double rsqrt_halley(double x, bool& ok) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const int ex = (hi >> 20) & 0x7ff;
+  ok = hi >= 0 && ex >= 1023 - 120 && ex <= 1023 + 120;
+  const int fe = min(max(ex - 1023 + 127, 1), 254);
+  const float xf = __int_as_float((fe << 23) | ((hi & 0xfffff) << 3) | (int)(lo >> 29));
+  const int rb = __float_as_int(rsqrtf(xf));
+  const int rexp = ((rb >> 23) & 0xff) - 127 + 1023;
+  const double y0 = __hiloint2double((rexp << 20) | ((rb & 0x7fffff) >> 3), (rb & 7) << 29);
+  const double t = x * y0;
+  const double e = fma(-t, y0, 1.0);
+  const double q = e * fma(0.375, e, 0.5);
+  return fma(y0, q, y0);
 }
 
-// Factor the 8x8 block D (row stride NP) in place with warp 0 (lane i holds row i in
-// registers) and push L_kk, the reciprocals of its diagonal and a non-PD flag to every
-// CTA of the cluster.  rdiag (may be null) keeps the reciprocals for the owner.
+// Entry-parallel layout of an 8x8 lower-triangular block in one warp: lanes 0-27 hold
+// the entries (i, j) with 1 <= j <= i (lane (i-1)i/2 + j-1); lanes 28-31 hold column 0,
+// rows 0-3 in slot 0 and rows 4-7 in slot 1.  A pivot then costs one scaling and one
+// update instruction instead of one update per remaining column.
+__device__ __forceinline__ int ep_lane(int i, int j) { return j >= 1 ? (i - 1) * i / 2 + (j - 1) : 28 + (i & 3); }
+__device__ __forceinline__ bool ep_slot1(int i, int j) { return j == 0 && i >= 4; }
+
+// Factor the 8x8 block D (row stride NP) in place with warp 0 and push L_kk, the
+// reciprocals of its diagonal and a non-PD flag to every CTA of the cluster.  rdiag (may
+// be null) keeps the reciprocals for the owner.
 __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk, int* flag, double* rdiag,
                                                  cooperative_groups::cluster_group& cluster, int CS) {
   const int tid = threadIdx.x;
   __shared__ double s_rs[kCB];
   if (tid < 32) {
-    const int i = tid;
-    double a[kCB];
-#pragma unroll
-    for (int j = 0; j < kCB; ++j) a[j] = (i < kCB && j <= i) ? D[i * NP + j] : 0.0;
+    const int lane = tid;
+    int i0, j0;                                    // slot-0 entry of this lane
+    if (lane < 28) {
+      i0 = 1;
+      while (i0 * (i0 + 1) / 2 <= lane) ++i0;
+      j0 = lane - (i0 - 1) * i0 / 2 + 1;
+    } else {
+      i0 = lane - 28;
+      j0 = 0;
+    }
+    double v0 = D[i0 * NP + j0];
+    double v1 = lane >= 28 ? D[(lane - 24) * NP] : 0.0;
     bool bad = false;
 #pragma unroll
     for (int c = 0; c < kCB; ++c) {
-      const double piv = __shfl_sync(0xffffffffu, a[c], c);
-      if (!(piv > 0.0) || !isfinite(piv)) bad = true;
-      const double rs = rsqrt_nr(fmax(piv, 1e-300));
-      double l = 0.0;
-      if (i == c) l = piv * rs;
-      else if (i > c && i < kCB) l = a[c] * rs;
-      a[c] = (i >= c) ? l : a[c];
-      if (i == c) s_rs[c] = rs;
-#pragma unroll
-      for (int j = c + 1; j < kCB; ++j) {
-        const double ljc = __shfl_sync(0xffffffffu, l, j);
-        if (i >= j && i < kCB) a[j] = fma(-l, ljc, a[j]);
+      const double piv = __shfl_sync(0xffffffffu, v0, ep_lane(c, c));
+      bool ok;
+      const double rs = rsqrt_halley(piv, ok);
+      bad |= !ok;
+      if (lane == 0) s_rs[c] = rs;
+      // scale column c: L_rc = a_rc / sqrt(piv) (the diagonal: piv rs)
+      if (c == 0) {
+        if (lane >= 28) {
+          v0 *= rs;
+          v1 *= rs;
+        }
+      } else if (j0 == c && lane < 28) {
+        v0 *= rs;
       }
+      // update the entries right of column c: a_ij -= L_ic L_jc
+      const int la = ep_lane(i0, c), lb = ep_lane(j0, c);
+      const double xa0 = __shfl_sync(0xffffffffu, v0, la), xa1 = __shfl_sync(0xffffffffu, v1, la);
+      const double xb0 = __shfl_sync(0xffffffffu, v0, lb), xb1 = __shfl_sync(0xffffffffu, v1, lb);
+      const double lic = ep_slot1(i0, c) ? xa1 : xa0;
+      const double ljc = ep_slot1(j0, c) ? xb1 : xb0;
+      if (lane < 28 && j0 > c) v0 = fma(-lic, ljc, v0);
     }
-    if (i < kCB)
-#pragma unroll
-      for (int j = 0; j < kCB; ++j)
-        if (j <= i) D[i * NP + j] = a[j];
-    if (i == 0 && bad) *flag = 1;
+    D[i0 * NP + j0] = v0;
+    if (lane >= 28) D[(lane - 24) * NP] = v1;
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0 && bad) *flag = 1;
   }
   __syncthreads();
   if (rdiag && tid < kCB) rdiag[tid] = s_rs[tid];
@@ -1351,31 +1599,31 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   for (int k = 0; k < NB; ++k) {
     cluster.sync();                                // L_kk (and flag) visible everywhere
     if (*flag) break;
-    // 1. TRSM of own block rows below k, and of the right-hand side on CTA 0
+    // 1. TRSM of own block rows below k, and of the right-hand side on CTA 0: solve
+    //    t L_kk^T = a for each row, entry-parallel (8 lanes per row, one column each;
+    //    per column one scaling and one update instruction)
     const double* linvd = lkk + kCB * kCB;
-    for (int e = tid; e < (Ls.nlb + 1) * kCB; e += nt) {
-      const int lb = e / kCB, i = e % kCB;
-      double* a;
-      if (lb < Ls.nlb) {
-        const int r = q + lb * CS;
-        if (r <= k || r >= NB) continue;
-        a = rowp(lb) + i * Ls.row_width(q, lb) + kCB * k;
-      } else {
-        if (q != 0 || i > 0) continue;
-        a = ybuf + kCB * k;
+    const int n_trsm = (Ls.nlb * kCB + 1) * kCB;
+    for (int e0 = 0; e0 < n_trsm; e0 += nt) {       // warp-uniform trip count
+      const int e = e0 + tid, row = e / kCB, c = e % kCB;
+      double* a = nullptr;
+      if (e < n_trsm) {
+        if (row < Ls.nlb * kCB) {
+          const int lb = row / kCB, i = row % kCB, r = q + lb * CS;
+          if (r > k && r < NB) a = rowp(lb) + i * Ls.row_width(q, lb) + kCB * k;
+        } else if (q == 0) {
+          a = ybuf + kCB * k;
+        }
       }
-      double t[kCB];
+      double t = a ? a[c] : 0.0;
+      const int base = (tid & 31) & ~(kCB - 1);
 #pragma unroll
-      for (int c = 0; c < kCB; ++c) t[c] = a[c];
-#pragma unroll
-      for (int c = 0; c < kCB; ++c) {
-        const double x = t[c] * linvd[c];
-        t[c] = x;
-#pragma unroll
-        for (int m = c + 1; m < kCB; ++m) t[m] = fma(-x, lkk[m * kCB + c], t[m]);
+      for (int m = 0; m < kCB; ++m) {
+        if (c == m) t *= linvd[m];
+        const double x = __shfl_sync(0xffffffffu, t, base + m);
+        if (c > m) t = fma(-x, lkk[c * kCB + m], t);
       }
-#pragma unroll
-      for (int c = 0; c < kCB; ++c) a[c] = t[c];
+      if (a) a[c] = t;
     }
     __syncthreads();
     for (int lb = 0; lb < Ls.nlb; ++lb) {          // push panel blocks L_rk to every CTA
@@ -1656,12 +1904,12 @@ __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
   }
   __syncthreads();
   // phase 2: dp_j = -V_j^-1 (g_l + acc); candidate landmark; predicted-reduction part
+  // (FP64 path: in FP64; mixed path: in FP32 with compensated sums, the new landmark
+  // position in FP64)
   double v[4] = {0.0, 0.0, 0.0, 0.0};
+  Acc<float> lp_f, st2_f;
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     const int j = tile.l0 + l;
-    const double* Vi = d.lm_Vinv + VINV_STRIDE * j;
-    const double tau = Vi[6];
-    const double* g = d.lm_g + 3 * j;
     Acc<T> w0, w1, w2;
     for (int q = d.lm_pair[j]; q < d.lm_pair[j + 1]; ++q) {
       const T* acc = s_acc + (q - tile.p0) * 3;
@@ -1669,26 +1917,56 @@ __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
       w1.add(acc[1]);
       w2.add(acc[2]);
     }
-    const double t0 = g[0] + w0.value(), t1 = g[1] + w1.value(), t2 = g[2] + w2.value();
-    const double dp0 = -(Vi[0] * t0 + Vi[1] * t1 + Vi[2] * t2);
-    const double dp1 = -(Vi[1] * t0 + Vi[3] * t1 + Vi[4] * t2);
-    const double dp2 = -(Vi[2] * t0 + Vi[4] * t1 + Vi[5] * t2);
-    const double* H = d.lm_H + 6 * j;
-    const double D0 = fmax(H[0], floor_), D1 = fmax(H[3], floor_), D2 = fmax(H[5], floor_);
-    v[1] += dp0 * ((lam * D0 + tau) * dp0 - g[0]) + dp1 * ((lam * D1 + tau) * dp1 - g[1]) +
-            dp2 * ((lam * D2 + tau) * dp2 - g[2]);
-    v[2] += dp0 * dp0 + dp1 * dp1 + dp2 * dp2;
-    d.dp[j * 3] = dp0;
-    d.dp[j * 3 + 1] = dp1;
-    d.dp[j * 3 + 2] = dp2;
     const double* p = d.lm[cur] + 3 * j;
     double* pn = d.lm[cur ^ 1] + 3 * j;
-    const double n0 = p[0] + dp0, n1 = p[1] + dp1, n2 = p[2] + dp2;
+    double n0, n1, n2;
+    if constexpr (sizeof(T) == 4) {
+      const float* Vi = reinterpret_cast<const float*>(d.lm_Vinv) + VINV_STRIDE * j;
+      const float tau = Vi[6];
+      const float g0 = (float)d.lm_g[3 * j], g1 = (float)d.lm_g[3 * j + 1], g2 = (float)d.lm_g[3 * j + 2];
+      const float t0 = g0 + w0.rounded(), t1 = g1 + w1.rounded(), t2 = g2 + w2.rounded();
+      const float dp0 = -(Vi[0] * t0 + Vi[1] * t1 + Vi[2] * t2);
+      const float dp1 = -(Vi[1] * t0 + Vi[3] * t1 + Vi[4] * t2);
+      const float dp2 = -(Vi[2] * t0 + Vi[4] * t1 + Vi[5] * t2);
+      const double* H = d.lm_H + 6 * j;
+      const float lamf = (float)lam, fl = (float)floor_;
+      const float D0 = fmaxf((float)H[0], fl), D1 = fmaxf((float)H[3], fl), D2 = fmaxf((float)H[5], fl);
+      lp_f.add(dp0 * ((lamf * D0 + tau) * dp0 - g0) + dp1 * ((lamf * D1 + tau) * dp1 - g1) +
+               dp2 * ((lamf * D2 + tau) * dp2 - g2));
+      st2_f.add(dp0 * dp0 + dp1 * dp1 + dp2 * dp2);
+      const double e0 = dp0, e1 = dp1, e2 = dp2;
+      d.dp[j * 3] = e0;
+      d.dp[j * 3 + 1] = e1;
+      d.dp[j * 3 + 2] = e2;
+      n0 = p[0] + e0;
+      n1 = p[1] + e1;
+      n2 = p[2] + e2;
+    } else {
+      const double* Vi = d.lm_Vinv + VINV_STRIDE * j;
+      const double tau = Vi[6];
+      const double* g = d.lm_g + 3 * j;
+      const double t0 = g[0] + w0.value(), t1 = g[1] + w1.value(), t2 = g[2] + w2.value();
+      const double dp0 = -(Vi[0] * t0 + Vi[1] * t1 + Vi[2] * t2);
+      const double dp1 = -(Vi[1] * t0 + Vi[3] * t1 + Vi[4] * t2);
+      const double dp2 = -(Vi[2] * t0 + Vi[4] * t1 + Vi[5] * t2);
+      const double* H = d.lm_H + 6 * j;
+      const double D0 = fmax(H[0], floor_), D1 = fmax(H[3], floor_), D2 = fmax(H[5], floor_);
+      v[1] += dp0 * ((lam * D0 + tau) * dp0 - g[0]) + dp1 * ((lam * D1 + tau) * dp1 - g[1]) +
+              dp2 * ((lam * D2 + tau) * dp2 - g[2]);
+      v[2] += dp0 * dp0 + dp1 * dp1 + dp2 * dp2;
+      d.dp[j * 3] = dp0;
+      d.dp[j * 3 + 1] = dp1;
+      d.dp[j * 3 + 2] = dp2;
+      n0 = p[0] + dp0;
+      n1 = p[1] + dp1;
+      n2 = p[2] + dp2;
+    }
     pn[0] = n0; pn[1] = n1; pn[2] = n2;
-    s_new[l * 3] = (T)n0; s_new[l * 3 + 1] = (T)n1; s_new[l * 3 + 2] = (T)n2;
-    if (d.mixed) {
+    const T m0 = (T)n0, m1 = (T)n1, m2 = (T)n2;
+    s_new[l * 3] = m0; s_new[l * 3 + 1] = m1; s_new[l * 3 + 2] = m2;
+    if constexpr (sizeof(T) == 4) {
       float* pf = d.lm_f[cur ^ 1] + 3 * j;
-      pf[0] = (float)n0; pf[1] = (float)n1; pf[2] = (float)n2;
+      pf[0] = m0; pf[1] = m1; pf[2] = m2;
     }
   }
   __syncthreads();
@@ -1702,8 +1980,17 @@ __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
     eval_pair<T, false>(pnew + a * POSE_STRIDE, s_new + 3 * (j - tile.l0), d.pair_obs[q], d.pair_obs[q + 1],
                         d.obs_cam, reinterpret_cast<const T*>(d.obs_uv), s_rig, hub, zmin, X, nullptr, nullptr, st);
   }
-  v[0] = st.cost.value();
-  block_sum4(v, s_red);
+  if constexpr (sizeof(T) == 4) {
+    DF f[3] = {st.cost.df(), lp_f.df(), st2_f.df()};
+    double o[3];
+    block_sum_df<3>(f, o, reinterpret_cast<float*>(s_red));
+    v[0] = o[0];
+    v[1] = o[1];
+    v[2] = o[2];
+  } else {
+    v[0] = st.cost.value();
+    block_sum4(v, s_red);
+  }
   if (threadIdx.x == 0) {
     d.bs_part[item * 4 + 0] = v[0];
     d.bs_part[item * 4 + 1] = v[1];
@@ -1787,6 +2074,7 @@ __device__ __forceinline__ void k_decide_body(const Dev& d, int item) {
       ctrl->need_lin = 0;
     }
     ctrl->nonpd = 0;
+    ctrl->maxdiag_kf = 0ull;                         // recomputed by k_kf_reduce every iteration
   }
 }
 

