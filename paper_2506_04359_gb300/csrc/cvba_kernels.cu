@@ -899,13 +899,14 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct_b(const Dev* __r
 //   S_ab += sum_j (U_ja - Y_ja W_ja^T) (a = b),   S_ab -= sum_j Y_ja W_jb^T (a > b),
 //   b_a  += sum_j Y_ja g_l,j,
 // (a keyframe of the window that does not observe a landmark contributes zero blocks).
-// Register-blocked: each working thread owns one 6x6 block (a, b), a >= b, of the window
-// and accumulates it over a share of the landmarks (G groups split the landmarks when the
-// window has fewer than 256 / G blocks): per landmark it reads Y_a and W_b (12 short
-// vectors) from the staged chunk and does 108 FMAs.  Sums run per chunk in T, then into
-// a compensated (Kahan) accumulator on the mixed path or a plain FP64 one; the groups are
-// combined in a fixed order, and the window is written as the tile's partial, summed over
-// tiles by k_rcs_reduce.
+// Register-blocked: a work item is half of a 6x6 block (a, b), a >= b (rows 3h..3h+2),
+// accumulated over a share of the tile's landmarks (G groups split the landmarks when the
+// window has few blocks; windows with more than 128 blocks take several passes over the
+// landmarks).  Per landmark an off-diagonal item reads three rows of Y_a and all of W_b
+// (9 short vectors) and does 54 FMAs.  Sums run per staged chunk in T, then into a
+// compensated (Kahan) accumulator on the mixed path or a plain FP64 one; groups are
+// combined in a fixed order and the window is written as the tile's partial, summed over
+// tiles by k_rcs_reduce.  About 100 registers on the mixed path: two CTAs per SM.
 constexpr int kStage = 76;         // per (landmark, block): Y[6][4] W[6][4] Dg[21] bY[6] pad
 template <typename T>
 struct GroupChunk {
@@ -935,10 +936,17 @@ __device__ __forceinline__ void load_row3<double>(const double* p, double& x, do
   z = p[2];
 }
 
+// Entries of a half block: off-diagonal (a > b): rows 3h..3h+2 x 6 columns, index
+// (r - 3h) * 6 + c.  Diagonal, h = 0: lower entries of rows 0-2 (6) then b rows 0-2 (3);
+// h = 1: lower entries of rows 3-5 (15) then b rows 3-5 (3).  In the staged Dg[21] the
+// lower entry (r, c) is r(r+1)/2 + c, so both halves are contiguous runs followed by bY.
+__device__ __forceinline__ int half_len(bool diag, int h) { return diag ? (h ? 18 : 9) : 18; }
+
 template <typename T>
 __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
   constexpr int CH = GroupChunk<T>::value;
   constexpr bool kKahan = sizeof(T) == 4;
+  using Out = typename std::conditional<sizeof(T) == 4, DF, double>::type;
   extern __shared__ __align__(16) double smem[];
   double* s_red = smem;                               // 64
   T* s_vinv = reinterpret_cast<T*>(s_red + 64);       // SCHUR_TILE_LMS * 6
@@ -957,137 +965,191 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
     for (int k = 0; k < 3; ++k) s_gl[l * 3 + k] = (T)d.lm_g[j * 3 + k];
   }
   if (span == 0) return;                             // landmarks seen only by the fixed keyframe
-  // work item: block (a, b) of the window and landmark group g
   const int nblk = span * (span + 1) / 2;            // <= 253 (span <= SPAN_MAX)
-  const int G = max(1, min(CH, SCHUR_THREADS / nblk));
-  const int t = threadIdx.x;
-  const bool working = t < nblk * G;
-  const int blk = t % nblk, g = t / nblk;
-  int ba = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
-  while (ba * (ba + 1) / 2 > blk) --ba;
-  while ((ba + 1) * (ba + 2) / 2 <= blk) ++ba;
-  const int bb = blk - ba * (ba + 1) / 2;
-  const bool diag = ba == bb;
-  T acc[36], cmp[36];
-#pragma unroll
-  for (int k = 0; k < 36; ++k) {
-    acc[k] = 0;
-    cmp[k] = 0;
-  }
+  const int n_half = 2 * nblk;
+  const int G = max(1, min(CH, SCHUR_THREADS / n_half));
+  const int n_items = n_half * G;                    // > SCHUR_THREADS only when G == 1
   const int stg_len = CH * span * kStage;
   const T* pose = st_pose<T>(d, d.ctrl->cur);
-  for (int c0 = 0; c0 < nl; c0 += CH) {
-    const int nc = min(CH, nl - c0);
-    __syncthreads();                                 // previous chunk consumed
-    for (int i = threadIdx.x; i < stg_len; i += blockDim.x) s_stg[i] = 0;
-    __syncthreads();
-    const int q0 = d.lm_pair[tile.l0 + c0], q1 = d.lm_pair[tile.l0 + c0 + nc];
-    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-      const int a = d.pair_kf[q];
-      const int pb = d.kf_pb[a];
-      if (pb < 0) continue;
-      const int l = d.pair_lm[q] - tile.l0;          // index in the tile
-      T W[18], Y[18], Dg[21], bY[6];
-      pair_schur_terms<T>(reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN, pose + a * POSE_STRIDE,
-                          s_vinv + l * 6, s_gl + l * 3, W, Y, Dg, bY);
-      T* st = s_stg + ((l - c0) * span + (pb - tile.k_lo)) * kStage;
+  Out* out = reinterpret_cast<Out*>(d.schur_part) + tile.part_off;
+  for (int it0 = 0; it0 < n_items; it0 += SCHUR_THREADS) {   // passes
+    const int t = it0 + threadIdx.x;
+    const bool working = t < n_items;
+    const int hb = t % n_half, g = t / n_half;
+    const int blk = hb >> 1, h = hb & 1;
+    int ba = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+    while (ba * (ba + 1) / 2 > blk) --ba;
+    while ((ba + 1) * (ba + 2) / 2 <= blk) ++ba;
+    const int bb = blk - ba * (ba + 1) / 2;
+    const bool diag = ba == bb;
+    const int doff = h ? 6 : 0;                      // diagonal: first staged Dg entry of the half
+    T acc[18], cmp[18];
 #pragma unroll
-      for (int r = 0; r < 6; ++r)
+    for (int k = 0; k < 18; ++k) {
+      acc[k] = 0;
+      cmp[k] = 0;
+    }
+    for (int c0 = 0; c0 < nl; c0 += CH) {
+      const int nc = min(CH, nl - c0);
+      __syncthreads();                               // previous chunk consumed
+      for (int i = threadIdx.x; i < stg_len * (int)sizeof(T) / 16; i += blockDim.x)   // 16-byte stores
+        reinterpret_cast<float4*>(s_stg)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      __syncthreads();
+      const int q0 = d.lm_pair[tile.l0 + c0], q1 = d.lm_pair[tile.l0 + c0 + nc];
+      for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        const int a = d.pair_kf[q];
+        const int pb = d.kf_pb[a];
+        if (pb < 0) continue;
+        const int l = d.pair_lm[q] - tile.l0;        // index in the tile
+        T W[18], Y[18], Dg[21], bY[6];
+        pair_schur_terms<T>(reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN, pose + a * POSE_STRIDE,
+                            s_vinv + l * 6, s_gl + l * 3, W, Y, Dg, bY);
+        T* st = s_stg + ((l - c0) * span + (pb - tile.k_lo)) * kStage;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          st[r * 4 + k] = Y[r * 3 + k];
-          st[24 + r * 4 + k] = W[r * 3 + k];
+        for (int r = 0; r < 6; ++r)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            st[r * 4 + k] = Y[r * 3 + k];
+            st[24 + r * 4 + k] = W[r * 3 + k];
+          }
+#pragma unroll
+        for (int k = 0; k < 21; ++k) st[48 + k] = Dg[k];
+#pragma unroll
+        for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
+      }
+      __syncthreads();
+      if (working) {
+        T part[18];
+#pragma unroll
+        for (int k = 0; k < 18; ++k) part[k] = 0;
+        for (int lr = g; lr < nc; lr += G) {
+          const T* base = s_stg + lr * span * kStage;
+          if (diag) {
+            const T* st = base + ba * kStage;
+            if (h == 0) {
+#pragma unroll
+              for (int k = 0; k < 6; ++k) part[k] += st[48 + k];
+#pragma unroll
+              for (int k = 0; k < 3; ++k) part[6 + k] += st[69 + k];
+            } else {
+#pragma unroll
+              for (int k = 0; k < 15; ++k) part[k] += st[48 + 6 + k];
+#pragma unroll
+              for (int k = 0; k < 3; ++k) part[15 + k] += st[72 + k];
+            }
+          } else {
+            const T* Ya = base + ba * kStage + 12 * h;
+            const T* Wb = base + bb * kStage + 24;
+            T w[18];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) load_row3<T>(Wb + 4 * c, w[3 * c], w[3 * c + 1], w[3 * c + 2]);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+              T y0, y1, y2;
+              load_row3<T>(Ya + 4 * r, y0, y1, y2);
+#pragma unroll
+              for (int c = 0; c < 6; ++c)
+                part[r * 6 + c] = fma(-y0, w[3 * c], fma(-y1, w[3 * c + 1], fma(-y2, w[3 * c + 2], part[r * 6 + c])));
+            }
+          }
         }
 #pragma unroll
-      for (int k = 0; k < 21; ++k) st[48 + k] = Dg[k];
-#pragma unroll
-      for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
-    }
-    __syncthreads();
-    if (working) {
-      T part[36];
-#pragma unroll
-      for (int k = 0; k < 36; ++k) part[k] = 0;
-      for (int lr = g; lr < nc; lr += G) {
-        const T* base = s_stg + lr * span * kStage;
-        if (diag) {
-          const T* st = base + ba * kStage + 48;
-#pragma unroll
-          for (int k = 0; k < 27; ++k) part[k] += st[k];
-        } else {
-          const T* Ya = base + ba * kStage;
-          const T* Wb = base + bb * kStage + 24;
-          T w[18];
-#pragma unroll
-          for (int c = 0; c < 6; ++c) load_row3<T>(Wb + 4 * c, w[3 * c], w[3 * c + 1], w[3 * c + 2]);
-#pragma unroll
-          for (int r = 0; r < 6; ++r) {
-            T y0, y1, y2;
-            load_row3<T>(Ya + 4 * r, y0, y1, y2);
-#pragma unroll
-            for (int c = 0; c < 6; ++c)
-              part[r * 6 + c] = fma(-y0, w[3 * c], fma(-y1, w[3 * c + 1], fma(-y2, w[3 * c + 2], part[r * 6 + c])));
+        for (int k = 0; k < 18; ++k) {
+          if (kKahan) {                              // acc - cmp is the running sum
+            const T yk = part[k] - cmp[k];
+            const T sm = acc[k] + yk;
+            cmp[k] = (sm - acc[k]) - yk;
+            acc[k] = sm;
+          } else {
+            acc[k] += part[k];
           }
         }
       }
+    }
+    if (G == 1) {
+      // one group: each item writes its own window entries
+      __syncthreads();
+      if (working) {
+        const int n_ent = half_len(diag, h);
 #pragma unroll
-      for (int k = 0; k < 36; ++k) {
-        if (kKahan) {                                // acc - cmp is the running sum
-          const T yk = part[k] - cmp[k];
-          const T s = acc[k] + yk;
-          cmp[k] = (s - acc[k]) - yk;
-          acc[k] = s;
-        } else {
-          acc[k] += part[k];
+        for (int k = 0; k < 18; ++k) {             // constant indices keep acc/cmp in registers
+          if (k >= n_ent) break;
+          int e;
+          if (!diag) {
+            const int r = 3 * h + k / 6, c = k % 6;
+            const int wr = 6 * ba + r;
+            e = wr * (wr + 1) / 2 + 6 * bb + c;
+          } else {
+            const int nlow = h ? 15 : 6;
+            if (k < nlow) {
+              int idx = doff + k, r = 0;             // lower entry idx -> (r, c)
+              while ((r + 1) * (r + 2) / 2 <= idx) ++r;
+              const int c = idx - r * (r + 1) / 2;
+              const int wr = 6 * ba + r;
+              e = wr * (wr + 1) / 2 + 6 * ba + c;
+            } else {
+              e = E + 6 * ba + 3 * h + (k - nlow);
+            }
+          }
+          if constexpr (sizeof(T) == 4)
+            out[e] = DF{(float)acc[k], -(float)cmp[k]};
+          else
+            out[e] = (double)acc[k];
         }
       }
-    }
-  }
-  // combine the landmark groups in a fixed order into the staging area as blocks
-  // [blk][36] (diagonal blocks: 21 lower entries of U - Y W^T, then 6 of b): FP64 on the
-  // FP64 path, compensated (hi, lo) floats on the mixed path
-  using Out = typename std::conditional<sizeof(T) == 4, DF, double>::type;
-  Out* s_out = reinterpret_cast<Out*>(s_stg);        // nblk * 36 entries of 8 bytes fit
-  for (int gg = 0; gg < G; ++gg) {
-    __syncthreads();
-    if (working && g == gg) {
-#pragma unroll
-      for (int k = 0; k < 36; ++k) {
-        if constexpr (sizeof(T) == 4) {
-          const DF v{(float)acc[k], -(float)cmp[k]};
-          s_out[blk * 36 + k] = gg == 0 ? v : df_add(s_out[blk * 36 + k], v);
-        } else {
-          const double v = (double)acc[k];
-          s_out[blk * 36 + k] = gg == 0 ? v : s_out[blk * 36 + k] + v;
-        }
-      }
-    }
-  }
-  __syncthreads();
-  // the window partial: lower triangle of the 6 span x 6 span window, row-major, then b
-  Out* out = reinterpret_cast<Out*>(d.schur_part) + tile.part_off;
-  for (int e = threadIdx.x; e < E + rows; e += blockDim.x) {
-    Out v;
-    if (e < E) {
-      int wr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-      while (wr * (wr + 1) / 2 > e) --wr;
-      while ((wr + 1) * (wr + 2) / 2 <= e) ++wr;
-      const int wc = e - wr * (wr + 1) / 2;
-      const int a = wr / 6, r = wr % 6, b = wc / 6, c = wc % 6;
-      const int kb = a * (a + 1) / 2 + b;
-      v = a == b ? s_out[kb * 36 + r * (r + 1) / 2 + c] : s_out[kb * 36 + r * 6 + c];
     } else {
-      const int wr = e - E, a = wr / 6;
-      v = s_out[(a * (a + 1) / 2 + a) * 36 + 21 + wr % 6];
+      // several groups (single pass): combine in a fixed order in the staging area
+      // [half block][18], then write the window in order
+      Out* s_out = reinterpret_cast<Out*>(s_stg);
+      for (int gg = 0; gg < G; ++gg) {
+        __syncthreads();
+        if (working && g == gg) {
+#pragma unroll
+          for (int k = 0; k < 18; ++k) {
+            if constexpr (sizeof(T) == 4) {
+              const DF v{(float)acc[k], -(float)cmp[k]};
+              s_out[hb * 18 + k] = gg == 0 ? v : df_add(s_out[hb * 18 + k], v);
+            } else {
+              const double v = (double)acc[k];
+              s_out[hb * 18 + k] = gg == 0 ? v : s_out[hb * 18 + k] + v;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < E + rows; e += blockDim.x) {
+        int src;
+        if (e < E) {
+          int wr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+          while (wr * (wr + 1) / 2 > e) --wr;
+          while ((wr + 1) * (wr + 2) / 2 <= e) ++wr;
+          const int wc = e - wr * (wr + 1) / 2;
+          const int a = wr / 6, r = wr % 6, b = wc / 6, c = wc % 6;
+          const int kb = a * (a + 1) / 2 + b;
+          if (a != b) {
+            src = (2 * kb + r / 3) * 18 + (r % 3) * 6 + c;
+          } else {
+            const int idx = r * (r + 1) / 2 + c;     // lower entry of the diagonal block
+            src = idx < 6 ? (2 * kb) * 18 + idx : (2 * kb + 1) * 18 + (idx - 6);
+          }
+        } else {
+          const int wr = e - E, a = wr / 6, r = wr % 6;
+          const int kb = a * (a + 1) / 2 + a;
+          src = r < 3 ? (2 * kb) * 18 + 6 + r : (2 * kb + 1) * 18 + 15 + (r - 3);
+        }
+        out[e] = s_out[src];
+      }
     }
-    out[e] = v;
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group(Dev d) { k_schur_group_body<T>(d, blockIdx.x); }
+__global__ void __launch_bounds__(SCHUR_THREADS, sizeof(T) == 4 ? 2 : 1) k_schur_group(Dev d) {
+  k_schur_group_body<T>(d, blockIdx.x);
+}
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_group_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(SCHUR_THREADS, sizeof(T) == 4 ? 2 : 1)
+    k_schur_group_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
