@@ -35,8 +35,10 @@ struct Ctrl {
   int pad_;
   double lam, nu;     // LM damping state
   double huber, zmin; // solve options
-  double pred_p;      // pose part of d^T (lam D d - g)
-  double step2_p;     // ||dc||^2
+  double pred_part[16];   // pose part of d^T (lam D d - g), one partial per Cholesky CTA
+  double step2_part[16];  // ||dc||^2, likewise
+  int n_parts;            // partials written by this iteration's factorisation
+  int pad2_;
   unsigned long long maxdiag_lm;   // bit pattern of max landmark diag(H) (non-negative double)
   unsigned long long maxdiag_kf;   // bit pattern of max keyframe diag(H), set by k_kf_reduce
   int refine_max;     // iterative-refinement corrections allowed per RCS solve

@@ -32,7 +32,6 @@ namespace cvba {
 namespace {
 
 constexpr double kDiagFloor = 1e-12;   // Marquardt floor relative to max(diag H)
-constexpr double kTaylorTheta = 1e-4;  // Exp uses its Taylor series below this angle
 
 // ------------------------------------------------------------------ reductions
 
@@ -342,38 +341,110 @@ __device__ __forceinline__ void pose_info(const T M[9], const T X[3], T U[36]) {
 
 // --------------------------------------------------------------- SE(3) update
 
-__device__ void pose_plus(const double* T0, const double* xi, double* T1) {
-  const double rho[3] = {xi[0], xi[1], xi[2]};
-  const double ph[3] = {xi[3], xi[4], xi[5]};
-  const double th2 = ph[0] * ph[0] + ph[1] * ph[1] + ph[2] * ph[2];
-  const double th = sqrt(th2);
-  double A, B, C;
-  if (th < kTaylorTheta) {
-    A = 1.0 - th2 / 6.0;
-    B = 0.5 - th2 / 24.0;
-    C = 1.0 / 6.0 - th2 / 120.0;
-  } else {
-    const double s = sin(th), c = cos(th);
-    A = s / th;
-    B = (1.0 - c) / th2;
-    C = (th - s) / (th2 * th);
+// Candidate pose Exp(xi) T0 computed by a group of 16 lanes (lane gl of the group; both
+// groups of the warp call it together; `act` false: shuffles only).  Lanes 0-8 produce the
+// rotation entries, lanes 9-11 the translation, so each step is one warp instruction for
+// all entries: on GB300 an FP64 instruction occupies its sub-partition's FP64 pipe for
+// ~64 cycles whatever the number of active lanes.  For theta < 0.1 the coefficients
+// A = sin t / t, B = (1 - cos t) / t^2, C = (t - sin t) / t^3 come from their Taylor
+// series in t^2 up to t^10 (truncation < 2e-19), computed by lanes 0, 1, 2 in parallel;
+// otherwise from sin and cos.  fixed: copy T0.
+__constant__ double c_exp_series[3][6] = {
+    {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0, -1.0 / 39916800.0},
+    {0.5, -1.0 / 24.0, 1.0 / 720.0, -1.0 / 40320.0, 1.0 / 3628800.0, -1.0 / 479001600.0},
+    {1.0 / 6.0, -1.0 / 120.0, 1.0 / 5040.0, -1.0 / 362880.0, 1.0 / 39916800.0, -1.0 / 6227020800.0}};
+
+__device__ __forceinline__ double sel3(const double v[3], int k) { return k == 0 ? v[0] : (k == 1 ? v[1] : v[2]); }
+
+__device__ __forceinline__ void pose_plus_group16(const double* T0, const double* xi, double* T1, float* F1,
+                                                  bool act, bool fixed, int gl) {
+  double ph[3] = {0.0, 0.0, 0.0}, rho[3] = {0.0, 0.0, 0.0};
+  if (act && !fixed)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      rho[k] = xi[k];
+      ph[k] = xi[3 + k];
+    }
+  const double th2 = fma(ph[2], ph[2], fma(ph[1], ph[1], ph[0] * ph[0]));
+  // th2 >= 0: compare bit patterns as integers (no FP64 compare)
+  const bool series = __double_as_longlong(th2) < __double_as_longlong(0.01);
+  double v = 0.0;
+  if (series) {
+    const int w = gl % 3;
+    v = c_exp_series[w][5];
+#pragma unroll
+    for (int k = 4; k >= 0; --k) v = fma(v, th2, c_exp_series[w][k]);
   }
-  const double P[9] = {0.0, -ph[2], ph[1], ph[2], 0.0, -ph[0], -ph[1], ph[0], 0.0};
-  double P2[9];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c) P2[r * 3 + c] = P[r * 3] * P[c] + P[r * 3 + 1] * P[3 + c] + P[r * 3 + 2] * P[6 + c];
-  double Re[9], V[9];
-  for (int k = 0; k < 9; ++k) {
-    const double I = (k % 4 == 0) ? 1.0 : 0.0;
-    Re[k] = I + A * P[k] + B * P2[k];
-    V[k] = I + B * P[k] + C * P2[k];
+  const double As = __shfl_sync(0xffffffffu, v, 0, 16);
+  const double Bs = __shfl_sync(0xffffffffu, v, 1, 16);
+  const double Cs = __shfl_sync(0xffffffffu, v, 2, 16);
+  double A = As, B = Bs, C = Cs;
+  if (!series) {
+    const double th = sqrt(th2);
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    A = sn / th;
+    B = (1.0 - cs) / th2;
+    C = (th - sn) / (th2 * th);
   }
-  double te[3];
-  for (int r = 0; r < 3; ++r) te[r] = V[r * 3] * rho[0] + V[r * 3 + 1] * rho[1] + V[r * 3 + 2] * rho[2];
-  for (int r = 0; r < 3; ++r) {
-    for (int c = 0; c < 3; ++c)
-      T1[r * 3 + c] = Re[r * 3] * T0[c] + Re[r * 3 + 1] * T0[3 + c] + Re[r * 3 + 2] * T0[6 + c];
-    T1[9 + r] = Re[r * 3] * T0[9] + Re[r * 3 + 1] * T0[10] + Re[r * 3 + 2] * T0[11] + te[r];
+  // rotation part, lanes 0-8: entry (r, c) of Re = I + A [ph]x + B [ph]x^2
+  const int r = gl < 9 ? gl / 3 : (gl < 12 ? gl - 9 : 0), c = gl < 9 ? gl % 3 : 0;
+  double Kx = 0.0;                                 // [ph]x (r, c)
+  if (r == 0 && c == 1) Kx = -ph[2];
+  if (r == 0 && c == 2) Kx = ph[1];
+  if (r == 1 && c == 0) Kx = ph[2];
+  if (r == 1 && c == 2) Kx = -ph[0];
+  if (r == 2 && c == 0) Kx = -ph[1];
+  if (r == 2 && c == 1) Kx = ph[0];
+  const double dg = (r == c) ? 1.0 : 0.0;
+  const double K2 = fma(sel3(ph, r), sel3(ph, c), (r == c) ? -th2 : 0.0);   // [ph]x^2 = ph ph^T - th2 I
+  const double Re = fma(A, Kx, fma(B, K2, dg));
+  // R1 (r, c) = sum_m Re(r, m) T0(m, c), lanes 0-8
+  const double e0 = __shfl_sync(0xffffffffu, Re, 3 * r, 16);
+  const double e1 = __shfl_sync(0xffffffffu, Re, 3 * r + 1, 16);
+  const double e2 = __shfl_sync(0xffffffffu, Re, 3 * r + 2, 16);
+  double t00 = 0.0, t01 = 0.0, t02 = 0.0;
+  if (act) {
+    if (gl < 9) {
+      t00 = T0[c];
+      t01 = T0[3 + c];
+      t02 = T0[6 + c];
+    } else {
+      t00 = T0[9];
+      t01 = T0[10];
+      t02 = T0[11];
+    }
+  }
+  const double rt = fma(e2, t02, fma(e1, t01, e0 * t00));        // (Re T0)(r, c) or (Re t0)_r
+  // translation, lanes 9-11: t1_r = (Re t0)_r + rho_r + B (ph x rho)_r + C (ph x (ph x rho))_r
+  const int r1 = (r + 1) % 3, r2 = (r + 2) % 3;
+  const double p1 = sel3(ph, r1), p2 = sel3(ph, r2);
+  const double u = fma(p1, sel3(rho, r2), -p2 * sel3(rho, r1));  // (ph x rho)_r on lanes 9-11
+  const double u1 = __shfl_sync(0xffffffffu, u, 9 + r1, 16);
+  const double u2 = __shfl_sync(0xffffffffu, u, 9 + r2, 16);
+  const double w = fma(p1, u2, -p2 * u1);
+  const double t1 = fma(C, w, fma(B, u, rt + sel3(rho, r)));
+  if (act && gl < 12) {
+    double o;
+    if (fixed) o = T0[gl];
+    else o = gl < 9 ? rt : t1;
+    T1[gl] = o;
+    if (F1) F1[gl] = (float)o;
+  }
+}
+
+// Candidate poses of all keyframes: keyframe (CTA q of CS, 16-lane group g) = q + CS g,
+// whole warps in step (every lane takes part in the group shuffles).
+__device__ __forceinline__ void pose_candidates(const Dev& d, int q, int CS) {
+  const int cur = d.ctrl->cur;
+  const int groups = blockDim.x / 16;
+  for (int base = 0; base < d.K; base += CS * groups) {
+    const int a = base + (int)(threadIdx.x / 16) * CS + q;
+    const bool act = a < d.K;
+    const int ac = act ? a : 0;
+    const int pb = d.kf_pb[ac];
+    pose_plus_group16(d.pose[cur] + ac * POSE_STRIDE, d.dc + 6 * max(pb, 0), d.pose[cur ^ 1] + ac * POSE_STRIDE,
+                      d.mixed ? d.pose_f[cur ^ 1] + ac * POSE_STRIDE : nullptr, act, pb < 0, threadIdx.x & 15);
   }
 }
 
@@ -402,8 +473,7 @@ __device__ __forceinline__ void solve_init_body(const Dev& d, double lam0, doubl
     }
     c->huber = huber;
     c->zmin = zmin;
-    c->pred_p = 0.0;
-    c->step2_p = 0.0;
+    c->n_parts = 0;
     c->maxdiag_lm = 0ull;
     c->maxdiag_kf = 0ull;
     c->refine_max = refine;
@@ -1347,25 +1417,12 @@ __device__ __forceinline__ void k_chol_body(const Dev& d, int item) {
   }
   block_sum4(v, s_red);
   if (tid == 0) {
-    ctrl->pred_p = v[0];
-    ctrl->step2_p = v[1];
+    ctrl->pred_part[0] = v[0];
+    ctrl->step2_part[0] = v[1];
+    ctrl->n_parts = 1;
   }
   __syncthreads();
-  const int cur = ctrl->cur;
-  for (int a = tid; a < d.K; a += nt) {
-    const double* T0 = d.pose[cur] + a * POSE_STRIDE;
-    double* T1 = d.pose[cur ^ 1] + a * POSE_STRIDE;
-    const int pb = d.kf_pb[a];
-    if (pb < 0) {
-      for (int k = 0; k < POSE_STRIDE; ++k) T1[k] = T0[k];
-    } else {
-      pose_plus(T0, d.dc + 6 * pb, T1);
-    }
-    if (d.mixed) {
-      float* F1 = d.pose_f[cur ^ 1] + a * POSE_STRIDE;
-      for (int k = 0; k < POSE_STRIDE; ++k) F1[k] = (float)T1[k];
-    }
-  }
+  pose_candidates(d, 0, 1);
   if (d.mixed)
     for (int i = threadIdx.x; i < d.n_c; i += blockDim.x) d.dc_f[i] = (float)d.dc[i];
 }
@@ -1591,6 +1648,17 @@ __device__ __forceinline__ void chol_backward(const Dev& d, const CholSmem& Ls, 
   }
 }
 
+// |x| to FP32 with a relative error below 2^-20 using integer operations only (no FP64
+// pipe instruction): exponent rebiased, mantissa truncated; below the FP32 normal range
+// gives 0, above it +inf (NaN in gives +inf or NaN).
+__device__ __forceinline__ float abs_f32_approx(double x) {
+  const int hi = __double2hiint(x) & 0x7fffffff;
+  const int fe = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  if (fe <= 0) return 0.f;
+  if (fe >= 255) return __int_as_float(0x7f800000);
+  return __int_as_float((fe << 23) | ((hi & 0xfffff) << 3));
+}
+
 __device__ __forceinline__ double rcs_rhs(const Dev& d, int i) {
   const int pb = i / 6, comp = i % 6;
   const int kf = pb < d.fixed_kf ? pb : pb + 1;
@@ -1782,10 +1850,11 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   // norms, eps = 2^-53) or after refine_max corrections dc += A^-1 r.
   const int refine_max = ctrl->refine_max;
   for (int it_r = 0; it_r < refine_max; ++it_r) {
-    // residual of own rows, one warp per row; the rows' entries of ybuf hold r
+    // residual of own rows, one warp per row; the rows' entries of ybuf hold r.  The
+    // norms only feed the stopping test and the reported backward error: kept in FP32.
     {
       const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-      double m_r = 0.0, m_a = 0.0, m_x = 0.0, m_b = 0.0;
+      float m_r = 0.f, m_a = 0.f, m_x = 0.f, m_b = 0.f;
       for (int e = warp; e < Ls.nlb * kCB; e += nw) {
         const int lb = e / kCB, i = e % kCB, gi = kCB * (q + lb * CS) + i;
         if (gi >= NP) continue;
@@ -1793,49 +1862,53 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
           if (lane == 0) ybuf[gi] = 0.0;
           continue;
         }
-        double s = 0.0, sa = 0.0;
+        double s = 0.0;
+        float sa = 0.f;
+#pragma unroll 4
         for (int j = lane; j < n; j += 32) {
           double a = j <= gi ? d.S[(size_t)gi * n + j] : d.S[(size_t)j * n + gi];
           if (j == gi) a += rcs_damp(d, gi, lam, floor_);
           s = fma(a, d.dc[j], s);
-          sa += fabs(a);
+          sa += abs_f32_approx(a);
         }
         s = warp_sum(s);
-        sa = warp_sum(sa);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sa += __shfl_xor_sync(0xffffffffu, sa, o);
         const double b = rcs_rhs(d, gi), r = b - s;
         if (lane == 0) ybuf[gi] = r;
-        m_r = fmax(m_r, fabs(r));
-        m_a = fmax(m_a, sa);
-        m_x = fmax(m_x, fabs(d.dc[gi]));
-        m_b = fmax(m_b, fabs(b));
+        m_r = fmaxf(m_r, abs_f32_approx(r));
+        m_a = fmaxf(m_a, sa);
+        m_x = fmaxf(m_x, abs_f32_approx(d.dc[gi]));
+        m_b = fmaxf(m_b, abs_f32_approx(b));
       }
+      float* redf = reinterpret_cast<float*>(red + 32);
       if (lane == 0) {
-        red[32 + warp] = m_r;
-        red[64 + warp] = m_a;
-        red[96 + warp] = m_x;
-        red[48 + warp] = m_b;
+        redf[warp] = m_r;
+        redf[32 + warp] = m_a;
+        redf[64 + warp] = m_x;
+        redf[96 + warp] = m_b;
       }
       __syncthreads();
       if (tid < CS * 4) {                          // push this CTA's maxima to every CTA
         const int dst = tid / 4, k = tid % 4;
-        const int base = k == 0 ? 32 : k == 1 ? 64 : k == 2 ? 96 : 48;
-        double v = 0.0;
-        for (int w = 0; w < nw; ++w) v = fmax(v, red[base + w]);
-        cluster.map_shared_rank(nrm, dst)[q * 4 + k] = v;
+        float v = 0.f;
+        for (int w = 0; w < nw; ++w) v = fmaxf(v, redf[32 * k + w]);
+        reinterpret_cast<float*>(cluster.map_shared_rank(nrm, dst))[q * 4 + k] = v;
       }
     }
     for (int e = tid; e < NP; e += nt) acc[e] = 0.0;
     for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
     cluster.sync();                                // norms and residual rows visible
-    double rn = 0.0, an = 0.0, xn = 0.0, bn = 0.0;
+    const float* nrmf = reinterpret_cast<const float*>(nrm);
+    float rn = 0.f, an = 0.f, xn = 0.f, bn = 0.f;
     for (int c = 0; c < CS; ++c) {
-      rn = fmax(rn, nrm[c * 4]);
-      an = fmax(an, nrm[c * 4 + 1]);
-      xn = fmax(xn, nrm[c * 4 + 2]);
-      bn = fmax(bn, nrm[c * 4 + 3]);
+      rn = fmaxf(rn, nrmf[c * 4]);
+      an = fmaxf(an, nrmf[c * 4 + 1]);
+      xn = fmaxf(xn, nrmf[c * 4 + 2]);
+      bn = fmaxf(bn, nrmf[c * 4 + 3]);
     }
-    if (it_r == 0 && q == 0 && tid == 0) ctrl->berr = rn / fmax(an * xn + bn, 1e-300);
-    if (rn <= an * xn * 0x1p-53 * sqrt((double)n)) break;   // uniform over the cluster
+    if (it_r == 0 && q == 0 && tid == 0) ctrl->berr = (double)(rn / fmaxf(an * xn + bn, 1e-30f));
+    if (rn <= an * xn * 0x1p-53f * sqrtf((float)n)) break;   // uniform over the cluster
     // forward sweep L y = r, right-looking: the owner of block k forms y_k = L_kk^-1 r_k
     // and pushes it to every CTA, which then updates its own rows below k
     for (int k = 0; k < NB; ++k) {
@@ -1867,38 +1940,44 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
     if (q == 0 && tid == 0) ctrl->refined = it_r + 1;
   }
 
-  // ---- epilogue: predicted-reduction part, step norm, candidate poses
-  if (q == 0) {
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int i = tid; i < n; i += nt) {
-      const int pb = i / 6, comp = i % 6;
-      const int kf = pb < d.fixed_kf ? pb : pb + 1;
-      const double D = fmax(d.kf_dp[kf * 6 + comp], floor_);
-      const double xi = d.dc[i];
-      v[0] += xi * (lam * D * xi - d.kf_gp[kf * 6 + comp]);
-      v[1] += xi * xi;
+  // ---- epilogue: predicted-reduction part and step norm of own rows (one partial per
+  // CTA, summed in order by k_decide), candidate poses
+  {
+    double v0 = 0.0, v1 = 0.0;
+    const int n_own = Ls.nlb * kCB;
+    for (int e = tid; e < n_own; e += nt) {
+      const int lb = e / kCB, i = kCB * (q + lb * CS) + e % kCB;
+      if (i < n) {
+        const int pb = i / 6, comp = i % 6;
+        const int kf = pb < d.fixed_kf ? pb : pb + 1;
+        const double D = fmax(d.kf_dp[kf * 6 + comp], floor_);
+        const double xi = d.dc[i];
+        v0 += xi * (lam * D * xi - d.kf_gp[kf * 6 + comp]);
+        v1 += xi * xi;
+      }
     }
-    block_sum4(v, red);
+    const int nw_own = min((n_own + 31) / 32, nt / 32);   // warps holding own rows
+    if ((tid >> 5) < nw_own) {
+      v0 = warp_sum(v0);
+      v1 = warp_sum(v1);
+      if ((tid & 31) == 0) {
+        red[2 * (tid >> 5)] = v0;
+        red[2 * (tid >> 5) + 1] = v1;
+      }
+    }
+    __syncthreads();
     if (tid == 0) {
-      ctrl->pred_p = v[0];
-      ctrl->step2_p = v[1];
+      double p0 = 0.0, p1 = 0.0;
+      for (int w = 0; w < nw_own; ++w) {             // fixed order
+        p0 += red[2 * w];
+        p1 += red[2 * w + 1];
+      }
+      ctrl->pred_part[q] = p0;
+      ctrl->step2_part[q] = p1;
+      if (q == 0) ctrl->n_parts = CS;
     }
   }
-  const int cur = ctrl->cur;
-  for (int a = q * nt + tid; a < d.K; a += CS * nt) {
-    const double* T0 = d.pose[cur] + a * POSE_STRIDE;
-    double* T1 = d.pose[cur ^ 1] + a * POSE_STRIDE;
-    const int pb = d.kf_pb[a];
-    if (pb < 0) {
-      for (int k = 0; k < POSE_STRIDE; ++k) T1[k] = T0[k];
-    } else {
-      pose_plus(T0, d.dc + 6 * pb, T1);
-    }
-    if (d.mixed) {
-      float* F1 = d.pose_f[cur ^ 1] + a * POSE_STRIDE;
-      for (int k = 0; k < POSE_STRIDE; ++k) F1[k] = (float)T1[k];
-    }
-  }
+  pose_candidates(d, q, CS);
   if (d.mixed)
     for (int i = q * nt + tid; i < d.n_c; i += CS * nt) d.dc_f[i] = (float)d.dc[i];
 }
@@ -2113,10 +2192,15 @@ __device__ __forceinline__ void k_decide_body(const Dev& d, int item) {
       rec.cost1 = rec.gain = rec.pred = rec.step_norm = CUDART_NAN;
     } else {
       const double F1 = bs[0];
-      const double L = 0.5 * (ctrl->pred_p + bs[1]);
+      double pp = 0.0, sp = 0.0;
+      for (int k = 0; k < ctrl->n_parts; ++k) {    // fixed order
+        pp += ctrl->pred_part[k];
+        sp += ctrl->step2_part[k];
+      }
+      const double L = 0.5 * (pp + bs[1]);
       rec.cost1 = F1;
       rec.pred = L;
-      rec.step_norm = sqrt(ctrl->step2_p + bs[2]);
+      rec.step_norm = sqrt(sp + bs[2]);
       rec.gain = L != 0.0 ? (F - F1) / L : CUDART_NAN;
       acc = L > 0.0 && isfinite(F1) && rec.gain > 0.0;
     }
