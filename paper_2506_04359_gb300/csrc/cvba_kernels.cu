@@ -1460,6 +1460,7 @@ __global__ void __launch_bounds__(CHOL_THREADS) k_chol_b(const Dev* __restrict__
 // writes x_k, and pushes the running contributions of block row k to the owners of blocks
 // < k.  All pushes are plain DSMEM stores made visible by the next cluster barrier.
 constexpr int kCB = 8;
+constexpr size_t kClusterSmemMaxBytes = 220 * 1024;   // dynamic shared memory of one Cholesky CTA
 
 struct CholSmem {
   int NP, NB, nlb, CS;
@@ -1467,7 +1468,7 @@ struct CholSmem {
   __host__ __device__ size_t rows_off() const { return 0; }
   __host__ __device__ size_t panel_off() const { return rows_off() + rows_len; }
   __host__ __device__ size_t lkk_off() const { return panel_off() + (size_t)NB * kCB * kCB; }
-  __host__ __device__ size_t y_off() const { return lkk_off() + kCB * kCB + kCB; }
+  __host__ __device__ size_t y_off() const { return lkk_off() + 2 * (kCB * kCB + kCB); }   // two L_kk buffers
   __host__ __device__ size_t acc_off() const { return y_off() + NP; }
   __host__ __device__ size_t contrib_off() const { return acc_off() + NP; }
   __host__ __device__ size_t linv_off() const { return contrib_off() + (size_t)nlb * CS * kCB; }
@@ -1475,7 +1476,16 @@ struct CholSmem {
   __host__ __device__ size_t nrm_off() const { return rdiag_off() + (size_t)nlb * kCB; }
   __host__ __device__ size_t red_off() const { return nrm_off() + (size_t)CS * 4; }
   __host__ __device__ size_t flag_off() const { return red_off() + 128; }
-  __host__ __device__ size_t doubles() const { return flag_off() + 8; }
+  // gathered factor on CTA 0 (small systems): packed lower block rows of all of L, then
+  // the inverses of all diagonal blocks
+  __host__ __device__ size_t gl_len() const { return (size_t)32 * NB * (NB + 1); }
+  __host__ __device__ size_t gl_off() const { return flag_off() + 8; }
+  __host__ __device__ size_t glinv_off() const { return gl_off() + gl_len(); }
+  __host__ __device__ size_t base_doubles() const { return flag_off() + 8; }
+  __host__ __device__ size_t doubles() const {
+    return gather ? glinv_off() + (size_t)NB * kCB * kCB : base_doubles();
+  }
+  bool gather;                                     // backward substitution on CTA 0
   // CTA q's lb-th block row is block row r = q + lb CS; only its columns [0, 8(r+1)) are
   // stored (the lower triangle), row-major with width 8(r+1), one block row after another.
   __host__ __device__ size_t row_off(int q, int lb) const {
@@ -1497,6 +1507,8 @@ __host__ __device__ inline CholSmem chol_layout(int n_c, int CS) {
     const size_t len = L.row_off(q, nb);
     if (len > L.rows_len) L.rows_len = len;
   }
+  L.gather = false;
+  L.gather = (L.base_doubles() + L.gl_len() + (size_t)L.NB * kCB * kCB) * sizeof(double) <= kClusterSmemMaxBytes;
   return L;
 }
 
@@ -1659,6 +1671,37 @@ __device__ __forceinline__ float abs_f32_approx(double x) {
   return __int_as_float((fe << 23) | ((hi & 0xfffff) << 3));
 }
 
+// Backward substitution L^T x = t by one CTA from the gathered factor G (packed lower
+// block rows) and the diagonal-block inverses GI: per block, from the last, x_k =
+// L_kk^-T t_k, then t_j -= (L_kj)^T x_k for the entries above.  t is overwritten; x goes
+// to d.dc; xs holds 8 doubles of CTA-local scratch.
+__device__ __forceinline__ void chol_backward_single(const Dev& d, const CholSmem& Ls, const double* G,
+                                                     const double* GI, double* t, double* xs) {
+  const int NB = Ls.NB, n = d.n_c, tid = threadIdx.x, nt = blockDim.x;
+  for (int k = NB - 1; k >= 0; --k) {
+    if (tid < kCB * kCB) {
+      const int i = tid / kCB, c = tid % kCB;
+      double v = GI[k * kCB * kCB + c * kCB + i] * t[kCB * k + c];
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 8);
+      if (c == 0) {
+        xs[i] = v;
+        if (kCB * k + i < n) d.dc[kCB * k + i] = v;
+      }
+    }
+    __syncthreads();
+    const double* Rk = G + (size_t)32 * k * (k + 1);
+    const int W = kCB * (k + 1);
+    for (int j = tid; j < kCB * k; j += nt) {
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < kCB; ++i) acc = fma(Rk[i * W + j], xs[i], acc);
+      t[j] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ double rcs_rhs(const Dev& d, int i) {
   const int pb = i / 6, comp = i % 6;
   const int kf = pb < d.fixed_kf ? pb : pb + 1;
@@ -1670,6 +1713,12 @@ __device__ __forceinline__ double rcs_damp(const Dev& d, int i, double lam, doub
   const int kf = pb < d.fixed_kf ? pb : pb + 1;
   return lam * fmax(d.kf_dp[kf * 6 + comp], floor_);
 }
+
+// Split-phase cluster barrier: arrive (release: this thread's earlier shared and DSMEM
+// writes become visible) and wait (acquire).  Every thread of every CTA calls both, in
+// alternation.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
 __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   namespace cg = cooperative_groups;
@@ -1684,7 +1733,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   const int NB = Ls.NB, NP = Ls.NP;
   double* rows = smem + Ls.rows_off();             // packed lower block rows of this CTA
   double* panel = smem + Ls.panel_off();           // [c][i][m] = L[8c+i][8k+m]
-  double* lkk = smem + Ls.lkk_off();               // [i][m], then 8 reciprocals of the diagonal
+  double* lkk0 = smem + Ls.lkk_off();              // two buffers: [i][m], then 8 reciprocals of the diagonal
   double* ybuf = smem + Ls.y_off();                // right-hand side row / y
   double* acc = smem + Ls.acc_off();               // backward contributions of own rows
   double* contrib = smem + Ls.contrib_off();       // [lb][from CTA][8]
@@ -1723,12 +1772,22 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
   if (tid == 0) *flag = 0;
   cluster.sync();
-  if (q == 0) chol_factor_push(rows, kCB, lkk, flag, rdiag, cluster, CS);   // block 0: CTA 0's first row block
+  if (q == 0) chol_factor_push(rows, kCB, lkk0, flag, rdiag, cluster, CS);   // block 0: CTA 0's first row block
+  cluster_arrive();                                // A_0
 
-  // ---- factorisation with the forward substitution fused
+  // ---- factorisation with the forward substitution fused.  Per step k two split
+  // barriers: A_k (L_kk pushed) and B_k (panel k pushed).  The owner of block k+1 factors
+  // it between its arrival at B_k and its wait there, so the factorisation does not wait
+  // for the whole cluster's panel exchange.  L_kk alternates between two buffers: the
+  // owner of k+1 may push while others still read L_kk.
+  bool broke = false;
   for (int k = 0; k < NB; ++k) {
-    cluster.sync();                                // L_kk (and flag) visible everywhere
-    if (*flag) break;
+    cluster_wait();                                // A_k: L_kk (and flag) visible everywhere
+    if (*flag) {                                   // uniform: pushed before A_k
+      broke = true;
+      break;
+    }
+    const double* lkk = lkk0 + (k & 1) * (kCB * kCB + kCB);
     // 1. TRSM of own block rows below k, and of the right-hand side on CTA 0: solve
     //    t L_kk^T = a for each row, entry-parallel (8 lanes per row, one column each;
     //    per column one scaling and one update instruction)
@@ -1766,23 +1825,26 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
         cluster.map_shared_rank(panel, dst)[(size_t)r * kCB * kCB + t] = R[i * W + kCB * k + m];
       }
     }
-    cluster.sync();                                // panel k visible everywhere
-    // 2a. look-ahead: owner of block k+1 updates and factors its diagonal block first
+    cluster_arrive();                              // B_k
+    // 2a. look-ahead: owner of block k+1 updates its diagonal block with its own L_{k+1,k}
+    //     and factors it
     if (k + 1 < NB && q == (k + 1) % CS) {
       const int lb = (k + 1) / CS;
       double* R = rowp(lb);
       const int W = Ls.row_width(q, lb);
-      const double* Lr = panel + (size_t)(k + 1) * kCB * kCB;
       for (int e = tid; e < kCB * kCB; e += nt) {
         const int i = e / kCB, j = e % kCB;
+        if (j > i) continue;
         double s = 0.0;
 #pragma unroll
-        for (int m = 0; m < kCB; ++m) s = fma(Lr[i * kCB + m], Lr[j * kCB + m], s);
+        for (int m = 0; m < kCB; ++m) s = fma(R[i * W + kCB * k + m], R[j * W + kCB * k + m], s);
         R[i * W + kCB * (k + 1) + j] -= s;
       }
       __syncthreads();
-      chol_factor_push(R + kCB * (k + 1), W, lkk, flag, rdiag + lb * kCB, cluster, CS);
+      chol_factor_push(R + kCB * (k + 1), W, lkk0 + ((k + 1) & 1) * (kCB * kCB + kCB), flag, rdiag + lb * kCB,
+                       cluster, CS);
     }
+    cluster_wait();                                // B_k: panel k visible everywhere
     // 2b. trailing update of own block rows: A_rc -= L_rk L_ck^T, c in (k, r]
     for (int lb = 0; lb < Ls.nlb; ++lb) {
       const int r = q + lb * CS;
@@ -1812,8 +1874,9 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
       }
     }
     __syncthreads();
+    cluster_arrive();                              // A_{k+1}
   }
-  cluster.sync();
+  if (!broke) cluster_wait();                      // A_NB: the factor complete everywhere
   if (*flag) {
     if (q == 0 && tid == 0) ctrl->nonpd = 1;
     return;
@@ -1835,15 +1898,34 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
 #pragma unroll
     for (int i = 0; i < kCB; ++i) linv[(lb * kCB + i) * kCB + j] = z[i];
   }
-  if (q == 0) {
-    for (int e = tid; e < CS * NP; e += nt) {
-      const int dst = e / NP, c = e % NP;
-      if (dst != 0) cluster.map_shared_rank(ybuf, dst)[c] = ybuf[c];
+  if (Ls.gather) {
+    // small system: own block rows and their diagonal inverses to CTA 0, which runs the
+    // backward substitution alone (no cluster barrier per block)
+    __syncthreads();
+    double* gl = smem + Ls.gl_off();
+    double* glinv = smem + Ls.glinv_off();
+    for (int lb = 0; lb < Ls.nlb; ++lb) {
+      const int r = q + lb * CS;
+      if (r >= NB) break;
+      const double* R = rowp(lb);
+      double* dst = cluster.map_shared_rank(gl, 0) + (size_t)32 * r * (r + 1);
+      for (int e = tid; e < kCB * kCB * (r + 1); e += nt) dst[e] = R[e];
+      double* dli = cluster.map_shared_rank(glinv, 0) + (size_t)r * kCB * kCB;
+      for (int e = tid; e < kCB * kCB; e += nt) dli[e] = linv[lb * kCB * kCB + e];
     }
+    cluster.sync();
+    if (q == 0) chol_backward_single(d, Ls, gl, glinv, ybuf, red);
+    cluster.sync();                                // dc visible everywhere
+  } else {
+    if (q == 0) {
+      for (int e = tid; e < CS * NP; e += nt) {
+        const int dst = e / NP, c = e % NP;
+        if (dst != 0) cluster.map_shared_rank(ybuf, dst)[c] = ybuf[c];
+      }
+    }
+    cluster.sync();
+    chol_backward(d, Ls, q, rows, ybuf, acc, contrib, linv, red, false, cluster);
   }
-  cluster.sync();
-
-  chol_backward(d, Ls, q, rows, ybuf, acc, contrib, linv, red, false, cluster);
 
   // ---- iterative refinement in FP64: r = rhs - A dc from the assembled S (global, lower
   // triangle), stopped by the backward-error test |r| <= |A| |dc| eps sqrt(n) (infinity
@@ -2305,7 +2387,7 @@ size_t backsub_smem(const Dev& d) {
 size_t eval_smem(const Dev& d) { return sizeof(double) * 128 + tsize(d) * d.C * RIG_STRIDE; }
 constexpr int kCholSmemMaxN = 160;
 size_t chol_smem(int n) { return sizeof(double) * ((size_t)n * n + n); }
-constexpr size_t kClusterSmemMax = 220 * 1024;
+constexpr size_t kClusterSmemMax = kClusterSmemMaxBytes;
 int g_cluster_max = 16;                         // largest cluster size the device launches
 
 // Cluster size for the distributed Cholesky, or 0 when the system is too large for the
