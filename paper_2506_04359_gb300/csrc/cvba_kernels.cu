@@ -2249,9 +2249,25 @@ __device__ void reduce_parts(const double* part, int n_tiles, double out[4], dou
 __device__ __forceinline__ void k_decide_body(const Dev& d, int item) {
   __shared__ double s_red[128];
   Ctrl* ctrl = d.ctrl;
+  // fixed-order sums of the tile partials: warp w < 7 takes value w (lin: cost, sum r^2,
+  // n_valid, n_inlier; candidate: cost, L part, |dp|^2), lane l the tiles l, l + 32, ...
+  // then a butterfly; the warps run on all four sub-partitions at once
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 7) {
+      const double* part = warp < 4 ? d.lin_part : d.bs_part;
+      const int k = warp < 4 ? warp : warp - 4;
+      double v = 0.0;
+      for (int t = lane; t < d.n_lin_tiles; t += 32) v += part[t * 4 + k];
+      v = warp_sum(v);
+      if (lane == 0) s_red[warp] = v;
+    }
+  }
+  __syncthreads();
   double lin[4], bs[4];
-  reduce_parts(d.lin_part, d.n_lin_tiles, lin, s_red);
-  reduce_parts(d.bs_part, d.n_lin_tiles, bs, s_red);
+  for (int k = 0; k < 4; ++k) lin[k] = s_red[k];
+  for (int k = 0; k < 3; ++k) bs[k] = s_red[4 + k];
+  bs[3] = 0.0;
   const int nonpd = ctrl->nonpd;
   __syncthreads();
   if (threadIdx.x == 0) {
