@@ -448,6 +448,14 @@ __device__ __forceinline__ void pose_candidates(const Dev& d, int q, int CS) {
   }
 }
 
+// Programmatic dependent launch: the iteration kernels are launched so that the next
+// kernel's launch overlaps this one's tail; each waits for its predecessor's completion
+// (and memory) before touching any memory, then lets its own successor launch.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // =================================================================== kernels
 
 // Per-window device view for the batched kernels: the CTA copies its window's Dev into
@@ -482,11 +490,11 @@ __device__ __forceinline__ void solve_init_body(const Dev& d, double lam0, doubl
   }
 }
 
-__global__ void k_solve_init(Dev d, double lam0, double huber, double zmin, int iters, int reset, int refine) {
+__global__ void k_solve_init(Dev d, double lam0, double huber, double zmin, int iters, int reset, int refine) { pdl_enter();
   solve_init_body(d, lam0, huber, zmin, iters, reset, refine);
 }
 __global__ void k_solve_init_b(const Dev* __restrict__ wins, double lam0, double huber, double zmin, int iters,
-                               int reset, int refine) {
+                               int reset, int refine) { pdl_enter();
   __shared__ Dev sd;
   load_dev(sd, wins + blockIdx.x);
   solve_init_body(sd, lam0, huber, zmin, iters, reset, refine);
@@ -623,9 +631,9 @@ __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) { k_lin_body<T>(d, blockIdx.x); }
+__global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) { pdl_enter(); k_lin_body<T>(d, blockIdx.x); }
 template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_lin_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(LIN_THREADS) k_lin_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -676,8 +684,8 @@ __device__ __forceinline__ void k_kf_reduce_body(const Dev& d, int item) {
   }
 }
 
-__global__ void __launch_bounds__(384) k_kf_reduce(Dev d) { k_kf_reduce_body(d, blockIdx.x); }
-__global__ void __launch_bounds__(384) k_kf_reduce_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(384) k_kf_reduce(Dev d) { pdl_enter(); k_kf_reduce_body(d, blockIdx.x); }
+__global__ void __launch_bounds__(384) k_kf_reduce_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -954,9 +962,9 @@ __device__ __forceinline__ void k_schur_direct_body(const Dev& d, int item) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct(Dev d) { k_schur_direct_body<T>(d, blockIdx.x); }
+__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct(Dev d) { pdl_enter(); k_schur_direct_body<T>(d, blockIdx.x); }
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -1214,12 +1222,12 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS, sizeof(T) == 4 ? 2 : 1) k_schur_group(Dev d) {
+__global__ void __launch_bounds__(SCHUR_THREADS, sizeof(T) == 4 ? 2 : 1) k_schur_group(Dev d) { pdl_enter();
   k_schur_group_body<T>(d, blockIdx.x);
 }
 template <typename T>
 __global__ void __launch_bounds__(SCHUR_THREADS, sizeof(T) == 4 ? 2 : 1)
-    k_schur_group_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+    k_schur_group_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -1316,8 +1324,8 @@ __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) { k_rcs_reduce_body(d, blockIdx.x); }
-__global__ void __launch_bounds__(256) k_rcs_reduce_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) { pdl_enter(); k_rcs_reduce_body(d, blockIdx.x); }
+__global__ void __launch_bounds__(256) k_rcs_reduce_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -1428,9 +1436,9 @@ __device__ __forceinline__ void k_chol_body(const Dev& d, int item) {
 }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(CHOL_THREADS) k_chol(Dev d) { k_chol_body<SMEM>(d, blockIdx.x); }
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol(Dev d) { pdl_enter(); k_chol_body<SMEM>(d, blockIdx.x); }
 template <bool SMEM>
-__global__ void __launch_bounds__(CHOL_THREADS) k_chol_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(CHOL_THREADS) k_chol_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -2064,9 +2072,9 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
     for (int i = q * nt + tid; i < d.n_c; i += CS * nt) d.dc_f[i] = (float)d.dc[i];
 }
 
-__global__ void __launch_bounds__(256) k_chol_cluster(Dev d) { chol_cluster_body(d); }
+__global__ void __launch_bounds__(256) k_chol_cluster(Dev d) { pdl_enter(); chol_cluster_body(d); }
 // Batched: one cluster per window (cluster index = window).
-__global__ void __launch_bounds__(256) k_chol_cluster_b(const Dev* __restrict__ wins) {
+__global__ void __launch_bounds__(256) k_chol_cluster_b(const Dev* __restrict__ wins) { pdl_enter();
   __shared__ Dev sd;
   load_dev(sd, wins + blockIdx.x / cooperative_groups::this_cluster().dim_blocks().x);
   if (sd.chol_fallback) return;                    // uniform over the cluster
@@ -2223,9 +2231,9 @@ __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) { k_backsub_body<T>(d, blockIdx.x); }
+__global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) { pdl_enter(); k_backsub_body<T>(d, blockIdx.x); }
 template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_backsub_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(LIN_THREADS) k_backsub_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -2322,8 +2330,8 @@ __device__ __forceinline__ void k_decide_body(const Dev& d, int item) {
   }
 }
 
-__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d) { k_decide_body(d, blockIdx.x); }
-__global__ void __launch_bounds__(DECIDE_THREADS) k_decide_b(const Dev* __restrict__ wins, const int2* __restrict__ items) {
+__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d) { pdl_enter(); k_decide_body(d, blockIdx.x); }
+__global__ void __launch_bounds__(DECIDE_THREADS) k_decide_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -2420,6 +2428,35 @@ int chol_cluster_size(int n_c) {
 
 // ================================================================ launchers
 
+// Programmatic dependent launch for the iteration kernels (captured into the solve graph as
+// programmatic edges).  cluster > 0 adds a cluster dimension.
+bool g_pdl = true;
+template <typename... P, typename... A>
+cudaError_t launch_ex(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, int cluster, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  int na = 0;
+  if (cluster > 0) {
+    at[na].id = cudaLaunchAttributeClusterDimension;
+    at[na].val.clusterDim.x = cluster;
+    at[na].val.clusterDim.y = 1;
+    at[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (g_pdl) {
+    at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
+  cfg.attrs = at;
+  cfg.numAttrs = na;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Opt a kernel into `want` bytes of dynamic shared memory, clamped to what is left of the
 // 227 KB per-CTA limit after its static shared memory (the batched kernels stage their
 // window's Dev there).  Launches request far less than the clamp except the Cholesky ones,
@@ -2500,64 +2537,54 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
   if ((e = mark(0)) != cudaSuccess) return e;
   if (d.mixed)
-    k_lin<float><<<d.n_lin_tiles, LIN_THREADS, lin_smem(d), s>>>(d);
+    { if ((e = launch_ex(k_lin<float>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), lin_smem(d), s, 0, d)) != cudaSuccess) return e; }
   else
-    k_lin<double><<<d.n_lin_tiles, LIN_THREADS, lin_smem(d), s>>>(d);
+    { if ((e = launch_ex(k_lin<double>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), lin_smem(d), s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(1)) != cudaSuccess) return e;
-  k_kf_reduce<<<d.K, 384, 0, s>>>(d);
+  { if ((e = launch_ex(k_kf_reduce, dim3(d.K), dim3(384), 0, s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(2)) != cudaSuccess) return e;
   if (d.n_schur_tiles > 0) {
     const size_t sm = group_smem_bytes(d.max_span, d.mixed != 0);
     if (d.mixed)
-      k_schur_group<float><<<d.n_schur_tiles, SCHUR_THREADS, sm, s>>>(d);
+      { if ((e = launch_ex(k_schur_group<float>, dim3(d.n_schur_tiles), dim3(SCHUR_THREADS), sm, s, 0, d)) != cudaSuccess) return e; }
     else
-      k_schur_group<double><<<d.n_schur_tiles, SCHUR_THREADS, sm, s>>>(d);
+      { if ((e = launch_ex(k_schur_group<double>, dim3(d.n_schur_tiles), dim3(SCHUR_THREADS), sm, s, 0, d)) != cudaSuccess) return e; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = mark(3)) != cudaSuccess) return e;
-  k_rcs_reduce<<<d.n_blk, 256, 0, s>>>(d);
+  { if ((e = launch_ex(k_rcs_reduce, dim3(d.n_blk), dim3(256), 0, s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(4)) != cudaSuccess) return e;
   if (d.n_direct_tiles > 0) {
     if (d.mixed)
-      k_schur_direct<float><<<d.n_direct_tiles, SCHUR_THREADS, SchurSmem<float>::bytes(), s>>>(d);
+      { if ((e = launch_ex(k_schur_direct<float>, dim3(d.n_direct_tiles), dim3(SCHUR_THREADS), SchurSmem<float>::bytes(), s, 0, d)) != cudaSuccess) return e; }
     else
-      k_schur_direct<double><<<d.n_direct_tiles, SCHUR_THREADS, SchurSmem<double>::bytes(), s>>>(d);
+      { if ((e = launch_ex(k_schur_direct<double>, dim3(d.n_direct_tiles), dim3(SCHUR_THREADS), SchurSmem<double>::bytes(), s, 0, d)) != cudaSuccess) return e; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
 
   if ((e = mark(5)) != cudaSuccess) return e;
   if (chol_cluster_size(d.n_c) > 0) {
     const int CS = chol_cluster_size(d.n_c);
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(CS);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = chol_layout(d.n_c, CS).doubles() * sizeof(double);
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = CS;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if ((e = cudaLaunchKernelEx(&cfg, k_chol_cluster, d)) != cudaSuccess) return e;
+    if ((e = launch_ex(k_chol_cluster, dim3(CS), dim3(256), chol_layout(d.n_c, CS).doubles() * sizeof(double), s, CS,
+                       d)) != cudaSuccess)
+      return e;
   } else if (d.n_c <= kCholSmemMaxN) {
-    k_chol<true><<<1, CHOL_THREADS, chol_smem(d.n_c), s>>>(d);
+    { if ((e = launch_ex(k_chol<true>, dim3(1), dim3(CHOL_THREADS), chol_smem(d.n_c), s, 0, d)) != cudaSuccess) return e; }
   } else {
-    k_chol<false><<<1, CHOL_THREADS, 0, s>>>(d);
+    { if ((e = launch_ex(k_chol<false>, dim3(1), dim3(CHOL_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(6)) != cudaSuccess) return e;
   if (d.mixed)
-    k_backsub<float><<<d.n_lin_tiles, LIN_THREADS, backsub_smem(d), s>>>(d);
+    { if ((e = launch_ex(k_backsub<float>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), backsub_smem(d), s, 0, d)) != cudaSuccess) return e; }
   else
-    k_backsub<double><<<d.n_lin_tiles, LIN_THREADS, backsub_smem(d), s>>>(d);
+    { if ((e = launch_ex(k_backsub<double>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), backsub_smem(d), s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(7)) != cudaSuccess) return e;
-  k_decide<<<1, DECIDE_THREADS, 0, s>>>(d);
+  { if ((e = launch_ex(k_decide, dim3(1), dim3(DECIDE_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return mark(8);
 }
@@ -2597,57 +2624,47 @@ cudaError_t enqueue_batch_init(const BatchLaunch& b, double lam0, double huber, 
 cudaError_t enqueue_batch_iteration(const BatchLaunch& b, cudaStream_t s) {
   cudaError_t e;
   if (b.mixed)
-    k_lin_b<float><<<b.n_lin, LIN_THREADS, b.lin_smem, s>>>(b.wins, b.lin_items);
+    { if ((e = launch_ex(k_lin_b<float>, dim3(b.n_lin), dim3(LIN_THREADS), b.lin_smem, s, 0, b.wins, b.lin_items)) != cudaSuccess) return e; }
   else
-    k_lin_b<double><<<b.n_lin, LIN_THREADS, b.lin_smem, s>>>(b.wins, b.lin_items);
+    { if ((e = launch_ex(k_lin_b<double>, dim3(b.n_lin), dim3(LIN_THREADS), b.lin_smem, s, 0, b.wins, b.lin_items)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_kf_reduce_b<<<b.n_kf, 384, 0, s>>>(b.wins, b.kf_items);
+  { if ((e = launch_ex(k_kf_reduce_b, dim3(b.n_kf), dim3(384), 0, s, 0, b.wins, b.kf_items)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (b.n_schur > 0) {
     if (b.mixed)
-      k_schur_group_b<float><<<b.n_schur, SCHUR_THREADS, b.group_smem, s>>>(b.wins, b.schur_items);
+      { if ((e = launch_ex(k_schur_group_b<float>, dim3(b.n_schur), dim3(SCHUR_THREADS), b.group_smem, s, 0, b.wins, b.schur_items)) != cudaSuccess) return e; }
     else
-      k_schur_group_b<double><<<b.n_schur, SCHUR_THREADS, b.group_smem, s>>>(b.wins, b.schur_items);
+      { if ((e = launch_ex(k_schur_group_b<double>, dim3(b.n_schur), dim3(SCHUR_THREADS), b.group_smem, s, 0, b.wins, b.schur_items)) != cudaSuccess) return e; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  k_rcs_reduce_b<<<b.n_blkit, 256, 0, s>>>(b.wins, b.blk_items);
+  { if ((e = launch_ex(k_rcs_reduce_b, dim3(b.n_blkit), dim3(256), 0, s, 0, b.wins, b.blk_items)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (b.n_direct > 0) {
     if (b.mixed)
-      k_schur_direct_b<float><<<b.n_direct, SCHUR_THREADS, b.direct_smem, s>>>(b.wins, b.direct_items);
+      { if ((e = launch_ex(k_schur_direct_b<float>, dim3(b.n_direct), dim3(SCHUR_THREADS), b.direct_smem, s, 0, b.wins, b.direct_items)) != cudaSuccess) return e; }
     else
-      k_schur_direct_b<double><<<b.n_direct, SCHUR_THREADS, b.direct_smem, s>>>(b.wins, b.direct_items);
+      { if ((e = launch_ex(k_schur_direct_b<double>, dim3(b.n_direct), dim3(SCHUR_THREADS), b.direct_smem, s, 0, b.wins, b.direct_items)) != cudaSuccess) return e; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (b.n_fallback < b.n_win) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(b.n_win * b.chol_cs);
-    cfg.blockDim = dim3(256);
-    cfg.dynamicSmemBytes = b.chol_smem;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = b.chol_cs;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    if ((e = cudaLaunchKernelEx(&cfg, k_chol_cluster_b, b.wins)) != cudaSuccess) return e;
+    if ((e = launch_ex(k_chol_cluster_b, dim3(b.n_win * b.chol_cs), dim3(256), b.chol_smem, s, b.chol_cs, b.wins)) !=
+        cudaSuccess)
+      return e;
   }
   for (int f = 0; f < b.n_fallback; ++f) {
     const Dev& d = b.fallback_host[f];
     if (d.n_c <= kCholSmemMaxN)
-      k_chol<true><<<1, CHOL_THREADS, chol_smem(d.n_c), s>>>(d);
+      { if ((e = launch_ex(k_chol<true>, dim3(1), dim3(CHOL_THREADS), chol_smem(d.n_c), s, 0, d)) != cudaSuccess) return e; }
     else
-      k_chol<false><<<1, CHOL_THREADS, 0, s>>>(d);
+      { if ((e = launch_ex(k_chol<false>, dim3(1), dim3(CHOL_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (b.mixed)
-    k_backsub_b<float><<<b.n_lin, LIN_THREADS, b.backsub_smem, s>>>(b.wins, b.lin_items);
+    { if ((e = launch_ex(k_backsub_b<float>, dim3(b.n_lin), dim3(LIN_THREADS), b.backsub_smem, s, 0, b.wins, b.lin_items)) != cudaSuccess) return e; }
   else
-    k_backsub_b<double><<<b.n_lin, LIN_THREADS, b.backsub_smem, s>>>(b.wins, b.lin_items);
+    { if ((e = launch_ex(k_backsub_b<double>, dim3(b.n_lin), dim3(LIN_THREADS), b.backsub_smem, s, 0, b.wins, b.lin_items)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_decide_b<<<b.n_win, DECIDE_THREADS, 0, s>>>(b.wins, b.win_items);
+  { if ((e = launch_ex(k_decide_b, dim3(b.n_win), dim3(DECIDE_THREADS), 0, s, 0, b.wins, b.win_items)) != cudaSuccess) return e; }
   return cudaGetLastError();
 }
 
