@@ -178,10 +178,11 @@ cvba_status cvba_set_landmarks_dev(cvba_ctx* ctx, const double* p_w /* device, n
 cvba_status cvba_get_poses_dev(cvba_ctx* ctx, double* T_bw /* device, n_kf*12 */);
 cvba_status cvba_get_landmarks_dev(cvba_ctx* ctx, double* p_w /* device, n_lm*3 */);
 
-/* Profiling: run `reps` iterations with CUDA events around each part of an iteration
- * (part names: cvba_profile_names(), comma separated) and return the mean milliseconds
- * per part in ms[*n_parts].  With ms == NULL only *n_parts is set.  Leaves the state as
- * `reps` LM iterations would. */
+/* Profiling: run `reps` one-iteration solves from the current state (each relinearises;
+ * opts->reset_lambda as given) with CUDA events around each kernel of the iteration (part
+ * names: cvba_profile_names(), comma separated) and return the mean milliseconds per part
+ * in ms[*n_parts].  With ms == NULL only *n_parts is set.  The state advances as the
+ * accepted steps of those solves take it. */
 cvba_status cvba_profile_iteration(cvba_ctx* ctx, const cvba_opts* opts, int reps, float* ms, int* n_parts);
 const char* cvba_profile_names(void);
 

@@ -893,12 +893,14 @@ cvba_status cvba_profile_iteration(cvba_ctx* c, const cvba_opts* o, int reps, fl
   for (auto& e : ev) CK(cudaEventCreate(&e), "event");
   std::vector<double> acc(np, 0.0);
   if (!opts_ok(&one)) return fail(c, CVBA_ERR_INVALID_ARG, "profile: bad options");
-  CK(enqueue_solve_init(c->d, one.lambda0, one.huber_delta, one.z_min, reps, one.reset_lambda,
-                        make_key(&one, c->prec == CVBA_MIXED).refine, c->stream),
-     "init");
+  const int refine = make_key(&one, c->prec == CVBA_MIXED).refine;
   cvba_status st = CVBA_OK;
   for (int r = 0; r < reps && st == CVBA_OK; ++r) {
-    cudaError_t e = enqueue_iteration(c->d, c->stream, ev.data());
+    // each repetition starts a one-iteration solve from the current state, so every one
+    // relinearises (a rejected step would otherwise skip the next linearisation)
+    cudaError_t e = enqueue_solve_init(c->d, one.lambda0, one.huber_delta, one.z_min, 1, one.reset_lambda, refine,
+                                       c->stream);
+    if (e == cudaSuccess) e = enqueue_iteration(c->d, c->stream, ev.data());
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[np]);
     if (e != cudaSuccess) {
       st = cuda_fail(c, e, "profile iteration");

@@ -1475,7 +1475,7 @@ struct CholSmem {
   size_t rows_len;                                 // packed lower block rows, max over CTAs
   __host__ __device__ size_t rows_off() const { return 0; }
   __host__ __device__ size_t panel_off() const { return rows_off() + rows_len; }
-  __host__ __device__ size_t lkk_off() const { return panel_off() + (size_t)NB * kCB * kCB; }
+  __host__ __device__ size_t lkk_off() const { return panel_off() + (size_t)2 * NB * kCB * kCB; }   // two panels
   __host__ __device__ size_t y_off() const { return lkk_off() + 2 * (kCB * kCB + kCB); }   // two L_kk buffers
   __host__ __device__ size_t acc_off() const { return y_off() + NP; }
   __host__ __device__ size_t contrib_off() const { return acc_off() + NP; }
@@ -1740,7 +1740,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   const CholSmem Ls = chol_layout(n, CS);
   const int NB = Ls.NB, NP = Ls.NP;
   double* rows = smem + Ls.rows_off();             // packed lower block rows of this CTA
-  double* panel = smem + Ls.panel_off();           // [c][i][m] = L[8c+i][8k+m]
+  double* panel0 = smem + Ls.panel_off();          // two buffers [c][i][m] = L[8c+i][8k+m]
   double* lkk0 = smem + Ls.lkk_off();              // two buffers: [i][m], then 8 reciprocals of the diagonal
   double* ybuf = smem + Ls.y_off();                // right-hand side row / y
   double* acc = smem + Ls.acc_off();               // backward contributions of own rows
@@ -1786,8 +1786,8 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   // ---- factorisation with the forward substitution fused.  Per step k two split
   // barriers: A_k (L_kk pushed) and B_k (panel k pushed).  The owner of block k+1 factors
   // it between its arrival at B_k and its wait there, so the factorisation does not wait
-  // for the whole cluster's panel exchange.  L_kk alternates between two buffers: the
-  // owner of k+1 may push while others still read L_kk.
+  // for the whole cluster's panel exchange, and every CTA arrives at A_{k+1} before its
+  // trailing update.  L_kk and the panels alternate between two buffers.
   bool broke = false;
   for (int k = 0; k < NB; ++k) {
     cluster_wait();                                // A_k: L_kk (and flag) visible everywhere
@@ -1796,6 +1796,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
       break;
     }
     const double* lkk = lkk0 + (k & 1) * (kCB * kCB + kCB);
+    double* panel = panel0 + (size_t)(k & 1) * NB * kCB * kCB;
     // 1. TRSM of own block rows below k, and of the right-hand side on CTA 0: solve
     //    t L_kk^T = a for each row, entry-parallel (8 lanes per row, one column each;
     //    per column one scaling and one update instruction)
@@ -1853,6 +1854,11 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
                        cluster, CS);
     }
     cluster_wait();                                // B_k: panel k visible everywhere
+    // L_{k+1,k+1} is pushed: signal A_{k+1} before this CTA's trailing update, which then
+    // overlaps the next step's chain.  Panels alternate between two buffers, and a CTA
+    // cannot reach the next write of this buffer (step k+2) before every CTA has arrived
+    // at A_{k+2}, after its own trailing update of step k.
+    cluster_arrive();                              // A_{k+1}
     // 2b. trailing update of own block rows: A_rc -= L_rk L_ck^T, c in (k, r]
     for (int lb = 0; lb < Ls.nlb; ++lb) {
       const int r = q + lb * CS;
@@ -1881,8 +1887,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
         ybuf[g] -= s;
       }
     }
-    __syncthreads();
-    cluster_arrive();                              // A_{k+1}
+    __syncthreads();                               // own rows updated before the next TRSM
   }
   if (!broke) cluster_wait();                      // A_NB: the factor complete everywhere
   if (*flag) {
