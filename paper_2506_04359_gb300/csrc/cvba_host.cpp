@@ -356,11 +356,11 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   size_t schur_part_len = 0;
   {
     for (auto& t : c->schur_tiles) {
-      const size_t rows = 6 * (size_t)t.span;
-      if (schur_part_len + rows * (rows + 1) / 2 + rows > (size_t)INT32_MAX)
+      const size_t part = (size_t)t.span * (t.span + 1) * 18;   // [half block][18]
+      if (schur_part_len + part > (size_t)INT32_MAX)
         return fail(c, CVBA_ERR_INVALID_ARG, "Schur partials exceed 2^31 entries");
       t.part_off = (int)schur_part_len;
-      schur_part_len += rows * (rows + 1) / 2 + rows;
+      schur_part_len += part;
       for (int a = t.k_lo; a < t.k_lo + t.span; ++a)
         for (int b = t.k_lo; b <= a; ++b) blk_tiles_off[a * (a + 1) / 2 + b + 1]++;
     }

@@ -994,7 +994,9 @@ struct GroupChunk {
 size_t group_smem_bytes(int max_span, bool mixed) {
   const size_t t = mixed ? 4 : 8;
   const int ch = mixed ? 16 : 8;
-  return sizeof(double) * 64 + t * ((size_t)SCHUR_TILE_LMS * 9 + (size_t)ch * max_span * kStage);
+  // the staging area also holds the groups' partials for the combine: <= 256 items x 18 x 8 B
+  const size_t stage = std::max((size_t)ch * max_span * kStage * t, (size_t)SCHUR_THREADS * 18 * 8);
+  return sizeof(double) * 64 + t * (size_t)SCHUR_TILE_LMS * 9 + stage;
 }
 
 template <typename T>
@@ -1014,11 +1016,11 @@ __device__ __forceinline__ void load_row3<double>(const double* p, double& x, do
   z = p[2];
 }
 
-// Entries of a half block: off-diagonal (a > b): rows 3h..3h+2 x 6 columns, index
+// Half-block work items: off-diagonal (a > b): rows 3h..3h+2 x 6 columns, index
 // (r - 3h) * 6 + c.  Diagonal, h = 0: lower entries of rows 0-2 (6) then b rows 0-2 (3);
 // h = 1: lower entries of rows 3-5 (15) then b rows 3-5 (3).  In the staged Dg[21] the
 // lower entry (r, c) is r(r+1)/2 + c, so both halves are contiguous runs followed by bY.
-__device__ __forceinline__ int half_len(bool diag, int h) { return diag ? (h ? 18 : 9) : 18; }
+// The tile's partial is written in this layout, [half block][18].
 
 template <typename T>
 __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
@@ -1030,9 +1032,10 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
   T* s_vinv = reinterpret_cast<T*>(s_red + 64);       // SCHUR_TILE_LMS * 6
   T* s_gl = s_vinv + SCHUR_TILE_LMS * 6;              // SCHUR_TILE_LMS * 3
   T* s_stg = s_gl + SCHUR_TILE_LMS * 3;               // CH * max_span * kStage
+  __shared__ unsigned s_mask[16];                     // per staged landmark: keyframes present
   const SchurTile tile = d.schur_tiles[item];
   const int nl = tile.l1 - tile.l0;
-  const int span = tile.span, rows = 6 * span, E = rows * (rows + 1) / 2;
+  const int span = tile.span;
   const double lam = d.ctrl->lam;
   const double floor_ = diag_floor(d, s_red);
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
@@ -1047,7 +1050,6 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
   const int n_half = 2 * nblk;
   const int G = max(1, min(CH, SCHUR_THREADS / n_half));
   const int n_items = n_half * G;                    // > SCHUR_THREADS only when G == 1
-  const int stg_len = CH * span * kStage;
   const T* pose = st_pose<T>(d, d.ctrl->cur);
   Out* out = reinterpret_cast<Out*>(d.schur_part) + tile.part_off;
   for (int it0 = 0; it0 < n_items; it0 += SCHUR_THREADS) {   // passes
@@ -1060,7 +1062,6 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
     while ((ba + 1) * (ba + 2) / 2 <= blk) ++ba;
     const int bb = blk - ba * (ba + 1) / 2;
     const bool diag = ba == bb;
-    const int doff = h ? 6 : 0;                      // diagonal: first staged Dg entry of the half
     T acc[18], cmp[18];
 #pragma unroll
     for (int k = 0; k < 18; ++k) {
@@ -1070,9 +1071,9 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
     for (int c0 = 0; c0 < nl; c0 += CH) {
       const int nc = min(CH, nl - c0);
       __syncthreads();                               // previous chunk consumed
-      for (int i = threadIdx.x; i < stg_len * (int)sizeof(T) / 16; i += blockDim.x)   // 16-byte stores
-        reinterpret_cast<float4*>(s_stg)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (threadIdx.x < CH) s_mask[threadIdx.x] = 0u;
       __syncthreads();
+      // stage each pair's terms as one 76-value record (16-byte stores) and mark it present
       const int q0 = d.lm_pair[tile.l0 + c0], q1 = d.lm_pair[tile.l0 + c0 + nc];
       for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
         const int a = d.pair_kf[q];
@@ -1083,17 +1084,40 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
         pair_schur_terms<T>(reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN, pose + a * POSE_STRIDE,
                             s_vinv + l * 6, s_gl + l * 3, W, Y, Dg, bY);
         T* st = s_stg + ((l - c0) * span + (pb - tile.k_lo)) * kStage;
+        if constexpr (sizeof(T) == 4) {              // 19 16-byte stores per record
+          float4* s4 = reinterpret_cast<float4*>(st);
 #pragma unroll
-        for (int r = 0; r < 6; ++r)
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            st[r * 4 + k] = Y[r * 3 + k];
-            st[24 + r * 4 + k] = W[r * 3 + k];
+          for (int r = 0; r < 6; ++r) {
+            s4[r] = make_float4(Y[r * 3], Y[r * 3 + 1], Y[r * 3 + 2], 0.f);
+            s4[6 + r] = make_float4(W[r * 3], W[r * 3 + 1], W[r * 3 + 2], 0.f);
           }
 #pragma unroll
-        for (int k = 0; k < 21; ++k) st[48 + k] = Dg[k];
+          for (int k = 0; k < 5; ++k) s4[12 + k] = make_float4(Dg[4 * k], Dg[4 * k + 1], Dg[4 * k + 2], Dg[4 * k + 3]);
+          s4[17] = make_float4(Dg[20], bY[0], bY[1], bY[2]);
+          s4[18] = make_float4(bY[3], bY[4], bY[5], 0.f);
+        } else {
 #pragma unroll
-        for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
+          for (int r = 0; r < 6; ++r) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              st[r * 4 + k] = Y[r * 3 + k];
+              st[24 + r * 4 + k] = W[r * 3 + k];
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 21; ++k) st[48 + k] = Dg[k];
+#pragma unroll
+          for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
+        }
+        atomicOr(&s_mask[l - c0], 1u << (pb - tile.k_lo));
+      }
+      __syncthreads();
+      // zero the records of keyframes of the window that a landmark does not observe
+      for (int i = threadIdx.x; i < nc * span; i += blockDim.x) {
+        const int l = i / span, sl = i % span;
+        if ((s_mask[l] >> sl) & 1u) continue;
+        float4* st = reinterpret_cast<float4*>(s_stg + (l * span + sl) * kStage);
+        for (int k = 0; k < kStage * (int)sizeof(T) / 16; ++k) st[k] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       __syncthreads();
       if (working) {
@@ -1145,78 +1169,47 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
       }
     }
     if (G == 1) {
-      // one group: each item writes its own window entries
-      __syncthreads();
+      // one group: each item writes its 18 values, contiguous ([half block][18])
       if (working) {
-        const int n_ent = half_len(diag, h);
 #pragma unroll
-        for (int k = 0; k < 18; ++k) {             // constant indices keep acc/cmp in registers
-          if (k >= n_ent) break;
-          int e;
-          if (!diag) {
-            const int r = 3 * h + k / 6, c = k % 6;
-            const int wr = 6 * ba + r;
-            e = wr * (wr + 1) / 2 + 6 * bb + c;
-          } else {
-            const int nlow = h ? 15 : 6;
-            if (k < nlow) {
-              int idx = doff + k, r = 0;             // lower entry idx -> (r, c)
-              while ((r + 1) * (r + 2) / 2 <= idx) ++r;
-              const int c = idx - r * (r + 1) / 2;
-              const int wr = 6 * ba + r;
-              e = wr * (wr + 1) / 2 + 6 * ba + c;
-            } else {
-              e = E + 6 * ba + 3 * h + (k - nlow);
-            }
-          }
+        for (int k = 0; k < 18; ++k) {
           if constexpr (sizeof(T) == 4)
-            out[e] = DF{(float)acc[k], -(float)cmp[k]};
+            out[hb * 18 + k] = DF{(float)acc[k], -(float)cmp[k]};
           else
-            out[e] = (double)acc[k];
+            out[hb * 18 + k] = (double)acc[k];
         }
       }
     } else {
-      // several groups (single pass): combine in a fixed order in the staging area
-      // [half block][18], then write the window in order
+      // several groups (single pass): every group's values in the staging area
+      // [group][half block][18], combined by a fixed pairwise tree (group g takes g + step),
+      // then group 0's written as it is
       Out* s_out = reinterpret_cast<Out*>(s_stg);
-      for (int gg = 0; gg < G; ++gg) {
+      __syncthreads();
+      if (working) {
+#pragma unroll
+        for (int k = 0; k < 18; ++k) {
+          if constexpr (sizeof(T) == 4)
+            s_out[(g * n_half + hb) * 18 + k] = DF{(float)acc[k], -(float)cmp[k]};
+          else
+            s_out[(g * n_half + hb) * 18 + k] = (double)acc[k];
+        }
+      }
+      for (int step = 1; step < G; step *= 2) {
         __syncthreads();
-        if (working && g == gg) {
+        if (working && g % (2 * step) == 0 && g + step < G) {
+          Out* dst = s_out + (g * n_half + hb) * 18;
+          const Out* src = s_out + ((g + step) * n_half + hb) * 18;
 #pragma unroll
           for (int k = 0; k < 18; ++k) {
-            if constexpr (sizeof(T) == 4) {
-              const DF v{(float)acc[k], -(float)cmp[k]};
-              s_out[hb * 18 + k] = gg == 0 ? v : df_add(s_out[hb * 18 + k], v);
-            } else {
-              const double v = (double)acc[k];
-              s_out[hb * 18 + k] = gg == 0 ? v : s_out[hb * 18 + k] + v;
-            }
+            if constexpr (sizeof(T) == 4)
+              dst[k] = df_add(dst[k], src[k]);
+            else
+              dst[k] += src[k];
           }
         }
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < E + rows; e += blockDim.x) {
-        int src;
-        if (e < E) {
-          int wr = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
-          while (wr * (wr + 1) / 2 > e) --wr;
-          while ((wr + 1) * (wr + 2) / 2 <= e) ++wr;
-          const int wc = e - wr * (wr + 1) / 2;
-          const int a = wr / 6, r = wr % 6, b = wc / 6, c = wc % 6;
-          const int kb = a * (a + 1) / 2 + b;
-          if (a != b) {
-            src = (2 * kb + r / 3) * 18 + (r % 3) * 6 + c;
-          } else {
-            const int idx = r * (r + 1) / 2 + c;     // lower entry of the diagonal block
-            src = idx < 6 ? (2 * kb) * 18 + idx : (2 * kb + 1) * 18 + (idx - 6);
-          }
-        } else {
-          const int wr = e - E, a = wr / 6, r = wr % 6;
-          const int kb = a * (a + 1) / 2 + a;
-          src = r < 3 ? (2 * kb) * 18 + 6 + r : (2 * kb + 1) * 18 + 15 + (r - 3);
-        }
-        out[e] = s_out[src];
-      }
+      for (int e = threadIdx.x; e < n_half * 18; e += blockDim.x) out[e] = s_out[e];
     }
   }
 }
@@ -1238,7 +1231,7 @@ __global__ void __launch_bounds__(SCHUR_THREADS, sizeof(T) == 4 ? 2 : 1)
 // of the window partials of the Schur tiles covering it, assigned (zero when no tile covers
 // it); the direct tiles' atomics are added after this kernel.
 __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
-  __shared__ int s_off[256], s_klo[256], s_rows[256];
+  __shared__ int s_off[256], s_klo[256];
   const int blk = item;
   const int t0 = d.blk_tiles_off[blk], t1 = d.blk_tiles_off[blk + 1];
   int a = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
@@ -1260,7 +1253,6 @@ __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
       const SchurTile st = d.schur_tiles[d.blk_tiles[c0 + threadIdx.x]];
       s_off[threadIdx.x] = st.part_off;
       s_klo[threadIdx.x] = st.k_lo;
-      s_rows[threadIdx.x] = 6 * st.span;
     }
     __syncthreads();
 #pragma unroll
@@ -1282,9 +1274,19 @@ __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
         is_b = true;
       }
       for (int t = lane; t < nc; t += 32) {
-        const int rows = s_rows[t];
-        const int wr = 6 * (a - s_klo[t]) + r;
-        const int idx = is_b ? rows * (rows + 1) / 2 + wr : wr * (wr + 1) / 2 + 6 * (b - s_klo[t]) + c;
+        // tile partial layout: [half block][18], half blocks 2 blk + h of the window's
+        // lower blocks (aa, bb) in row-major order (k_schur_group)
+        const int aa = a - s_klo[t], bb = b - s_klo[t];
+        const int hb0 = 2 * (aa * (aa + 1) / 2 + bb);
+        int idx;
+        if (is_b) {
+          idx = r < 3 ? hb0 * 18 + 6 + r : (hb0 + 1) * 18 + 15 + (r - 3);
+        } else if (a != b) {
+          idx = (hb0 + r / 3) * 18 + (r % 3) * 6 + c;
+        } else {
+          const int il = r * (r + 1) / 2 + c;
+          idx = il < 6 ? hb0 * 18 + il : (hb0 + 1) * 18 + (il - 6);
+        }
         if (mixed) {
           const DF x = reinterpret_cast<const DF*>(d.schur_part)[s_off[t] + idx];
           vf[k] = df_add(vf[k], x);
