@@ -141,6 +141,18 @@ def cores() -> int:
         return os.cpu_count() or 1
 
 
+def pose_errors(P, Q) -> dict:
+    """Largest keyframe translation error (m) and rotation error (rad, angle of R_P R_Q^T)."""
+    dt = float(max(np.linalg.norm(P[i, :, 3] - Q[i, :, 3]) for i in range(len(P))))
+    dr = 0.0
+    for i in range(len(P)):
+        E = P[i, :, :3] @ Q[i, :, :3].T
+        s = np.linalg.norm(np.array([E[2, 1] - E[1, 2], E[0, 2] - E[2, 0], E[1, 0] - E[0, 1]])) / 2.0
+        c = (np.trace(E) - 1.0) / 2.0
+        dr = max(dr, float(np.arctan2(s, c)))
+    return {"translation_m": dt, "rotation_rad": dr}
+
+
 # -------------------------------------------------------------- algorithmic work model
 
 def work_model(p, P: int, mixed: bool) -> dict:
@@ -303,6 +315,7 @@ def run_ours(args):
     dev_s = max_over_ranks(dev_s, ws)
     tr = ctx.cvba_get_trace(p.iters)
     ev = ctx.cvba_evaluate(p.huber_delta)
+    final_poses = ctx.cvba_get_poses()                 # before profiling moves the state on
     iters_total = args.steps * p.iters * ws
     value = iters_total / dev_s
     gobs = float(np.sum(tr["n_valid"])) * args.steps * ws / dev_s / 1e9
@@ -319,12 +332,14 @@ def run_ours(args):
 
     # --- FP64 path on the same window
     fp64 = None
+    fp64_poses = None
     if precision != "fp64":
         c64 = make_ctx("fp64")
         d64, _ = timed_solves(c64, max(3, args.steps // 2), 1)
         d64 = max_over_ranks(d64, ws)
         fp64 = {"value": max(3, args.steps // 2) * p.iters * ws / d64, "unit": "LM iters/s",
                 "rms_px": c64.cvba_evaluate(p.huber_delta)["rms"]}
+        fp64_poses = c64.cvba_get_poses()
         c64.close()
 
     # --- end to end through the public API with host buffers
@@ -479,10 +494,20 @@ def run_ours(args):
             c.close()
 
     golden_rms = None
+    vs_oracle = None
     gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle.json")
     if os.path.exists(gpath):
         with open(gpath) as f:
-            golden_rms = json.load(f)["final_rms_px"]
+            gold = json.load(f)
+        golden_rms = gold["final_rms_px"]
+        fp64_err = None
+        if fp64_poses is not None:
+            fp64_err = dict(pose_errors(fp64_poses, np.array(gold["final_poses"])),
+                            rms_px=abs(fp64["rms_px"] - golden_rms))
+        # per-result error of the timed path's final state against the oracle's
+        vs_oracle = dict(pose_errors(final_poses, np.array(gold["final_poses"])),
+                         rms_px=abs(ev["rms"] - golden_rms), precision=precision,
+                         **({"fp64": fp64_err} if fp64_err else {}))
 
     if rank == 0:
         line = {
@@ -494,7 +519,7 @@ def run_ours(args):
                        "precision": precision, "lm_iters_per_step": p.iters, "parallelism": "replicas",
                        "l2": "flushed between steps (512 MiB write outside the timed events)"},
             "gobs_per_s": gobs,
-            "rms_px": ev["rms"], "rms_oracle_px": golden_rms,
+            "rms_px": ev["rms"], "rms_oracle_px": golden_rms, "vs_oracle": vs_oracle,
             "rms_ok": None if golden_rms is None else bool(abs(ev["rms"] - golden_rms) <= 1e-3),
             "fp64": fp64,
             "roofline": roof,
