@@ -1554,14 +1554,30 @@ __device__ __forceinline__ double rsqrt_halley(double x, bool& ok) {
 __device__ __forceinline__ int ep_lane(int i, int j) { return j >= 1 ? (i - 1) * i / 2 + (j - 1) : 28 + (i & 3); }
 __device__ __forceinline__ bool ep_slot1(int i, int j) { return j == 0 && i >= 4; }
 
-// Factor the 8x8 block D (row stride NP) in place with warp 0 and push L_kk, the
-// reciprocals of its diagonal and a non-PD flag to every CTA of the cluster.  rdiag (may
-// be null) keeps the reciprocals for the owner.
+// Factor the 8x8 block D (row stride NP) in place with warp 0 and push, to every CTA of
+// the cluster, the block M with M_im = L_im / L_mm (m < i) and the reciprocals 1/L_mm of
+// its diagonal (the form the panel solve uses), and a non-PD flag.  rdiag (may be null)
+// keeps the reciprocals for the owner.
+//
+// The pivot chain avoids square roots and divisions: column c is eliminated as
+//   a_ij <- (a_ij p_c - a_ic a_jc) 2^-e_c,   p_c = a_cc = m 2^e_c (1 <= m < 2),
+// so an entry after pivot c is s_{c+1} times the Schur complement entry of ordinary
+// elimination, with s_0 = 1 and s_{c+1} = s_c p_c 2^-e_c in [1, 2^(c+1)).  The power-of-two
+// scaling is exact and is applied to the exponent bits on the integer pipe, which leaves one
+// multiplication and one FMA on the FP64 chain per pivot.  Afterwards, with
+// R_j = (p_j s_j)^-1/2: L_ij = a_ij R_j (i >= j, a_ij the value when column j was the pivot
+// column), 1/L_jj = s_j R_j and M_ij = a_ij / p_j.
+__device__ __forceinline__ double scale_exp_bits(double u, int de) {
+  const int hi = __double2hiint(u);               // u 2^de for normal u (zero kept as is)
+  return __hiloint2double((hi & 0x7ff00000) ? hi + de : hi, __double2loint(u));
+}
+
 __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk, int* flag, double* rdiag,
                                                  cooperative_groups::cluster_group& cluster, int CS) {
   const int tid = threadIdx.x;
-  __shared__ double s_rs[kCB];
+  __shared__ double s_blk[kCB * kCB + kCB];      // M (lower part), then the reciprocals 1/L_mm
   if (tid < 32) {
+    const unsigned full = 0xffffffffu;
     const int lane = tid;
     int i0, j0;                                    // slot-0 entry of this lane
     if (lane < 28) {
@@ -1575,46 +1591,59 @@ __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk,
     double v0 = D[i0 * NP + j0];
     double v1 = lane >= 28 ? D[(lane - 24) * NP] : 0.0;
     bool bad = false;
+    double pk = 1.0, ph = 1.0;                     // lane c < 8: p_c and its mantissa p_c 2^-e_c
 #pragma unroll
     for (int c = 0; c < kCB; ++c) {
-      const double piv = __shfl_sync(0xffffffffu, v0, ep_lane(c, c));
-      bool ok;
-      const double rs = rsqrt_halley(piv, ok);
-      bad |= !ok;
-      if (lane == 0) s_rs[c] = rs;
-      // scale column c: L_rc = a_rc / sqrt(piv) (the diagonal: piv rs)
-      if (c == 0) {
-        if (lane >= 28) {
-          v0 *= rs;
-          v1 *= rs;
-        }
-      } else if (j0 == c && lane < 28) {
-        v0 *= rs;
+      const double p = __shfl_sync(full, v0, ep_lane(c, c));
+      const int phi = __double2hiint(p);
+      const int ex = (phi >> 20) & 0x7ff;
+      bad |= phi < 0x00100000 || ex == 0x7ff;      // not a positive normal number
+      if (lane == c) {
+        pk = p;
+        ph = __hiloint2double((phi & 0x800fffff) | 0x3ff00000, __double2loint(p));
       }
-      // update the entries right of column c: a_ij -= L_ic L_jc
       const int la = ep_lane(i0, c), lb = ep_lane(j0, c);
-      const double xa0 = __shfl_sync(0xffffffffu, v0, la), xa1 = __shfl_sync(0xffffffffu, v1, la);
-      const double xb0 = __shfl_sync(0xffffffffu, v0, lb), xb1 = __shfl_sync(0xffffffffu, v1, lb);
-      const double lic = ep_slot1(i0, c) ? xa1 : xa0;
-      const double ljc = ep_slot1(j0, c) ? xb1 : xb0;
-      if (lane < 28 && j0 > c) v0 = fma(-lic, ljc, v0);
+      const double xa0 = __shfl_sync(full, v0, la), xa1 = __shfl_sync(full, v1, la);
+      const double xb0 = __shfl_sync(full, v0, lb), xb1 = __shfl_sync(full, v1, lb);
+      const double aic = ep_slot1(i0, c) ? xa1 : xa0;
+      const double ajc = ep_slot1(j0, c) ? xb1 : xb0;
+      if (lane < 28 && j0 > c) v0 = scale_exp_bits(fma(v0, p, -(aic * ajc)), (1023 - ex) * 0x100000);
     }
-    D[i0 * NP + j0] = v0;
-    if (lane >= 28) D[(lane - 24) * NP] = v1;
-    bad = __any_sync(0xffffffffu, bad);
+    // s_c = prod_{m < c} mantissa(p_m): inclusive scan over lanes 0-7, then shifted by one
+    double sc = ph;
+#pragma unroll
+    for (int o = 1; o < kCB; o <<= 1) {
+      const double y = __shfl_up_sync(full, sc, o);
+      if (lane >= o) sc *= y;
+    }
+    sc = __shfl_up_sync(full, sc, 1);
+    if (lane == 0) sc = 1.0;
+    bool ok;
+    const double R = rsqrt_halley(pk * sc, ok);
+    if (lane < kCB) bad |= !ok;
+    const double dinv = sc * R;                    // 1/L_cc
+    const double qinv = dinv * R;                  // 1/p_c
+    const double Rj = __shfl_sync(full, R, j0), Qj = __shfl_sync(full, qinv, j0);
+    D[i0 * NP + j0] = v0 * Rj;
+    if (lane >= 28) D[(lane - 24) * NP] = v1 * Rj;
+    if (lane < 28) s_blk[i0 * kCB + j0] = v0 * Qj;
+    else if (i0 > 0) s_blk[i0 * kCB] = v0 * Qj;
+    if (lane >= 28) s_blk[(lane - 24) * kCB] = v1 * Qj;
+    if (lane < kCB) s_blk[kCB * kCB + lane] = dinv;
+    bad = __any_sync(full, bad);
     if (lane == 0 && bad) *flag = 1;
   }
   __syncthreads();
-  if (rdiag && tid < kCB) rdiag[tid] = s_rs[tid];
+  if (rdiag && tid < kCB) rdiag[tid] = s_blk[kCB * kCB + tid];
   const int bad = *flag;
   constexpr int W = kCB * kCB + kCB + 1;           // block, reciprocals, flag
   for (int e = tid; e < CS * W; e += blockDim.x) {
     const int dst = e / W, t = e % W;
     if (t < kCB * kCB) {
       const int i = t / kCB, m = t % kCB;
-      cluster.map_shared_rank(lkk, dst)[t] = m <= i ? D[i * NP + m] : 0.0;
+      cluster.map_shared_rank(lkk, dst)[t] = m < i ? s_blk[t] : 0.0;
     } else if (t < kCB * kCB + kCB) {
-      cluster.map_shared_rank(lkk, dst)[t] = s_rs[t - kCB * kCB];
+      cluster.map_shared_rank(lkk, dst)[t] = s_blk[t];
     } else if (bad) {
       *cluster.map_shared_rank(flag, dst) = 1;
     }
@@ -1800,8 +1829,9 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
     const double* lkk = lkk0 + (k & 1) * (kCB * kCB + kCB);
     double* panel = panel0 + (size_t)(k & 1) * NB * kCB * kCB;
     // 1. TRSM of own block rows below k, and of the right-hand side on CTA 0: solve
-    //    t L_kk^T = a for each row, entry-parallel (8 lanes per row, one column each;
-    //    per column one scaling and one update instruction)
+    //    t L_kk^T = a for each row, entry-parallel (8 lanes per row, one column each).
+    //    With u_c = t_c L_cc: u_c = a_c - sum_{m<c} u_m M_cm (M_cm = L_cm / L_mm, pushed
+    //    with L_kk), one update instruction per column, and t_c = u_c / L_cc at the end.
     const double* linvd = lkk + kCB * kCB;
     const int n_trsm = (Ls.nlb * kCB + 1) * kCB;
     for (int e0 = 0; e0 < n_trsm; e0 += nt) {       // warp-uniform trip count
@@ -1818,12 +1848,11 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
       double t = a ? a[c] : 0.0;
       const int base = (tid & 31) & ~(kCB - 1);
 #pragma unroll
-      for (int m = 0; m < kCB; ++m) {
-        if (c == m) t *= linvd[m];
+      for (int m = 0; m < kCB - 1; ++m) {
         const double x = __shfl_sync(0xffffffffu, t, base + m);
         if (c > m) t = fma(-x, lkk[c * kCB + m], t);
       }
-      if (a) a[c] = t;
+      if (a) a[c] = t * linvd[c];
     }
     __syncthreads();
     for (int lb = 0; lb < Ls.nlb; ++lb) {          // push panel blocks L_rk to every CTA
