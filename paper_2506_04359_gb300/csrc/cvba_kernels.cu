@@ -1555,9 +1555,11 @@ __device__ __forceinline__ int ep_lane(int i, int j) { return j >= 1 ? (i - 1) *
 __device__ __forceinline__ bool ep_slot1(int i, int j) { return j == 0 && i >= 4; }
 
 // Factor the 8x8 block D (row stride NP) in place with warp 0 and push, to every CTA of
-// the cluster, the block M with M_im = L_im / L_mm (m < i) and the reciprocals 1/L_mm of
-// its diagonal (the form the panel solve uses), and a non-PD flag.  rdiag (may be null)
-// keeps the reciprocals for the owner.
+// the cluster, the strictly lower block M with M_im = L_im / L_mm (m < i, 28 entries packed
+// row by row at (i-1)i/2 + m) and the reciprocals 1/L_mm of its diagonal: the form the
+// panel solve uses, 36 doubles sent as 16-byte stores (the number of remote stores, not
+// their size, sets the cost of the push).  A non-PD flag goes to every CTA.  rdiag (may be
+// null) keeps the reciprocals for the owner.
 //
 // The pivot chain avoids square roots and divisions: column c is eliminated as
 //   a_ij <- (a_ij p_c - a_ic a_jc) 2^-e_c,   p_c = a_cc = m 2^e_c (1 <= m < 2),
@@ -1575,7 +1577,7 @@ __device__ __forceinline__ double scale_exp_bits(double u, int de) {
 __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk, int* flag, double* rdiag,
                                                  cooperative_groups::cluster_group& cluster, int CS) {
   const int tid = threadIdx.x;
-  __shared__ double s_blk[kCB * kCB + kCB];      // M (lower part), then the reciprocals 1/L_mm
+  __shared__ __align__(16) double s_blk[kCB * (kCB - 1) / 2 + kCB];   // packed M, then 1/L_mm
   if (tid < 32) {
     const unsigned full = 0xffffffffu;
     const int lane = tid;
@@ -1626,28 +1628,25 @@ __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk,
     const double Rj = __shfl_sync(full, R, j0), Qj = __shfl_sync(full, qinv, j0);
     D[i0 * NP + j0] = v0 * Rj;
     if (lane >= 28) D[(lane - 24) * NP] = v1 * Rj;
-    if (lane < 28) s_blk[i0 * kCB + j0] = v0 * Qj;
-    else if (i0 > 0) s_blk[i0 * kCB] = v0 * Qj;
-    if (lane >= 28) s_blk[(lane - 24) * kCB] = v1 * Qj;
-    if (lane < kCB) s_blk[kCB * kCB + lane] = dinv;
+    if (lane < 28) {
+      if (j0 < i0) s_blk[(i0 - 1) * i0 / 2 + j0] = v0 * Qj;
+    } else {
+      if (i0 > 0) s_blk[(i0 - 1) * i0 / 2] = v0 * Qj;
+      const int r1 = lane - 24;
+      s_blk[(r1 - 1) * r1 / 2] = v1 * Qj;
+    }
+    if (lane < kCB) s_blk[kCB * (kCB - 1) / 2 + lane] = dinv;
     bad = __any_sync(full, bad);
     if (lane == 0 && bad) *flag = 1;
   }
   __syncthreads();
-  if (rdiag && tid < kCB) rdiag[tid] = s_blk[kCB * kCB + tid];
-  const int bad = *flag;
-  constexpr int W = kCB * kCB + kCB + 1;           // block, reciprocals, flag
-  for (int e = tid; e < CS * W; e += blockDim.x) {
-    const int dst = e / W, t = e % W;
-    if (t < kCB * kCB) {
-      const int i = t / kCB, m = t % kCB;
-      cluster.map_shared_rank(lkk, dst)[t] = m < i ? s_blk[t] : 0.0;
-    } else if (t < kCB * kCB + kCB) {
-      cluster.map_shared_rank(lkk, dst)[t] = s_blk[t];
-    } else if (bad) {
-      *cluster.map_shared_rank(flag, dst) = 1;
-    }
+  if (rdiag && tid < kCB) rdiag[tid] = s_blk[kCB * (kCB - 1) / 2 + tid];
+  constexpr int NV2 = (kCB * (kCB - 1) / 2 + kCB) / 2;   // 16-byte stores per CTA
+  for (int e = tid; e < CS * NV2; e += blockDim.x) {
+    const int dst = e / NV2, t = e % NV2;
+    reinterpret_cast<double2*>(cluster.map_shared_rank(lkk, dst))[t] = reinterpret_cast<const double2*>(s_blk)[t];
   }
+  if (*flag && tid < CS) *cluster.map_shared_rank(flag, tid) = 1;
 }
 
 // Backward substitution L^T x = y (y in ybuf on every CTA, acc and contrib zero).  The
@@ -1772,7 +1771,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   const int NB = Ls.NB, NP = Ls.NP;
   double* rows = smem + Ls.rows_off();             // packed lower block rows of this CTA
   double* panel0 = smem + Ls.panel_off();          // two buffers [c][i][m] = L[8c+i][8k+m]
-  double* lkk0 = smem + Ls.lkk_off();              // two buffers: [i][m], then 8 reciprocals of the diagonal
+  double* lkk0 = smem + Ls.lkk_off();              // two buffers: packed M of L_kk, then 8 reciprocals of the diagonal
   double* ybuf = smem + Ls.y_off();                // right-hand side row / y
   double* acc = smem + Ls.acc_off();               // backward contributions of own rows
   double* contrib = smem + Ls.contrib_off();       // [lb][from CTA][8]
@@ -1832,7 +1831,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
     //    t L_kk^T = a for each row, entry-parallel (8 lanes per row, one column each).
     //    With u_c = t_c L_cc: u_c = a_c - sum_{m<c} u_m M_cm (M_cm = L_cm / L_mm, pushed
     //    with L_kk), one update instruction per column, and t_c = u_c / L_cc at the end.
-    const double* linvd = lkk + kCB * kCB;
+    const double* linvd = lkk + kCB * (kCB - 1) / 2;
     const int n_trsm = (Ls.nlb * kCB + 1) * kCB;
     for (int e0 = 0; e0 < n_trsm; e0 += nt) {       // warp-uniform trip count
       const int e = e0 + tid, row = e / kCB, c = e % kCB;
@@ -1850,7 +1849,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
 #pragma unroll
       for (int m = 0; m < kCB - 1; ++m) {
         const double x = __shfl_sync(0xffffffffu, t, base + m);
-        if (c > m) t = fma(-x, lkk[c * kCB + m], t);
+        if (c > m) t = fma(-x, lkk[(c - 1) * c / 2 + m], t);
       }
       if (a) a[c] = t * linvd[c];
     }
@@ -1860,9 +1859,10 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
       if (r <= k || r >= NB) continue;
       const double* R = rowp(lb);
       const int W = Ls.row_width(q, lb);
-      for (int e = tid; e < CS * kCB * kCB; e += nt) {
-        const int dst = e / (kCB * kCB), t = e % (kCB * kCB), i = t / kCB, m = t % kCB;
-        cluster.map_shared_rank(panel, dst)[(size_t)r * kCB * kCB + t] = R[i * W + kCB * k + m];
+      for (int e = tid; e < CS * kCB * kCB / 2; e += nt) {
+        const int dst = e / (kCB * kCB / 2), t = e % (kCB * kCB / 2), i = t / (kCB / 2), m = 2 * (t % (kCB / 2));
+        reinterpret_cast<double2*>(cluster.map_shared_rank(panel, dst) + (size_t)r * kCB * kCB)[t] =
+            *reinterpret_cast<const double2*>(R + i * W + kCB * k + m);
       }
     }
     cluster_arrive();                              // B_k
