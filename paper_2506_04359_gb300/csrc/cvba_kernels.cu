@@ -991,12 +991,19 @@ struct GroupChunk {
   static constexpr int value = sizeof(T) == 4 ? 16 : 8;
 };
 
+// Per-tile tables in front of the staging area: the landmarks' pair offsets, the window's
+// rotations and each keyframe's window slot (16-byte multiples).
+constexpr size_t kGroupLpBytes = ((SCHUR_TILE_LMS + 1) * sizeof(int) + 15) / 16 * 16;
+__host__ __device__ constexpr size_t group_rot_bytes(size_t t) { return (SPAN_MAX * 9 * t + 15) / 16 * 16; }
+constexpr size_t kGroupSlotBytes = K_MAX;
+
 size_t group_smem_bytes(int max_span, bool mixed) {
   const size_t t = mixed ? 4 : 8;
   const int ch = mixed ? 16 : 8;
   // the staging area also holds the groups' partials for the combine: <= 256 items x 18 x 8 B
   const size_t stage = std::max((size_t)ch * max_span * kStage * t, (size_t)SCHUR_THREADS * 18 * 8);
-  return sizeof(double) * 64 + t * (size_t)SCHUR_TILE_LMS * 9 + stage;
+  return sizeof(double) * 64 + t * (size_t)SCHUR_TILE_LMS * 9 + kGroupLpBytes + group_rot_bytes(t) +
+         kGroupSlotBytes + stage;
 }
 
 template <typename T>
@@ -1031,7 +1038,10 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
   double* s_red = smem;                               // 64
   T* s_vinv = reinterpret_cast<T*>(s_red + 64);       // SCHUR_TILE_LMS * 6
   T* s_gl = s_vinv + SCHUR_TILE_LMS * 6;              // SCHUR_TILE_LMS * 3
-  T* s_stg = s_gl + SCHUR_TILE_LMS * 3;               // CH * max_span * kStage
+  int* s_lp = reinterpret_cast<int*>(s_gl + SCHUR_TILE_LMS * 3);   // pair offsets of the tile's landmarks
+  T* s_rot = reinterpret_cast<T*>(reinterpret_cast<char*>(s_lp) + kGroupLpBytes);   // window rotations
+  signed char* s_slot = reinterpret_cast<signed char*>(s_rot) + group_rot_bytes(sizeof(T));   // per keyframe
+  T* s_stg = reinterpret_cast<T*>(s_slot + kGroupSlotBytes);   // CH * max_span * kStage
   __shared__ unsigned s_mask[16];                     // per staged landmark: keyframes present
   const SchurTile tile = d.schur_tiles[item];
   const int nl = tile.l1 - tile.l0;
@@ -1046,11 +1056,22 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
     for (int k = 0; k < 3; ++k) s_gl[l * 3 + k] = (T)d.lm_g[j * 3 + k];
   }
   if (span == 0) return;                             // landmarks seen only by the fixed keyframe
+  const T* pose = st_pose<T>(d, d.ctrl->cur);
+  // per tile, once: pair offsets, window slot of each keyframe (-1: fixed or outside) and
+  // the window's rotations, so that a chunk's pairs need only independent loads
+  for (int i = threadIdx.x; i <= nl; i += blockDim.x) s_lp[i] = d.lm_pair[tile.l0 + i];
+  for (int a = threadIdx.x; a < d.K; a += blockDim.x) {
+    const int pb = d.kf_pb[a];
+    s_slot[a] = (signed char)(pb >= tile.k_lo && pb < tile.k_lo + span ? pb - tile.k_lo : -1);
+  }
+  for (int e = threadIdx.x; e < span * 9; e += blockDim.x) {
+    const int pbk = tile.k_lo + e / 9, a = pbk < d.fixed_kf ? pbk : pbk + 1;
+    s_rot[e] = pose[a * POSE_STRIDE + e % 9];
+  }
   const int nblk = span * (span + 1) / 2;            // <= 253 (span <= SPAN_MAX)
   const int n_half = 2 * nblk;
   const int G = max(1, min(CH, SCHUR_THREADS / n_half));
   const int n_items = n_half * G;                    // > SCHUR_THREADS only when G == 1
-  const T* pose = st_pose<T>(d, d.ctrl->cur);
   Out* out = reinterpret_cast<Out*>(d.schur_part) + tile.part_off;
   for (int it0 = 0; it0 < n_items; it0 += SCHUR_THREADS) {   // passes
     const int t = it0 + threadIdx.x;
@@ -1074,16 +1095,19 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
       if (threadIdx.x < CH) s_mask[threadIdx.x] = 0u;
       __syncthreads();
       // stage each pair's terms as one 76-value record (16-byte stores) and mark it present
-      const int q0 = d.lm_pair[tile.l0 + c0], q1 = d.lm_pair[tile.l0 + c0 + nc];
+      const int q0 = s_lp[c0], q1 = s_lp[c0 + nc];
       for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
         const int a = d.pair_kf[q];
-        const int pb = d.kf_pb[a];
-        if (pb < 0) continue;
         const int l = d.pair_lm[q] - tile.l0;        // index in the tile
+        const T* plq = reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN;
+        T pv[PAIR_LIN];                              // loaded before the slot test: no load chain
+#pragma unroll
+        for (int k = 0; k < PAIR_LIN; ++k) pv[k] = plq[k];
+        const int w = s_slot[a];
+        if (w < 0) continue;
         T W[18], Y[18], Dg[21], bY[6];
-        pair_schur_terms<T>(reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN, pose + a * POSE_STRIDE,
-                            s_vinv + l * 6, s_gl + l * 3, W, Y, Dg, bY);
-        T* st = s_stg + ((l - c0) * span + (pb - tile.k_lo)) * kStage;
+        pair_schur_terms<T>(pv, s_rot + w * 9, s_vinv + l * 6, s_gl + l * 3, W, Y, Dg, bY);
+        T* st = s_stg + ((l - c0) * span + w) * kStage;
         if constexpr (sizeof(T) == 4) {              // 19 16-byte stores per record
           float4* s4 = reinterpret_cast<float4*>(st);
 #pragma unroll
@@ -1109,7 +1133,7 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
 #pragma unroll
           for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
         }
-        atomicOr(&s_mask[l - c0], 1u << (pb - tile.k_lo));
+        atomicOr(&s_mask[l - c0], 1u << w);
       }
       __syncthreads();
       // zero the records of keyframes of the window that a landmark does not observe
