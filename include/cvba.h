@@ -213,6 +213,20 @@ cvba_status cvba_batch_launch_count(cvba_batch* batch, const cvba_opts* opts, in
  * or 16).  cvba_batch_autotune times short batched solves over a grid of these sizes,
  * keeps the fastest, restores every window's state and reports the choice. */
 cvba_status cvba_set_tuning(cvba_ctx* ctx, int lin_tile_pairs, int schur_tile_landmarks);
+/* How the reduced camera system is factored (re-plans the window, keeping its state):
+ * 0 = by size (the default): systems of 320 rows or more take the blocked form, smaller ones
+ *     the cluster form;
+ * 1 = cluster form: one thread-block cluster factors A = L L^T in shared memory, 8-row
+ *     block steps, with the forward substitution fused;
+ * 2 = blocked form: right-looking by 32-column panels, the diagonal block of each panel
+ *     factored by one CTA and the panel solve and trailing update spread over the GPU (the
+ *     factor and y = L^-1 b in global memory); the cluster then runs the backward
+ *     substitution, the refinement and the candidate step from the factor.
+ * Both compute the FP64 Cholesky factorisation of the same damped reduced camera system
+ * (the pose system left by the Schur complement of Sec. 2.2) and differ in rounding order
+ * only.  Windows in a batch always use the cluster form.  CVBA_ERR_INVALID_ARG for another
+ * mode. */
+cvba_status cvba_set_chol_mode(cvba_ctx* ctx, int mode);
 cvba_status cvba_batch_set_chol_cluster(cvba_batch* batch, int cluster_size);
 cvba_status cvba_batch_autotune(cvba_batch* batch, const cvba_opts* opts, int* lin_tile_pairs,
                                 int* schur_tile_landmarks, int* cluster_size);

@@ -28,6 +28,7 @@ struct cvba_ctx {
   std::vector<int32_t> h_kf, h_cam, h_lm;       // caller's observations (for re-planning)
   std::vector<double> h_uv;
   int tune_lin_pairs = 0, tune_schur_lms = 0;   // 0: size-based defaults
+  int chol_mode = 0;                            // 0 size-based, 1 cluster, 2 blocked
   std::vector<LinTile> lin_tiles;
   std::vector<SchurTile> schur_tiles, direct_tiles;
 
@@ -478,6 +479,13 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   CK(dalloc(c, &d.S, (size_t)n_c * n_c), "alloc RCS");
   CK(dalloc(c, &d.bS, (size_t)n_c), "alloc");
   CK(dalloc(c, &d.dc, (size_t)n_c), "alloc");
+  // blocked factorisation of large systems: the factor and y in global memory (one element
+  // each otherwise, so that the buffers keep their places in the arena)
+  d.npw = (n_c + 31) / 32 * 32;
+  d.chol_blocked = c->chol_mode == 2 || (c->chol_mode == 0 && n_c >= kCholBlockedMinN) ? 1 : 0;
+  CK(dalloc(c, &d.Lw, d.chol_blocked ? (size_t)d.npw * d.npw : 1), "alloc");
+  CK(dalloc(c, &d.Ldinv, d.chol_blocked ? (size_t)d.npw : 1), "alloc");
+  CK(dalloc(c, &d.yw, d.chol_blocked ? (size_t)d.npw : 1), "alloc");
   CK(dalloc(c, &d.dp, (size_t)M * 3), "alloc");
   {
     double *kp, *sp;
@@ -736,12 +744,9 @@ cvba_status cvba_set_observations(cvba_ctx* c, int n_obs, const int32_t* kf, con
   return build_layout(c, kf, cam, lm, uv);
 }
 
-cvba_status cvba_set_tuning(cvba_ctx* c, int lin_tile_pairs, int schur_tile_landmarks) {
-  if (!c) return CVBA_ERR_INVALID_ARG;
-  if (lin_tile_pairs < 0 || schur_tile_landmarks < 0)
-    return fail(c, CVBA_ERR_INVALID_ARG, "set_tuning: sizes must be >= 0 (0 = default)");
-  c->tune_lin_pairs = lin_tile_pairs;
-  c->tune_schur_lms = schur_tile_landmarks;
+namespace {
+// Re-plan the layout with the same observations, keeping the state on the device.
+cvba_status replan(cvba_ctx* c) {
   if (!c->have_layout) return CVBA_OK;
   DeviceGuard g(c->device);
   // re-plan with the same observations; the state on the device is kept
@@ -758,6 +763,23 @@ cvba_status cvba_set_tuning(cvba_ctx* c, int lin_tile_pairs, int schur_tile_land
   st = build_layout(c, c->h_kf.data(), c->h_cam.data(), c->h_lm.data(), c->h_uv.data());
   if (st == CVBA_OK) st = cvba_set_damping(c, lam, nu);
   return st;
+}
+}  // namespace
+
+cvba_status cvba_set_tuning(cvba_ctx* c, int lin_tile_pairs, int schur_tile_landmarks) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (lin_tile_pairs < 0 || schur_tile_landmarks < 0)
+    return fail(c, CVBA_ERR_INVALID_ARG, "set_tuning: sizes must be >= 0 (0 = default)");
+  c->tune_lin_pairs = lin_tile_pairs;
+  c->tune_schur_lms = schur_tile_landmarks;
+  return replan(c);
+}
+
+cvba_status cvba_set_chol_mode(cvba_ctx* c, int mode) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 2) return fail(c, CVBA_ERR_INVALID_ARG, "set_chol_mode: mode must be 0, 1 or 2");
+  c->chol_mode = mode;
+  return replan(c);
 }
 
 namespace {

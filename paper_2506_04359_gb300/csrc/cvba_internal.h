@@ -24,6 +24,7 @@ constexpr int LIN_TILE_LMS = 256;       // landmarks per linearisation tile
 constexpr int SCHUR_TILE_PAIRS = 256;   // pairs staged in shared memory per Schur tile
 constexpr int SCHUR_TILE_LMS = 128;
 constexpr int SPAN_MAX = 22;            // free keyframes in one Schur tile's window (<= 253 blocks)
+constexpr int kCholBlockedMinN = 320;   // RCS size from which the blocked factorisation runs (mode 0)
 
 // Device-resident LM control block.  Written only by the solve's kernels.
 struct Ctrl {
@@ -100,6 +101,13 @@ struct Dev {
   double* bS;                 // n_c   sum of W V^-1 g_l
   double* dc;                 // n_c   pose increment
   double* dp;                 // M * 3 landmark increment
+  // blocked factorisation of large systems (chol_blocked = 1): the factor L (npw x npw, row
+  // stride npw, lower triangle; npw = n_c rounded up to whole 32-column panels), the
+  // reciprocals of its diagonal and y = L^-1 (rhs), read back by the cluster kernel
+  double* Lw;
+  double* Ldinv;
+  double* yw;
+  int npw, chol_blocked;
   // per-tile partials and the lists of tiles covering each keyframe / RCS block
   double* kf_part;            // per lin tile: kf_n * 12 (g_p 6, diag Hpp 6); mixed: float (hi, lo) pairs
   const int32_t* lin_kf_off;  // per lin tile, per keyframe of its range: start in lin_kf_idx (kf_n + 1)

@@ -631,7 +631,9 @@ __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_lin(Dev d) { pdl_enter(); k_lin_body<T>(d, blockIdx.x); }
+// Mixed path: five CTAs per SM (48 registers, a few spilled) hide more of the per-pair
+// global-load latency than three without spills (about 20 % faster on a 4M-observation window).
+__global__ void __launch_bounds__(LIN_THREADS, sizeof(T) == 4 ? 5 : 1) k_lin(Dev d) { pdl_enter(); k_lin_body<T>(d, blockIdx.x); }
 template <typename T>
 __global__ void __launch_bounds__(LIN_THREADS) k_lin_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
@@ -1578,12 +1580,18 @@ __device__ __forceinline__ double rsqrt_halley(double x, bool& ok) {
 __device__ __forceinline__ int ep_lane(int i, int j) { return j >= 1 ? (i - 1) * i / 2 + (j - 1) : 28 + (i & 3); }
 __device__ __forceinline__ bool ep_slot1(int i, int j) { return j == 0 && i >= 4; }
 
-// Factor the 8x8 block D (row stride NP) in place with warp 0 and push, to every CTA of
-// the cluster, the strictly lower block M with M_im = L_im / L_mm (m < i, 28 entries packed
-// row by row at (i-1)i/2 + m) and the reciprocals 1/L_mm of its diagonal: the form the
-// panel solve uses, 36 doubles sent as 16-byte stores (the number of remote stores, not
-// their size, sets the cost of the push).  A non-PD flag goes to every CTA.  rdiag (may be
-// null) keeps the reciprocals for the owner.
+// u 2^de for a normal u by adding de to the exponent bits (zero is kept as it is).
+__device__ __forceinline__ double scale_exp_bits(double u, int de) {
+  const int hi = __double2hiint(u);
+  return __hiloint2double((hi & 0x7ff00000) ? hi + de : hi, __double2loint(u));
+}
+
+// Packed index of the strictly lower entry (i, m), m < i, of an 8x8 diagonal block.
+__device__ __forceinline__ int pk_lower(int i, int m) { return (i - 1) * i / 2 + m; }
+
+// Factor the 8x8 block D (row stride NP) in place with warp 0 (other threads return at
+// once): L overwrites D, blk receives M_im = L_im / L_mm at pk_lower(i, m) (m < i) and the
+// reciprocals 1/L_ii at blk[28 + i]; a pivot that is not a positive normal number sets *flag.
 //
 // The pivot chain avoids square roots and divisions: column c is eliminated as
 //   a_ij <- (a_ij p_c - a_ic a_jc) 2^-e_c,   p_c = a_cc = m 2^e_c (1 <= m < 2),
@@ -1593,76 +1601,79 @@ __device__ __forceinline__ bool ep_slot1(int i, int j) { return j == 0 && i >= 4
 // multiplication and one FMA on the FP64 chain per pivot.  Afterwards, with
 // R_j = (p_j s_j)^-1/2: L_ij = a_ij R_j (i >= j, a_ij the value when column j was the pivot
 // column), 1/L_jj = s_j R_j and M_ij = a_ij / p_j.
-__device__ __forceinline__ double scale_exp_bits(double u, int de) {
-  const int hi = __double2hiint(u);               // u 2^de for normal u (zero kept as is)
-  return __hiloint2double((hi & 0x7ff00000) ? hi + de : hi, __double2loint(u));
+__device__ __forceinline__ void factor8_warp(double* D, int NP, double* blk, int* flag) {
+  const int tid = threadIdx.x;
+  if (tid >= 32) return;
+  const unsigned full = 0xffffffffu;
+  const int lane = tid;
+  int i0, j0;                                      // slot-0 entry of this lane
+  if (lane < 28) {
+    i0 = 1;
+    while (i0 * (i0 + 1) / 2 <= lane) ++i0;
+    j0 = lane - (i0 - 1) * i0 / 2 + 1;
+  } else {
+    i0 = lane - 28;
+    j0 = 0;
+  }
+  double v0 = D[i0 * NP + j0];
+  double v1 = lane >= 28 ? D[(lane - 24) * NP] : 0.0;
+  bool bad = false;
+  double pk = 1.0, ph = 1.0;                       // lane c < 8: p_c and its mantissa p_c 2^-e_c
+#pragma unroll
+  for (int c = 0; c < kCB; ++c) {
+    const double p = __shfl_sync(full, v0, ep_lane(c, c));
+    const int phi = __double2hiint(p);
+    const int ex = (phi >> 20) & 0x7ff;
+    bad |= phi < 0x00100000 || ex == 0x7ff;        // not a positive normal number
+    if (lane == c) {
+      pk = p;
+      ph = __hiloint2double((phi & 0x800fffff) | 0x3ff00000, __double2loint(p));
+    }
+    const int la = ep_lane(i0, c), lb = ep_lane(j0, c);
+    const double xa0 = __shfl_sync(full, v0, la), xa1 = __shfl_sync(full, v1, la);
+    const double xb0 = __shfl_sync(full, v0, lb), xb1 = __shfl_sync(full, v1, lb);
+    const double aic = ep_slot1(i0, c) ? xa1 : xa0;
+    const double ajc = ep_slot1(j0, c) ? xb1 : xb0;
+    if (lane < 28 && j0 > c) v0 = scale_exp_bits(fma(v0, p, -(aic * ajc)), (1023 - ex) * 0x100000);
+  }
+  // s_c = prod_{m < c} mantissa(p_m): inclusive scan over lanes 0-7, then shifted by one
+  double sc = ph;
+#pragma unroll
+  for (int o = 1; o < kCB; o <<= 1) {
+    const double y = __shfl_up_sync(full, sc, o);
+    if (lane >= o) sc *= y;
+  }
+  sc = __shfl_up_sync(full, sc, 1);
+  if (lane == 0) sc = 1.0;
+  bool ok;
+  const double R = rsqrt_halley(pk * sc, ok);
+  if (lane < kCB) bad |= !ok;
+  const double dinv = sc * R;                      // 1/L_cc
+  const double qinv = dinv * R;                    // 1/p_c
+  const double Rj = __shfl_sync(full, R, j0), Qj = __shfl_sync(full, qinv, j0);
+  D[i0 * NP + j0] = v0 * Rj;
+  if (lane >= 28) D[(lane - 24) * NP] = v1 * Rj;
+  if (lane < 28) {
+    if (j0 < i0) blk[pk_lower(i0, j0)] = v0 * Qj;
+  } else {
+    if (i0 > 0) blk[pk_lower(i0, 0)] = v0 * Qj;
+    blk[pk_lower(lane - 24, 0)] = v1 * Qj;
+  }
+  if (lane < kCB) blk[kCB * (kCB - 1) / 2 + lane] = dinv;
+  bad = __any_sync(full, bad);
+  if (lane == 0 && bad) *flag = 1;
 }
 
+// Factor the 8x8 block D (row stride NP) in place and push, to every CTA of the cluster, the
+// strictly lower block M (28 entries packed row by row) and the reciprocals 1/L_mm of its
+// diagonal: the form the panel solve uses, 36 doubles sent as 16-byte stores (the number of
+// remote stores, not their size, sets the cost of the push).  A non-PD flag goes to every
+// CTA.  rdiag (may be null) keeps the reciprocals for the owner.
 __device__ __forceinline__ void chol_factor_push(double* D, int NP, double* lkk, int* flag, double* rdiag,
                                                  cooperative_groups::cluster_group& cluster, int CS) {
   const int tid = threadIdx.x;
   __shared__ __align__(16) double s_blk[kCB * (kCB - 1) / 2 + kCB];   // packed M, then 1/L_mm
-  if (tid < 32) {
-    const unsigned full = 0xffffffffu;
-    const int lane = tid;
-    int i0, j0;                                    // slot-0 entry of this lane
-    if (lane < 28) {
-      i0 = 1;
-      while (i0 * (i0 + 1) / 2 <= lane) ++i0;
-      j0 = lane - (i0 - 1) * i0 / 2 + 1;
-    } else {
-      i0 = lane - 28;
-      j0 = 0;
-    }
-    double v0 = D[i0 * NP + j0];
-    double v1 = lane >= 28 ? D[(lane - 24) * NP] : 0.0;
-    bool bad = false;
-    double pk = 1.0, ph = 1.0;                     // lane c < 8: p_c and its mantissa p_c 2^-e_c
-#pragma unroll
-    for (int c = 0; c < kCB; ++c) {
-      const double p = __shfl_sync(full, v0, ep_lane(c, c));
-      const int phi = __double2hiint(p);
-      const int ex = (phi >> 20) & 0x7ff;
-      bad |= phi < 0x00100000 || ex == 0x7ff;      // not a positive normal number
-      if (lane == c) {
-        pk = p;
-        ph = __hiloint2double((phi & 0x800fffff) | 0x3ff00000, __double2loint(p));
-      }
-      const int la = ep_lane(i0, c), lb = ep_lane(j0, c);
-      const double xa0 = __shfl_sync(full, v0, la), xa1 = __shfl_sync(full, v1, la);
-      const double xb0 = __shfl_sync(full, v0, lb), xb1 = __shfl_sync(full, v1, lb);
-      const double aic = ep_slot1(i0, c) ? xa1 : xa0;
-      const double ajc = ep_slot1(j0, c) ? xb1 : xb0;
-      if (lane < 28 && j0 > c) v0 = scale_exp_bits(fma(v0, p, -(aic * ajc)), (1023 - ex) * 0x100000);
-    }
-    // s_c = prod_{m < c} mantissa(p_m): inclusive scan over lanes 0-7, then shifted by one
-    double sc = ph;
-#pragma unroll
-    for (int o = 1; o < kCB; o <<= 1) {
-      const double y = __shfl_up_sync(full, sc, o);
-      if (lane >= o) sc *= y;
-    }
-    sc = __shfl_up_sync(full, sc, 1);
-    if (lane == 0) sc = 1.0;
-    bool ok;
-    const double R = rsqrt_halley(pk * sc, ok);
-    if (lane < kCB) bad |= !ok;
-    const double dinv = sc * R;                    // 1/L_cc
-    const double qinv = dinv * R;                  // 1/p_c
-    const double Rj = __shfl_sync(full, R, j0), Qj = __shfl_sync(full, qinv, j0);
-    D[i0 * NP + j0] = v0 * Rj;
-    if (lane >= 28) D[(lane - 24) * NP] = v1 * Rj;
-    if (lane < 28) {
-      if (j0 < i0) s_blk[(i0 - 1) * i0 / 2 + j0] = v0 * Qj;
-    } else {
-      if (i0 > 0) s_blk[(i0 - 1) * i0 / 2] = v0 * Qj;
-      const int r1 = lane - 24;
-      s_blk[(r1 - 1) * r1 / 2] = v1 * Qj;
-    }
-    if (lane < kCB) s_blk[kCB * (kCB - 1) / 2 + lane] = dinv;
-    bad = __any_sync(full, bad);
-    if (lane == 0 && bad) *flag = 1;
-  }
+  factor8_warp(D, NP, s_blk, flag);
   __syncthreads();
   if (rdiag && tid < kCB) rdiag[tid] = s_blk[kCB * (kCB - 1) / 2 + tid];
   constexpr int NV2 = (kCB * (kCB - 1) / 2 + kCB) / 2;   // 16-byte stores per CTA
@@ -1809,142 +1820,165 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   const double floor_ = diag_floor(d, red);        // block-level, contains barriers
   auto rowp = [&](int lb) { return rows + Ls.row_off(q, lb); };
 
-  // ---- load own block rows (damped, padded), rhs on CTA 0
-  for (int lb = 0; lb < Ls.nlb; ++lb) {
-    const int r = q + lb * CS;
-    if (r >= NB) break;
-    const int W = Ls.row_width(q, lb);
-    double* R = rowp(lb);
-    for (int e = tid; e < kCB * W; e += nt) {
-      const int i = e / W, c = e % W, gi = kCB * r + i;
-      double v = 0.0;
-      if (gi < n && c < n) {
-        if (c <= gi) v = d.S[(size_t)gi * n + c];
-        if (c == gi) v += rcs_damp(d, gi, lam, floor_);
-      } else if (gi >= n && c == gi) {
-        v = 1.0;
-      }
-      R[e] = v;
-    }
-  }
-  for (int c = tid; c < NP; c += nt) {
-    ybuf[c] = (q == 0 && c < n) ? rcs_rhs(d, c) : 0.0;
-    acc[c] = 0.0;
-  }
-  for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
-  if (tid == 0) *flag = 0;
-  cluster.sync();
-  if (q == 0) chol_factor_push(rows, kCB, lkk0, flag, rdiag, cluster, CS);   // block 0: CTA 0's first row block
-  cluster_arrive();                                // A_0
-
-  // ---- factorisation with the forward substitution fused.  Per step k two split
-  // barriers: A_k (L_kk pushed) and B_k (panel k pushed).  The owner of block k+1 factors
-  // it between its arrival at B_k and its wait there, so the factorisation does not wait
-  // for the whole cluster's panel exchange, and every CTA arrives at A_{k+1} before its
-  // trailing update.  L_kk and the panels alternate between two buffers.
-  bool broke = false;
-  for (int k = 0; k < NB; ++k) {
-    cluster_wait();                                // A_k: L_kk (and flag) visible everywhere
-    if (*flag) {                                   // uniform: pushed before A_k
-      broke = true;
-      break;
-    }
-    const double* lkk = lkk0 + (k & 1) * (kCB * kCB + kCB);
-    double* panel = panel0 + (size_t)(k & 1) * NB * kCB * kCB;
-    // 1. TRSM of own block rows below k, and of the right-hand side on CTA 0: solve
-    //    t L_kk^T = a for each row, entry-parallel (8 lanes per row, one column each).
-    //    With u_c = t_c L_cc: u_c = a_c - sum_{m<c} u_m M_cm (M_cm = L_cm / L_mm, pushed
-    //    with L_kk), one update instruction per column, and t_c = u_c / L_cc at the end.
-    const double* linvd = lkk + kCB * (kCB - 1) / 2;
-    const int n_trsm = (Ls.nlb * kCB + 1) * kCB;
-    for (int e0 = 0; e0 < n_trsm; e0 += nt) {       // warp-uniform trip count
-      const int e = e0 + tid, row = e / kCB, c = e % kCB;
-      double* a = nullptr;
-      if (e < n_trsm) {
-        if (row < Ls.nlb * kCB) {
-          const int lb = row / kCB, i = row % kCB, r = q + lb * CS;
-          if (r > k && r < NB) a = rowp(lb) + i * Ls.row_width(q, lb) + kCB * k;
-        } else if (q == 0) {
-          a = ybuf + kCB * k;
-        }
-      }
-      double t = a ? a[c] : 0.0;
-      const int base = (tid & 31) & ~(kCB - 1);
-#pragma unroll
-      for (int m = 0; m < kCB - 1; ++m) {
-        const double x = __shfl_sync(0xffffffffu, t, base + m);
-        if (c > m) t = fma(-x, lkk[(c - 1) * c / 2 + m], t);
-      }
-      if (a) a[c] = t * linvd[c];
-    }
-    __syncthreads();
-    for (int lb = 0; lb < Ls.nlb; ++lb) {          // push panel blocks L_rk to every CTA
-      const int r = q + lb * CS;
-      if (r <= k || r >= NB) continue;
-      const double* R = rowp(lb);
-      const int W = Ls.row_width(q, lb);
-      for (int e = tid; e < CS * kCB * kCB / 2; e += nt) {
-        const int dst = e / (kCB * kCB / 2), t = e % (kCB * kCB / 2), i = t / (kCB / 2), m = 2 * (t % (kCB / 2));
-        reinterpret_cast<double2*>(cluster.map_shared_rank(panel, dst) + (size_t)r * kCB * kCB)[t] =
-            *reinterpret_cast<const double2*>(R + i * W + kCB * k + m);
-      }
-    }
-    cluster_arrive();                              // B_k
-    // 2a. look-ahead: owner of block k+1 updates its diagonal block with its own L_{k+1,k}
-    //     and factors it
-    if (k + 1 < NB && q == (k + 1) % CS) {
-      const int lb = (k + 1) / CS;
-      double* R = rowp(lb);
-      const int W = Ls.row_width(q, lb);
-      for (int e = tid; e < kCB * kCB; e += nt) {
-        const int i = e / kCB, j = e % kCB;
-        if (j > i) continue;
-        double s = 0.0;
-#pragma unroll
-        for (int m = 0; m < kCB; ++m) s = fma(R[i * W + kCB * k + m], R[j * W + kCB * k + m], s);
-        R[i * W + kCB * (k + 1) + j] -= s;
-      }
-      __syncthreads();
-      chol_factor_push(R + kCB * (k + 1), W, lkk0 + ((k + 1) & 1) * (kCB * kCB + kCB), flag, rdiag + lb * kCB,
-                       cluster, CS);
-    }
-    cluster_wait();                                // B_k: panel k visible everywhere
-    // L_{k+1,k+1} is pushed: signal A_{k+1} before this CTA's trailing update, which then
-    // overlaps the next step's chain.  Panels alternate between two buffers, and a CTA
-    // cannot reach the next write of this buffer (step k+2) before every CTA has arrived
-    // at A_{k+2}, after its own trailing update of step k.
-    cluster_arrive();                              // A_{k+1}
-    // 2b. trailing update of own block rows: A_rc -= L_rk L_ck^T, c in (k, r]
+  if (d.chol_blocked) {
+    // ---- the factor, the reciprocals of its diagonal and y = L^-1 rhs come from the blocked
+    // kernels (global memory): own block rows, every CTA a copy of y
     for (int lb = 0; lb < Ls.nlb; ++lb) {
       const int r = q + lb * CS;
-      if (r <= k + 1 || r >= NB) continue;
-      double* R = rowp(lb);
+      if (r >= NB) break;
       const int W = Ls.row_width(q, lb);
-      const double* Lr = panel + (size_t)r * kCB * kCB;
-      const int cnt = (r - k) * kCB * kCB;
-      for (int e = tid; e < cnt; e += nt) {
-        const int c = k + 1 + e / (kCB * kCB), t = e % (kCB * kCB), i = t / kCB, j = t % kCB;
-        const double* Lc = panel + (size_t)c * kCB * kCB + j * kCB;
-        double s = 0.0;
-#pragma unroll
-        for (int m = 0; m < kCB; ++m) s = fma(Lr[i * kCB + m], Lc[m], s);
-        R[i * W + kCB * c + j] -= s;
+      double* R = rowp(lb);
+      for (int e = tid; e < kCB * W; e += nt) {
+        const int i = e / W, c = e % W, gi = kCB * r + i;
+        R[e] = c <= gi ? d.Lw[(size_t)gi * d.npw + c] : 0.0;
+      }
+      if (tid < kCB) rdiag[lb * kCB + tid] = d.Ldinv[kCB * r + tid];
+    }
+    for (int c = tid; c < NP; c += nt) {
+      ybuf[c] = d.yw[c];
+      acc[c] = 0.0;
+    }
+    for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
+    if (tid == 0) *flag = 0;
+    cluster.sync();
+  } else {
+    // ---- load own block rows (damped, padded), rhs on CTA 0
+    for (int lb = 0; lb < Ls.nlb; ++lb) {
+      const int r = q + lb * CS;
+      if (r >= NB) break;
+      const int W = Ls.row_width(q, lb);
+      double* R = rowp(lb);
+      for (int e = tid; e < kCB * W; e += nt) {
+        const int i = e / W, c = e % W, gi = kCB * r + i;
+        double v = 0.0;
+        if (gi < n && c < n) {
+          if (c <= gi) v = d.S[(size_t)gi * n + c];
+          if (c == gi) v += rcs_damp(d, gi, lam, floor_);
+        } else if (gi >= n && c == gi) {
+          v = 1.0;
+        }
+        R[e] = v;
       }
     }
-    if (q == 0) {
-      const double* y = ybuf + kCB * k;
-      for (int e = tid; e < NP - kCB * (k + 1); e += nt) {
-        const int g = kCB * (k + 1) + e, c = g / kCB, j = g % kCB;
-        const double* Lc = panel + (size_t)c * kCB * kCB + j * kCB;
-        double s = 0.0;
-#pragma unroll
-        for (int m = 0; m < kCB; ++m) s = fma(y[m], Lc[m], s);
-        ybuf[g] -= s;
-      }
+    for (int c = tid; c < NP; c += nt) {
+      ybuf[c] = (q == 0 && c < n) ? rcs_rhs(d, c) : 0.0;
+      acc[c] = 0.0;
     }
-    __syncthreads();                               // own rows updated before the next TRSM
+    for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
+    if (tid == 0) *flag = 0;
+    cluster.sync();
+    if (q == 0) chol_factor_push(rows, kCB, lkk0, flag, rdiag, cluster, CS);   // block 0: CTA 0's first row block
+    cluster_arrive();                                // A_0
+
+    // ---- factorisation with the forward substitution fused.  Per step k two split
+    // barriers: A_k (L_kk pushed) and B_k (panel k pushed).  The owner of block k+1 factors
+    // it between its arrival at B_k and its wait there, so the factorisation does not wait
+    // for the whole cluster's panel exchange, and every CTA arrives at A_{k+1} before its
+    // trailing update.  L_kk and the panels alternate between two buffers.
+    bool broke = false;
+    for (int k = 0; k < NB; ++k) {
+      cluster_wait();                                // A_k: L_kk (and flag) visible everywhere
+      if (*flag) {                                   // uniform: pushed before A_k
+        broke = true;
+        break;
+      }
+      const double* lkk = lkk0 + (k & 1) * (kCB * kCB + kCB);
+      double* panel = panel0 + (size_t)(k & 1) * NB * kCB * kCB;
+      // 1. TRSM of own block rows below k, and of the right-hand side on CTA 0: solve
+      //    t L_kk^T = a for each row, entry-parallel (8 lanes per row, one column each).
+      //    With u_c = t_c L_cc: u_c = a_c - sum_{m<c} u_m M_cm (M_cm = L_cm / L_mm, pushed
+      //    with L_kk), one update instruction per column, and t_c = u_c / L_cc at the end.
+      const double* linvd = lkk + kCB * (kCB - 1) / 2;
+      const int n_trsm = (Ls.nlb * kCB + 1) * kCB;
+      for (int e0 = 0; e0 < n_trsm; e0 += nt) {       // warp-uniform trip count
+        const int e = e0 + tid, row = e / kCB, c = e % kCB;
+        double* a = nullptr;
+        if (e < n_trsm) {
+          if (row < Ls.nlb * kCB) {
+            const int lb = row / kCB, i = row % kCB, r = q + lb * CS;
+            if (r > k && r < NB) a = rowp(lb) + i * Ls.row_width(q, lb) + kCB * k;
+          } else if (q == 0) {
+            a = ybuf + kCB * k;
+          }
+        }
+        double t = a ? a[c] : 0.0;
+        const int base = (tid & 31) & ~(kCB - 1);
+  #pragma unroll
+        for (int m = 0; m < kCB - 1; ++m) {
+          const double x = __shfl_sync(0xffffffffu, t, base + m);
+          if (c > m) t = fma(-x, lkk[(c - 1) * c / 2 + m], t);
+        }
+        if (a) a[c] = t * linvd[c];
+      }
+      __syncthreads();
+      for (int lb = 0; lb < Ls.nlb; ++lb) {          // push panel blocks L_rk to every CTA
+        const int r = q + lb * CS;
+        if (r <= k || r >= NB) continue;
+        const double* R = rowp(lb);
+        const int W = Ls.row_width(q, lb);
+        for (int e = tid; e < CS * kCB * kCB / 2; e += nt) {
+          const int dst = e / (kCB * kCB / 2), t = e % (kCB * kCB / 2), i = t / (kCB / 2), m = 2 * (t % (kCB / 2));
+          reinterpret_cast<double2*>(cluster.map_shared_rank(panel, dst) + (size_t)r * kCB * kCB)[t] =
+              *reinterpret_cast<const double2*>(R + i * W + kCB * k + m);
+        }
+      }
+      cluster_arrive();                              // B_k
+      // 2a. look-ahead: owner of block k+1 updates its diagonal block with its own L_{k+1,k}
+      //     and factors it
+      if (k + 1 < NB && q == (k + 1) % CS) {
+        const int lb = (k + 1) / CS;
+        double* R = rowp(lb);
+        const int W = Ls.row_width(q, lb);
+        for (int e = tid; e < kCB * kCB; e += nt) {
+          const int i = e / kCB, j = e % kCB;
+          if (j > i) continue;
+          double s = 0.0;
+  #pragma unroll
+          for (int m = 0; m < kCB; ++m) s = fma(R[i * W + kCB * k + m], R[j * W + kCB * k + m], s);
+          R[i * W + kCB * (k + 1) + j] -= s;
+        }
+        __syncthreads();
+        chol_factor_push(R + kCB * (k + 1), W, lkk0 + ((k + 1) & 1) * (kCB * kCB + kCB), flag, rdiag + lb * kCB,
+                         cluster, CS);
+      }
+      cluster_wait();                                // B_k: panel k visible everywhere
+      // L_{k+1,k+1} is pushed: signal A_{k+1} before this CTA's trailing update, which then
+      // overlaps the next step's chain.  Panels alternate between two buffers, and a CTA
+      // cannot reach the next write of this buffer (step k+2) before every CTA has arrived
+      // at A_{k+2}, after its own trailing update of step k.
+      cluster_arrive();                              // A_{k+1}
+      // 2b. trailing update of own block rows: A_rc -= L_rk L_ck^T, c in (k, r]
+      for (int lb = 0; lb < Ls.nlb; ++lb) {
+        const int r = q + lb * CS;
+        if (r <= k + 1 || r >= NB) continue;
+        double* R = rowp(lb);
+        const int W = Ls.row_width(q, lb);
+        const double* Lr = panel + (size_t)r * kCB * kCB;
+        const int cnt = (r - k) * kCB * kCB;
+        for (int e = tid; e < cnt; e += nt) {
+          const int c = k + 1 + e / (kCB * kCB), t = e % (kCB * kCB), i = t / kCB, j = t % kCB;
+          const double* Lc = panel + (size_t)c * kCB * kCB + j * kCB;
+          double s = 0.0;
+  #pragma unroll
+          for (int m = 0; m < kCB; ++m) s = fma(Lr[i * kCB + m], Lc[m], s);
+          R[i * W + kCB * c + j] -= s;
+        }
+      }
+      if (q == 0) {
+        const double* y = ybuf + kCB * k;
+        for (int e = tid; e < NP - kCB * (k + 1); e += nt) {
+          const int g = kCB * (k + 1) + e, c = g / kCB, j = g % kCB;
+          const double* Lc = panel + (size_t)c * kCB * kCB + j * kCB;
+          double s = 0.0;
+  #pragma unroll
+          for (int m = 0; m < kCB; ++m) s = fma(y[m], Lc[m], s);
+          ybuf[g] -= s;
+        }
+      }
+      __syncthreads();                               // own rows updated before the next TRSM
+    }
+    if (!broke) cluster_wait();                      // A_NB: the factor complete everywhere
   }
-  if (!broke) cluster_wait();                      // A_NB: the factor complete everywhere
   if (*flag) {
     if (q == 0 && tid == 0) ctrl->nonpd = 1;
     return;
@@ -2141,6 +2175,175 @@ __global__ void __launch_bounds__(256) k_chol_cluster_b(const Dev* __restrict__ 
   chol_cluster_body(sd);
 }
 
+// ------------------------------------------------- blocked Cholesky (large systems)
+// When the reduced camera system is large, the trailing updates of one cluster (16 SMs of
+// FP64) bound the factorisation, so A = L L^T is factored right-looking by 32-column
+// panels with the updates spread over the whole GPU.  Per panel p (columns [32p, 32p + 32)):
+//   k_blk_panel  one CTA factors the 32 x 32 diagonal block (8x8 sub-blocks: factor, panel
+//                solve and update inside the CTA) and forward-substitutes its part of y;
+//   k_blk_trsm   a warp per row below solves L_ip L_pp^T = A_ip and updates y_i -= L_ip y_p;
+//   k_blk_syrk   16 x 16 tiles of the trailing lower triangle take A_ij -= L_ip L_jp^T.
+// k_blk_load first copies the damped system (padding rows: identity) and the right-hand side
+// to the working arrays.  The cluster kernel then reads the factor back for the backward
+// substitution, the refinement and the epilogue.  The right-hand side is carried the same
+// way as in the cluster kernel (y = L^-1 (b - g_p) formed during the factorisation).
+constexpr int kPW = 32;                            // panel width
+constexpr int kPD = kPW + 1;                       // shared-memory row stride (no bank conflicts)
+
+__global__ void __launch_bounds__(256) k_blk_load(Dev d) { pdl_enter();
+  __shared__ double s_red[64];
+  Ctrl* ctrl = d.ctrl;
+  if (ctrl->nonpd) return;
+  const double lam = ctrl->lam;
+  const double floor_ = diag_floor(d, s_red);      // block-level, contains barriers
+  const int n = d.n_c, npw = d.npw;
+  const size_t total = (size_t)npw * npw;
+  for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / npw), j = (int)(e % npw);
+    double v = 0.0;
+    if (j <= i) {
+      if (i < n) {
+        v = d.S[(size_t)i * n + j];
+        if (i == j) v += rcs_damp(d, i, lam, floor_);
+      } else if (i == j) {
+        v = 1.0;
+      }
+    }
+    d.Lw[e] = v;
+  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npw; i += gridDim.x * blockDim.x)
+    d.yw[i] = i < n ? rcs_rhs(d, i) : 0.0;
+}
+
+__global__ void __launch_bounds__(256) k_blk_panel(Dev d, int p) { pdl_enter();
+  __shared__ double D[kPW * kPD];                  // the diagonal block
+  __shared__ __align__(16) double s_b8[kCB * (kCB - 1) / 2 + kCB];
+  __shared__ double s_dinv[kPW], s_y[kPW];
+  __shared__ int s_flag;
+  Ctrl* ctrl = d.ctrl;
+  if (ctrl->nonpd) return;
+  const int npw = d.npw, o = p * kPW, tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < kPW * kPW; e += nt) {
+    const int i = e / kPW, j = e % kPW;
+    D[i * kPD + j] = j <= i ? d.Lw[(size_t)(o + i) * npw + o + j] : 0.0;
+  }
+  if (tid < kPW) s_y[tid] = d.yw[o + tid];
+  if (tid == 0) s_flag = 0;
+  __syncthreads();
+  for (int kb = 0; kb < kPW / kCB; ++kb) {
+    const int c0 = kb * kCB;
+    factor8_warp(D + c0 * kPD + c0, kPD, s_b8, &s_flag);
+    __syncthreads();
+    if (tid < kCB) s_dinv[c0 + tid] = s_b8[kCB * (kCB - 1) / 2 + tid];
+    // sub-block rows below: t L_kk^T = a, 8 lanes per row (one column each)
+    {
+      const int row = c0 + kCB + tid / kCB, c = tid % kCB, base = (tid & 31) & ~(kCB - 1);
+      double t = row < kPW ? D[row * kPD + c0 + c] : 0.0;
+#pragma unroll
+      for (int m = 0; m < kCB - 1; ++m) {
+        const double x = __shfl_sync(0xffffffffu, t, base + m);
+        if (c > m) t = fma(-x, s_b8[pk_lower(c, m)], t);
+      }
+      if (row < kPW) D[row * kPD + c0 + c] = t * s_b8[kCB * (kCB - 1) / 2 + c];
+    }
+    __syncthreads();
+    // trailing entries of the block: D_rc -= sum_m L_r,m L_c,m over this sub-block's columns
+    const int r0 = c0 + kCB, R = kPW - r0;
+    for (int e = tid; e < R * R; e += nt) {
+      const int r = r0 + e / R, c = r0 + e % R;
+      if (c > r) continue;
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < kCB; ++m) acc = fma(D[r * kPD + c0 + m], D[c * kPD + c0 + m], acc);
+      D[r * kPD + c] -= acc;
+    }
+    __syncthreads();
+  }
+  // y_p = L_pp^-1 y_p: v_c = y_c - sum_{m<c} (L_cm / L_mm) v_m, then y_c = v_c / L_cc
+  if (tid < 32) {
+    double v = s_y[tid];
+#pragma unroll 4
+    for (int m = 0; m < kPW - 1; ++m) {
+      const double mcm = tid > m ? D[tid * kPD + m] * s_dinv[m] : 0.0;
+      const double x = __shfl_sync(0xffffffffu, v, m);
+      if (tid > m) v = fma(-x, mcm, v);
+    }
+    s_y[tid] = v * s_dinv[tid];
+  }
+  __syncthreads();
+  for (int e = tid; e < kPW * kPW; e += nt) {
+    const int i = e / kPW, j = e % kPW;
+    if (j <= i) d.Lw[(size_t)(o + i) * npw + o + j] = D[i * kPD + j];
+  }
+  if (tid < kPW) {
+    d.Ldinv[o + tid] = s_dinv[tid];
+    d.yw[o + tid] = s_y[tid];
+  }
+  if (tid == 0 && s_flag) ctrl->nonpd = 1;
+}
+
+// One warp per row below panel p (8 rows per CTA): L_ip = A_ip L_pp^-T by the same
+// column recursion as the cluster's panel solve, then y_i -= L_ip y_p.
+__global__ void __launch_bounds__(256) k_blk_trsm(Dev d, int p) { pdl_enter();
+  __shared__ double s_mt[kPW * kPW];               // s_mt[m * 32 + c] = L_cm / L_mm (c > m)
+  __shared__ double s_dv[kPW], s_yp[kPW];
+  Ctrl* ctrl = d.ctrl;
+  if (ctrl->nonpd) return;
+  const int npw = d.npw, o = p * kPW, tid = threadIdx.x;
+  for (int e = tid; e < kPW * kPW; e += blockDim.x) {
+    const int m = e / kPW, c = e % kPW;
+    s_mt[e] = c > m ? d.Lw[(size_t)(o + c) * npw + o + m] * d.Ldinv[o + m] : 0.0;
+  }
+  if (tid < kPW) {
+    s_dv[tid] = d.Ldinv[o + tid];
+    s_yp[tid] = d.yw[o + tid];
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;
+  const int row = o + kPW + blockIdx.x * 8 + warp;
+  double* a = d.Lw + (size_t)row * npw + o;
+  double u = a[lane];
+#pragma unroll 4
+  for (int m = 0; m < kPW - 1; ++m) {
+    const double x = __shfl_sync(0xffffffffu, u, m);
+    if (lane > m) u = fma(-x, s_mt[m * kPW + lane], u);
+  }
+  const double t = u * s_dv[lane];
+  a[lane] = t;
+  const double sy = warp_sum(t * s_yp[lane]);
+  if (lane == 0) d.yw[row] -= sy;
+}
+
+// Trailing update after panel p: 16 x 16 tile (ti, tj), ti >= tj, of the rows and columns
+// below the panel: A_ij -= sum over the panel's 32 columns of L_i,m L_j,m.
+__global__ void __launch_bounds__(256) k_blk_syrk(Dev d, int p) { pdl_enter();
+  __shared__ double s_a[16 * kPD], s_b[16 * kPD];
+  Ctrl* ctrl = d.ctrl;
+  if (ctrl->nonpd) return;
+  const int npw = d.npw, o = p * kPW, o2 = o + kPW, tid = threadIdx.x;
+  const int blk = blockIdx.x;
+  int ti = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+  while (ti * (ti + 1) / 2 > blk) --ti;
+  while ((ti + 1) * (ti + 2) / 2 <= blk) ++ti;
+  const int tj = blk - ti * (ti + 1) / 2;
+  for (int e = tid; e < 16 * kPW; e += blockDim.x) {
+    const int r = e / kPW, m = e % kPW;
+    s_a[r * kPD + m] = d.Lw[(size_t)(o2 + 16 * ti + r) * npw + o + m];
+    s_b[r * kPD + m] = d.Lw[(size_t)(o2 + 16 * tj + r) * npw + o + m];
+  }
+  __syncthreads();
+  const int r = tid / 16, c = tid % 16;
+  const int gi = o2 + 16 * ti + r, gj = o2 + 16 * tj + c;
+  if (gj > gi) return;
+  double acc0 = 0.0, acc1 = 0.0;
+#pragma unroll
+  for (int m = 0; m < kPW; m += 2) {
+    acc0 = fma(s_a[r * kPD + m], s_b[c * kPD + m], acc0);
+    acc1 = fma(s_a[r * kPD + m + 1], s_b[c * kPD + m + 1], acc1);
+  }
+  d.Lw[(size_t)gi * npw + gj] -= acc0 + acc1;
+}
+
 // --------------------------------------------------------------- k_backsub
 template <typename T>
 __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
@@ -2291,7 +2494,8 @@ __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(LIN_THREADS) k_backsub(Dev d) { pdl_enter(); k_backsub_body<T>(d, blockIdx.x); }
+// Mixed path: seven CTAs per SM (32 registers), likewise latency-bound (about 12 % faster).
+__global__ void __launch_bounds__(LIN_THREADS, sizeof(T) == 4 ? 7 : 1) k_backsub(Dev d) { pdl_enter(); k_backsub_body<T>(d, blockIdx.x); }
 template <typename T>
 __global__ void __launch_bounds__(LIN_THREADS) k_backsub_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
@@ -2628,6 +2832,21 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   if ((e = mark(5)) != cudaSuccess) return e;
   if (chol_cluster_size(d.n_c) > 0) {
     const int CS = chol_cluster_size(d.n_c);
+    if (d.chol_blocked) {
+      // blocked factorisation; the cluster kernel below then solves from the factor
+      const int npan = d.npw / kPW;
+      const size_t n_load = std::min(((size_t)d.npw * d.npw + 255) / 256, (size_t)152 * 8);
+      if ((e = launch_ex(k_blk_load, dim3((unsigned)n_load), dim3(256), 0, s, 0, d)) != cudaSuccess) return e;
+      for (int p = 0; p < npan; ++p) {
+        if ((e = launch_ex(k_blk_panel, dim3(1), dim3(256), 0, s, 0, d, p)) != cudaSuccess) return e;
+        const int below = d.npw - kPW * (p + 1);
+        if (below == 0) break;
+        if ((e = launch_ex(k_blk_trsm, dim3(below / 8), dim3(256), 0, s, 0, d, p)) != cudaSuccess) return e;
+        const int nt16 = below / 16;
+        if ((e = launch_ex(k_blk_syrk, dim3(nt16 * (nt16 + 1) / 2), dim3(256), 0, s, 0, d, p)) != cudaSuccess)
+          return e;
+      }
+    }
     if ((e = launch_ex(k_chol_cluster, dim3(CS), dim3(256), chol_layout(d.n_c, CS).doubles() * sizeof(double), s, CS,
                        d)) != cudaSuccess)
       return e;
@@ -2650,7 +2869,8 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
 }
 
 int solve_kernels_per_iteration(const Dev& d) {
-  return 6 + (d.n_schur_tiles > 0 ? 1 : 0) + (d.n_direct_tiles > 0 ? 1 : 0);
+  const int blocked = chol_cluster_size(d.n_c) > 0 && d.chol_blocked ? 3 * (d.npw / kPW) - 1 : 0;
+  return 6 + (d.n_schur_tiles > 0 ? 1 : 0) + (d.n_direct_tiles > 0 ? 1 : 0) + blocked;
 }
 
 void batch_plan_sizes(Dev* hd, int n_win, BatchLaunch& b) {
@@ -2665,6 +2885,7 @@ void batch_plan_sizes(Dev* hd, int n_win, BatchLaunch& b) {
     max_span = std::max(max_span, d.max_span);
     const size_t cs = chol_layout(d.n_c, b.chol_cs).doubles() * sizeof(double);
     hd[w].chol_fallback = cs > kClusterSmemMax ? 1 : 0;
+    hd[w].chol_blocked = 0;                        // batched windows factor in their cluster
     if (hd[w].chol_fallback) b.n_fallback++;
     else b.chol_smem = std::max(b.chol_smem, cs);
   }

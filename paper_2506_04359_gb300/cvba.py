@@ -87,6 +87,7 @@ def _load() -> C.CDLL:
         "cvba_profile_names": (C.c_char_p, []),
         "cvba_evaluate_noalloc": (i, [i, i, i, i] + [vp] * 8 + [d, d, vp, vp]),
         "cvba_set_tuning": (i, [vp, i, i]),
+        "cvba_set_chol_mode": (i, [vp, i]),
         "cvba_batch_create": (i, [C.POINTER(vp), i, C.POINTER(vp)]),
         "cvba_batch_destroy": (None, [vp]),
         "cvba_batch_last_error": (C.c_char_p, [vp]),
@@ -262,6 +263,10 @@ class Context:
 
     def cvba_set_tuning(self, lin_tile_pairs: int = 0, schur_tile_landmarks: int = 0):
         self._check(lib.cvba_set_tuning(self._h, int(lin_tile_pairs), int(schur_tile_landmarks)))
+
+    def cvba_set_chol_mode(self, mode: int = 0):
+        """0: by size, 1: cluster form, 2: blocked form of the reduced-system factorisation."""
+        self._check(lib.cvba_set_chol_mode(self._h, int(mode)))
 
     # --- convenience
     def load(self, problem, poses=None, landmarks=None):

@@ -155,3 +155,52 @@ def test_fp64_with_refinement_keeps_oracle_parity(cvba):
     np.testing.assert_allclose(ctx.cvba_get_poses(), P, rtol=0, atol=1e-6)
     assert np.all(tr["berr"][tr["nonpd"] == 0] < 1e-12)
     ctx.close()
+
+
+@pytest.mark.parametrize("cfg", ["c1", "c2", "c4"])
+def test_blocked_and_cluster_factorisations_agree(cvba, cfg, c2, c4):
+    """The blocked (32-column panels over the GPU) and cluster forms of the FP64
+    reduced-camera-system factorisation solve the same damped system: the increments of one
+    step agree to 1e-9 relative and the traces of five steps to 1e-9 in cost and gain."""
+    p = {"c2": c2, "c4": c4}.get(cfg) or synth.make_problem(cfg, 0)
+    res = {}
+    for mode in (1, 2):
+        ctx = cvba.Context("fp64").load(p)
+        ctx.cvba_set_chol_mode(mode)
+        tr1 = ctx.cvba_solve(1)
+        delta = ctx.cvba_get_increment()
+        ctx.cvba_set_poses(p.poses0, p.fixed_kf)
+        ctx.cvba_set_landmarks(p.lm0)
+        tr5 = ctx.cvba_solve(5)
+        res[mode] = (tr1, delta, tr5)
+        ctx.close()
+    (t1a, da, t5a), (t1b, db, t5b) = res[1], res[2]
+    assert t1a[0]["nonpd"] == 0 and t1b[0]["nonpd"] == 0
+    assert np.abs(da - db).max() <= 1e-9 * np.abs(da).max()
+    for k in ("cost0", "cost1", "gain"):
+        np.testing.assert_allclose(t5b[k], t5a[k], rtol=1e-9, atol=0)
+    assert np.array_equal(t5a["accepted"], t5b["accepted"])
+
+
+def test_blocked_factorisation_solves_the_normal_equations_c1(cvba):
+    """Mode 2 on the stereo window: each increment solves the damped normal equations
+    (evaluated by the oracle without the Schur complement) as tightly as the cluster form."""
+    p = synth.make_problem("c1", 0)
+    win = ba.Window.from_problem(p)
+    worst = {}
+    for mode in (1, 2):
+        ctx = cvba.Context("fp64").load(p)
+        ctx.cvba_set_chol_mode(mode)
+        tr = ctx.cvba_solve(1)
+        worst[mode] = ba.normal_residual(win, p.poses0, p.lm0, float(tr[0]["lambda"]), ctx.cvba_get_increment())
+        ctx.close()
+    assert worst[2] <= max(4 * worst[1], 1e-10)
+
+
+def test_chol_mode_rejects_unknown_modes(cvba):
+    ctx = cvba.Context("fp64")
+    for bad in (-1, 3):
+        with pytest.raises(Exception):
+            ctx.cvba_set_chol_mode(bad)
+    ctx.cvba_set_chol_mode(2)                      # before a window is loaded: kept for later
+    ctx.close()
