@@ -1733,6 +1733,60 @@ __device__ __forceinline__ void chol_backward(const Dev& d, const CholSmem& Ls, 
   }
 }
 
+constexpr int kPW = 32;                            // panel width of the blocked factorisation
+constexpr int kPD = kPW + 1;                       // shared-memory row stride (no bank conflicts)
+
+// Backward substitution L^T x = y from the factor of the blocked form (global memory, row
+// stride npw), by 32-column panels from the last.  Panel p belongs to CTA p mod CS, which
+// keeps its entries of w (indexed by column, y on entry) up to date: it solves
+// L_pp^T x_p = w_p with one warp (column recursion, v_c = w_c - sum_{m>c} (L_mc / L_mm) v_m,
+// x = v / L_cc), writes x_p to d.dc and pushes it to every CTA (xb: two buffers of 32); after
+// a cluster barrier every CTA subtracts L_pq^T x_p from the panels q < p it owns.  scratch
+// holds 32 x 33 doubles.  Ends with a cluster barrier.
+__device__ __forceinline__ void chol_backward_panels(const Dev& d, int q, int CS, double* w, double* xb,
+                                                     double* scratch, cooperative_groups::cluster_group& cluster) {
+  const int n = d.n_c, npw = d.npw, npan = npw / kPW, tid = threadIdx.x, nt = blockDim.x;
+  for (int p = npan - 1; p >= 0; --p) {
+    const int o = p * kPW;
+    if (q == p % CS) {                             // uniform over the CTA
+      for (int e = tid; e < kPW * kPW; e += nt) {
+        const int m = e / kPW, c = e % kPW;
+        scratch[m * kPD + c] = m > c ? d.Lw[(size_t)(o + m) * npw + o + c] * d.Ldinv[o + m] : 0.0;
+      }
+      __syncthreads();
+      if (tid < kPW) {
+        double v = o + tid < n ? w[o + tid] : 0.0;
+#pragma unroll 4
+        for (int m = kPW - 1; m > 0; --m) {
+          const double x = __shfl_sync(0xffffffffu, v, m);
+          if (tid < m) v = fma(-scratch[m * kPD + tid], x, v);
+        }
+        const double xv = v * d.Ldinv[o + tid];
+        if (o + tid < n) d.dc[o + tid] = xv;
+        for (int dst = 0; dst < CS; ++dst) cluster.map_shared_rank(xb, dst)[(p & 1) * kPW + tid] = xv;
+      }
+    }
+    cluster.sync();
+    // own panels q' < p: w_q' -= L_pq'^T x_p (thread per column, four partial sums)
+    const double* xp = xb + (p & 1) * kPW;
+    const int n_own = p > q ? (p - 1 - q) / CS + 1 : 0;   // panels q, q + CS, ... below p
+    for (int e = tid; e < n_own * kPW; e += nt) {
+      const int oq = (q + (e / kPW) * CS) * kPW, c = oq + e % kPW;
+      if (c >= n) continue;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+#pragma unroll
+      for (int m = 0; m < kPW; m += 4) {
+        a0 = fma(d.Lw[(size_t)(o + m) * npw + c], xp[m], a0);
+        a1 = fma(d.Lw[(size_t)(o + m + 1) * npw + c], xp[m + 1], a1);
+        a2 = fma(d.Lw[(size_t)(o + m + 2) * npw + c], xp[m + 2], a2);
+        a3 = fma(d.Lw[(size_t)(o + m + 3) * npw + c], xp[m + 3], a3);
+      }
+      w[c] -= (a0 + a1) + (a2 + a3);
+    }
+  }
+  cluster.sync();                                  // dc complete
+}
+
 // |x| to FP32 with a relative error below 2^-20 using integer operations only (no FP64
 // pipe instruction): exponent rebiased, mantissa truncated; below the FP32 normal range
 // gives 0, above it +inf (NaN in gives +inf or NaN).
@@ -2018,6 +2072,8 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
     cluster.sync();
     if (q == 0) chol_backward_single(d, Ls, gl, glinv, ybuf, red);
     cluster.sync();                                // dc visible everywhere
+  } else if (d.chol_blocked) {
+    chol_backward_panels(d, q, CS, ybuf, acc, panel0, cluster);   // acc, panels: free here
   } else {
     if (q == 0) {
       for (int e = tid; e < CS * NP; e += nt) {
@@ -2187,9 +2243,6 @@ __global__ void __launch_bounds__(256) k_chol_cluster_b(const Dev* __restrict__ 
 // to the working arrays.  The cluster kernel then reads the factor back for the backward
 // substitution, the refinement and the epilogue.  The right-hand side is carried the same
 // way as in the cluster kernel (y = L^-1 (b - g_p) formed during the factorisation).
-constexpr int kPW = 32;                            // panel width
-constexpr int kPD = kPW + 1;                       // shared-memory row stride (no bank conflicts)
-
 __global__ void __launch_bounds__(256) k_blk_load(Dev d) { pdl_enter();
   __shared__ double s_red[64];
   Ctrl* ctrl = d.ctrl;
