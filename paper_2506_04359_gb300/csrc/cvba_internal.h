@@ -97,7 +97,7 @@ struct Dev {
   double* kf_dp;              // K * 6  diag of Hpp
   // Schur / solve
   double* lm_Vinv;            // M * VINV_STRIDE
-  double* S;                  // n_c * n_c (lower triangle used)
+  double* S;                  // n_c * n_c, both triangles (the factorisations read the lower one)
   double* bS;                 // n_c   sum of W V^-1 g_l
   double* dc;                 // n_c   pose increment
   double* dp;                 // M * 3 landmark increment

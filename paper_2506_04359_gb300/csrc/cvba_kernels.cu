@@ -840,7 +840,9 @@ __device__ __forceinline__ void k_schur_direct_body(const Dev& d, int item) {
 
   auto acc_S = [&](int pr, int pc, int r, int c, double v) {
     if (tile.direct) {
-      atomicAdd(d.S + (size_t)(6 * pr + r) * n_c + 6 * pc + c, v);
+      const int gr = 6 * pr + r, gc = 6 * pc + c;  // a lower entry; S is kept symmetric
+      atomicAdd(d.S + (size_t)gr * n_c + gc, v);
+      if (gr != gc) atomicAdd(d.S + (size_t)gc * n_c + gr, v);
     } else {
       const int wr = 6 * (pr - tile.k_lo) + r, wc = 6 * (pc - tile.k_lo) + c;
       atomicAdd(s_win + wr * (wr + 1) / 2 + wc, v);
@@ -1346,7 +1348,9 @@ __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
           while ((r + 1) * (r + 2) / 2 <= e) ++r;
           c = e - r * (r + 1) / 2;
         }
-        d.S[(size_t)(6 * a + r) * d.n_c + 6 * b + c] = sum;
+        const int gr = 6 * a + r, gc = 6 * b + c;  // both triangles: rows read contiguously
+        d.S[(size_t)gr * d.n_c + gc] = sum;
+        if (gr != gc) d.S[(size_t)gc * d.n_c + gr] = sum;
       }
     }
   }
@@ -2106,7 +2110,7 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
         float sa = 0.f;
 #pragma unroll 4
         for (int j = lane; j < n; j += 32) {
-          double a = j <= gi ? d.S[(size_t)gi * n + j] : d.S[(size_t)j * n + gi];
+          double a = d.S[(size_t)gi * n + j];       // S holds both triangles
           if (j == gi) a += rcs_damp(d, gi, lam, floor_);
           s = fma(a, d.dc[j], s);
           sa += abs_f32_approx(a);
