@@ -17,6 +17,7 @@ struct cvba_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  SideStream side;                              // overlapping work of an iteration
   cvba_precision prec = CVBA_FP64;
   std::string err;
 
@@ -647,8 +648,15 @@ cvba_status cvba_create(cvba_ctx** out, int device, void* stream, cvba_precision
       c->own_stream = true;
     }
   }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side.s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cudaGetLastError();
+    if (c->side.join) cudaEventDestroy(c->side.join);
+    if (c->side.fork) cudaEventDestroy(c->side.fork);
+    if (c->side.s) cudaStreamDestroy(c->side.s);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
     return CVBA_ERR_CUDA;
   }
@@ -661,7 +669,11 @@ void cvba_destroy(cvba_ctx* c) {
   {
     DeviceGuard g(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->side.s) cudaStreamSynchronize(c->side.s);
     free_device(c);
+    if (c->side.join) cudaEventDestroy(c->side.join);
+    if (c->side.fork) cudaEventDestroy(c->side.fork);
+    if (c->side.s) cudaStreamDestroy(c->side.s);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   }
   delete c;
@@ -819,7 +831,7 @@ cvba_status enqueue_solve(cvba_ctx* c, const cvba_opts* o) {
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = enqueue_solve_init(c->d, o->lambda0, o->huber_delta, o->z_min, o->iters, key.reset, key.refine,
                                        c->stream);
-    for (int it = 0; it < o->iters && e == cudaSuccess; ++it) e = enqueue_iteration(c->d, c->stream, nullptr);
+    for (int it = 0; it < o->iters && e == cudaSuccess; ++it) e = enqueue_iteration(c->d, c->stream, nullptr, &c->side);
     cudaError_t e2 = cudaStreamEndCapture(c->stream, &gr);
     if (e != cudaSuccess) return cuda_fail(c, e, "enqueue solve");
     if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
@@ -922,7 +934,7 @@ cvba_status cvba_profile_iteration(cvba_ctx* c, const cvba_opts* o, int reps, fl
     // relinearises (a rejected step would otherwise skip the next linearisation)
     cudaError_t e = enqueue_solve_init(c->d, one.lambda0, one.huber_delta, one.z_min, 1, one.reset_lambda, refine,
                                        c->stream);
-    if (e == cudaSuccess) e = enqueue_iteration(c->d, c->stream, ev.data());
+    if (e == cudaSuccess) e = enqueue_iteration(c->d, c->stream, ev.data(), &c->side);
     if (e == cudaSuccess) e = cudaEventSynchronize(ev[np]);
     if (e != cudaSuccess) {
       st = cuda_fail(c, e, "profile iteration");

@@ -153,9 +153,15 @@ int solve_kernels_per_iteration(const Dev& d);
 // Launchers (cvba_kernels.cu).  All enqueue on `s` and return the launch status.
 cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double zmin, int iters,
                                int reset_lambda, int refine, cudaStream_t s);
+// A second stream and two events of the context, for work of an iteration that overlaps the
+// main stream (the blocked factorisation's trailing updates).  Null members: no overlap.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
 // One LM iteration.  With ev != nullptr, profile_parts() + 1 events are recorded around
 // the iteration's parts (for cvba_profile_iteration).
-cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev);
+cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, const SideStream* side = nullptr);
 int profile_parts();
 const char* profile_names();
 // State transfer between a caller's device array (caller layout and landmark order) and

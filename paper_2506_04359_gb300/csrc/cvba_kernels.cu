@@ -2372,17 +2372,26 @@ __global__ void __launch_bounds__(256) k_blk_trsm(Dev d, int p) { pdl_enter();
 }
 
 // Trailing update after panel p: 16 x 16 tile (ti, tj), ti >= tj, of the rows and columns
-// below the panel: A_ij -= sum over the panel's 32 columns of L_i,m L_j,m.
-__global__ void __launch_bounds__(256) k_blk_syrk(Dev d, int p) { pdl_enter();
+// below the panel: A_ij -= sum over the panel's 32 columns of L_i,m L_j,m.  part 0 takes the
+// tiles of the next panel's columns (tj < 2), which the next panel's factor and solve need;
+// part 1 the rest (tj >= 2), which can overlap them.
+__global__ void __launch_bounds__(256) k_blk_syrk(Dev d, int p, int part) { pdl_enter();
   __shared__ double s_a[16 * kPD], s_b[16 * kPD];
   Ctrl* ctrl = d.ctrl;
   if (ctrl->nonpd) return;
   const int npw = d.npw, o = p * kPW, o2 = o + kPW, tid = threadIdx.x;
-  const int blk = blockIdx.x;
-  int ti = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
-  while (ti * (ti + 1) / 2 > blk) --ti;
-  while ((ti + 1) * (ti + 2) / 2 <= blk) ++ti;
-  const int tj = blk - ti * (ti + 1) / 2;
+  const int blk = blockIdx.x, nt = (npw - o2) / 16;
+  int ti, tj;
+  if (part == 0) {
+    ti = blk < nt ? blk : blk - nt + 1;
+    tj = blk < nt ? 0 : 1;
+  } else {                                         // triangle of the tiles ti >= tj >= 2
+    int t = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
+    while (t * (t + 1) / 2 > blk) --t;
+    while ((t + 1) * (t + 2) / 2 <= blk) ++t;
+    ti = t + 2;
+    tj = blk - t * (t + 1) / 2 + 2;
+  }
   for (int e = tid; e < 16 * kPW; e += blockDim.x) {
     const int r = e / kPW, m = e % kPW;
     s_a[r * kPD + m] = d.Lw[(size_t)(o2 + 16 * ti + r) * npw + o + m];
@@ -2853,7 +2862,7 @@ cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double z
 int profile_parts() { return 8; }
 const char* profile_names() { return "lin,kf_reduce,schur_group,rcs_reduce,schur_direct,chol,backsub,decide"; }
 
-cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
+cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, const SideStream* side) {
   cudaError_t e;
   auto mark = [&](int k) { return ev ? cudaEventRecord(ev[k], s) : cudaSuccess; };
   if ((e = mark(0)) != cudaSuccess) return e;
@@ -2894,15 +2903,36 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
       const int npan = d.npw / kPW;
       const size_t n_load = std::min(((size_t)d.npw * d.npw + 255) / 256, (size_t)152 * 8);
       if ((e = launch_ex(k_blk_load, dim3((unsigned)n_load), dim3(256), 0, s, 0, d)) != cudaSuccess) return e;
+      // The trailing update's tiles outside the next panel's columns run on the side stream
+      // (in order there, as every panel updates the same tiles), overlapping the next panel's
+      // factor and solve; the next panel's column update waits for them.
+      const bool overlap = side && side->s && side->fork && side->join;
+      bool pending = false;
       for (int p = 0; p < npan; ++p) {
         if ((e = launch_ex(k_blk_panel, dim3(1), dim3(256), 0, s, 0, d, p)) != cudaSuccess) return e;
         const int below = d.npw - kPW * (p + 1);
         if (below == 0) break;
         if ((e = launch_ex(k_blk_trsm, dim3(below / 8), dim3(256), 0, s, 0, d, p)) != cudaSuccess) return e;
-        const int nt16 = below / 16;
-        if ((e = launch_ex(k_blk_syrk, dim3(nt16 * (nt16 + 1) / 2), dim3(256), 0, s, 0, d, p)) != cudaSuccess)
-          return e;
+        const int nt16 = below / 16, n_rest = (nt16 - 2) * (nt16 - 1) / 2;
+        if (n_rest > 0 && overlap) {
+          if ((e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
+          if ((e = cudaStreamWaitEvent(side->s, side->fork, 0)) != cudaSuccess) return e;
+          k_blk_syrk<<<n_rest, 256, 0, side->s>>>(d, p, 1);
+          if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if (pending) {
+          if ((e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
+          pending = false;
+        }
+        if (n_rest > 0 && overlap) {
+          if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return e;
+          pending = true;
+        }
+        if ((e = launch_ex(k_blk_syrk, dim3(2 * nt16 - 1), dim3(256), 0, s, 0, d, p, 0)) != cudaSuccess) return e;
+        if (n_rest > 0 && !overlap)
+          if ((e = launch_ex(k_blk_syrk, dim3(n_rest), dim3(256), 0, s, 0, d, p, 1)) != cudaSuccess) return e;
       }
+      if (pending && (e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
     }
     if ((e = launch_ex(k_chol_cluster, dim3(CS), dim3(256), chol_layout(d.n_c, CS).doubles() * sizeof(double), s, CS,
                        d)) != cudaSuccess)
@@ -2926,7 +2956,14 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
 }
 
 int solve_kernels_per_iteration(const Dev& d) {
-  const int blocked = chol_cluster_size(d.n_c) > 0 && d.chol_blocked ? 3 * (d.npw / kPW) - 1 : 0;
+  int blocked = 0;
+  if (chol_cluster_size(d.n_c) > 0 && d.chol_blocked) {
+    blocked = 1 + d.npw / kPW;                     // load, panel factors
+    for (int below = d.npw - kPW; below > 0; below -= kPW) {
+      const int nt16 = below / 16;
+      blocked += 2 + ((nt16 - 2) * (nt16 - 1) / 2 > 0 ? 1 : 0);   // solve, update (two parts)
+    }
+  }
   return 6 + (d.n_schur_tiles > 0 ? 1 : 0) + (d.n_direct_tiles > 0 ? 1 : 0) + blocked;
 }
 
