@@ -281,12 +281,18 @@ cvba_status cvba_cost_backward(int dtype, int n_obs, int n_kf, int n_cams, int n
  * sum |r|^2, n_valid, n_inlier, and the number of observations skipped because an index
  * was out of range.  The call is asynchronous: out is ready when the stream reaches it.
  *
- * It allocates nothing: its scratch (per-block partial sums) is a fixed 640 KB device
- * array inside the library, held by every GPU that loads it until the process exits.
- * n_obs is limited to 4,194,304 (CVBA_ERR_INVALID_ARG beyond).  The first call on each
- * device looks up the array's device address; make that first call before capturing any
- * stream.  All calls on a device share the array: calls whose kernels overlap on the GPU
- * race on it and must be serialised by the caller. */
+ * It allocates nothing on the device while running: its scratch (per-block partial sums)
+ * is a fixed 640 KB device array inside the library's device module.  With lazy module
+ * loading (the CUDA default) that module, and the array with it, is loaded onto a device
+ * by the first call there, so the FIRST call on each device may allocate: make it during
+ * initialisation, before any stream capture (CUDA_MODULE_LOADING=EAGER loads it with the
+ * context instead).  The array stays until the context is destroyed.  Its device address
+ * is looked up on every call, so a module reloaded after a device reset is found again.
+ * n_obs is limited to 4,194,304 (CVBA_ERR_INVALID_ARG beyond), as are a huber_delta that
+ * is not a finite positive number, a non-finite z_min and NULL pointers.  If the calling
+ * thread already has a CUDA error pending, the call launches nothing, leaves that error
+ * pending and returns CVBA_ERR_CUDA.  All calls on a device share the array: calls whose
+ * kernels overlap on the GPU race on it and must be serialised by the caller. */
 cvba_status cvba_evaluate_noalloc(int n_obs, int n_kf, int n_cams, int n_lm, const double* intr,
                                   const double* T_cb, const double* T_bw, const double* p_w,
                                   const int32_t* kf, const int32_t* cam, const int32_t* lm,

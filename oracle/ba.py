@@ -280,6 +280,22 @@ class IterRecord:
     delta: np.ndarray | None
 
 
+def accept_step(L: float, F1: float, gain: float) -> bool:
+    """A candidate is accepted iff the predicted reduction L is positive, its cost is finite
+    and the gain ratio (F - F') / L is positive."""
+    return bool(L > 0.0 and np.isfinite(F1) and gain > 0.0)
+
+
+def nielsen_update(lam: float, nu: float, gain: float, accepted: bool):
+    """Nielsen's damping update (H. B. Nielsen, "Damping parameter in Marquardt's method",
+    IMM-REP-1999-05): after an accepted step lambda <- lambda * max(1/3, 1 - (2 gain - 1)^3)
+    and nu <- 2; after a rejected (or not positive definite) step lambda <- lambda * nu and
+    nu <- 2 nu."""
+    if accepted:
+        return lam * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3), 2.0
+    return lam * nu, 2.0 * nu
+
+
 def lm_iteration(win: Window, poses, lms, lam, nu, lin=None):
     """One LM iteration from state x with damping (lam, nu).
 
@@ -292,18 +308,19 @@ def lm_iteration(win: Window, poses, lms, lam, nu, lin=None):
     if delta is None:
         rec = IterRecord(ev.F, float("nan"), lam, float("nan"), float("nan"), float("nan"), False,
                          ev.n_valid, ev.n_inlier, ev.rms, True, None)
-        return poses, lms, lam * nu, 2.0 * nu, rec, lin
+        lam_new, nu_new = nielsen_update(lam, nu, float("nan"), False)
+        return poses, lms, lam_new, nu_new, rec, lin
     L = 0.5 * float(delta @ (lam * D * delta - g))
     p1, l1 = apply_step(win, poses, lms, delta)
     F1 = evaluate(win, p1, l1).F
     gain = (ev.F - F1) / L if L != 0.0 else float("nan")
-    acc = bool(L > 0.0 and np.isfinite(F1) and gain > 0.0)
+    acc = accept_step(L, F1, gain)
     rec = IterRecord(ev.F, F1, lam, gain, L, float(np.linalg.norm(delta)), acc,
                      ev.n_valid, ev.n_inlier, ev.rms, False, delta)
+    lam_new, nu_new = nielsen_update(lam, nu, gain, acc)
     if acc:
-        lam_new = lam * max(1.0 / 3.0, 1.0 - (2.0 * gain - 1.0) ** 3)
-        return p1, l1, lam_new, 2.0, rec, None
-    return poses, lms, lam * nu, 2.0 * nu, rec, lin
+        return p1, l1, lam_new, nu_new, rec, None
+    return poses, lms, lam_new, nu_new, rec, lin
 
 
 def lm_solve(win: Window, poses0, lms0, iters: int, lam0: float = 1e-4, keep_delta: bool = True):

@@ -13,11 +13,15 @@
 // The scratch array is shared by every call in the process on a given GPU and keeps the
 // last call's contents; each call overwrites the entries it reads, so nothing needs
 // clearing between calls.  Calls whose kernels overlap on the GPU (different streams, or
-// other threads) race on it: serialise them.  Every GPU that loads this library holds the
-// array (640 KB) until the process exits.
+// other threads) race on it: serialise them.  The array (640 KB) lives in this library's
+// device module: with lazy module loading (the CUDA default) the module, and with it the
+// array, is loaded onto a GPU by the first call there, which therefore may allocate; with
+// CUDA_MODULE_LOADING=EAGER it is loaded with the context.  Either way it stays until the
+// context is destroyed.  The array's device address is looked up on every call, so a
+// module reloaded after a device reset is found at its new address.
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <cmath>
 
 #include "../../include/cvba.h"
 
@@ -27,14 +31,10 @@ constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 16384;
 constexpr int kMaxObs = kMaxBlocks * kThreads;   // 4,194,304 observations per call
 constexpr int kParts = 5;                        // cost, sum r^2, n_valid, n_inlier, n_bad_index
-constexpr int kMaxDevices = 64;
 
+// Host code must not pass this name to a kernel: on the host it is only a stand-in, and
+// kernels are given the address that cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) double g_partials[kMaxBlocks * kParts];
-
-// Host-side table of the array's device address on each GPU.  The array's host name is
-// only a stand-in: kernels must be given the address returned by cudaGetSymbolAddress.
-std::mutex g_mutex;
-double* g_addr[kMaxDevices] = {};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -112,25 +112,18 @@ __global__ void __launch_bounds__(kThreads) k_eval_obs_reduce(const double* __re
     for (int k = 0; k < kParts; ++k) out[k] = v[k];
 }
 
-// Device address of the scratch array on the current device, looked up once per device
-// (with that device current) and cached.
+// Device address of the scratch array on the current device, looked up with that device
+// current.  Not cached: after a device reset (or in another context on the same ordinal)
+// the module is loaded again and the array can sit at a new address.  The lookup is cheap
+// once the module is loaded and allocates nothing then.
 cvba_status scratch_address(double** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
+  if (e != cudaSuccess || !p) {
     cudaGetLastError();
     return CVBA_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_partials);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return CVBA_ERR_CUDA;
-    }
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<double*>(p);
   return CVBA_OK;
 }
 
@@ -143,7 +136,10 @@ extern "C" cvba_status cvba_evaluate_noalloc(int n_obs, int n_kf, int n_cams, in
                                              void* stream) {
   if (n_obs < 1 || n_obs > kMaxObs || n_kf < 1 || n_cams < 1 || n_lm < 1) return CVBA_ERR_INVALID_ARG;
   if (!intr || !T_cb || !T_bw || !p_w || !kf || !cam || !lm || !uv || !out) return CVBA_ERR_INVALID_ARG;
-  if (!(huber_delta > 0.0) || !(z_min == z_min)) return CVBA_ERR_INVALID_ARG;
+  if (!(huber_delta > 0.0) || !std::isfinite(huber_delta) || !std::isfinite(z_min)) return CVBA_ERR_INVALID_ARG;
+  // An error left pending by the caller's own earlier work is not ours: launch nothing,
+  // leave it pending for the caller, and report it.
+  if (cudaPeekAtLastError() != cudaSuccess) return CVBA_ERR_CUDA;
   double* partials = nullptr;
   const cvba_status st = scratch_address(&partials);
   if (st != CVBA_OK) return st;
@@ -151,6 +147,7 @@ extern "C" cvba_status cvba_evaluate_noalloc(int n_obs, int n_kf, int n_cams, in
   const int n_blocks = (n_obs + kThreads - 1) / kThreads;
   k_eval_obs<<<n_blocks, kThreads, 0, s>>>(n_obs, n_kf, n_cams, n_lm, intr, T_cb, T_bw, p_w, kf, cam, lm, uv,
                                            huber_delta, z_min, partials);
+  if (cudaGetLastError() != cudaSuccess) return CVBA_ERR_CUDA;
   k_eval_obs_reduce<<<1, kThreads, 0, s>>>(partials, n_blocks, out);
   if (cudaGetLastError() != cudaSuccess) return CVBA_ERR_CUDA;
   return CVBA_OK;
