@@ -1,15 +1,19 @@
 """Benchmark: LM iterations/s of sliding-window bundle adjustment on one GB300.
 
-Default workload: the 20-keyframe stereo window (5000 landmarks, ~53k observations, 5%
-outliers), mixed precision, 20 LM iterations per solve; one step = one full solve from
-the same initial state.  The plain FP64 path is timed on the same window beside it.
+Default workload: the largest window (100 keyframes, a 32-camera ring of 16 stereo pairs,
+200,000 landmarks, 3.75M observations with 3% outliers), mixed precision, 15 LM
+iterations per solve; one step = one full solve from the same initial state.  The plain
+FP64 path is timed on the same window beside it.
 
-Prints one JSON line (rank 0).  Keys beyond the base contract: gobs_per_s, rms_px and the
-oracle's RMS (validity gate |diff| <= 1e-3 px), fp64 (the FP64 path's throughput),
-roofline (dominant kernel, achieved vs peak), cpu_baseline (oracle on the host cores),
-e2e (through the public API with host buffers), clocks, gpu_launches.
+Prints one JSON line (rank 0).  Keys beyond the base contract: gobs_per_s; rms_px, the
+oracle's RMS (stored Oracle-S result, tests/golden/<workload>_oracle.json) and the
+validity gate |diff| <= 1e-3 px; vs_oracle (per-result error of the final state); fp64
+(the FP64 path's throughput and error); roofline (dominant kernel) and roofline_all
+(every kernel with a work model); cpu_baseline (Oracle-S on the host cores, a bounded
+sample); e2e (through the public C API with host buffers); clocks; gpu_launches; and the
+extra sections c1 (20-keyframe stereo window) and batched (256 independent windows).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c1] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c4] [--impl reference]
 """
 from __future__ import annotations
 
@@ -30,9 +34,11 @@ sys.path.insert(0, ROOT)
 MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCE = os.path.join(ROOT, "paper_2506_04359_gb300", "csrc", "cvba_kernels.cu")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 METRIC = "BA LM iters/s & Gobs/s at RMS reproj within 1e-3 px of oracle; % HBM peak"
 FALLBACK_HBM_GBS = 6800.0
-FP64_NOMINAL_GFLOPS = 1250.0     # 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz (nominal)
+FP64_NOMINAL_GFLOPS = 1250.0     # GB300 FP64 (non-tensor) nominal: 1.25 TFLOP/s
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 80.5 TFLOP/s at the maximum SM clock
 
 
 def parse():
@@ -40,12 +46,12 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="c1")
-    ap.add_argument("--precision", default=None, help="mixed (default for c1) or fp64")
+    ap.add_argument("--workload", default="c4")
+    ap.add_argument("--precision", default=None, help="mixed (the workload's default) or fp64")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the c4 and batched c3 sections")
+    ap.add_argument("--no-extras", action="store_true", help="skip the c1 and batched c3 sections")
     return ap.parse_args()
 
 
@@ -156,24 +162,38 @@ def pose_errors(P, Q) -> dict:
 # -------------------------------------------------------------- algorithmic work model
 
 def work_model(p, P: int, mixed: bool) -> dict:
-    """Algorithmic bytes and FLOPs of each kernel of one LM iteration (per-unit figures x units).
+    """Work of each kernel of one LM iteration: per-unit figures x units.
 
-    Per observation: uv (2 values) + packed camera/keyframe index (4 B).  Per (landmark,
-    keyframe) pair: its index (4 B) and 9 values (M3 = sum w A^T A, 6; X_b, 3).  Per
-    landmark: position (3 FP64), H_ll + g_l (9 values), V^-1 (6) and dp (3).  The reduced
-    camera system is n_c^2 FP64."""
+    "bytes" are the ALGORITHMIC bytes (what the method itself must move, with the
+    linearisation, Schur and back-substitution fused and no per-pair intermediate in HBM):
+    per observation its pixel (2 values) and a packed keyframe/camera index (4 B), read once
+    by the linearisation and once by the candidate-cost pass; per landmark its position read
+    by the linearisation (3 values + 4 B segment offset) and by the candidate pass, which also
+    writes the candidate (FP64, plus its FP32 mirror on the mixed path).  "impl_bytes" add what
+    this implementation moves besides: the 9-value summary of each (landmark, keyframe) pair
+    and its index, written by the linearisation and read by the Schur and back-substitution
+    kernels, and the landmark blocks (H_ll, g_l, V^-1).  The Schur complement and the reduced
+    system's factorisation are arithmetic-bound: FP32 (mixed) or FP64 FLOPs, with
+    m_j(m_j+1)/2 x 216 + m_j x 108 per landmark (m_j free keyframes observing it) and
+    n_c^3/3 + 2 n_c^2."""
     t = 4 if mixed else 8
     N, M, K = p.N, p.M, p.K
     n_c = 6 * (K - 1)
-    m = np.bincount(np.unique(p.obs_lm.astype(np.int64) * K + p.obs_kf) // K, minlength=M)
+    free = np.asarray(p.obs_kf) != p.fixed_kf
+    keys = np.unique(p.obs_lm[free].astype(np.int64) * K + p.obs_kf[free])
+    m = np.bincount(keys // K, minlength=M).astype(np.float64)
     blocks = float(np.sum(m * (m + 1) / 2))
+    obs = N * (2 * t + 4)
+    lm_lin = M * (3 * t + 4)
+    lm_back = M * (3 * t + 4 + 24 + (12 if mixed else 0))
+    pair = P * (4 + 9 * t)
     return {
-        "lin": {"bytes": N * (2 * t + 4) + P * (4 + 9 * t) + M * (24 + 9 * t) + K * 96,
+        "lin": {"bytes": obs + lm_lin, "impl_bytes": obs + lm_lin + pair + M * 9 * t + K * 96,
                 "flops": 110.0 * N + 130.0 * P},
-        "schur_group": {"bytes": P * (4 + 9 * t) + M * (9 * t + 6 * t) + 8 * n_c * n_c,
-                        "flops": 216.0 * blocks + 135.0 * P},
+        "schur_group": {"bytes": 8 * n_c * n_c, "impl_bytes": pair + M * 15 * t + 8 * n_c * n_c,
+                        "flops": 216.0 * blocks + 108.0 * float(np.sum(m)), "fp32": mixed},
         "chol": {"bytes": 16.0 * n_c * n_c, "flops": n_c ** 3 / 3.0 + 2.0 * n_c ** 2},
-        "backsub": {"bytes": N * (2 * t + 4) + P * (4 + 9 * t) + M * (24 * 2 + 9 * t),
+        "backsub": {"bytes": obs + lm_back, "impl_bytes": obs + lm_back + pair + M * 9 * t,
                     "flops": 40.0 * N + 24.0 * P},
         "schur_blocks": blocks,
     }
@@ -195,48 +215,93 @@ def traffic_of(kernel: str, workload: str):
     return rec.get("dram_bytes_per_launch")
 
 
-def roofline(prof: dict, wm: dict, workload: str, only_hbm: bool = False) -> dict:
-    """Achieved vs peak for each kernel with a work model, and the dominant one."""
+def chol_kernel_name(ctx_mode_blocked: bool) -> str:
+    return "k_blk_* + k_chol_cluster" if ctx_mode_blocked else "k_chol_cluster"
+
+
+def roofline(prof: dict, wm: dict, workload: str, only_hbm: bool = False, chol_name: str = "k_chol_cluster") -> dict:
+    """Achieved vs peak for each kernel with a work model, keyed by part name."""
     pk, pk_kind = peaks()
     out = {}
     for k, ms in prof.items():
         if k not in wm or ms <= 0:
             continue
-        if k == "chol":
+        if k in ("chol", "schur_group"):
             if only_hbm:
                 continue
+            fp32 = wm[k].get("fp32", False)
+            peak = FP32_NOMINAL_TFLOPS if fp32 else FP64_NOMINAL_GFLOPS / 1e3
             ach = wm[k]["flops"] / (ms * 1e-3) / 1e12
-            out[k] = {"kernel": "k_chol_cluster", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_GFLOPS / 1e3,
-                      "unit": "TFLOP/s", "frac": ach / (FP64_NOMINAL_GFLOPS / 1e3),
-                      "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2.07 GHz); a probe measured 1.19 TFLOP/s",
-                      "ms_per_launch": ms}
+            out[k] = {"kernel": chol_name if k == "chol" else "k_schur_group", "bound": "alu", "achieved": ach,
+                      "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                      "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x 2.07 GHz = 80.5 TFLOP/s" if fp32 else
+                                      "FP64: GB300 nominal 1.25 TFLOP/s (a probe measured 1.19)") +
+                                     "; MEASURED_PEAKS.json has no FP32/FP64 figure",
+                      "algorithmic_flops": wm[k]["flops"], "ms_per_launch": ms}
+            if "impl_bytes" in wm[k]:
+                out[k]["impl_gbs"] = wm[k]["impl_bytes"] / (ms * 1e-3) / 1e9
         else:
             ach = wm[k]["bytes"] / (ms * 1e-3) / 1e9
             out[k] = {"kernel": "k_" + k, "bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                      "frac": ach / pk["hbm_gbs"], "peak_source": pk_kind + " (copy bandwidth)",
-                      "algorithmic_bytes": wm[k]["bytes"], "ms_per_launch": ms}
-        out[k]["traffic"] = traffic_of(out[k]["kernel"], workload)
+                      "frac": ach / pk["hbm_gbs"], "peak_source": pk_kind + " (copy bandwidth, burst)",
+                      "algorithmic_bytes": wm[k]["bytes"], "impl_bytes": wm[k]["impl_bytes"],
+                      "impl_frac": wm[k]["impl_bytes"] / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "ms_per_launch": ms}
+        t = traffic_of(out[k]["kernel"], workload)
+        out[k]["traffic"] = t
+        if t is not None:
+            out[k]["traffic_over_algorithmic"] = t / wm[k]["bytes"]
     return out
+
+
+def load_golden(name: str):
+    path = os.path.join(GOLDEN, f"{name}_oracle.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
 
 
 # ------------------------------------------------------------------------- reference
 
+def oracle_sample(p, seconds: float, max_iters: int):
+    """Oracle-S (block-sparse FP64 oracle, OpenMP on the host cores) run from the initial
+    state for up to `max_iters` LM iterations or about `seconds` of CPU time; returns
+    (iterations, elapsed seconds, threads)."""
+    from oracle import ba, ba_sparse
+    w = ba.Window.from_problem(p)
+    sw = ba_sparse.SparseWindow(w)
+    poses, lms, lam, nu = p.poses0.copy(), p.lm0.copy(), 1e-4, 2.0
+    t0 = time.perf_counter()
+    n_it = 0
+    while n_it < max_iters:
+        poses, lms, lam, nu, _ = ba_sparse.lm_iteration(sw, poses, lms, lam, nu)
+        n_it += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    threads = sw.threads
+    sw.close()
+    return n_it, dt, threads
+
+
 def run_reference(args):
-    """The oracle (CPU, FP64 dense normal equations) on the same workload: each step is one
-    LM iteration of the oracle's solve (a bounded sample of the 20-iteration solve)."""
+    """The oracle (Oracle-S: exact block-sparse FP64 normal equations, on the host cores) on
+    the same workload: each step is one LM iteration of its solve from the initial state
+    (a bounded sample of the 15-iteration solve)."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    from oracle import ba
+    from oracle import ba, ba_sparse
     from paper_2506_04359_gb300 import synth
     p = synth.make_problem(args.workload)
     w = ba.Window.from_problem(p)
-    poses, lms, lam, nu, lin = p.poses0.copy(), p.lm0.copy(), 1e-4, 2.0, None
+    sw = ba_sparse.SparseWindow(w)
+    poses, lms, lam, nu = p.poses0.copy(), p.lm0.copy(), 1e-4, 2.0
     for _ in range(args.warmup):
-        poses, lms, lam, nu, _, lin = ba.lm_iteration(w, poses, lms, lam, nu, lin)
+        ba_sparse.lm_iteration(sw, poses, lms, lam, nu)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        poses, lms, lam, nu, _, lin = ba.lm_iteration(w, poses, lms, lam, nu, lin)
+        poses, lms, lam, nu, _ = ba_sparse.lm_iteration(sw, poses, lms, lam, nu)
     dt = time.perf_counter() - t0
     v = args.steps / dt
     print(json.dumps({
@@ -244,11 +309,14 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "K": p.K, "C": p.C, "M": p.M, "N": p.N, "precision": "fp64",
-                   "step": "one oracle LM iteration (dense full normal equations, LAPACK Cholesky)"},
-        "cpu_baseline": {"value": v, "unit": "LM iters/s", "cores": cores(), "kind": "oracle",
-                         "sample": f"{args.steps} LM iterations of the {args.workload} window"},
+                   "step": "one LM iteration of the oracle (block-sparse FP64 normal equations, generic sparse "
+                           "Cholesky, OpenMP)"},
+        "cpu_baseline": {"value": v, "unit": "LM iters/s", "cores": sw.threads, "kind": "oracle",
+                         "sample": f"LM iterations {args.warmup + 1}..{args.warmup + args.steps} of the "
+                                   f"{args.workload} window"},
         "e2e": {"value": v, "unit": "LM iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+    sw.close()
 
 
 # ------------------------------------------------------------------------------- ours
@@ -269,24 +337,18 @@ def run_ours(args):
     precision = args.precision or ("mixed" if p.precision == "mixed" else "fp64")
     stream = torch.cuda.Stream(device=dev)
     l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    extra_launches = 0
 
-    def make_ctx(prec):
-        ctx = cvba.Context(prec, device=local, stream=stream.cuda_stream).load(p)
-        return ctx
-
-    poses0 = torch.tensor(p.poses0.reshape(p.K, 12), dtype=torch.float64, device=dev)
-    lms0 = torch.tensor(p.lm0, dtype=torch.float64, device=dev)
-    launches_per_solve = None
-
-    def timed_solves(ctx, steps, warmup, sampler=None):
-        """Device time of `steps` solves, L2 flushed between solves outside the events."""
-        nonlocal launches_per_solve
-        launches_per_solve = ctx.cvba_solve_launch_count(p.iters) + 2
+    def timed_solves(q, ctx, steps, warmup):
+        """Device time of `steps` solves of window q from its initial state (reset on the
+        device, inside the events), L2 flushed between solves outside the events."""
+        q_p = torch.tensor(q.poses0.reshape(q.K, 12), dtype=torch.float64, device=dev)
+        q_l = torch.tensor(q.lm0, dtype=torch.float64, device=dev)
         for _ in range(warmup):
             with torch.cuda.stream(stream):
-                ctx.cvba_set_poses_dev(poses0.data_ptr())
-                ctx.cvba_set_landmarks_dev(lms0.data_ptr())
-                ctx.cvba_solve_async(p.iters, huber_delta=p.huber_delta)
+                ctx.cvba_set_poses_dev(q_p.data_ptr())
+                ctx.cvba_set_landmarks_dev(q_l.data_ptr())
+                ctx.cvba_solve_async(q.iters, huber_delta=q.huber_delta)
         stream.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         barrier(ws)
@@ -296,22 +358,29 @@ def run_ours(args):
             for k in range(steps):
                 l2_flush.fill_(float(k))
                 ev[k][0].record(stream)
-                ctx.cvba_set_poses_dev(poses0.data_ptr())
-                ctx.cvba_set_landmarks_dev(lms0.data_ptr())
-                ctx.cvba_solve_async(p.iters, huber_delta=p.huber_delta)
+                ctx.cvba_set_poses_dev(q_p.data_ptr())
+                ctx.cvba_set_landmarks_dev(q_l.data_ptr())
+                ctx.cvba_solve_async(q.iters, huber_delta=q.huber_delta)
                 ev[k][1].record(stream)
         stream.synchronize()
         torch.cuda.synchronize()
         barrier(ws)
         wall = time.perf_counter() - t0
         dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-        return dev_s, wall
+        launches = steps * (ctx.cvba_solve_launch_count(q.iters) + 2)
+        return dev_s, wall, launches
+
+    def vs_golden(q, gold, P, rms):
+        if gold is None:
+            return None
+        return dict(pose_errors(P, np.array(gold["final_poses"])), rms_px=abs(rms - gold["final_rms_px"]))
 
     # --- main timed run (mixed by default)
-    ctx = make_ctx(precision)
-    P = ctx.cvba_get_sizes()["P"]
+    ctx = cvba.Context(precision, device=local, stream=stream.cuda_stream).load(p)
+    sizes = ctx.cvba_get_sizes()
+    P = sizes["P"]
     with ClockSampler(local) as cs:
-        dev_s, wall = timed_solves(ctx, args.steps, args.warmup)
+        dev_s, wall, launches = timed_solves(p, ctx, args.steps, args.warmup)
     dev_s = max_over_ranks(dev_s, ws)
     tr = ctx.cvba_get_trace(p.iters)
     ev = ctx.cvba_evaluate(p.huber_delta)
@@ -319,27 +388,32 @@ def run_ours(args):
     iters_total = args.steps * p.iters * ws
     value = iters_total / dev_s
     gobs = float(np.sum(tr["n_valid"])) * args.steps * ws / dev_s / 1e9
+    gold = load_golden(args.workload)
 
-    # --- roofline of the dominant kernel (CUDA events around each kernel, same stream)
-    prof = ctx.cvba_profile_iteration(20, huber_delta=p.huber_delta)
+    # --- roofline of every kernel with a work model (CUDA events around each kernel of one
+    #     iteration, on the library's stream), and the dominant one
+    prof = ctx.cvba_profile_iteration(10, huber_delta=p.huber_delta)
     wm = work_model(p, P, precision == "mixed")
     label = f"{args.workload} {precision}"
-    roofs = roofline(prof, wm, label)
+    blocked = 6 * (p.K - 1) >= 320
+    roofs = roofline(prof, wm, label, chol_name=chol_kernel_name(blocked))
     dom = max(roofs, key=lambda k: roofs[k]["ms_per_launch"])
     roof = dict(roofs[dom])
-    roof["parts_ms"] = prof
     roof["workload"] = label
+    roof["parts_ms"] = prof
+    ctx.close()
 
     # --- FP64 path on the same window
     fp64 = None
-    fp64_poses = None
     if precision != "fp64":
-        c64 = make_ctx("fp64")
-        d64, _ = timed_solves(c64, max(3, args.steps // 2), 1)
+        c64 = cvba.Context("fp64", device=local, stream=stream.cuda_stream).load(p)
+        n64 = max(3, args.steps // 4)
+        d64, _, l64 = timed_solves(p, c64, n64, 1)
+        extra_launches += l64
         d64 = max_over_ranks(d64, ws)
-        fp64 = {"value": max(3, args.steps // 2) * p.iters * ws / d64, "unit": "LM iters/s",
-                "rms_px": c64.cvba_evaluate(p.huber_delta)["rms"]}
-        fp64_poses = c64.cvba_get_poses()
+        rms64 = c64.cvba_evaluate(p.huber_delta)["rms"]
+        fp64 = {"value": n64 * p.iters * ws / d64, "unit": "LM iters/s", "rms_px": rms64,
+                "vs_oracle": vs_golden(p, gold, c64.cvba_get_poses(), rms64)}
         c64.close()
 
     # --- end to end through the public API with host buffers
@@ -347,6 +421,7 @@ def run_ours(args):
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         h_intr, h_tcb = pin(p.rig.intr), pin(p.rig.T_cb.reshape(-1, 12))
+        h_wh = pin(p.rig.wh.astype(np.int32))
         h_poses, h_lms = pin(p.poses0.reshape(p.K, 12)), pin(p.lm0)
         h_kf, h_cam, h_lm = pin(p.obs_kf.astype(np.int32)), pin(p.obs_cam.astype(np.int32)), pin(p.obs_lm.astype(np.int32))
         h_uv = pin(p.obs_uv)
@@ -355,7 +430,7 @@ def run_ours(args):
         ce = cvba.Context(precision, device=local, stream=stream.cuda_stream)
 
         def e2e_step():
-            ce.cvba_set_rig(h_intr, h_tcb)
+            ce.cvba_set_rig(h_intr, h_tcb, h_wh)
             ce.cvba_set_poses(h_poses, p.fixed_kf)
             ce.cvba_set_landmarks(h_lms)
             ce.cvba_set_observations(h_kf, h_cam, h_lm, h_uv)
@@ -363,86 +438,56 @@ def run_ours(args):
             cvba.lib.cvba_get_poses(ce._h, cvba._dptr(out_p))
             cvba.lib.cvba_get_landmarks(ce._h, cvba._dptr(out_l))
 
-        for _ in range(args.warmup):
+        n_e2e = max(3, args.steps // 4)
+        for _ in range(min(args.warmup, 2)):
             e2e_step()
         barrier(ws)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(n_e2e):
             e2e_step()
         torch.cuda.synchronize()
         barrier(ws)
         e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
-        h2d = sum(a.nbytes for a in (h_intr, h_tcb, h_poses, h_lms, h_kf, h_cam, h_lm, h_uv))
+        h2d = sum(a.nbytes for a in (h_intr, h_tcb, h_wh, h_poses, h_lms, h_kf, h_cam, h_lm, h_uv))
         d2h = out_p.nbytes + out_l.nbytes + p.iters * 64
-        e2e = {"value": iters_total / e2e_s, "unit": "LM iters/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / args.steps}
+        extra_launches += n_e2e * (ce.cvba_solve_launch_count(p.iters) + 2)
+        e2e = {"value": n_e2e * p.iters * ws / e2e_s, "unit": "LM iters/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": 1e3 * e2e_s / n_e2e, "steps": n_e2e,
+               "note": "each step: set rig, poses, landmarks, observations (host layout and upload), solve, "
+                       "read poses and landmarks"}
         ce.close()
 
-    # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    # --- CPU baseline: Oracle-S on a bounded sample (rank 0, N = 1)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        from oracle import ba
-        w = ba.Window.from_problem(p)
-        t0 = time.perf_counter()
-        poses, lms, lam, nu, lin = p.poses0.copy(), p.lm0.copy(), 1e-4, 2.0, None
-        n_it = 0
-        while n_it < p.iters:
-            poses, lms, lam, nu, _, lin = ba.lm_iteration(w, poses, lms, lam, nu, lin)
-            n_it += 1
-            if time.perf_counter() - t0 > 12.0:
-                break
-        dt = time.perf_counter() - t0
-        cpu = {"value": n_it / dt, "unit": "LM iters/s", "cores": cores(), "kind": "oracle",
-               "sample": f"first {n_it} LM iterations of the {args.workload} window (dense FP64 normal equations)"}
+        n_it, dt, thr = oracle_sample(p, 12.0, p.iters)
+        cpu = {"value": n_it / dt, "unit": "LM iters/s", "cores": thr, "kind": "oracle",
+               "sample": f"first {n_it} LM iterations of the {args.workload} window (Oracle-S: block-sparse "
+                         f"FP64 normal equations, generic sparse Cholesky, OpenMP)"}
 
-    # --- the 100-keyframe, 32-camera window (3.75M observations): HBM fractions of the
-    #     observation-streaming kernels, mixed vs FP64 throughput
-    c4 = None
+    # --- extra sections: the 20-keyframe stereo window, and 256 batched windows
+    c1 = None
     batched = None
-    extra_launches = 0
     if not args.no_extras:
-        q = synth.make_problem("c4")
-        qs = {}
+        q = synth.make_problem("c1") if args.workload != "c1" else p
+        g1 = load_golden("c1")
+        c1 = {"workload": "c1", "K": q.K, "C": q.C, "M": q.M, "N": q.N, "iters": q.iters}
         for prec in ("mixed", "fp64"):
             cq = cvba.Context(prec, device=local, stream=stream.cuda_stream).load(q)
-            q_p = torch.tensor(q.poses0.reshape(q.K, 12), dtype=torch.float64, device=dev)
-            q_l = torch.tensor(q.lm0, dtype=torch.float64, device=dev)
-            n_steps = 3
-            with torch.cuda.stream(stream):
-                cq.cvba_set_poses_dev(q_p.data_ptr())
-                cq.cvba_set_landmarks_dev(q_l.data_ptr())
-                cq.cvba_solve_async(q.iters, huber_delta=q.huber_delta)
-            stream.synchronize()
-            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
-            with torch.cuda.stream(stream):
-                for k in range(n_steps):
-                    l2_flush.fill_(float(k))
-                    evs[k][0].record(stream)
-                    cq.cvba_set_poses_dev(q_p.data_ptr())
-                    cq.cvba_set_landmarks_dev(q_l.data_ptr())
-                    cq.cvba_solve_async(q.iters, huber_delta=q.huber_delta)
-                    evs[k][1].record(stream)
-            stream.synchronize()
-            t_q = sum(a.elapsed_time(b) for a, b in evs) / 1e3
-            extra_launches += n_steps * (cq.cvba_solve_launch_count(q.iters) + 2)
-            trq = cq.cvba_get_trace(q.iters)
-            qs[prec] = {"value": n_steps * q.iters / t_q, "unit": "LM iters/s",
-                        "gobs_per_s": float(np.sum(trq["n_valid"])) * n_steps / t_q / 1e9,
-                        "rms_px": cq.cvba_evaluate(q.huber_delta)["rms"]}
+            t_q, _, lq = timed_solves(q, cq, 10, 2)
+            extra_launches += lq
+            rq = cq.cvba_evaluate(q.huber_delta)["rms"]
+            c1[prec] = {"value": 10 * q.iters / t_q, "unit": "LM iters/s", "rms_px": rq,
+                        "vs_oracle": vs_golden(q, g1, cq.cvba_get_poses(), rq)}
             if prec == "mixed":
-                pq = cq.cvba_profile_iteration(5, huber_delta=q.huber_delta)
-                wq = work_model(q, cq.cvba_get_sizes()["P"], True)
-                qs[prec]["parts_ms"] = pq
-                qs[prec]["roofline"] = roofline(pq, wq, "c4 mixed", only_hbm=True)
+                pq = cq.cvba_profile_iteration(10, huber_delta=q.huber_delta)
+                c1[prec]["parts_ms"] = pq
+                c1[prec]["roofline"] = roofline(pq, work_model(q, cq.cvba_get_sizes()["P"], True), "c1 mixed")
             cq.close()
-        c4 = {"workload": "c4", "K": q.K, "C": q.C, "M": q.M, "N": q.N, "iters": q.iters, **qs,
-              "rms_diff_px": abs(qs["mixed"]["rms_px"] - qs["fp64"]["rms_px"]),
-              "note": "the FP64 final state is the reference here (the dense oracle does not fit); the "
-                      "paths branch at a z_min crossing of one landmark with 3% outliers"}
 
-        # --- 256 independent windows (c3): one batched graph vs the windows one by one
         wins = synth.make_batch(256)
+        g3 = load_golden("c3")
         bctx = [cvba.Context("mixed", device=local, stream=stream.cuda_stream).load(w) for w in wins]
         batch = cvba.Batch(bctx)
         tuned = batch.cvba_batch_autotune(iters=2)
@@ -466,8 +511,13 @@ def run_ours(args):
             stream.synchronize()
         t_b = sum(a.elapsed_time(b) for a, b in evs) / 1e3
         extra_launches += n_steps * batch.cvba_batch_launch_count(it_b)
+        gate = None
+        if g3 is not None:
+            diffs = [abs(c.cvba_evaluate(w.huber_delta)["rms"] - g["final_rms_px"])
+                     for c, w, g in zip(bctx, wins, g3["windows"])]
+            gate = {"max_rms_diff_px": float(max(diffs)), "windows_within_1e-3_px": int(sum(d <= 1e-3 for d in diffs)),
+                    "n_windows": len(diffs)}
         n_obs_b = sum(w.N for w in wins)
-        # the same windows one at a time, FP64 single-window graphs
         seq = {}
         for prec in ("fp64", "mixed"):
             cs_ = [cvba.Context(prec, device=local, stream=stream.cuda_stream).load(w) for w in wins]
@@ -488,27 +538,13 @@ def run_ours(args):
         batched = {"workload": "c3 (256 windows, K 5-30, M 300-3000, 1/2/4/8 stereo pairs)", "precision": "mixed",
                    "iters": it_b, "value": n_steps * len(wins) * it_b / t_b, "unit": "window LM iters/s",
                    "gobs_per_s": n_obs_b * it_b * n_steps / t_b / 1e9, "ms_per_solve": 1e3 * t_b / n_steps,
-                   "one_by_one_fp64": seq["fp64"], "one_by_one_mixed": seq["mixed"], "autotuned": tuned}
+                   "one_by_one_fp64": seq["fp64"], "one_by_one_mixed": seq["mixed"], "autotuned": tuned,
+                   "vs_oracle": gate}
         batch.close()
         for c in bctx:
             c.close()
 
-    golden_rms = None
-    vs_oracle = None
-    gpath = os.path.join(ROOT, "tests", "golden", f"{args.workload}_oracle.json")
-    if os.path.exists(gpath):
-        with open(gpath) as f:
-            gold = json.load(f)
-        golden_rms = gold["final_rms_px"]
-        fp64_err = None
-        if fp64_poses is not None:
-            fp64_err = dict(pose_errors(fp64_poses, np.array(gold["final_poses"])),
-                            rms_px=abs(fp64["rms_px"] - golden_rms))
-        # per-result error of the timed path's final state against the oracle's
-        vs_oracle = dict(pose_errors(final_poses, np.array(gold["final_poses"])),
-                         rms_px=abs(ev["rms"] - golden_rms), precision=precision,
-                         **({"fp64": fp64_err} if fp64_err else {}))
-
+    golden_rms = gold["final_rms_px"] if gold else None
     if rank == 0:
         line = {
             "metric": METRIC,
@@ -519,21 +555,22 @@ def run_ours(args):
                        "precision": precision, "lm_iters_per_step": p.iters, "parallelism": "replicas",
                        "l2": "flushed between steps (512 MiB write outside the timed events)"},
             "gobs_per_s": gobs,
-            "rms_px": ev["rms"], "rms_oracle_px": golden_rms, "vs_oracle": vs_oracle,
+            "rms_px": ev["rms"], "rms_oracle_px": golden_rms,
             "rms_ok": None if golden_rms is None else bool(abs(ev["rms"] - golden_rms) <= 1e-3),
+            "vs_oracle": vs_golden(p, gold, final_poses, ev["rms"]),
             "fp64": fp64,
             "roofline": roof,
+            "roofline_all": roofs,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": cs.summary(),
-            "c4": c4,
+            "c1": c1,
             "batched": batched,
-            "gpu_launches": launches_per_solve * args.steps,
+            "gpu_launches": launches,
             "gpu_launches_extras": extra_launches,
             "wall_s_timed": wall,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

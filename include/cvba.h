@@ -53,7 +53,8 @@ typedef enum {
   CVBA_ERR_OOM = 5,          /* device allocation failed */
   CVBA_ERR_NOT_PD = 6,       /* reserved: a system was not positive definite (solve
                                 reports this per iteration in cvba_iter.nonpd instead) */
-  CVBA_ERR_TIMEOUT = 7,      /* a bounded device-side wait gave up */
+  CVBA_ERR_TIMEOUT = 7,      /* reserved: a bounded device-side wait gave up (no call of this
+                                library waits on the device without a bound today) */
   CVBA_ERR_STATE = 8         /* call out of order (e.g. solve before all setters) */
 } cvba_status;
 
@@ -108,8 +109,16 @@ const char* cvba_last_error(const cvba_ctx* ctx);
 /* Problem definition (Sec. 2.2: rig T^cb_k and intrinsics, poses T^bw_i, landmarks
  * p^w_j, observations o_{j,k}) ---------------------------------------------------- */
 
-/* n_cams >= 1 cameras: intr[n_cams*4] (fx, fy, cx, cy), T_cb[n_cams*12]. */
-cvba_status cvba_set_rig(cvba_ctx* ctx, int n_cams, const double* intr, const double* T_cb);
+/* n_cams >= 1 cameras: intr[n_cams*4] (fx, fy, cx, cy), T_cb[n_cams*12], and optionally
+ * each camera's image width and height wh[n_cams*2] (> 0; NULL = not given).  The image size
+ * plays no part in the objective (an observation outside its image is still a residual; the
+ * paper's Eq. r^repr has no bounds), so the solve does not use it: it is kept with the rig
+ * and returned by cvba_get_rig. */
+cvba_status cvba_set_rig(cvba_ctx* ctx, int n_cams, const double* intr, const double* T_cb, const int32_t* wh);
+
+/* The rig as set: intr[n_cams*4], T_cb[n_cams*12], wh[n_cams*2] (zeros when not given).
+ * Any pointer may be NULL. */
+cvba_status cvba_get_rig(cvba_ctx* ctx, double* intr, double* T_cb, int32_t* wh);
 
 /* n_kf >= 2 keyframe poses T_bw[n_kf*12]; keyframe `fixed_kf` is held constant. */
 cvba_status cvba_set_poses(cvba_ctx* ctx, int n_kf, const double* T_bw, int fixed_kf);
@@ -118,8 +127,10 @@ cvba_status cvba_set_poses(cvba_ctx* ctx, int n_kf, const double* T_bw, int fixe
 cvba_status cvba_set_landmarks(cvba_ctx* ctx, int n_lm, const double* p_w);
 
 /* n_obs observations: keyframe kf[n], camera cam[n], landmark lm[n] and pixel uv[2n..2n+1].
- * Indices are validated (CVBA_ERR_INDEX); every landmark needs >= 2 observations
- * (CVBA_ERR_INVALID_ARG).  Must follow set_rig, set_poses and set_landmarks.
+ * Indices are validated (CVBA_ERR_INDEX); every landmark needs >= 2 observations and every
+ * keyframe except the fixed one >= 1 (otherwise its columns of the normal equations are
+ * zero and no damping makes the system well posed): CVBA_ERR_INVALID_ARG.  Must follow
+ * set_rig, set_poses and set_landmarks.
  * This call builds the device layout: observations sorted by (landmark, keyframe,
  * camera), landmarks reordered by keyframe span, and the solve's work tiles. */
 cvba_status cvba_set_observations(cvba_ctx* ctx, int n_obs, const int32_t* kf, const int32_t* cam,
@@ -149,6 +160,20 @@ cvba_status cvba_get_increment(cvba_ctx* ctx, double* dx);
 /* Current LM damping state (lambda, nu) and its replacement. */
 cvba_status cvba_get_damping(cvba_ctx* ctx, double* lambda, double* nu);
 cvba_status cvba_set_damping(cvba_ctx* ctx, double lambda, double nu);
+
+/* Checkpoint of the solve state: everything a later solve depends on besides the problem
+ * itself, i.e. the current poses, the landmarks (caller order) and the LM damping (lambda,
+ * nu), in an opaque, versioned byte buffer (a fixed header with the window's sizes, then
+ * FP64 values).  With buf == NULL, cvba_get_state only writes the size needed to *bytes;
+ * otherwise *bytes must be at least that size (CVBA_ERR_INVALID_ARG) and receives it.
+ * cvba_set_state restores a buffer into a context holding the same problem (same keyframe,
+ * landmark and observation counts and fixed keyframe: CVBA_ERR_INVALID_ARG otherwise).
+ * Resuming is exact: on the FP64 path, a solve of N iterations gives bit-identical results
+ * to a solve of k iterations, a checkpoint, a restore (into this or another context with the
+ * same problem) and a solve of N - k iterations with reset_lambda = 0.  Requires a layout
+ * (CVBA_ERR_STATE). */
+cvba_status cvba_get_state(cvba_ctx* ctx, void* buf, size_t* bytes);
+cvba_status cvba_set_state(cvba_ctx* ctx, const void* buf, size_t bytes);
 
 /* Device layout, for exact integer checks: lm_order[n_lm] = caller landmark index of each
  * internal landmark; obs_order[n_obs] = caller observation index of each internal slot;

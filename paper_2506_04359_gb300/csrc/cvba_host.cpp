@@ -23,6 +23,7 @@ struct cvba_ctx {
 
   int C = 0, K = 0, M = 0, N = 0, P = 0, fixed_kf = 0;
   std::vector<double> intr, T_cb, poses, lms;
+  std::vector<int32_t> wh;                      // image sizes (zeros when not given)
   bool have_rig = false, have_poses = false, have_lms = false, have_layout = false;
 
   std::vector<int32_t> lm_order, lm_rank, obs_order, lm_off;
@@ -186,6 +187,13 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   for (int j = 0; j < M; ++j)
     if (count[j] < 2)
       return fail(c, CVBA_ERR_INVALID_ARG, "landmark " + std::to_string(j) + " has fewer than 2 observations");
+  {
+    std::vector<int32_t> kf_count(K, 0);
+    for (int n = 0; n < N; ++n) kf_count[kf[n]]++;
+    for (int a = 0; a < K; ++a)
+      if (a != c->fixed_kf && kf_count[a] == 0)
+        return fail(c, CVBA_ERR_INVALID_ARG, "keyframe " + std::to_string(a) + " is free but has no observations");
+  }
   c->lm_order.resize(M);
   for (int j = 0; j < M; ++j) c->lm_order[j] = j;
   {
@@ -679,17 +687,24 @@ void cvba_destroy(cvba_ctx* c) {
   delete c;
 }
 
-cvba_status cvba_set_rig(cvba_ctx* c, int n_cams, const double* intr, const double* T_cb) {
+cvba_status cvba_set_rig(cvba_ctx* c, int n_cams, const double* intr, const double* T_cb, const int32_t* wh) {
   if (!c) return CVBA_ERR_INVALID_ARG;
   if (n_cams < 1 || n_cams > C_MAX || !intr || !T_cb)
     return fail(c, CVBA_ERR_INVALID_ARG, "set_rig: need 1 <= n_cams <= 64 and non-NULL arrays");
   if (!all_finite(intr, (size_t)n_cams * 4) || !all_finite(T_cb, (size_t)n_cams * 12))
     return fail(c, CVBA_ERR_NONFINITE, "set_rig: non-finite value");
+  if (wh)
+    for (int k = 0; k < 2 * n_cams; ++k)
+      if (wh[k] <= 0) return fail(c, CVBA_ERR_INVALID_ARG, "set_rig: image sizes must be positive");
   DeviceGuard g(c->device);
   if (c->have_layout && n_cams != c->C) c->have_layout = false;
   c->C = n_cams;
   c->intr.assign(intr, intr + (size_t)n_cams * 4);
   c->T_cb.assign(T_cb, T_cb + (size_t)n_cams * 12);
+  if (wh)
+    c->wh.assign(wh, wh + (size_t)n_cams * 2);
+  else
+    c->wh.assign((size_t)n_cams * 2, 0);
   c->have_rig = true;
   if (c->have_layout) {
     std::vector<double> righ((size_t)c->C * RIG_STRIDE);
@@ -703,6 +718,15 @@ cvba_status cvba_set_rig(cvba_ctx* c, int n_cams, const double* intr, const doub
     CK(h2d(c, const_cast<double*>(c->d.rig), righ.data(), righ.size() * 8), "upload rig");
     CK(upload_f32(c, const_cast<float*>(c->d.rig_f), righ.data(), righ.size()), "upload rig");
   }
+  return CVBA_OK;
+}
+
+cvba_status cvba_get_rig(cvba_ctx* c, double* intr, double* T_cb, int32_t* wh) {
+  if (!c) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_rig) return fail(c, CVBA_ERR_STATE, "get_rig: no rig");
+  if (intr) std::copy(c->intr.begin(), c->intr.end(), intr);
+  if (T_cb) std::copy(c->T_cb.begin(), c->T_cb.end(), T_cb);
+  if (wh) std::copy(c->wh.begin(), c->wh.end(), wh);
   return CVBA_OK;
 }
 
@@ -1038,6 +1062,65 @@ cvba_status cvba_set_damping(cvba_ctx* c, double lam, double nu) {
   CK(h2d(c, &c->d.ctrl->lam, &lam, sizeof(double)), "set lambda");
   CK(h2d(c, &c->d.ctrl->nu, &nu, sizeof(double)), "set nu");
   return CVBA_OK;
+}
+
+namespace {
+// Checkpoint buffer: header, then poses (K x 12) and landmarks (M x 3, caller order).
+struct StateHeader {
+  char magic[8];        // "CVBASTA1"
+  int32_t K, M, N, fixed_kf;
+  double lam, nu;
+};
+constexpr char kStateMagic[8] = {'C', 'V', 'B', 'A', 'S', 'T', 'A', '1'};
+size_t state_bytes(const cvba_ctx* c) {
+  return sizeof(StateHeader) + sizeof(double) * ((size_t)c->K * 12 + (size_t)c->M * 3);
+}
+}  // namespace
+
+cvba_status cvba_get_state(cvba_ctx* c, void* buf, size_t* bytes) {
+  if (!c || !bytes) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "get_state: set_observations first");
+  const size_t need = state_bytes(c);
+  if (!buf) {
+    *bytes = need;
+    return CVBA_OK;
+  }
+  if (*bytes < need) return fail(c, CVBA_ERR_INVALID_ARG, "get_state: buffer too small");
+  StateHeader h{};
+  std::memcpy(h.magic, kStateMagic, sizeof(h.magic));
+  h.K = c->K, h.M = c->M, h.N = c->N, h.fixed_kf = c->fixed_kf;
+  cvba_status st = cvba_get_damping(c, &h.lam, &h.nu);
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  double* poses = reinterpret_cast<double*>(out + sizeof(StateHeader));
+  std::vector<double> P((size_t)c->K * 12), L((size_t)c->M * 3);
+  if (st == CVBA_OK) st = cvba_get_poses(c, P.data());
+  if (st == CVBA_OK) st = cvba_get_landmarks(c, L.data());
+  if (st != CVBA_OK) return st;
+  std::memcpy(out, &h, sizeof(h));
+  std::memcpy(poses, P.data(), P.size() * sizeof(double));
+  std::memcpy(poses + P.size(), L.data(), L.size() * sizeof(double));
+  *bytes = need;
+  return CVBA_OK;
+}
+
+cvba_status cvba_set_state(cvba_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return CVBA_ERR_INVALID_ARG;
+  if (!c->have_layout) return fail(c, CVBA_ERR_STATE, "set_state: set_observations first");
+  if (bytes < sizeof(StateHeader)) return fail(c, CVBA_ERR_INVALID_ARG, "set_state: buffer too small");
+  StateHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kStateMagic, sizeof(h.magic)) != 0)
+    return fail(c, CVBA_ERR_INVALID_ARG, "set_state: not a checkpoint of this library");
+  if (h.K != c->K || h.M != c->M || h.N != c->N || h.fixed_kf != c->fixed_kf || bytes < state_bytes(c))
+    return fail(c, CVBA_ERR_INVALID_ARG, "set_state: checkpoint of a different problem");
+  std::vector<double> P((size_t)c->K * 12), L((size_t)c->M * 3);
+  const unsigned char* in = static_cast<const unsigned char*>(buf) + sizeof(StateHeader);
+  std::memcpy(P.data(), in, P.size() * sizeof(double));
+  std::memcpy(L.data(), in + P.size() * sizeof(double), L.size() * sizeof(double));
+  cvba_status st = cvba_set_poses(c, c->K, P.data(), c->fixed_kf);
+  if (st == CVBA_OK) st = cvba_set_landmarks(c, c->M, L.data());
+  if (st == CVBA_OK) st = cvba_set_damping(c, h.lam, h.nu);
+  return st;
 }
 
 cvba_status cvba_get_layout(cvba_ctx* c, int32_t* lm_order, int32_t* obs_order, int32_t* lm_off) {

@@ -63,7 +63,10 @@ def _load() -> C.CDLL:
         "cvba_destroy": (None, [vp]),
         "cvba_status_string": (C.c_char_p, [i]),
         "cvba_last_error": (C.c_char_p, [vp]),
-        "cvba_set_rig": (i, [vp, i, dp, dp]),
+        "cvba_set_rig": (i, [vp, i, dp, dp, ip]),
+        "cvba_get_rig": (i, [vp, dp, dp, ip]),
+        "cvba_get_state": (i, [vp, vp, C.POINTER(C.c_size_t)]),
+        "cvba_set_state": (i, [vp, vp, C.c_size_t]),
         "cvba_set_poses": (i, [vp, i, dp, i]),
         "cvba_set_landmarks": (i, [vp, i, dp]),
         "cvba_set_observations": (i, [vp, i, ip, ip, ip, dp]),
@@ -151,9 +154,31 @@ class Context:
             raise CvbaError(st, lib.cvba_last_error(self._h).decode())
 
     # --- setters
-    def cvba_set_rig(self, intr, T_cb):
+    def cvba_set_rig(self, intr, T_cb, wh=None):
         intr, T_cb = _f64(intr).reshape(-1, 4), _f64(T_cb).reshape(-1, 12)
-        self._check(lib.cvba_set_rig(self._h, intr.shape[0], _dptr(intr), _dptr(T_cb)))
+        whp = None
+        if wh is not None:
+            wh = _i32(wh).reshape(-1, 2)
+            whp = _iptr(wh)
+        self._check(lib.cvba_set_rig(self._h, intr.shape[0], _dptr(intr), _dptr(T_cb), whp))
+
+    def cvba_get_rig(self):
+        C_ = self.cvba_get_sizes()["C"]
+        intr, T_cb, wh = np.zeros((C_, 4)), np.zeros((C_, 3, 4)), np.zeros((C_, 2), np.int32)
+        self._check(lib.cvba_get_rig(self._h, _dptr(intr), _dptr(T_cb), _iptr(wh)))
+        return intr, T_cb, wh
+
+    def cvba_get_state(self) -> bytes:
+        """Checkpoint of the solve state (poses, landmarks, damping) as bytes."""
+        n = C.c_size_t()
+        self._check(lib.cvba_get_state(self._h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(lib.cvba_get_state(self._h, buf, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def cvba_set_state(self, state: bytes):
+        buf = C.create_string_buffer(bytes(state), len(state))
+        self._check(lib.cvba_set_state(self._h, buf, len(state)))
 
     def cvba_set_poses(self, T_bw, fixed_kf: int = 0):
         T = _f64(T_bw).reshape(-1, 12)
@@ -271,7 +296,7 @@ class Context:
     # --- convenience
     def load(self, problem, poses=None, landmarks=None):
         """Load a synth.Problem (rig, initial poses and landmarks, observations)."""
-        self.cvba_set_rig(problem.rig.intr, problem.rig.T_cb)
+        self.cvba_set_rig(problem.rig.intr, problem.rig.T_cb, problem.rig.wh)
         self.cvba_set_poses(problem.poses0 if poses is None else poses, problem.fixed_kf)
         self.cvba_set_landmarks(problem.lm0 if landmarks is None else landmarks)
         self.cvba_set_observations(problem.obs_kf, problem.obs_cam, problem.obs_lm, problem.obs_uv)

@@ -1,0 +1,177 @@
+"""GPU parity on the full-size multi-camera windows and on every batched window, against
+Oracle-S (the block-sparse FP64 oracle: the same damped normal equations as the dense
+oracle, factored by a generic sparse Cholesky instead of the Schur complement).
+
+FP64 path, the method itself:
+* lock-step: from the same state and damping, the solved increment within 1e-9 relative of
+  Oracle-S's, plus four times the residual-rounding floor (the rule of the dense parity
+  tests);
+* free-running: identical accept sequences, per-iteration costs within 1e-9 relative, final
+  poses within 1e-6 (translation relative to max(|t|, 1 m); rotation angle in rad) and
+  landmarks within 1e-6 relative; integer counts identical.
+Mixed path: final RMS reprojection error within 1e-3 px of Oracle-S's, with the workload's
+outliers in.
+"""
+import numpy as np
+import pytest
+
+from oracle import ba, ba_sparse
+from paper_2506_04359_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cvba(cuda_device):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_04359_gb300 import cvba as m
+    return m
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def state_errors(P, L, Po, Lo):
+    """(max translation error / max(|t|, 1 m), max rotation angle (rad), max landmark error /
+    |p|) between a final state and the oracle's."""
+    dt = max(np.linalg.norm(P[i, :, 3] - Po[i, :, 3]) / max(np.linalg.norm(Po[i, :, 3]), 1.0) for i in range(len(P)))
+    dr = 0.0
+    for i in range(len(P)):
+        E = P[i, :, :3] @ Po[i, :, :3].T
+        s = np.linalg.norm([E[2, 1] - E[1, 2], E[0, 2] - E[2, 0], E[1, 0] - E[0, 1]]) / 2.0
+        dr = max(dr, float(np.arctan2(s, (np.trace(E) - 1.0) / 2.0)))
+    dl = float(np.max(np.linalg.norm(L - Lo, axis=1) / np.linalg.norm(Lo, axis=1)))
+    return dt, dr, dl
+
+
+class Oracle:
+    """Oracle-S results of one window, computed once per test module."""
+
+    def __init__(self, p, iters=None, threads=None):
+        self.p = p
+        self.win = ba.Window.from_problem(p)
+        self.sw = ba_sparse.SparseWindow(self.win, threads)
+        self.iters = p.iters if iters is None else iters
+        self.P, self.L, self.lam, self.nu, self.trace = ba_sparse.lm_solve(
+            self.win, p.poses0, p.lm0, self.iters, keep_delta=False, sw=self.sw)
+        self.final = self.sw.evaluate(self.P, self.L)
+
+    def floor(self, poses, lms, delta):
+        """One-ulp residual rounding mapped through Oracle-S's factor, relative to |delta|
+        (the factor of the last linearise_solve, at `poses`, `lms`)."""
+        w = self.win
+        r, _ = ba.residuals(w, poses, lms)
+        _, wt = ba.huber(np.einsum("ni,ni->n", r, r), w.huber_delta)
+        Jp, Jl = ba.jacobians(w, poses, lms)
+        scale = 2.0 ** -52 * (np.abs(w.obs_uv) + np.abs(r) + np.abs(w.intr[w.obs_cam][:, 2:4]))
+        e = scale * np.random.default_rng(0).standard_normal(scale.shape)
+        pc = w.pose_col()[w.obs_kf]
+        dg = np.zeros(w.n_f + 1)
+        np.add.at(dg, np.where(pc[:, None] >= 0, pc[:, None] + np.arange(6), w.n_f),
+                  wt[:, None] * np.einsum("nai,na->ni", Jp, e))
+        np.add.at(dg, w.n_c + 3 * w.obs_lm[:, None] + np.arange(3), wt[:, None] * np.einsum("nai,na->ni", Jl, e))
+        return float(np.linalg.norm(self.sw.solve_rhs(dg[:-1]))) / float(np.linalg.norm(delta))
+
+
+@pytest.fixture(scope="module")
+def c2():
+    return Oracle(synth.make_problem("c2", 0))
+
+
+@pytest.fixture(scope="module")
+def c4():
+    return Oracle(synth.make_problem("c4", 0))
+
+
+def check_free_running(cvba, o: Oracle, precision="fp64"):
+    p = o.p
+    ctx = cvba.Context(precision).load(p)
+    tr = ctx.cvba_solve(o.iters, huber_delta=p.huber_delta)
+    P, L = ctx.cvba_get_poses(), ctx.cvba_get_landmarks()
+    ctx.close()
+    return tr, P, L
+
+
+@pytest.mark.parametrize("name", ["c2", "c4"])
+def test_fp64_free_running_matches_oracle_s(cvba, name, c2, c4):
+    o = {"c2": c2, "c4": c4}[name]
+    tr, P, L = check_free_running(cvba, o)
+    assert tr["accepted"].tolist() == [int(r.accepted) for r in o.trace]
+    assert np.all(tr["nonpd"] == 0)
+    c0 = np.array([r.cost0 for r in o.trace])
+    np.testing.assert_allclose(tr["cost0"], c0, rtol=1e-9, atol=0)
+    assert tr["n_valid"].tolist() == [r.n_valid for r in o.trace]
+    assert tr["n_inlier"].tolist() == [r.n_inlier for r in o.trace]
+    dt, dr, dl = state_errors(P, L, o.P, o.L)
+    print(f"{name}: translation {dt:.2e}, rotation {dr:.2e} rad, landmarks {dl:.2e}")
+    assert dt <= 1e-6 and dr <= 1e-6 and dl <= 1e-6
+
+
+@pytest.mark.parametrize("name, steps", [("c2", 3), ("c4", 2)])
+def test_fp64_lockstep_increment_matches_oracle_s(cvba, name, steps, c2, c4):
+    o = {"c2": c2, "c4": c4}[name]
+    p = o.p
+    ctx = cvba.Context("fp64").load(p)
+    poses, lms, lam, nu = p.poses0.copy(), p.lm0.copy(), 1e-4, 2.0
+    for it in range(steps):
+        ctx.cvba_set_poses(poses, p.fixed_kf)
+        ctx.cvba_set_landmarks(lms)
+        ctx.cvba_set_damping(lam, nu)
+        tr = ctx.cvba_solve(1, huber_delta=p.huber_delta, reset_lambda=False)
+        dx = ctx.cvba_get_increment()
+        delta, D, g, ev = o.sw.linearise_solve(poses, lms, lam)
+        tol = 1e-9 + 4.0 * o.floor(poses, lms, delta)
+        d = rel(dx, delta)
+        print(f"{name} step {it}: |d - d_oracle| / |d_oracle| = {d:.2e} (allowed {tol:.2e})")
+        assert d <= tol
+        assert int(tr[0]["n_valid"]) == ev.n_valid and int(tr[0]["n_inlier"]) == ev.n_inlier
+        assert abs(tr[0]["cost0"] - ev.F) <= 1e-10 * ev.F
+        poses, lms, lam, nu, _ = ba_sparse.lm_iteration(o.sw, poses, lms, lam, nu)
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["c2", "c4"])
+def test_mixed_final_rms_matches_oracle_s(cvba, name, c2, c4):
+    """With the workload's outliers (3% on the 100-keyframe window)."""
+    o = {"c2": c2, "c4": c4}[name]
+    tr, P, L = check_free_running(cvba, o, "mixed")
+    rms = o.sw.evaluate(P, L).rms
+    dt, dr, dl = state_errors(P, L, o.P, o.L)
+    print(f"{name} mixed: RMS {rms:.9f} vs oracle {o.final.rms:.9f} px; translation {dt:.2e}, rotation {dr:.2e}")
+    assert abs(rms - o.final.rms) <= 1e-3
+
+
+@pytest.fixture(scope="module")
+def c3():
+    wins = synth.make_batch(256)
+    return wins, [Oracle(p, threads=1) for p in wins]
+
+
+def test_batched_all_256_windows_match_oracle_s(cvba, c3):
+    """Every window of the batched workload, FP64 and mixed, solved in one batched graph."""
+    wins, oracles = c3
+    for precision in ("fp64", "mixed"):
+        ctxs = [cvba.Context(precision).load(p) for p in wins]
+        batch = cvba.Batch(ctxs)
+        iters = wins[0].iters
+        tr = batch.cvba_batch_solve(iters)
+        worst = dict(rms=0.0, dt=0.0, dr=0.0, dl=0.0, cost=0.0)
+        for w, (ctx, o) in enumerate(zip(ctxs, oracles)):
+            P, L = ctx.cvba_get_poses(), ctx.cvba_get_landmarks()
+            rms = o.sw.evaluate(P, L).rms
+            worst["rms"] = max(worst["rms"], abs(rms - o.final.rms))
+            if precision == "fp64":
+                assert tr[w]["accepted"].tolist() == [int(r.accepted) for r in o.trace], w
+                c0 = np.array([r.cost0 for r in o.trace])
+                worst["cost"] = max(worst["cost"], float(np.max(np.abs(tr[w]["cost0"] - c0) / c0)))
+                dt, dr, dl = state_errors(P, L, o.P, o.L)
+                worst.update(dt=max(worst["dt"], dt), dr=max(worst["dr"], dr), dl=max(worst["dl"], dl))
+        print(precision, worst)
+        assert worst["rms"] <= 1e-3
+        if precision == "fp64":
+            assert worst["cost"] <= 1e-9 and worst["dt"] <= 1e-6 and worst["dr"] <= 1e-6 and worst["dl"] <= 1e-6
+        batch.close()
+        for c in ctxs:
+            c.close()
