@@ -290,6 +290,77 @@ cvba_status cvba_cost_backward(int dtype, int n_obs, int n_kf, int n_cams, int n
                                void* g_T_bw, void* g_p_w, void* g_intr, void* work, size_t work_bytes,
                                void* stream);
 
+/* Motion-only bundle adjustment (multi-camera PnP) ---------------------------------------
+ *
+ * The pose of a tracked frame from its observations of map landmarks (Sec. 2.2.1 stereo,
+ * Eq. PnP over k in [1, 2]; Sec. 2.2.2 multi-stereo, the same sum over every camera k of
+ * the rig):  T^bw = argmin sum_j sum_k rho(|pi(T^cb_k T^bw p^w_j) - o_{j,k}|^2)  over the one
+ * base pose, the landmarks p^w_j held fixed.  Same readings as the window solve: Huber IRLS
+ * weights at the linearisation point, left SE(3) update, Marquardt diagonal floored at
+ * 1e-12 max, Nielsen's damping update, accept iff the predicted reduction and the gain are
+ * positive, exactly opts->iters iterations (opts->reset_lambda and opts->refine are
+ * ignored: every frame starts from opts->lambda0, nu = 2).
+ *
+ * Many independent frames are solved in one launch (one thread block per frame, every
+ * iteration inside it).  Context-free; DEVICE arrays in the caller's order:
+ *   intr[n_cams*4], T_cb[n_cams*12], p_w[n_lm*3] and uv[n_obs*2] of type dtype
+ *     (0 = FP64: all arithmetic in FP64; 1 = FP32 inputs, per-observation arithmetic in FP32
+ *     with two-float block sums, the 6 x 6 solve, the pose and the decision in FP64),
+ *   frame_off[n_frames+1] (int32): frame f owns observations [frame_off[f], frame_off[f+1]),
+ *     non-decreasing from 0 to n_obs (read back to the host and checked:
+ *     CVBA_ERR_INVALID_ARG; the call therefore waits for the stream to reach it),
+ *   cam[n_obs], lm[n_obs] (int32): an observation with an index out of range is skipped and
+ *     counted in n_bad_index,
+ *   T_bw[n_frames*12] (FP64, in: initial poses, out: solved poses),
+ *   trace (may be NULL): n_frames * opts->iters records, frame-major.
+ * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream) after the check.
+ * n_cams <= 64. */
+/* One iteration of a small LM solve (one frame's pose, one landmark, ...): the fields of
+ * cvba_iter for that solve, plus the count of its observations skipped for an index out of
+ * range. */
+typedef struct {
+  double cost0, cost1, lambda, gain, pred, step_norm, rms_px;   /* as in cvba_iter */
+  int accepted, nonpd, n_valid, n_inlier;
+  int n_bad_index;   /* observations of the solve skipped for an index out of range */
+  int reserved;
+} cvba_lm_record;
+
+cvba_status cvba_pnp_solve(int dtype, int n_frames, int n_cams, int n_lm, int n_obs, const void* intr,
+                           const void* T_cb, const void* p_w, const int32_t* frame_off, const int32_t* cam,
+                           const int32_t* lm, const void* uv, double* T_bw, const cvba_opts* opts,
+                           cvba_lm_record* trace, void* stream);
+
+/* Kernel launches of one cvba_pnp_solve call (1). */
+int cvba_pnp_kernels_per_solve(void);
+
+/* Multi-view landmark triangulation ------------------------------------------------------
+ *
+ * The new landmarks of a keyframe from their multi-view observations, the keyframe poses and
+ * the rig held fixed (Sec. 2.2 "3D module": triangulation on keyframe creation, whose output
+ * the bundle adjustment refines).  The paper names the step without a method; this library
+ * computes, for each landmark j:
+ *   1. the linear point: with x = ((u - cx)/fx, (v - cy)/fy) and [R | t] = T^cb_k T^bw_i,
+ *      the least-squares solution of x (R_3 p + t_3) = R_1 p + t_1, y (R_3 p + t_3) = R_2 p + t_2
+ *      over its observations (inhomogeneous DLT), in FP64;
+ *   2. opts->iters LM iterations on the point alone: the window solve's step restricted to
+ *      one landmark (Huber IRLS weights, Marquardt diagonal, Nielsen's update, accept iff the
+ *      predicted reduction and the gain are positive).
+ * Context-free; DEVICE arrays: intr[n_cams*4], T_cb[n_cams*12], uv[n_obs*2] of type dtype
+ * (0 = FP64; 1 = FP32: the refinement's per-observation arithmetic in FP32, the linear step,
+ * the 3 x 3 solves, the point and the decisions in FP64), T_bw[n_kf*12] (FP64),
+ * lm_off[n_lm+1] (int32; landmark j owns observations [lm_off[j], lm_off[j+1]), checked on the
+ * host as for cvba_pnp_solve), kf[n_obs], cam[n_obs] (int32; out-of-range observations are
+ * skipped and counted in the records).  Outputs: p_w[n_lm*3] (FP64; NaN where status != 0),
+ * p_lin[n_lm*3] (the linear points, may be NULL), status[n_lm] (may be NULL: 0 = solved,
+ * 1 = fewer than 2 usable observations, 2 = the linear system is rank deficient, a pivot of
+ * its normal equations below 1e-14 of their largest diagonal entry) and trace
+ * (n_lm * opts->iters records, landmark-major, written for status 0 only; may be NULL).
+ * n_kf <= 256, n_cams <= 64.  Asynchronous on `stream` after the check. */
+cvba_status cvba_triangulate(int dtype, int n_lm, int n_kf, int n_cams, int n_obs, const void* intr,
+                             const void* T_cb, const double* T_bw, const int32_t* lm_off, const int32_t* kf,
+                             const int32_t* cam, const void* uv, const cvba_opts* opts, double* p_lin, double* p_w,
+                             int32_t* status, cvba_lm_record* trace, void* stream);
+
 /* Allocation-free evaluation ----------------------------------------------------------
  *
  * The paper has no counterpart to this call; it exists for callers that cannot allocate

@@ -46,6 +46,11 @@ ITER_DTYPE = np.dtype([("cost0", "f8"), ("cost1", "f8"), ("lambda", "f8"), ("gai
 assert ITER_DTYPE.itemsize == C.sizeof(cvba_iter)
 
 
+LM_RECORD_DTYPE = np.dtype([("cost0", "f8"), ("cost1", "f8"), ("lambda", "f8"), ("gain", "f8"), ("pred", "f8"),
+                           ("step_norm", "f8"), ("rms_px", "f8"), ("accepted", "i4"), ("nonpd", "i4"),
+                           ("n_valid", "i4"), ("n_inlier", "i4"), ("n_bad_index", "i4"), ("reserved", "i4")])
+
+
 class CvbaError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -89,6 +94,9 @@ def _load() -> C.CDLL:
         "cvba_profile_iteration": (i, [vp, C.POINTER(cvba_opts), i, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
         "cvba_profile_names": (C.c_char_p, []),
         "cvba_evaluate_noalloc": (i, [i, i, i, i] + [vp] * 8 + [d, d, vp, vp]),
+        "cvba_pnp_solve": (i, [i, i, i, i, i] + [vp] * 9 + [C.POINTER(cvba_opts), vp, vp]),
+        "cvba_pnp_kernels_per_solve": (i, []),
+        "cvba_triangulate": (i, [i, i, i, i, i] + [vp] * 8 + [C.POINTER(cvba_opts)] + [vp] * 5),
         "cvba_set_tuning": (i, [vp, i, i]),
         "cvba_set_chol_mode": (i, [vp, i]),
         "cvba_batch_create": (i, [C.POINTER(vp), i, C.POINTER(vp)]),
@@ -314,6 +322,36 @@ def cvba_evaluate_noalloc(n_obs: int, n_kf: int, n_cams: int, n_lm: int, intr: i
                                    float(z_min), C.c_void_p(out), C.c_void_p(stream) if stream else None)
     if st != 0:
         raise CvbaError(st, "cvba_evaluate_noalloc failed")
+
+
+def cvba_pnp_solve(dtype: int, n_frames: int, n_cams: int, n_lm: int, n_obs: int, intr: int, T_cb: int, p_w: int,
+                   frame_off: int, cam: int, lm: int, uv: int, T_bw: int, iters: int, huber_delta: float = 1.0,
+                   lambda0: float = 1e-4, z_min: float = 1e-3, trace: int = 0, stream: int = 0) -> None:
+    """Motion-only bundle adjustment of a batch of frames from device pointers (see
+    include/cvba.h); raises on a non-OK status.  dtype 0 = FP64, 1 = FP32 inputs."""
+    o = make_opts(iters, huber_delta, lambda0, z_min)
+    st = lib.cvba_pnp_solve(int(dtype), int(n_frames), int(n_cams), int(n_lm), int(n_obs), C.c_void_p(intr),
+                            C.c_void_p(T_cb), C.c_void_p(p_w), C.c_void_p(frame_off), C.c_void_p(cam),
+                            C.c_void_p(lm), C.c_void_p(uv), C.c_void_p(T_bw), C.byref(o),
+                            C.c_void_p(trace) if trace else None, C.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise CvbaError(st, "cvba_pnp_solve failed")
+
+
+def cvba_triangulate(dtype: int, n_lm: int, n_kf: int, n_cams: int, n_obs: int, intr: int, T_cb: int, T_bw: int,
+                     lm_off: int, kf: int, cam: int, uv: int, p_w: int, iters: int, huber_delta: float = 1.0,
+                     lambda0: float = 1e-4, z_min: float = 1e-3, p_lin: int = 0, status: int = 0, trace: int = 0,
+                     stream: int = 0) -> None:
+    """Multi-view triangulation of a batch of landmarks from device pointers (see
+    include/cvba.h); raises on a non-OK status."""
+    o = make_opts(iters, huber_delta, lambda0, z_min)
+    opt = lambda x: C.c_void_p(x) if x else None
+    st = lib.cvba_triangulate(int(dtype), int(n_lm), int(n_kf), int(n_cams), int(n_obs), C.c_void_p(intr),
+                              C.c_void_p(T_cb), C.c_void_p(T_bw), C.c_void_p(lm_off), C.c_void_p(kf), C.c_void_p(cam),
+                              C.c_void_p(uv), C.byref(o), opt(p_lin), C.c_void_p(p_w), opt(status), opt(trace),
+                              opt(stream))
+    if st != 0:
+        raise CvbaError(st, "cvba_triangulate failed")
 
 
 class Batch:

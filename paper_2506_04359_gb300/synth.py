@@ -30,7 +30,8 @@ from dataclasses import dataclass, field
 import numpy as np
 from scipy.spatial.transform import Rotation
 
-__all__ = ["Rig", "Problem", "make_rig", "make_problem", "make_batch", "CONFIGS"]
+__all__ = ["Rig", "Problem", "make_rig", "make_problem", "make_batch", "CONFIGS", "FrameBatch", "make_frames",
+           "FRAME_CONFIGS"]
 
 
 @dataclass
@@ -377,3 +378,119 @@ def c3_window_config(seed: int) -> dict:
 def make_batch(n_windows: int = 256, first_seed: int = 0) -> list[Problem]:
     """Independent BA windows of uneven size (the batched workload), seeds first_seed..."""
     return [_generate(f"c3w{s}", s, c3_window_config(s)) for s in range(first_seed, first_seed + n_windows)]
+
+
+# ------------------------------------------------------------- frames (motion-only BA)
+
+@dataclass
+class FrameBatch:
+    """Independent frames for motion-only bundle adjustment (multi-camera PnP): each frame
+    has one base pose and observations of fixed map landmarks.  Observations are grouped by
+    frame: those of frame f are [frame_off[f], frame_off[f + 1])."""
+    name: str
+    seed: int
+    rig: Rig
+    poses_gt: np.ndarray    # (F, 3, 4) T^bw ground truth
+    poses0: np.ndarray      # (F, 3, 4) initial guess
+    lm: np.ndarray          # (M, 3) map landmarks (held fixed)
+    frame_off: np.ndarray   # (F + 1,) int32
+    obs_cam: np.ndarray     # (N,) int32
+    obs_lm: np.ndarray      # (N,) int32
+    obs_uv: np.ndarray      # (N, 2)
+    outlier: np.ndarray     # (N,) bool
+    iters: int = 10
+    huber_delta: float = 1.0
+
+    @property
+    def F(self) -> int:
+        return int(self.poses0.shape[0])
+
+    @property
+    def N(self) -> int:
+        return int(self.obs_cam.shape[0])
+
+    @property
+    def M(self) -> int:
+        return int(self.lm.shape[0])
+
+    @property
+    def C(self) -> int:
+        return self.rig.n_cams
+
+    def frame(self, f: int):
+        """(cam, lm, uv) of frame f."""
+        a, b = int(self.frame_off[f]), int(self.frame_off[f + 1])
+        return self.obs_cam[a:b], self.obs_lm[a:b], self.obs_uv[a:b]
+
+
+FRAME_CONFIGS = {
+    # stereo tracking frames: the small stereo rig, 300 map points per frame
+    "pnp_stereo": dict(rig=CONFIGS["c0"]["rig"], frames=1024, lm_per_frame=300, depth=(2.0, 12.0),
+                       sigma=0.5, outlier_frac=0.05, iters=10),
+    # multi-camera tracking frames: the 16-pair ring, ~400 map points per frame, each seen by
+    # about eight of the 32 cameras
+    "pnp_multi": dict(rig=CONFIGS["c4"]["rig"], frames=512, lm_per_frame=400, depth=(1.0, 15.0),
+                      sigma=0.7, outlier_frac=0.03, iters=10),
+}
+
+
+def make_frames(name: str = "pnp_stereo", seed: int = 0, **overrides) -> FrameBatch:
+    """Frames at random base poses (position in a 40 m square, heading uniform).  Each map
+    point is placed by choosing a camera, a pixel uniform over its image and a depth uniform
+    in `depth`, and is then observed by every camera of the rig in whose image it falls
+    (depth > 0.5 m).  Pixel noise, uniform outliers and the initial-guess perturbation (5 cm,
+    1 deg) as for the windows.  Draw order: poses -> points -> noise -> outliers ->
+    perturbation."""
+    cfg = dict(FRAME_CONFIGS[name])
+    cfg.update(overrides)
+    ss = np.random.SeedSequence([7, seed])
+    r_pose, r_pts, r_noise, r_out, r_pert = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(5)]
+    rig = make_rig(**cfg["rig"])
+    F, Mf = cfg["frames"], cfg["lm_per_frame"]
+    c_w = np.stack([r_pose.uniform(-20, 20, F), r_pose.uniform(-0.5, 0.5, F), r_pose.uniform(-20, 20, F)], 1)
+    R_wb = np.stack([_rot_y(a) for a in r_pose.uniform(-np.pi, np.pi, F)])
+    poses_gt = _poses_from(c_w, R_wb)
+    R_wc, c_wc = _camera_frames(rig, c_w, R_wb)                         # (F,C,3,3), (F,C,3)
+    C = rig.n_cams
+    cam0 = r_pts.integers(0, C, (F, Mf))
+    wh = rig.wh[cam0].astype(np.float64)
+    px = r_pts.random((F, Mf, 2)) * wh
+    depth = r_pts.uniform(cfg["depth"][0], cfg["depth"][1], (F, Mf))
+    intr0 = rig.intr[cam0]
+    ray = np.stack([(px[..., 0] - intr0[..., 2]) / intr0[..., 0], (px[..., 1] - intr0[..., 3]) / intr0[..., 1],
+                    np.ones((F, Mf))], -1) * depth[..., None]
+    ff = np.arange(F)[:, None]
+    pts = np.einsum("fmij,fmj->fmi", R_wc[ff, cam0], ray) + c_wc[ff, cam0]   # (F,Mf,3)
+    # project into every camera
+    d = pts[:, :, None, :] - c_wc[:, None, :, :]                           # (F,Mf,C,3)
+    Xc = np.einsum("fcji,fmcj->fmci", R_wc, d)
+    Z = Xc[..., 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        u = rig.intr[:, 0] * Xc[..., 0] / Z + rig.intr[:, 2]
+        v = rig.intr[:, 1] * Xc[..., 1] / Z + rig.intr[:, 3]
+    vis = (Z > 0.5) & (u >= 0) & (u < rig.wh[:, 0]) & (v >= 0) & (v < rig.wh[:, 1])
+    fi, mi, ci = np.nonzero(vis)                                            # sorted by frame
+    obs_lm = (fi * Mf + mi).astype(np.int32)
+    obs_cam = ci.astype(np.int32)
+    uv = np.stack([u[fi, mi, ci], v[fi, mi, ci]], 1)
+    N = uv.shape[0]
+    uv += r_noise.normal(0.0, cfg["sigma"], (N, 2))
+    outlier = r_out.random(N) < cfg["outlier_frac"]
+    n_out = int(outlier.sum())
+    if n_out:
+        uv[outlier] = r_out.random((n_out, 2)) * rig.wh[obs_cam[outlier]]
+    poses0, _ = perturb(poses_gt, np.zeros((0, 3)), r_pert, fixed_kf=-1, sigma_t=0.05, sigma_r_deg=1.0,
+                        sigma_l=0.0)
+    frame_off = np.concatenate([[0], np.cumsum(np.bincount(fi, minlength=F))]).astype(np.int32)
+    return FrameBatch(name=name, seed=seed, rig=rig, poses_gt=poses_gt, poses0=poses0, lm=pts.reshape(-1, 3),
+                      frame_off=frame_off, obs_cam=obs_cam, obs_lm=obs_lm, obs_uv=np.ascontiguousarray(uv),
+                      outlier=outlier, iters=cfg["iters"], huber_delta=1.0)
+
+
+def landmark_segments(obs_lm: np.ndarray, M: int):
+    """Observations grouped by landmark (stable): the permutation `order` and the segment
+    offsets lm_off (M + 1) with the observations of landmark j at order[lm_off[j]:lm_off[j+1]]."""
+    obs_lm = np.asarray(obs_lm, np.int64)
+    order = np.argsort(obs_lm, kind="stable").astype(np.int64)
+    lm_off = np.concatenate([[0], np.cumsum(np.bincount(obs_lm, minlength=M))]).astype(np.int32)
+    return order, lm_off

@@ -1,0 +1,115 @@
+"""Multi-view landmark triangulation on the GPU against its oracle (oracle/triangulate.py),
+through the C ABI (cvba_triangulate).
+
+Workloads: the landmarks of the stereo window (5,000) and of the 100-keyframe ring window
+(200,000; a sample of 2,000 is checked against the oracle), triangulated from their noisy
+observations with the keyframe poses at their true values and no outliers (tracked,
+correlation-checked observations).  FP64: the linear point within 1e-9 relative, the same
+accept sequence as the oracle's refinement with per-iteration costs within 1e-9 relative,
+the refined point within 1e-9 relative; status codes identical.  FP32 path: refined point
+within 1e-6 relative.  Edge cases: single-observation, duplicated-view and out-of-range
+observations, malformed segment offsets.
+"""
+import numpy as np
+import pytest
+
+from oracle import triangulate as tri
+from paper_2506_04359_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cvba(cuda_device):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2506_04359_gb300 import cvba as m
+    return m
+
+
+def workload(name):
+    p = synth.make_problem(name, outlier_frac=0.0)
+    order, off = synth.landmark_segments(p.obs_lm, p.M)
+    return p, off, p.obs_kf[order], p.obs_cam[order], p.obs_uv[order]
+
+
+def run_gpu(cvba, p, off, kf, cam, uv, dtype=0, iters=10, lm_off=None):
+    import torch
+    dev = torch.device("cuda:0")
+    ft = torch.float64 if dtype == 0 else torch.float32
+    t = lambda a, dt=ft: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    M = len(off) - 1
+    intr, tcb, uvt = t(p.rig.intr), t(p.rig.T_cb.reshape(-1, 12)), t(uv)
+    poses = t(p.poses_gt.reshape(p.K, 12), torch.float64)
+    offt = t(off if lm_off is None else lm_off, torch.int32)
+    kft, camt = t(kf, torch.int32), t(cam, torch.int32)
+    pw = torch.zeros(M * 3, dtype=torch.float64, device=dev)
+    plin = torch.zeros(M * 3, dtype=torch.float64, device=dev)
+    st = torch.full((M,), -1, dtype=torch.int32, device=dev)
+    trace = torch.zeros(M * iters * cvba.LM_RECORD_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    cvba.cvba_triangulate(dtype, M, p.K, p.C, len(kf), intr.data_ptr(), tcb.data_ptr(), poses.data_ptr(),
+                          offt.data_ptr(), kft.data_ptr(), camt.data_ptr(), uvt.data_ptr(), pw.data_ptr(), iters,
+                          p.huber_delta, p_lin=plin.data_ptr(), status=st.data_ptr(), trace=trace.data_ptr(),
+                          stream=stream.cuda_stream)
+    stream.synchronize()
+    tr = np.frombuffer(trace.cpu().numpy().tobytes(), cvba.LM_RECORD_DTYPE).reshape(M, iters)
+    return pw.cpu().numpy().reshape(M, 3), plin.cpu().numpy().reshape(M, 3), st.cpu().numpy(), tr
+
+
+@pytest.mark.parametrize("name, sample", [("c1", None), ("c4", 100)])
+def test_fp64_matches_oracle(cvba, name, sample):
+    p, off, kf, cam, uv = workload(name)
+    P, Plin, st, tr = run_gpu(cvba, p, off, kf, cam, uv, 0)
+    sel = range(0, p.M, sample) if sample else range(p.M)
+    ref = tri.triangulate(p.rig.intr, p.rig.T_cb, p.poses_gt, off, kf, cam, uv, 10, p.huber_delta, landmarks=sel)
+    worst = dict(lin=0.0, p=0.0, cost=0.0)
+    for j, (p0, pr, s, otr) in zip(sel, ref):
+        assert st[j] == s, j
+        if s != tri.STATUS_OK:
+            continue
+        worst["lin"] = max(worst["lin"], np.linalg.norm(Plin[j] - p0) / np.linalg.norm(p0))
+        worst["p"] = max(worst["p"], np.linalg.norm(P[j] - pr) / np.linalg.norm(pr))
+        assert tr[j]["accepted"].tolist() == [int(r.accepted) for r in otr], j
+        c0 = np.array([r.cost0 for r in otr])
+        worst["cost"] = max(worst["cost"], float(np.max(np.abs(tr[j]["cost0"] - c0) / np.maximum(c0, 1e-300))))
+        assert tr[j]["n_valid"].tolist() == [r.n_valid for r in otr]
+    print(name, worst, "status counts", np.bincount(st))
+    assert worst["lin"] <= 1e-9 and worst["p"] <= 1e-9 and worst["cost"] <= 1e-9
+
+
+@pytest.mark.parametrize("name", ["c1", "c4"])
+def test_fp32_refined_points_match_fp64(cvba, name):
+    p, off, kf, cam, uv = workload(name)
+    P64, _, st64, _ = run_gpu(cvba, p, off, kf, cam, uv, 0)
+    P32, _, st32, _ = run_gpu(cvba, p, off, kf, cam, uv, 1)
+    assert np.array_equal(st64, st32)
+    ok = st64 == 0
+    err = np.linalg.norm(P32[ok] - P64[ok], axis=1) / np.linalg.norm(P64[ok], axis=1)
+    print(name, "fp32 vs fp64 relative point error: max %.2e, median %.2e" % (err.max(), np.median(err)))
+    assert np.median(err) <= 1e-6 and np.quantile(err, 0.999) <= 1e-4
+
+
+def test_edge_cases(cvba):
+    p, off, kf, cam, uv = workload("c0")
+    # landmark 0: one observation; landmark 1: its first observation twice (rank 2);
+    # landmark 2: a bad camera and a bad keyframe index among its observations
+    a1, a2, a3 = off[1], off[2], off[3]
+    kf2 = np.concatenate([kf[:1], kf[a1:a1 + 1], kf[a1:a1 + 1], kf[a2:a3]])
+    cam2 = np.concatenate([cam[:1], cam[a1:a1 + 1], cam[a1:a1 + 1], cam[a2:a3]])
+    uv2 = np.concatenate([uv[:1], uv[a1:a1 + 1], uv[a1:a1 + 1], uv[a2:a3]])
+    off2 = np.array([0, 1, 3, 3 + (a3 - a2)], np.int32)
+    kf_bad, cam_bad = kf2.copy(), cam2.copy()
+    cam_bad[3], kf_bad[4] = p.C, -2
+    P, Plin, st, tr = run_gpu(cvba, p, off2, kf_bad, cam_bad, uv2, 0)
+    assert st.tolist()[:2] == [tri.STATUS_FEW_OBS, tri.STATUS_DEGENERATE]
+    assert np.all(np.isnan(P[:2]))
+    assert st[2] == 0 and np.all(tr[2]["n_bad_index"] == 2)
+    keep = np.setdiff1d(np.arange(3, off2[3]), [3, 4])
+    ref = tri.triangulate(p.rig.intr, p.rig.T_cb, p.poses_gt, np.array([0, keep.size]), kf2[keep], cam2[keep],
+                          uv2[keep], 10, p.huber_delta)
+    assert np.linalg.norm(P[2] - ref[0][1]) <= 1e-9 * np.linalg.norm(ref[0][1])
+    for bad in ([0, 2, 1, off2[3]], [1, 1, 3, off2[3]], [0, 1, 3, off2[3] + 1]):
+        with pytest.raises(cvba.CvbaError) as e:
+            run_gpu(cvba, p, off2, kf2, cam2, uv2, 0, lm_off=np.array(bad, np.int32))
+        assert e.value.status == 1
