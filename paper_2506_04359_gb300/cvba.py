@@ -94,9 +94,9 @@ def _load() -> C.CDLL:
         "cvba_profile_iteration": (i, [vp, C.POINTER(cvba_opts), i, C.POINTER(C.c_float), C.POINTER(C.c_int)]),
         "cvba_profile_names": (C.c_char_p, []),
         "cvba_evaluate_noalloc": (i, [i, i, i, i] + [vp] * 8 + [d, d, vp, vp]),
-        "cvba_pnp_solve": (i, [i, i, i, i, i] + [vp] * 9 + [C.POINTER(cvba_opts), vp, vp]),
+        "cvba_pnp_solve": (i, [i, i, i, i, i] + [vp] * 8 + [C.POINTER(cvba_opts), vp, vp]),
         "cvba_pnp_kernels_per_solve": (i, []),
-        "cvba_triangulate": (i, [i, i, i, i, i] + [vp] * 8 + [C.POINTER(cvba_opts)] + [vp] * 5),
+        "cvba_triangulate": (i, [i, i, i, i, i] + [vp] * 7 + [C.POINTER(cvba_opts)] + [vp] * 5),
         "cvba_set_tuning": (i, [vp, i, i]),
         "cvba_set_chol_mode": (i, [vp, i]),
         "cvba_batch_create": (i, [C.POINTER(vp), i, C.POINTER(vp)]),

@@ -103,3 +103,27 @@ def test_oracle_device_layout_definition():
     ref_oo = sorted(range(N), key=lambda n: (rank[lm[n]], kf[n], cam[n], n))
     assert oo.tolist() == ref_oo
     assert off[-1] == N and all(off[r + 1] - off[r] == int((lm == ref_lo[r]).sum()) for r in range(M))
+
+
+def _declared_arity():
+    """Parameter count of every function declared in include/*.h."""
+    out = {}
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if not f.endswith(".h"):
+            continue
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", f)).read(), flags=re.S)
+        for m in re.finditer(r"(cvba_\w+)\s*\(([^;{]*?)\)\s*;", src):
+            args = m.group(2).strip()
+            out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header(lib):
+    """Every function the ctypes binding declares takes as many arguments as the header says."""
+    from paper_2506_04359_gb300 import cvba
+    arity = _declared_arity()
+    for name, n in arity.items():
+        f = getattr(cvba.lib, name, None)
+        if f is None or f.argtypes is None:
+            continue
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
