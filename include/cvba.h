@@ -330,7 +330,18 @@ cvba_status cvba_pnp_solve(int dtype, int n_frames, int n_cams, int n_lm, int n_
                            const int32_t* lm, const void* uv, double* T_bw, const cvba_opts* opts,
                            cvba_lm_record* trace, void* stream);
 
-/* Kernel launches of one cvba_pnp_solve call (1). */
+/* Loop-closure relative pose (Sec. 2.3, relative pose estimation): for each query frame,
+ * T^bm = argmin sum_j sum_k rho(|pi(T^cb_k T^bm T^mw p^w_j) - o_{j,k}|^2) with the map pose
+ * T^mw (world to map frame) fixed: the landmarks are shifted into the map frame and the
+ * pose is solved exactly as by cvba_pnp_solve.  Arguments as cvba_pnp_solve, plus
+ * T_mw[n_frames*12] (DEVICE, FP64, [R | t] row-major, one per frame; NULL is
+ * CVBA_ERR_INVALID_ARG) and T_bm[n_frames*12] (in: initial relative poses, out: solved). */
+cvba_status cvba_relpose_solve(int dtype, int n_frames, int n_cams, int n_lm, int n_obs, const void* intr,
+                               const void* T_cb, const void* p_w, const int32_t* frame_off, const int32_t* cam,
+                               const int32_t* lm, const void* uv, const double* T_mw, double* T_bm,
+                               const cvba_opts* opts, cvba_lm_record* trace, void* stream);
+
+/* Kernel launches of one cvba_pnp_solve or cvba_relpose_solve call (1). */
 int cvba_pnp_kernels_per_solve(void);
 
 /* Multi-view landmark triangulation ------------------------------------------------------

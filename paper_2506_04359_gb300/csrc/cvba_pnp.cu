@@ -1,4 +1,6 @@
-// Motion-only bundle adjustment (multi-camera PnP), batched over independent frames.
+// Motion-only bundle adjustment (multi-camera PnP), batched over independent frames, and the
+// loop-closure relative pose that is the same problem with the landmarks shifted into a map
+// frame.
 //
 // cuVSLAM (arXiv 2506.04359) estimates the pose of every tracked frame from the 2D
 // observations of map landmarks (Sec. 2.2.1 stereo, Eq. PnP over the two cameras; Sec. 2.2.2
@@ -6,7 +8,10 @@
 //     T^bw = argmin  sum_j sum_k rho(|pi(T^cb_k T^bw p^w_j) - o_{j,k}|^2),
 // the landmarks held fixed.  The residual, Jacobian, Huber weights, Marquardt diagonal,
 // Nielsen damping update and accept rule are those of the bundle-adjustment solve, with a
-// single 6-DoF pose: the normal equations are one 6 x 6 system.
+// single 6-DoF pose: the normal equations are one 6 x 6 system.  The loop-closure step
+// (Sec. 2.3, relative pose estimation) solves T^bm = argmin sum rho(|pi(T^cb_k T^bm T^mw p^w_j)
+// - o_{j,k}|^2) for a fixed map pose T^mw per query frame: the landmarks are staged as
+// T^mw p^w_j (in FP64) and the rest is the PnP solve.
 //
 // Design: one CTA per frame runs all LM iterations of its frame (frames are independent,
 // so a batch is one launch with no grid-wide waits).  The frame's observations, with their
@@ -267,6 +272,7 @@ struct PnpArgs {
   const void* uv;
   double* T_bw;
   cvba_lm_record* trace;
+  const double* T_mw;       // per-frame fixed transform applied to the landmarks, or null
 };
 
 struct PnpShared {
@@ -276,6 +282,19 @@ struct PnpShared {
   double lam, nu, F1;
   int need_lin, nonpd, accept;
 };
+
+// The landmark position the frame's residuals use: p itself, or T^mw p (FP64) when the frame
+// has a fixed transform (the loop-closure query: landmarks shifted into the map frame).
+template <typename T>
+__device__ __forceinline__ void landmark_in_frame(const PnpArgs& a, int f, const T* p, T q[3]) {
+  if (!a.T_mw) {
+    q[0] = p[0], q[1] = p[1], q[2] = p[2];
+    return;
+  }
+  const double* M = a.T_mw + 12 * (size_t)f;
+  const double x = (double)p[0], y = (double)p[1], z = (double)p[2];
+  for (int r = 0; r < 3; ++r) q[r] = (T)(M[4 * r] * x + M[4 * r + 1] * y + M[4 * r + 2] * z + M[4 * r + 3]);
+}
 
 template <typename T, bool STAGED>
 __global__ void __launch_bounds__(kThreads) k_pnp(PnpArgs a) {
@@ -318,9 +337,11 @@ __global__ void __launch_bounds__(kThreads) k_pnp(PnpArgs a) {
       o.cam = ok ? c : -1;
       o.u = uv[2 * (size_t)(o0 + i)];
       o.v = uv[2 * (size_t)(o0 + i) + 1];
-      o.x = ok ? pw[3 * (size_t)j] : T(0);
-      o.y = ok ? pw[3 * (size_t)j + 1] : T(0);
-      o.z = ok ? pw[3 * (size_t)j + 2] : T(0);
+      T q[3] = {T(0), T(0), T(0)};
+      if (ok) landmark_in_frame(a, f, pw + 3 * (size_t)j, q);
+      o.x = q[0];
+      o.y = q[1];
+      o.z = q[2];
       so[i] = o;
       bad += ok ? 0 : 1;
     }
@@ -343,7 +364,9 @@ __global__ void __launch_bounds__(kThreads) k_pnp(PnpArgs a) {
     const int c = a.cam[o0 + i], j = a.lm[o0 + i];
     if (c < 0 || c >= a.n_cams || j < 0 || j >= a.n_lm) return -1;
     u = uv[2 * (size_t)(o0 + i)], v = uv[2 * (size_t)(o0 + i) + 1];
-    x = pw[3 * (size_t)j], y = pw[3 * (size_t)j + 1], z = pw[3 * (size_t)j + 2];
+    T q[3];
+    landmark_in_frame(a, f, pw + 3 * (size_t)j, q);
+    x = q[0], y = q[1], z = q[2];
     return c;
   };
 
@@ -462,10 +485,11 @@ cudaError_t launch(const PnpArgs& a, size_t smem, cudaStream_t s) {
 
 }  // namespace
 
-extern "C" cvba_status cvba_pnp_solve(int dtype, int n_frames, int n_cams, int n_lm, int n_obs, const void* intr,
-                                      const void* T_cb, const void* p_w, const int32_t* frame_off,
-                                      const int32_t* cam, const int32_t* lm, const void* uv, double* T_bw,
-                                      const cvba_opts* opts, cvba_lm_record* trace, void* stream) {
+namespace {
+cvba_status pnp_solve(int dtype, int n_frames, int n_cams, int n_lm, int n_obs, const void* intr, const void* T_cb,
+                      const void* p_w, const int32_t* frame_off, const int32_t* cam, const int32_t* lm,
+                      const void* uv, const double* T_mw, double* T_bw, const cvba_opts* opts,
+                      cvba_lm_record* trace, void* stream) {
   if ((dtype != 0 && dtype != 1) || n_frames < 1 || n_cams < 1 || n_cams > kCMax || n_lm < 1 || n_obs < 0 || !opts)
     return CVBA_ERR_INVALID_ARG;
   if (!intr || !T_cb || !p_w || !frame_off || !T_bw || (n_obs > 0 && (!cam || !lm || !uv)))
@@ -491,7 +515,7 @@ extern "C" cvba_status cvba_pnp_solve(int dtype, int n_frames, int n_cams, int n
   }
   if (opts->iters == 0) return CVBA_OK;
   PnpArgs a{n_frames, n_cams, n_lm, opts->iters, opts->lambda0, opts->huber_delta, opts->z_min,
-            intr, T_cb, p_w, frame_off, cam, lm, uv, T_bw, trace};
+            intr, T_cb, p_w, frame_off, cam, lm, uv, T_bw, trace, T_mw};
   const size_t per = dtype == 0 ? sizeof(ObsS<double>) : sizeof(ObsS<float>);
   const size_t smem = per * (size_t)max_n;
   cudaError_t e;
@@ -504,6 +528,25 @@ extern "C" cvba_status cvba_pnp_solve(int dtype, int n_frames, int n_cams, int n
     return e == cudaErrorMemoryAllocation ? CVBA_ERR_OOM : CVBA_ERR_CUDA;
   }
   return CVBA_OK;
+}
+
+}  // namespace
+
+extern "C" cvba_status cvba_pnp_solve(int dtype, int n_frames, int n_cams, int n_lm, int n_obs, const void* intr,
+                                      const void* T_cb, const void* p_w, const int32_t* frame_off,
+                                      const int32_t* cam, const int32_t* lm, const void* uv, double* T_bw,
+                                      const cvba_opts* opts, cvba_lm_record* trace, void* stream) {
+  return pnp_solve(dtype, n_frames, n_cams, n_lm, n_obs, intr, T_cb, p_w, frame_off, cam, lm, uv, nullptr, T_bw, opts,
+                   trace, stream);
+}
+
+extern "C" cvba_status cvba_relpose_solve(int dtype, int n_frames, int n_cams, int n_lm, int n_obs, const void* intr,
+                                          const void* T_cb, const void* p_w, const int32_t* frame_off,
+                                          const int32_t* cam, const int32_t* lm, const void* uv, const double* T_mw,
+                                          double* T_bm, const cvba_opts* opts, cvba_lm_record* trace, void* stream) {
+  if (!T_mw) return CVBA_ERR_INVALID_ARG;
+  return pnp_solve(dtype, n_frames, n_cams, n_lm, n_obs, intr, T_cb, p_w, frame_off, cam, lm, uv, T_mw, T_bm, opts,
+                   trace, stream);
 }
 
 extern "C" int cvba_pnp_kernels_per_solve(void) { return 1; }

@@ -96,6 +96,7 @@ def _load() -> C.CDLL:
         "cvba_evaluate_noalloc": (i, [i, i, i, i] + [vp] * 8 + [d, d, vp, vp]),
         "cvba_pnp_solve": (i, [i, i, i, i, i] + [vp] * 8 + [C.POINTER(cvba_opts), vp, vp]),
         "cvba_pnp_kernels_per_solve": (i, []),
+        "cvba_relpose_solve": (i, [i, i, i, i, i] + [vp] * 9 + [C.POINTER(cvba_opts), vp, vp]),
         "cvba_triangulate": (i, [i, i, i, i, i] + [vp] * 7 + [C.POINTER(cvba_opts)] + [vp] * 5),
         "cvba_set_tuning": (i, [vp, i, i]),
         "cvba_set_chol_mode": (i, [vp, i]),
@@ -336,6 +337,21 @@ def cvba_pnp_solve(dtype: int, n_frames: int, n_cams: int, n_lm: int, n_obs: int
                             C.c_void_p(trace) if trace else None, C.c_void_p(stream) if stream else None)
     if st != 0:
         raise CvbaError(st, "cvba_pnp_solve failed")
+
+
+def cvba_relpose_solve(dtype: int, n_frames: int, n_cams: int, n_lm: int, n_obs: int, intr: int, T_cb: int,
+                       p_w: int, frame_off: int, cam: int, lm: int, uv: int, T_mw: int, T_bm: int, iters: int,
+                       huber_delta: float = 1.0, lambda0: float = 1e-4, z_min: float = 1e-3, trace: int = 0,
+                       stream: int = 0) -> None:
+    """Loop-closure relative poses of a batch of query frames from device pointers (see
+    include/cvba.h); raises on a non-OK status."""
+    o = make_opts(iters, huber_delta, lambda0, z_min)
+    st = lib.cvba_relpose_solve(int(dtype), int(n_frames), int(n_cams), int(n_lm), int(n_obs), C.c_void_p(intr),
+                                C.c_void_p(T_cb), C.c_void_p(p_w), C.c_void_p(frame_off), C.c_void_p(cam),
+                                C.c_void_p(lm), C.c_void_p(uv), C.c_void_p(T_mw), C.c_void_p(T_bm), C.byref(o),
+                                C.c_void_p(trace) if trace else None, C.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise CvbaError(st, "cvba_relpose_solve failed")
 
 
 def cvba_triangulate(dtype: int, n_lm: int, n_kf: int, n_cams: int, n_obs: int, intr: int, T_cb: int, T_bw: int,

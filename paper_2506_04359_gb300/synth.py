@@ -494,3 +494,21 @@ def landmark_segments(obs_lm: np.ndarray, M: int):
     order = np.argsort(obs_lm, kind="stable").astype(np.int64)
     lm_off = np.concatenate([[0], np.cumsum(np.bincount(obs_lm, minlength=M))]).astype(np.int32)
     return order, lm_off
+
+
+def make_map_poses(batch: FrameBatch, seed: int = 0, sigma_r_deg: float = 20.0, sigma_t: float = 5.0):
+    """Loop-closure queries on a frame batch: a map keyframe pose T^mw per frame (world to map
+    frame: rotation N(0, sigma_r) about a random axis, translation N(0, sigma_t) per axis) and
+    the initial relative pose T^bm0 = T^bw0 (T^mw)^-1 from the frame's initial guess.
+    Returns (T_mw, T_bm0), each (F, 3, 4)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([11, seed])))
+    F = batch.F
+    R = Rotation.from_rotvec(rng.normal(0.0, np.deg2rad(sigma_r_deg), (F, 3))).as_matrix()
+    t = rng.normal(0.0, sigma_t, (F, 3))
+    T_mw = np.concatenate([R, t[:, :, None]], axis=2)
+    Rinv = np.transpose(R, (0, 2, 1))
+    tinv = -np.einsum("fij,fj->fi", Rinv, t)
+    T_bm0 = np.empty((F, 3, 4))
+    T_bm0[:, :, :3] = np.einsum("fij,fjk->fik", batch.poses0[:, :, :3], Rinv)
+    T_bm0[:, :, 3] = np.einsum("fij,fj->fi", batch.poses0[:, :, :3], tinv) + batch.poses0[:, :, 3]
+    return T_mw, T_bm0

