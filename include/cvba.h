@@ -352,7 +352,8 @@ int cvba_pnp_kernels_per_solve(void);
  * computes, for each landmark j:
  *   1. the linear point: with x = ((u - cx)/fx, (v - cy)/fy) and [R | t] = T^cb_k T^bw_i,
  *      the least-squares solution of x (R_3 p + t_3) = R_1 p + t_1, y (R_3 p + t_3) = R_2 p + t_2
- *      over its observations (inhomogeneous DLT), in FP64;
+ *      over its observations (inhomogeneous DLT), in FP64 (normal equations with one step of
+ *      iterative refinement);
  *   2. opts->iters LM iterations on the point alone: the window solve's step restricted to
  *      one landmark (Huber IRLS weights, Marquardt diagonal, Nielsen's update, accept iff the
  *      predicted reduction and the gain are positive).

@@ -3,6 +3,7 @@
 // camera; (landmark, keyframe) pairs; work tiles), device memory and the CUDA graph that
 // replays a whole LM solve.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -27,6 +28,7 @@ struct cvba_ctx {
   bool have_rig = false, have_poses = false, have_lms = false, have_layout = false;
 
   std::vector<int32_t> lm_order, lm_rank, obs_order, lm_off;
+  HostLayout hl;                                // host layout and its work arrays (reused)
   std::vector<int32_t> h_kf, h_cam, h_lm;       // caller's observations (for re-planning)
   std::vector<double> h_uv;
   int tune_lin_pairs = 0, tune_schur_lms = 0;   // 0: size-based defaults
@@ -164,81 +166,29 @@ cudaError_t upload_f32(cvba_ctx* c, float* dst, const double* src, size_t n) {
   return h2d(c, dst, h.data(), n * sizeof(float));
 }
 
-// Stable counting sort of idx by key[idx] in [0, n_keys).
-void counting_sort(std::vector<int32_t>& idx, const std::vector<int32_t>& key, int n_keys) {
-  std::vector<int64_t> cnt((size_t)n_keys + 1, 0);
-  for (int32_t i : idx) cnt[(size_t)key[i] + 1]++;
-  for (int k = 0; k < n_keys; ++k) cnt[k + 1] += cnt[k];
-  std::vector<int32_t> out(idx.size());
-  for (int32_t i : idx) out[cnt[key[i]]++] = i;
-  idx.swap(out);
-}
-
 cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, const int32_t* lm, const double* uv) {
   const int K = c->K, C = c->C, M = c->M, N = c->N;
-  // --- landmark order: by (first keyframe, last keyframe, caller index)
-  std::vector<int32_t> first(M, K), last(M, -1), count(M, 0);
-  for (int n = 0; n < N; ++n) {
-    const int j = lm[n];
-    first[j] = std::min(first[j], kf[n]);
-    last[j] = std::max(last[j], kf[n]);
-    count[j]++;
-  }
-  for (int j = 0; j < M; ++j)
-    if (count[j] < 2)
-      return fail(c, CVBA_ERR_INVALID_ARG, "landmark " + std::to_string(j) + " has fewer than 2 observations");
+  HostLayout& HL = c->hl;
+  // the previous layout's arrays are reused as this one's storage
+  HL.lm_order.swap(c->lm_order);
+  HL.lm_rank.swap(c->lm_rank);
+  HL.obs_order.swap(c->obs_order);
+  HL.lm_off.swap(c->lm_off);
   {
-    std::vector<int32_t> kf_count(K, 0);
-    for (int n = 0; n < N; ++n) kf_count[kf[n]]++;
-    for (int a = 0; a < K; ++a)
-      if (a != c->fixed_kf && kf_count[a] == 0)
-        return fail(c, CVBA_ERR_INVALID_ARG, "keyframe " + std::to_string(a) + " is free but has no observations");
+    std::string err;
+    if (!compute_host_layout(K, C, M, N, c->fixed_kf, kf, cam, lm, HL, err))
+      return fail(c, CVBA_ERR_INVALID_ARG, err);
   }
-  c->lm_order.resize(M);
-  for (int j = 0; j < M; ++j) c->lm_order[j] = j;
-  {
-    std::vector<int32_t> key_last(M), key_first(M);
-    for (int j = 0; j < M; ++j) {
-      key_last[j] = last[j];
-      key_first[j] = first[j];
-    }
-    counting_sort(c->lm_order, key_last, K);
-    counting_sort(c->lm_order, key_first, K);
-  }
-  c->lm_rank.assign(M, 0);
-  for (int i = 0; i < M; ++i) c->lm_rank[c->lm_order[i]] = i;
-  // --- observation order: by (internal landmark, keyframe, camera, caller index)
-  std::vector<int32_t> key_kc(N), key_lm(N);
-  for (int n = 0; n < N; ++n) {
-    key_kc[n] = kf[n] * C + cam[n];
-    key_lm[n] = c->lm_rank[lm[n]];
-  }
-  c->obs_order.resize(N);
-  for (int n = 0; n < N; ++n) c->obs_order[n] = n;
-  counting_sort(c->obs_order, key_kc, K * C);
-  counting_sort(c->obs_order, key_lm, M);
-  c->lm_off.assign(M + 1, 0);
-  for (int n = 0; n < N; ++n) c->lm_off[key_lm[n] + 1]++;
-  for (int j = 0; j < M; ++j) c->lm_off[j + 1] += c->lm_off[j];
-  // --- pairs (internal landmark, keyframe)
-  std::vector<int32_t> pair_kf, pair_lm, pair_obs, lm_pair(M + 1, 0), obs_cam(N);
-  pair_kf.reserve(N);
-  pair_lm.reserve(N);
-  pair_obs.reserve(N + 1);
-  for (int s = 0; s < N; ++s) {
-    const int n = c->obs_order[s];
-    const int jl = key_lm[n];
-    obs_cam[s] = cam[n];
-    if (s == 0 || jl != key_lm[c->obs_order[s - 1]] || kf[n] != kf[c->obs_order[s - 1]]) {
-      pair_kf.push_back(kf[n]);
-      pair_lm.push_back(jl);
-      pair_obs.push_back(s);
-      lm_pair[jl + 1]++;
-    }
-  }
+  c->lm_order.swap(HL.lm_order);
+  c->lm_rank.swap(HL.lm_rank);
+  c->obs_order.swap(HL.obs_order);
+  c->lm_off.swap(HL.lm_off);
+  std::vector<int32_t>& pair_kf = HL.pair_kf;
+  std::vector<int32_t>& pair_lm = HL.pair_lm;
+  std::vector<int32_t>& pair_obs = HL.pair_obs;
+  std::vector<int32_t>& lm_pair = HL.lm_pair;
+  std::vector<int32_t>& obs_cam = HL.obs_cam;
   const int P = (int)pair_kf.size();
-  pair_obs.push_back(N);
-  for (int j = 0; j < M; ++j) lm_pair[j + 1] += lm_pair[j];
   std::vector<int32_t> lm_blk(M + 1, 0);
   {
     int64_t acc = 0;
@@ -457,10 +407,12 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     float* uvf;
     CK(dalloc(c, &uvf, (size_t)N * 2), "alloc obs");
     std::vector<float> h(2 * (size_t)N);
-    for (int s = 0; s < N; ++s) {
-      h[2 * s] = (float)uv[2 * (size_t)c->obs_order[s]];
-      h[2 * s + 1] = (float)uv[2 * (size_t)c->obs_order[s] + 1];
-    }
+    parallel_for(N, host_threads(), [&](int64_t s0, int64_t s1, int) {
+      for (int64_t s = s0; s < s1; ++s) {
+        h[2 * s] = (float)uv[2 * (size_t)c->obs_order[s]];
+        h[2 * s + 1] = (float)uv[2 * (size_t)c->obs_order[s] + 1];
+      }
+    });
     CK(cudaMemcpy(uvf, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice), "upload obs");
     d.obs_uv = uvf;
     float* pl;
@@ -470,10 +422,12 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     double* uvd;
     CK(dalloc(c, &uvd, (size_t)N * 2), "alloc obs");
     std::vector<double> h(2 * (size_t)N);
-    for (int s = 0; s < N; ++s) {
-      h[2 * s] = uv[2 * (size_t)c->obs_order[s]];
-      h[2 * s + 1] = uv[2 * (size_t)c->obs_order[s] + 1];
-    }
+    parallel_for(N, host_threads(), [&](int64_t s0, int64_t s1, int) {
+      for (int64_t s = s0; s < s1; ++s) {
+        h[2 * s] = uv[2 * (size_t)c->obs_order[s]];
+        h[2 * s + 1] = uv[2 * (size_t)c->obs_order[s] + 1];
+      }
+    });
     CK(cudaMemcpy(uvd, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice), "upload obs");
     d.obs_uv = uvd;
     double* pl;
@@ -766,17 +720,41 @@ cvba_status cvba_set_observations(cvba_ctx* c, int n_obs, const int32_t* kf, con
     return fail(c, CVBA_ERR_STATE, "set_observations: set rig, poses and landmarks first");
   if (n_obs < 1 || !kf || !cam || !lm || !uv)
     return fail(c, CVBA_ERR_INVALID_ARG, "set_observations: need n_obs >= 1 and non-NULL arrays");
-  for (int n = 0; n < n_obs; ++n) {
-    if (kf[n] < 0 || kf[n] >= c->K || cam[n] < 0 || cam[n] >= c->C || lm[n] < 0 || lm[n] >= c->M)
-      return fail(c, CVBA_ERR_INDEX, "set_observations: index out of range at observation " + std::to_string(n));
+  {
+    // index and finiteness checks, in parallel; the first failing observation is reported
+    const int T = host_threads();
+    std::vector<int64_t> bad_idx((size_t)T, INT64_MAX), bad_uv((size_t)T, INT64_MAX);
+    parallel_for(n_obs, T, [&](int64_t n0, int64_t n1, int t) {
+      for (int64_t n = n0; n < n1; ++n) {
+        if (kf[n] < 0 || kf[n] >= c->K || cam[n] < 0 || cam[n] >= c->C || lm[n] < 0 || lm[n] >= c->M) {
+          bad_idx[t] = std::min(bad_idx[t], n);
+          break;
+        }
+      }
+      for (int64_t n = n0; n < n1; ++n)
+        if (!std::isfinite(uv[2 * n]) || !std::isfinite(uv[2 * n + 1])) {
+          bad_uv[t] = std::min(bad_uv[t], n);
+          break;
+        }
+    });
+    const int64_t bi = *std::min_element(bad_idx.begin(), bad_idx.end());
+    const int64_t bu = *std::min_element(bad_uv.begin(), bad_uv.end());
+    if (bi != INT64_MAX)
+      return fail(c, CVBA_ERR_INDEX, "set_observations: index out of range at observation " + std::to_string(bi));
+    if (bu != INT64_MAX) return fail(c, CVBA_ERR_NONFINITE, "set_observations: non-finite uv");
   }
-  if (!all_finite(uv, (size_t)n_obs * 2)) return fail(c, CVBA_ERR_NONFINITE, "set_observations: non-finite uv");
   DeviceGuard g(c->device);
   c->N = n_obs;
-  c->h_kf.assign(kf, kf + n_obs);
-  c->h_cam.assign(cam, cam + n_obs);
-  c->h_lm.assign(lm, lm + n_obs);
-  c->h_uv.assign(uv, uv + 2 * (size_t)n_obs);
+  c->h_kf.resize(n_obs);
+  c->h_cam.resize(n_obs);
+  c->h_lm.resize(n_obs);
+  c->h_uv.resize(2 * (size_t)n_obs);
+  parallel_for(n_obs, host_threads(), [&](int64_t n0, int64_t n1, int) {   // kept for re-planning
+    std::copy(kf + n0, kf + n1, c->h_kf.begin() + n0);
+    std::copy(cam + n0, cam + n1, c->h_cam.begin() + n0);
+    std::copy(lm + n0, lm + n1, c->h_lm.begin() + n0);
+    std::copy(uv + 2 * n0, uv + 2 * n1, c->h_uv.begin() + 2 * n0);
+  });
   return build_layout(c, kf, cam, lm, uv);
 }
 

@@ -5,6 +5,10 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <functional>
+#include <string>
+#include <vector>
+
 #include "../../include/cvba.h"
 
 namespace cvba {
@@ -25,6 +29,28 @@ constexpr int SCHUR_TILE_PAIRS = 256;   // pairs staged in shared memory per Sch
 constexpr int SCHUR_TILE_LMS = 128;
 constexpr int SPAN_MAX = 22;            // free keyframes in one Schur tile's window (<= 253 blocks)
 constexpr int kCholBlockedMinN = 320;   // RCS size from which the blocked factorisation runs (mode 0)
+
+// Host threads (cvba_layout.cpp): fn(t) for t in [0, n) on n threads; fn(begin, end, thread)
+// over [0, n) split in contiguous ranges over up to `threads` threads.
+int host_threads();
+void parallel_tasks(int n, const std::function<void(int)>& fn);
+void parallel_for(int64_t n, int threads, const std::function<void(int64_t, int64_t, int)>& fn);
+
+// Host part of a window's layout (cvba_layout.cpp): landmark order and rank, observation
+// slots (caller index per slot, camera per slot), landmark slot offsets, and the (landmark,
+// keyframe) pairs with their slot offsets and the landmarks' pair offsets.
+struct HostLayout {
+  std::vector<int32_t> lm_order, lm_rank, obs_order, lm_off, obs_cam;
+  std::vector<int32_t> pair_kf, pair_lm, pair_obs, lm_pair;
+  // work arrays, kept for the next layout of the same context
+  std::vector<int32_t> rec_lm;
+  std::vector<uint64_t> rec_key, grp;
+  std::vector<int64_t> goff;
+};
+// False (with a message) if a landmark has fewer than 2 observations or a free keyframe has
+// none.  Indices must be valid.
+bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t* kf, const int32_t* cam,
+                         const int32_t* lm, HostLayout& L, std::string& err);
 
 // Device-resident LM control block.  Written only by the solve's kernels.
 struct Ctrl {

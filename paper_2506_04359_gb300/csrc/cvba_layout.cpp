@@ -1,0 +1,228 @@
+// Host part of a window's device layout: the landmark order, the observation order and the
+// (landmark, keyframe) pairs, computed in parallel on the host cores.
+//
+// Definition (what the solve's kernels rely on, and what the layout tests check exactly):
+//  - internal landmarks are the caller's ordered by (first observing keyframe, last observing
+//    keyframe, caller index);
+//  - observation slots are ordered by (internal landmark, keyframe, camera, caller index);
+//  - pairs are the distinct (internal landmark, keyframe) runs of the slots, in slot order.
+//
+// Algorithm: every observation becomes a 64-bit key (keyframe * C + camera, caller index);
+// the keys are grouped by the caller's landmark index with a parallel two-level counting
+// sort (a radix pass into one landmark range per thread, then a counting sort inside each
+// range); each landmark's keys are sorted in place (insertion sort: groups hold a few to a
+// few tens of observations), which orders them by (keyframe, camera, caller index); the
+// landmarks are ordered by two stable counting sorts; and the slots and pairs are filled group
+// by group from the keys, with no gather of the caller's arrays.  Every step is
+// deterministic and independent of the thread count.
+#include <algorithm>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "cvba_internal.h"
+
+namespace cvba {
+
+int host_threads() {
+  const unsigned h = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(h == 0 ? 1u : h, 32u));
+}
+
+void parallel_tasks(int n, const std::function<void(int)>& fn) {
+  std::vector<std::thread> pool;
+  pool.reserve(n > 0 ? n - 1 : 0);
+  for (int t = 1; t < n; ++t) pool.emplace_back(fn, t);
+  if (n > 0) fn(0);
+  for (auto& th : pool) th.join();
+}
+
+void parallel_for(int64_t n, int threads, const std::function<void(int64_t, int64_t, int)>& fn) {
+  threads = (int)std::max<int64_t>(1, std::min<int64_t>(threads, n / 4096 + 1));
+  if (threads == 1) {
+    fn(0, n, 0);
+    return;
+  }
+  std::vector<std::thread> pool;
+  pool.reserve(threads - 1);
+  for (int t = 1; t < threads; ++t) pool.emplace_back(fn, n * t / threads, n * (t + 1) / threads, t);
+  fn(0, n / threads, 0);
+  for (auto& th : pool) th.join();
+}
+
+namespace {
+
+// Stable counting sort of idx by key[idx] in [0, n_keys).
+void counting_sort(std::vector<int32_t>& idx, const std::vector<int32_t>& key, int n_keys) {
+  std::vector<int64_t> cnt((size_t)n_keys + 1, 0);
+  for (int32_t i : idx) cnt[(size_t)key[i] + 1]++;
+  for (int k = 0; k < n_keys; ++k) cnt[k + 1] += cnt[k];
+  std::vector<int32_t> out(idx.size());
+  for (int32_t i : idx) out[cnt[key[i]]++] = i;
+  idx.swap(out);
+}
+
+}  // namespace
+
+bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t* kf, const int32_t* cam,
+                         const int32_t* lm, HostLayout& L, std::string& err) {
+  const int T = host_threads();
+  // work arrays live in L (kept between calls, so a window of the same size reuses them
+  // without new pages)
+  std::vector<int32_t>& rec_lm = L.rec_lm;
+  std::vector<uint64_t>& rec_key = L.rec_key;
+  std::vector<uint64_t>& grp = L.grp;
+  std::vector<int64_t>& goff = L.goff;
+  // Every observation as a 64-bit sort key: (keyframe * C + camera) above, caller index
+  // below, so ordering the keys orders by (keyframe, camera, caller index), and the
+  // keyframe and camera come back out of the key without a gather.
+  auto key_of = [&](int64_t n) { return ((uint64_t)(uint32_t)(kf[n] * C + cam[n]) << 32) | (uint32_t)n; };
+  // --- group by caller landmark: parallel radix pass (T landmark ranges), then a counting
+  //     sort inside each range
+  std::vector<int32_t> bucket_lo((size_t)T + 1);
+  for (int b = 0; b <= T; ++b) bucket_lo[b] = (int32_t)((int64_t)M * b / T);
+  std::vector<uint8_t> bucket_of((size_t)M);
+  for (int b = 0; b < T; ++b)
+    for (int j = bucket_lo[b]; j < bucket_lo[b + 1]; ++j) bucket_of[j] = (uint8_t)b;
+  std::vector<int64_t> cnt((size_t)T * T, 0);          // [chunk][bucket]
+  std::vector<int64_t> kf_cnt((size_t)T * K, 0);       // [chunk][keyframe]
+  parallel_tasks(T, [&](int c) {
+    const int64_t n0 = (int64_t)N * c / T, n1 = (int64_t)N * (c + 1) / T;
+    int64_t* cc = cnt.data() + (size_t)c * T;
+    int64_t* kc = kf_cnt.data() + (size_t)c * K;
+    for (int64_t n = n0; n < n1; ++n) {
+      cc[bucket_of[lm[n]]]++;
+      kc[kf[n]]++;
+    }
+  });
+  std::vector<int64_t> pos((size_t)T * T), boff((size_t)T + 1, 0);
+  {
+    int64_t acc = 0;
+    for (int b = 0; b < T; ++b) {
+      boff[b] = acc;
+      for (int c = 0; c < T; ++c) {
+        pos[(size_t)c * T + b] = acc;
+        acc += cnt[(size_t)c * T + b];
+      }
+    }
+    boff[T] = acc;
+  }
+  rec_lm.resize((size_t)N);
+  rec_key.resize((size_t)N);
+  parallel_tasks(T, [&](int c) {
+    const int64_t n0 = (int64_t)N * c / T, n1 = (int64_t)N * (c + 1) / T;
+    int64_t* p = pos.data() + (size_t)c * T;
+    for (int64_t n = n0; n < n1; ++n) {
+      const int b = bucket_of[lm[n]];
+      const int64_t q = p[b]++;
+      rec_lm[q] = lm[n];
+      rec_key[q] = key_of(n);
+    }
+  });
+  goff.resize((size_t)M + 1);
+  grp.resize((size_t)N);
+  parallel_tasks(T, [&](int b) {
+    const int lo = bucket_lo[b], hi = bucket_lo[b + 1];
+    std::vector<int64_t> fill((size_t)(hi - lo), 0);
+    for (int64_t q = boff[b]; q < boff[b + 1]; ++q) fill[rec_lm[q] - lo]++;
+    int64_t acc = boff[b];
+    for (int j = lo; j < hi; ++j) {       // goff[j] for the range's own landmarks only
+      const int64_t m = fill[j - lo];
+      goff[j] = acc;
+      fill[j - lo] = acc;
+      acc += m;
+    }
+    for (int64_t q = boff[b]; q < boff[b + 1]; ++q) grp[fill[rec_lm[q] - lo]++] = rec_key[q];
+  });
+  goff[M] = N;
+  // --- per landmark: sort its keys (stable order is kept by the caller index in the key),
+  //     first / last keyframe
+  std::vector<int32_t> first((size_t)M), last((size_t)M);
+  parallel_for(M, T, [&](int64_t j0, int64_t j1, int) {
+    for (int64_t j = j0; j < j1; ++j) {
+      uint64_t* g = grp.data() + goff[j];
+      const int64_t m = goff[j + 1] - goff[j];
+      for (int64_t a = 1; a < m; ++a) {
+        const uint64_t v = g[a];
+        int64_t b = a - 1;
+        while (b >= 0 && g[b] > v) {
+          g[b + 1] = g[b];
+          --b;
+        }
+        g[b + 1] = v;
+      }
+      first[j] = m > 0 ? (int32_t)((g[0] >> 32) / C) : K;
+      last[j] = m > 0 ? (int32_t)((g[m - 1] >> 32) / C) : -1;
+    }
+  });
+  for (int j = 0; j < M; ++j)
+    if (goff[j + 1] - goff[j] < 2) {
+      err = "landmark " + std::to_string(j) + " has fewer than 2 observations";
+      return false;
+    }
+  for (int a = 0; a < K; ++a) {
+    int64_t n_a = 0;
+    for (int c = 0; c < T; ++c) n_a += kf_cnt[(size_t)c * K + a];
+    if (a != fixed_kf && n_a == 0) {
+      err = "keyframe " + std::to_string(a) + " is free but has no observations";
+      return false;
+    }
+  }
+  // --- landmark order: (first, last, caller index)
+  L.lm_order.resize(M);
+  for (int j = 0; j < M; ++j) L.lm_order[j] = j;
+  counting_sort(L.lm_order, last, K);
+  counting_sort(L.lm_order, first, K);
+  L.lm_rank.resize(M);
+  for (int i = 0; i < M; ++i) L.lm_rank[L.lm_order[i]] = i;
+  // --- slots: groups in internal order; distinct keyframe runs are the pairs
+  L.lm_off.resize((size_t)M + 1);
+  L.lm_off[0] = 0;
+  for (int i = 0; i < M; ++i) L.lm_off[i + 1] = L.lm_off[i] + (int32_t)(goff[L.lm_order[i] + 1] - goff[L.lm_order[i]]);
+  std::vector<int32_t> npair((size_t)M, 0);
+  L.obs_order.resize(N);
+  L.obs_cam.resize(N);
+  parallel_for(M, T, [&](int64_t i0, int64_t i1, int) {
+    for (int64_t i = i0; i < i1; ++i) {
+      const int j = L.lm_order[i];
+      const uint64_t* g = grp.data() + goff[j];
+      const int64_t m = goff[j + 1] - goff[j];
+      const int64_t s0 = L.lm_off[i];
+      int np = 0;
+      for (int64_t a = 0; a < m; ++a) {
+        const uint32_t kc = (uint32_t)(g[a] >> 32);
+        L.obs_order[s0 + a] = (int32_t)(uint32_t)g[a];
+        L.obs_cam[s0 + a] = (int32_t)(kc % C);
+        if (a == 0 || kc / C != (uint32_t)(g[a - 1] >> 32) / C) ++np;
+      }
+      npair[i] = np;
+    }
+  });
+  L.lm_pair.resize((size_t)M + 1);
+  L.lm_pair[0] = 0;
+  for (int i = 0; i < M; ++i) L.lm_pair[i + 1] = L.lm_pair[i] + npair[i];
+  const int P = L.lm_pair[M];
+  L.pair_kf.resize(P);
+  L.pair_lm.resize(P);
+  L.pair_obs.resize((size_t)P + 1);
+  parallel_for(M, T, [&](int64_t i0, int64_t i1, int) {
+    for (int64_t i = i0; i < i1; ++i) {
+      const uint64_t* g = grp.data() + goff[L.lm_order[i]];
+      const int64_t m = L.lm_off[i + 1] - L.lm_off[i];
+      int q = L.lm_pair[i];
+      for (int64_t a = 0; a < m; ++a) {
+        const uint32_t k = (uint32_t)(g[a] >> 32) / C;
+        if (a == 0 || k != (uint32_t)(g[a - 1] >> 32) / C) {
+          L.pair_kf[q] = (int32_t)k;
+          L.pair_lm[q] = (int32_t)i;
+          L.pair_obs[q] = L.lm_off[i] + (int32_t)a;
+          ++q;
+        }
+      }
+    }
+  });
+  L.pair_obs[P] = N;
+  return true;
+}
+
+}  // namespace cvba

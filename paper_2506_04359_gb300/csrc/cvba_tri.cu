@@ -7,7 +7,9 @@
 //   1. linear triangulation: with x = ((u - cx)/fx, (v - cy)/fy) and [R | t] = T^cb_k T^bw_i,
 //      each observation gives x (R_3 p + t_3) = R_1 p + t_1 and y (R_3 p + t_3) = R_2 p + t_2;
 //      p0 solves these in the least-squares sense (inhomogeneous DLT), through the 3 x 3
-//      normal equations factored by Cholesky in FP64;
+//      normal equations factored by Cholesky in FP64 with one step of iterative refinement
+//      (corrected semi-normal equations, Bjorck, "Numerical Methods for Least Squares
+//      Problems", 1996, Sec. 2.2.3), which restores the accuracy of an orthogonal solve;
 //   2. opts->iters Levenberg-Marquardt iterations on p alone: the bundle-adjustment step
 //      restricted to one landmark (Huber IRLS weights, Marquardt diagonal, Nielsen's update,
 //      accept iff the predicted reduction and the gain are positive), a 3 x 3 system.
@@ -190,7 +192,35 @@ __global__ void __launch_bounds__(kThreads) k_triangulate(TriArgs a) {
         c[0] += A[0] * b, c[1] += A[1] * b, c[2] += A[2] * b;
       }
     }
-    if (!solve3(N, c, p, 1e-14)) st = 2;
+    if (!solve3(N, c, p, 1e-14)) {
+      st = 2;
+    } else {
+      // one step of iterative refinement on the linear system (corrected semi-normal
+      // equations): N dp = A^T (b - A p) recovers the accuracy the normal equations lose to
+      // the squared condition number
+      double c2[3] = {0, 0, 0}, dp[3];
+      for (int n = o0; n < o1; ++n) {
+        if (!valid_idx(n)) continue;
+        const double* P = pose_d + 12 * a.kf[n];
+        const double* Q = rig_d + 16 * a.cam[n];
+        double R[9], t[3];
+        for (int r = 0; r < 3; ++r) {
+          for (int k = 0; k < 3; ++k) R[3 * r + k] = Q[4 + 3 * r] * P[k] + Q[5 + 3 * r] * P[3 + k] + Q[6 + 3 * r] * P[6 + k];
+          t[r] = Q[4 + 3 * r] * P[9] + Q[5 + 3 * r] * P[10] + Q[6 + 3 * r] * P[11] + Q[13 + r];
+        }
+        const double x = ((double)uv[2 * (size_t)n] - Q[2]) / Q[0];
+        const double y = ((double)uv[2 * (size_t)n + 1] - Q[3]) / Q[1];
+        for (int row = 0; row < 2; ++row) {
+          const double s = row == 0 ? x : y;
+          double A[3];
+          for (int k = 0; k < 3; ++k) A[k] = s * R[6 + k] - R[3 * row + k];
+          const double res = (t[row] - s * t[2]) - (A[0] * p[0] + A[1] * p[1] + A[2] * p[2]);
+          c2[0] += A[0] * res, c2[1] += A[1] * res, c2[2] += A[2] * res;
+        }
+      }
+      if (solve3(N, c2, dp, 0.0))
+        for (int k = 0; k < 3; ++k) p[k] += dp[k];
+    }
   }
   if (a.p_lin) {
     for (int k = 0; k < 3; ++k) a.p_lin[3 * (size_t)j + k] = st == 0 ? p[k] : CUDART_NAN;
