@@ -344,6 +344,29 @@ cvba_status cvba_relpose_solve(int dtype, int n_frames, int n_cams, int n_lm, in
 /* Kernel launches of one cvba_pnp_solve or cvba_relpose_solve call (1). */
 int cvba_pnp_kernels_per_solve(void);
 
+/* Pose-graph optimisation ----------------------------------------------------------------
+ *
+ * Sec. 2.3, Eq. PGO: T_{1:N} = argmin sum_{(i,j) in E} |Log(D_ij^-1 T_i^-1 T_j)|^2 over the
+ * keyframe poses, from the pose deltas D_ij of odometry and loop-closure edges.  Readings:
+ * T_i are WORLD-FROM-BASE poses (T_i^-1 T_j is pose j seen from i, what D_ij measures; the
+ * inverse of the window solve's T^bw); Log is the SE(3) logarithm with the twist (rho, phi),
+ * translation first; the norm is plain (no weights, no robust kernel); pose `fixed` is held
+ * (gauge); left updates T_i <- Exp(xi_i) T_i; LM as the window solve (Marquardt diagonal
+ * floored at 1e-12 max, Nielsen's update, accept iff L > 0 and gain > 0, opts->iters
+ * iterations; huber_delta, z_min, reset_lambda and refine are ignored).  FP64 throughout; the
+ * normal equations are factored densely (6 (n_poses - 1) unknowns).
+ * DEVICE arrays: edges[n_edges*2] (int32 i, j: distinct, in range: CVBA_ERR_INDEX),
+ * deltas[n_edges*12] ([R | t] row-major), poses[n_poses*12] (in: initial, out: solved),
+ * trace (opts->iters records or NULL; n_valid = n_edges, rms_px = sqrt(2 F / n_edges)), and a
+ * caller-allocated workspace `work` (256-byte aligned) of at least
+ * cvba_pgo_workspace_bytes(n_poses, n_edges) bytes.  The edge list is read back to the host
+ * (every free pose needs an edge: CVBA_ERR_INVALID_ARG), so the call waits for the stream to
+ * reach it; the solve itself is then asynchronous on `stream`. */
+size_t cvba_pgo_workspace_bytes(int n_poses, int n_edges);
+cvba_status cvba_pgo_solve(int n_poses, int n_edges, const int32_t* edges, const double* deltas, double* poses,
+                           int fixed, const cvba_opts* opts, cvba_lm_record* trace, void* work, size_t work_bytes,
+                           void* stream);
+
 /* Multi-view landmark triangulation ------------------------------------------------------
  *
  * The new landmarks of a keyframe from their multi-view observations, the keyframe poses and

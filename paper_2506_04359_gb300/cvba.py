@@ -96,6 +96,8 @@ def _load() -> C.CDLL:
         "cvba_evaluate_noalloc": (i, [i, i, i, i] + [vp] * 8 + [d, d, vp, vp]),
         "cvba_pnp_solve": (i, [i, i, i, i, i] + [vp] * 8 + [C.POINTER(cvba_opts), vp, vp]),
         "cvba_pnp_kernels_per_solve": (i, []),
+        "cvba_pgo_workspace_bytes": (C.c_size_t, [i, i]),
+        "cvba_pgo_solve": (i, [i, i, vp, vp, vp, i, C.POINTER(cvba_opts), vp, vp, C.c_size_t, vp]),
         "cvba_relpose_solve": (i, [i, i, i, i, i] + [vp] * 9 + [C.POINTER(cvba_opts), vp, vp]),
         "cvba_triangulate": (i, [i, i, i, i, i] + [vp] * 7 + [C.POINTER(cvba_opts)] + [vp] * 5),
         "cvba_set_tuning": (i, [vp, i, i]),
@@ -352,6 +354,22 @@ def cvba_relpose_solve(dtype: int, n_frames: int, n_cams: int, n_lm: int, n_obs:
                                 C.c_void_p(trace) if trace else None, C.c_void_p(stream) if stream else None)
     if st != 0:
         raise CvbaError(st, "cvba_relpose_solve failed")
+
+
+def cvba_pgo_workspace_bytes(n_poses: int, n_edges: int) -> int:
+    return int(lib.cvba_pgo_workspace_bytes(int(n_poses), int(n_edges)))
+
+
+def cvba_pgo_solve(n_poses: int, n_edges: int, edges: int, deltas: int, poses: int, iters: int, fixed: int = 0,
+                   lambda0: float = 1e-4, trace: int = 0, work: int = 0, work_bytes: int = 0, stream: int = 0) -> None:
+    """Pose-graph optimisation from device pointers (see include/cvba.h); raises on a non-OK
+    status."""
+    o = make_opts(iters, 1.0, lambda0, 1e-3)
+    st = lib.cvba_pgo_solve(int(n_poses), int(n_edges), C.c_void_p(edges), C.c_void_p(deltas), C.c_void_p(poses),
+                            int(fixed), C.byref(o), C.c_void_p(trace) if trace else None, C.c_void_p(work),
+                            int(work_bytes), C.c_void_p(stream) if stream else None)
+    if st != 0:
+        raise CvbaError(st, "cvba_pgo_solve failed")
 
 
 def cvba_triangulate(dtype: int, n_lm: int, n_kf: int, n_cams: int, n_obs: int, intr: int, T_cb: int, T_bw: int,

@@ -512,3 +512,88 @@ def make_map_poses(batch: FrameBatch, seed: int = 0, sigma_r_deg: float = 20.0, 
     T_bm0[:, :, :3] = np.einsum("fij,fjk->fik", batch.poses0[:, :, :3], Rinv)
     T_bm0[:, :, 3] = np.einsum("fij,fj->fi", batch.poses0[:, :, :3], tinv) + batch.poses0[:, :, 3]
     return T_mw, T_bm0
+
+
+# ------------------------------------------------------------------------ pose graphs
+
+@dataclass
+class PoseGraph:
+    """A pose graph: world-from-base keyframe poses and relative-pose edges (i, j) with
+    measured deltas D_ij ~ T_i^-1 T_j.  Pose `fixed` is the gauge."""
+    name: str
+    seed: int
+    poses_gt: np.ndarray    # (K, 3, 4) world-from-base
+    poses0: np.ndarray      # (K, 3, 4) initial guess (dead reckoning along the odometry chain)
+    edges: np.ndarray       # (E, 2) int32
+    deltas: np.ndarray      # (E, 3, 4)
+    fixed: int = 0
+    iters: int = 10
+
+    @property
+    def K(self) -> int:
+        return int(self.poses0.shape[0])
+
+    @property
+    def E(self) -> int:
+        return int(self.edges.shape[0])
+
+
+def _compose(A, B):
+    out = np.empty((3, 4))
+    out[:, :3] = A[:, :3] @ B[:, :3]
+    out[:, 3] = A[:, :3] @ B[:, 3] + A[:, 3]
+    return out
+
+
+def _inverse(A):
+    out = np.empty((3, 4))
+    out[:, :3] = A[:, :3].T
+    out[:, 3] = -A[:, :3].T @ A[:, 3]
+    return out
+
+
+def _exp_noise(rng, sigma_t, sigma_r_deg):
+    """A small random transform: rotation Exp(phi), phi ~ N(0, sigma_r^2 I), translation N(0, sigma_t^2 I)."""
+    out = np.empty((3, 4))
+    out[:, :3] = Rotation.from_rotvec(rng.normal(0.0, np.deg2rad(sigma_r_deg), 3)).as_matrix()
+    out[:, 3] = rng.normal(0.0, sigma_t, 3)
+    return out
+
+
+PGO_CONFIGS = {
+    # two laps of a 10 m circle (with a slow vertical wave), odometry between consecutive
+    # keyframes, loop closures from every fifth keyframe of the first lap to the second
+    "pgo_loop": dict(K=200, laps=2, radius=10.0, odo=(0.02, 0.2), loop=(0.01, 0.1), loop_every=5, iters=10),
+    # a longer map: four laps, 600 keyframes
+    "pgo_large": dict(K=600, laps=4, radius=15.0, odo=(0.02, 0.2), loop=(0.01, 0.1), loop_every=5, iters=10),
+}
+
+
+def make_pose_graph(name: str = "pgo_loop", seed: int = 0, **overrides) -> PoseGraph:
+    """Draw order: odometry noise -> loop-closure noise (independent streams)."""
+    cfg = dict(PGO_CONFIGS[name])
+    cfg.update(overrides)
+    ss = np.random.SeedSequence([13, seed])
+    r_odo, r_loop = [np.random.Generator(np.random.PCG64(s)) for s in ss.spawn(2)]
+    K, laps, rad = cfg["K"], cfg["laps"], cfg["radius"]
+    th = 2.0 * np.pi * laps * np.arange(K) / K
+    poses = np.empty((K, 3, 4))
+    for k in range(K):
+        R = Rotation.from_euler("yxz", [th[k] + np.pi / 2, 0.05 * np.sin(3 * th[k]), 0.0]).as_matrix()
+        poses[k, :, :3] = R
+        poses[k, :, 3] = [rad * np.cos(th[k]), 0.3 * np.sin(th[k] / laps), rad * np.sin(th[k])]
+    edges, deltas = [], []
+    for k in range(K - 1):
+        edges.append((k, k + 1))
+        deltas.append(_compose(_compose(_inverse(poses[k]), poses[k + 1]), _exp_noise(r_odo, *cfg["odo"])))
+    per_lap = K // laps
+    for k in (range(0, K - per_lap, cfg["loop_every"]) if cfg["loop_every"] > 0 else []):
+        j = k + per_lap
+        edges.append((k, j))
+        deltas.append(_compose(_compose(_inverse(poses[k]), poses[j]), _exp_noise(r_loop, *cfg["loop"])))
+    poses0 = np.empty_like(poses)
+    poses0[0] = poses[0]
+    for k in range(K - 1):
+        poses0[k + 1] = _compose(poses0[k], deltas[k])
+    return PoseGraph(name=name, seed=seed, poses_gt=poses, poses0=poses0, edges=np.array(edges, np.int32),
+                     deltas=np.array(deltas), fixed=0, iters=cfg["iters"])
