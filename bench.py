@@ -11,7 +11,9 @@ validity gate |diff| <= 1e-3 px; vs_oracle (per-result error of the final state)
 (the FP64 path's throughput and error); roofline (dominant kernel) and roofline_all
 (every kernel with a work model); cpu_baseline (Oracle-S on the host cores, a bounded
 sample); e2e (through the public C API with host buffers); clocks; gpu_launches; and the
-extra sections c1 (20-keyframe stereo window) and batched (256 independent windows).
+extra sections c1 (20-keyframe stereo window), batched (256 independent windows) and
+small_solves (motion-only BA, loop-closure relative pose, triangulation, pose-graph
+optimisation).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c4] [--impl reference]
 """
@@ -259,6 +261,148 @@ def load_golden(name: str):
         return None
     with open(path) as f:
         return json.load(f)
+
+
+# ---------------------------------------------------------------- small solves (f1-f4)
+
+def small_solves(cvba, synth, dev, l2_flush, reps: int = 3):
+    """Motion-only BA (multi-camera PnP), the loop-closure relative pose, multi-view
+    triangulation and pose-graph optimisation: device time of each batched solve (CUDA
+    events, L2 flushed before each repetition), its throughput, the roofline of its single
+    kernel (algorithmic FLOPs per launch / time against the FP32 or FP64 rate), and its
+    error against the oracle on a sample."""
+    import torch
+    from oracle import ba, pnp, pgo, relpose
+    from oracle import triangulate as tri
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    t = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), dtype=dt, device=dev)
+    launches = 0
+
+    def timed(fn):
+        ms = []
+        for k in range(reps + 1):
+            l2_flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            stream.synchronize()
+            if k > 0:
+                ms.append(e0.elapsed_time(e1))
+        return float(np.median(ms))
+
+    def alu(flops, ms, fp32):
+        peak = FP32_NOMINAL_TFLOPS if fp32 else FP64_NOMINAL_GFLOPS / 1e3
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "algorithmic_flops": flops, "ms_per_launch": ms,
+                "peak_source": "FP32 152 x 128 x 2 x 2.07 GHz" if fp32 else "FP64 nominal 1.25 TFLOP/s"}
+
+    # --- f1: motion-only BA, 512 frames of the 32-camera ring (~1.5M observations)
+    b = synth.make_frames("pnp_multi")
+    res = {"workload": "512 frames of the 16-pair ring, 400 map points each (%d observations), %d LM iterations"
+                       % (b.N, b.iters)}
+    per_obs = 250.0            # FLOPs per observation and iteration: linearisation ~200, candidate ~50
+    for dtype, name in ((0, "fp64"), (1, "fp32")):
+        ft = torch.float64 if dtype == 0 else torch.float32
+        intr, tcb, pw, uv = t(b.rig.intr, ft), t(b.rig.T_cb.reshape(-1, 12), ft), t(b.lm, ft), t(b.obs_uv, ft)
+        off, cm, lmi = t(b.frame_off, torch.int32), t(b.obs_cam, torch.int32), t(b.obs_lm, torch.int32)
+        p0 = t(b.poses0.reshape(b.F, 12))
+        poses = p0.clone()
+
+        def run():
+            poses.copy_(p0)
+            cvba.cvba_pnp_solve(dtype, b.F, b.C, b.M, b.N, intr.data_ptr(), tcb.data_ptr(), pw.data_ptr(),
+                                off.data_ptr(), cm.data_ptr(), lmi.data_ptr(), uv.data_ptr(), poses.data_ptr(),
+                                b.iters, b.huber_delta, stream=stream.cuda_stream)
+        ms = timed(run)
+        launches += (reps + 1) * 2
+        P = poses.cpu().numpy().reshape(b.F, 3, 4)
+        sample = list(range(0, b.F, 32))
+        t0 = time.perf_counter()
+        ref = pnp.solve_frames(b, frames=sample)
+        t_or = time.perf_counter() - t0
+        err = pose_errors(P[sample], np.stack([T for T, _ in ref]))
+        res[name] = {"value": b.F / (ms * 1e-3), "unit": "frames/s", "gobs_per_s": b.N * b.iters / (ms * 1e-3) / 1e9,
+                     "ms": ms, "roofline": alu(per_obs * b.N * b.iters, ms, dtype == 1),
+                     "vs_oracle": dict(err, frames=len(sample)), "oracle_frames_per_s": len(sample) / t_or}
+    out["pnp"] = res
+
+    # --- f2: loop-closure relative pose, the same frames with a map pose each
+    T_mw, T_bm0 = synth.make_map_poses(b, seed=1)
+    intr, tcb, pw, uv = t(b.rig.intr), t(b.rig.T_cb.reshape(-1, 12)), t(b.lm), t(b.obs_uv)
+    off, cm, lmi = t(b.frame_off, torch.int32), t(b.obs_cam, torch.int32), t(b.obs_lm, torch.int32)
+    mw, bm0 = t(T_mw.reshape(b.F, 12)), t(T_bm0.reshape(b.F, 12))
+    bm = bm0.clone()
+
+    def run_rel():
+        bm.copy_(bm0)
+        cvba.cvba_relpose_solve(0, b.F, b.C, b.M, b.N, intr.data_ptr(), tcb.data_ptr(), pw.data_ptr(), off.data_ptr(),
+                                cm.data_ptr(), lmi.data_ptr(), uv.data_ptr(), mw.data_ptr(), bm.data_ptr(), b.iters,
+                                b.huber_delta, stream=stream.cuda_stream)
+    ms = timed(run_rel)
+    launches += (reps + 1) * 2
+    sample = list(range(0, b.F, 32))
+    ref = relpose.solve_queries(b, T_mw, T_bm0, frames=sample)
+    Tbm = bm.cpu().numpy().reshape(b.F, 3, 4)
+    out["relpose"] = {"workload": "the same 512 frames, each against a map pose", "precision": "fp64",
+                      "value": b.F / (ms * 1e-3), "unit": "queries/s", "ms": ms,
+                      "roofline": alu(per_obs * b.N * b.iters, ms, False),
+                      "vs_oracle": dict(pose_errors(Tbm[sample], np.stack([T for T, _ in ref])), frames=len(sample))}
+
+    # --- f4: triangulation of the 200k landmarks of the 100-keyframe window (3.75M observations)
+    q = synth.make_problem("c4", outlier_frac=0.0)
+    order, loff = synth.landmark_segments(q.obs_lm, q.M)
+    kf_s, cam_s, uv_s = q.obs_kf[order], q.obs_cam[order], q.obs_uv[order]
+    res = {"workload": "200,000 landmarks of the 100-keyframe ring window from 3.75M observations, 10 LM iterations"}
+    per_obs_t = 2 * 40.0 + 10 * 180.0    # linear step with refinement + per refinement iteration
+    for dtype, name in ((0, "fp64"), (1, "fp32")):
+        ft = torch.float64 if dtype == 0 else torch.float32
+        intr, tcb, uvt = t(q.rig.intr, ft), t(q.rig.T_cb.reshape(-1, 12), ft), t(uv_s, ft)
+        poses = t(q.poses_gt.reshape(q.K, 12))
+        offt, kft, camt = t(loff, torch.int32), t(kf_s, torch.int32), t(cam_s, torch.int32)
+        pwo = torch.zeros(q.M * 3, dtype=torch.float64, device=dev)
+
+        def run_tri():
+            cvba.cvba_triangulate(dtype, q.M, q.K, q.C, q.N, intr.data_ptr(), tcb.data_ptr(), poses.data_ptr(),
+                                  offt.data_ptr(), kft.data_ptr(), camt.data_ptr(), uvt.data_ptr(), pwo.data_ptr(), 10,
+                                  q.huber_delta, stream=stream.cuda_stream)
+        ms = timed(run_tri)
+        launches += reps + 1
+        Pt = pwo.cpu().numpy().reshape(q.M, 3)
+        sel = list(range(0, q.M, 400))
+        ref = tri.triangulate(q.rig.intr, q.rig.T_cb, q.poses_gt, loff, kf_s, cam_s, uv_s, 10, q.huber_delta,
+                              landmarks=sel)
+        rel = [np.linalg.norm(Pt[j] - r[1]) / np.linalg.norm(r[1]) for j, r in zip(sel, ref) if r[2] == 0]
+        res[name] = {"value": q.M / (ms * 1e-3), "unit": "landmarks/s", "ms": ms,
+                     "gobs_per_s": q.N * 10 / (ms * 1e-3) / 1e9,
+                     "roofline": alu(per_obs_t * q.N, ms, dtype == 1),
+                     "vs_oracle": {"max_rel_point_error": float(max(rel)), "landmarks": len(rel)}}
+    out["triangulation"] = res
+
+    # --- f3: pose-graph optimisation, the 600-keyframe four-lap map
+    g = synth.make_pose_graph("pgo_large")
+    ed, de, p0 = t(g.edges, torch.int32), t(g.deltas.reshape(g.E, 12)), t(g.poses0.reshape(g.K, 12))
+    pos = p0.clone()
+    need = cvba.cvba_pgo_workspace_bytes(g.K, g.E)
+    work = torch.empty(need, dtype=torch.uint8, device=dev)
+
+    def run_pgo():
+        pos.copy_(p0)
+        cvba.cvba_pgo_solve(g.K, g.E, ed.data_ptr(), de.data_ptr(), pos.data_ptr(), g.iters, g.fixed,
+                            work=work.data_ptr(), work_bytes=need, stream=stream.cuda_stream)
+    ms = timed(run_pgo)
+    n = 6 * (g.K - 1)
+    npan = (n + 31) // 32
+    launches += (reps + 1) * (2 + g.iters * (8 + 3 * npan))
+    Po, _, _, otr = pgo.lm_solve(g.poses0, g.edges, g.deltas, g.iters, fixed=g.fixed)
+    out["pgo"] = {"workload": "600 keyframes on four laps, %d edges, %d LM iterations" % (g.E, g.iters),
+                  "precision": "fp64", "value": g.iters / (ms * 1e-3), "unit": "LM iters/s", "ms": ms,
+                  "roofline": alu(g.iters * (n ** 3 / 3.0 + 4.0 * n * n), ms, False),
+                  "vs_oracle": pose_errors(pos.cpu().numpy().reshape(g.K, 3, 4), Po)}
+    out["gpu_launches"] = launches
+    return out
 
 
 # ------------------------------------------------------------------------- reference
@@ -544,6 +688,11 @@ def run_ours(args):
         for c in bctx:
             c.close()
 
+    small = None
+    if not args.no_extras:
+        small = small_solves(cvba, synth, dev, l2_flush)
+        extra_launches += small.pop("gpu_launches")
+
     golden_rms = gold["final_rms_px"] if gold else None
     if rank == 0:
         line = {
@@ -566,6 +715,7 @@ def run_ours(args):
             "clocks": cs.summary(),
             "c1": c1,
             "batched": batched,
+            "small_solves": small,
             "gpu_launches": launches,
             "gpu_launches_extras": extra_launches,
             "wall_s_timed": wall,

@@ -235,8 +235,13 @@ cvba_status cvba_batch_launch_count(cvba_batch* batch, const cvba_opts* opts, in
 /* Tuning.  cvba_set_tuning re-plans one window's tiles (pairs per linearisation tile,
  * landmarks per Schur tile; 0 = size-based default) keeping its state.
  * cvba_batch_set_chol_cluster picks the CTAs per window of the batched Cholesky (2, 4, 8
- * or 16).  cvba_batch_autotune times short batched solves over a grid of these sizes,
- * keeps the fastest, restores every window's state and reports the choice. */
+ * or 16).  cvba_batch_autotune times short batched solves over a grid of these sizes
+ * (pairs per linearisation tile 32, 64, 128, 256; landmarks per Schur tile 8 to 128; cluster
+ * sizes 2 to 16), keeps the fastest, restores every window's state and reports the choice.
+ * Choices are cached per device (name, SM count, compute capability) and batch
+ * configuration (precision and every window's keyframe, camera, landmark, observation and
+ * pair counts) for the life of the process: a later call for the same configuration applies
+ * the cached choice without timing.  cvba_batch_autotune_clear empties the cache. */
 cvba_status cvba_set_tuning(cvba_ctx* ctx, int lin_tile_pairs, int schur_tile_landmarks);
 /* How the reduced camera system is factored (re-plans the window, keeping its state):
  * 0 = by size (the default): systems of 320 rows or more take the blocked form, smaller ones
@@ -255,6 +260,7 @@ cvba_status cvba_set_chol_mode(cvba_ctx* ctx, int mode);
 cvba_status cvba_batch_set_chol_cluster(cvba_batch* batch, int cluster_size);
 cvba_status cvba_batch_autotune(cvba_batch* batch, const cvba_opts* opts, int* lin_tile_pairs,
                                 int* schur_tile_landmarks, int* cluster_size);
+void cvba_batch_autotune_clear(void);
 
 /* Differentiable cost -------------------------------------------------------------------
  *

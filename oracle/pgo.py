@@ -17,7 +17,9 @@ with J_r(xi) = J_l(-xi) the right Jacobian of SE(3) (J_l: oracle/ba.py's closed 
 Barfoot 2017, Eq. 7.86) and Ad(T) = [[R, [t]x R], [0, R]].  The LM iteration is the window
 solve's: H = sum J^T J, g = sum J^T r (dense over the free poses), D = diag(H) floored at
 1e-12 max, (H + lambda D) delta = -g by Cholesky, F = 1/2 sum |r|^2, Nielsen's damping
-update, accept iff L > 0 and gain > 0, exactly `iters` iterations.
+update, accept iff L > 0 and gain > 0, exactly `iters` iterations.  Iteration records count
+every edge as valid and as an inlier (there is no robust kernel) and report the RMS edge
+residual sqrt(2 F / |E|).
 """
 from __future__ import annotations
 
@@ -144,7 +146,7 @@ def lm_solve(poses0, edges, deltas, iters: int, lam0: float = 1e-4, fixed: int =
             ok = False
         if not ok:
             trace.append(ba.IterRecord(F, float("nan"), lam, float("nan"), float("nan"), float("nan"), False,
-                                       len(edges), 0, 0.0, True, None))
+                                       len(edges), len(edges), math.sqrt(2.0 * F / len(edges)), True, None))
             lam, nu = ba.nielsen_update(lam, nu, float("nan"), False)
             continue
         L = 0.5 * float(delta @ (lam * D * delta - g))
@@ -152,8 +154,8 @@ def lm_solve(poses0, edges, deltas, iters: int, lam0: float = 1e-4, fixed: int =
         F1 = cost(P1, edges, deltas)
         gain = (F - F1) / L if L != 0.0 else float("nan")
         acc = ba.accept_step(L, F1, gain)
-        trace.append(ba.IterRecord(F, F1, lam, gain, L, float(np.linalg.norm(delta)), acc, len(edges), 0, 0.0,
-                                   False, delta))
+        trace.append(ba.IterRecord(F, F1, lam, gain, L, float(np.linalg.norm(delta)), acc, len(edges), len(edges),
+                                   math.sqrt(2.0 * F / len(edges)), False, delta))
         lam, nu = ba.nielsen_update(lam, nu, gain, acc)
         if acc:
             poses, lin = P1, None

@@ -4,6 +4,8 @@
 // replays a whole LM solve.
 #include <algorithm>
 #include <climits>
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -446,6 +448,31 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   // each otherwise, so that the buffers keep their places in the arena)
   d.npw = (n_c + 31) / 32 * 32;
   d.chol_blocked = c->chol_mode == 2 || (c->chol_mode == 0 && n_c >= kCholBlockedMinN) ? 1 : 0;
+  {
+    // factor envelope: first free keyframe coupled with each free keyframe (through a shared
+    // landmark), then per panel the last row whose first coupled column falls in or before it
+    std::vector<int> first_blk(K, INT32_MAX);
+    for (int j = 0; j < M; ++j) {
+      int lo = INT32_MAX;
+      for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q)
+        if (kf_pb[pair_kf[q]] >= 0) lo = std::min(lo, kf_pb[pair_kf[q]]);
+      for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
+        const int pb = kf_pb[pair_kf[q]];
+        if (pb >= 0) first_blk[pb] = std::min(first_blk[pb], lo);
+      }
+    }
+    const int npan = d.npw / 32;
+    for (int pn = 0; pn < kMaxPanels; ++pn) d.panel_end[pn] = 0;
+    for (int pn = 0; pn < npan; ++pn) {
+      const int end_col = 32 * pn + 31;
+      int last = 32 * (pn + 1) - 1;             // the panel itself
+      for (int i = 32 * (pn + 1); i < n_c; ++i) {
+        const int f = first_blk[i / 6] == INT32_MAX ? i : 6 * first_blk[i / 6];
+        if (f <= end_col) last = i;
+      }
+      d.panel_end[pn] = (int16_t)std::min(d.npw, (last + 1 + 31) / 32 * 32);
+    }
+  }
   CK(dalloc(c, &d.Lw, d.chol_blocked ? (size_t)d.npw * d.npw : 1), "alloc");
   CK(dalloc(c, &d.Ldinv, d.chol_blocked ? (size_t)d.npw : 1), "alloc");
   CK(dalloc(c, &d.yw, d.chol_blocked ? (size_t)d.npw : 1), "alloc");
@@ -1343,13 +1370,65 @@ cvba_status cvba_batch_launch_count(cvba_batch* b, const cvba_opts* o, int* n) {
   return CVBA_OK;
 }
 
+namespace {
+// Autotune results, per device and batch configuration: the device (name, SM count, compute
+// capability) and every window's shape (keyframes, cameras, landmarks, observations, pairs)
+// with the precision.  Process-wide; guarded by a mutex.
+struct TuneKey {
+  std::string device;
+  std::vector<int64_t> shape;
+  bool operator<(const TuneKey& o) const { return device != o.device ? device < o.device : shape < o.shape; }
+};
+struct TuneValue {
+  int lin, schur, cs;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneValue> g_tune_cache;
+
+TuneKey tune_key(const cvba_batch* b) {
+  TuneKey k;
+  cudaDeviceProp prop{};
+  if (cudaGetDeviceProperties(&prop, b->device) != cudaSuccess) cudaGetLastError();
+  k.device = std::string(prop.name) + "/" + std::to_string(prop.multiProcessorCount) + "/" +
+             std::to_string(prop.major) + "." + std::to_string(prop.minor);
+  k.shape.push_back(b->mixed);
+  for (const cvba_ctx* c : b->ctxs)
+    for (int64_t v : {(int64_t)c->K, (int64_t)c->C, (int64_t)c->M, (int64_t)c->N, (int64_t)c->P}) k.shape.push_back(v);
+  return k;
+}
+}  // namespace
+
+extern "C" void cvba_batch_autotune_clear(void) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache.clear();
+}
+
 // Autotuner: times a 2-iteration batched solve for each candidate (lin tile pairs, Schur
 // tile landmarks), then each Cholesky cluster size, keeps the fastest and restores every
-// window's state.  Writes the chosen values (any pointer may be NULL).
+// window's state.  The choice is cached per device and batch configuration: a later call
+// with the same configuration applies it without timing.  Writes the chosen values (any
+// pointer may be NULL).
 cvba_status cvba_batch_autotune(cvba_batch* b, const cvba_opts* o, int* best_lin, int* best_schur, int* best_cs) {
   if (!b || !o) return CVBA_ERR_INVALID_ARG;
   DeviceGuard g(b->device);
   const int n = (int)b->ctxs.size();
+  const TuneKey key = tune_key(b);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      const TuneValue v = it->second;
+      for (int w = 0; w < n; ++w) {
+        const cvba_status st = cvba_set_tuning(b->ctxs[w], v.lin, v.schur);
+        if (st != CVBA_OK) return bfail(b, st, b->ctxs[w]->err);
+      }
+      b->chol_cs = v.cs;
+      if (best_lin) *best_lin = v.lin;
+      if (best_schur) *best_schur = v.schur;
+      if (best_cs) *best_cs = v.cs;
+      return CVBA_OK;
+    }
+  }
   std::vector<std::vector<double>> P(n), Lm(n);
   std::vector<double> lam(n), nu(n);
   for (int w = 0; w < n; ++w) {
@@ -1387,8 +1466,8 @@ cvba_status cvba_batch_autotune(cvba_batch* b, const cvba_opts* o, int* best_lin
     cvba_status st2 = restore();
     return st != CVBA_OK ? st : st2;
   };
-  const int lin_c[] = {64, 128, 256};
-  const int sch_c[] = {16, 32, 64, 128};
+  const int lin_c[] = {32, 64, 128, 256};
+  const int sch_c[] = {8, 16, 32, 64, 128};
   float best = 1e30f;
   int bl = 0, bs = 0, bc = b->chol_cs;
   cvba_status st = CVBA_OK;
@@ -1410,7 +1489,7 @@ cvba_status cvba_batch_autotune(cvba_batch* b, const cvba_opts* o, int* best_lin
     for (int w = 0; w < n && st == CVBA_OK; ++w) st = cvba_set_tuning(b->ctxs[w], bl, bs);
   if (st == CVBA_OK) {
     best = 1e30f;
-    for (int cs : {2, 4, 8}) {
+    for (int cs : {2, 4, 8, 16}) {
       b->chol_cs = cs;
       float ms = 0.f;
       st = timed(&ms);
@@ -1425,6 +1504,10 @@ cvba_status cvba_batch_autotune(cvba_batch* b, const cvba_opts* o, int* best_lin
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != CVBA_OK) return bfail(b, st, "autotune failed: " + b->ctxs[0]->err);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = TuneValue{bl, bs, bc};
+  }
   if (best_lin) *best_lin = bl;
   if (best_schur) *best_schur = bs;
   if (best_cs) *best_cs = bc;

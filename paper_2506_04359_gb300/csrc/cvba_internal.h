@@ -29,6 +29,7 @@ constexpr int SCHUR_TILE_PAIRS = 256;   // pairs staged in shared memory per Sch
 constexpr int SCHUR_TILE_LMS = 128;
 constexpr int SPAN_MAX = 22;            // free keyframes in one Schur tile's window (<= 253 blocks)
 constexpr int kCholBlockedMinN = 320;   // RCS size from which the blocked factorisation runs (mode 0)
+constexpr int kMaxPanels = (6 * (K_MAX - 1) + 31) / 32;   // 32-column panels of the largest system
 
 // Host threads (cvba_layout.cpp): fn(t) for t in [0, n) on n threads; fn(begin, end, thread)
 // over [0, n) split in contiguous ranges over up to `threads` threads.
@@ -134,6 +135,10 @@ struct Dev {
   double* Ldinv;
   double* yw;
   int npw, chol_blocked;
+  // envelope of the factor by 32-column panel: rows [32 (p + 1), panel_end[p]) are the only
+  // rows below panel p with nonzeros in its columns (first coupled keyframe of each row's
+  // keyframe at or before the panel; the Cholesky fill stays inside this envelope)
+  int16_t panel_end[kMaxPanels];
   // per-tile partials and the lists of tiles covering each keyframe / RCS block
   double* kf_part;            // per lin tile: kf_n * 12 (g_p 6, diag Hpp 6); mixed: float (hi, lo) pairs
   const int32_t* lin_kf_off;  // per lin tile, per keyframe of its range: start in lin_kf_idx (kf_n + 1)

@@ -1004,8 +1004,8 @@ constexpr size_t kGroupSlotBytes = K_MAX;
 size_t group_smem_bytes(int max_span, bool mixed) {
   const size_t t = mixed ? 4 : 8;
   const int ch = mixed ? 16 : 8;
-  // the staging area also holds the groups' partials for the combine: <= 256 items x 18 x 8 B
-  const size_t stage = std::max((size_t)ch * max_span * kStage * t, (size_t)SCHUR_THREADS * 18 * 8);
+  // the staging area also holds the groups' partials for the combine: <= 256 items x 36 x 8 B
+  const size_t stage = std::max((size_t)ch * max_span * kStage * t, (size_t)SCHUR_THREADS * 36 * 8);
   return sizeof(double) * 64 + t * (size_t)SCHUR_TILE_LMS * 9 + kGroupLpBytes + group_rot_bytes(t) +
          kGroupSlotBytes + stage;
 }
@@ -1072,24 +1072,26 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
     const int pbk = tile.k_lo + e / 9, a = pbk < d.fixed_kf ? pbk : pbk + 1;
     s_rot[e] = pose[a * POSE_STRIDE + e % 9];
   }
+  // One work item per window block (a >= b) and landmark group: a thread accumulates a whole
+  // 6 x 6 block (off-diagonal: -sum Y_a W_b^T, 108 FMAs per landmark from 12 vector loads;
+  // diagonal: the staged lower entries of U - Y_a W_a^T and Y_a g_l), so every tile takes
+  // one pass over its landmarks (nblk <= 253 <= the CTA's threads).
   const int nblk = span * (span + 1) / 2;            // <= 253 (span <= SPAN_MAX)
-  const int n_half = 2 * nblk;
-  const int G = max(1, min(CH, SCHUR_THREADS / n_half));
-  const int n_items = n_half * G;                    // > SCHUR_THREADS only when G == 1
+  const int G = max(1, min(CH, SCHUR_THREADS / nblk));
+  const int n_items = nblk * G;
   Out* out = reinterpret_cast<Out*>(d.schur_part) + tile.part_off;
-  for (int it0 = 0; it0 < n_items; it0 += SCHUR_THREADS) {   // passes
-    const int t = it0 + threadIdx.x;
+  {
+    const int t = threadIdx.x;
     const bool working = t < n_items;
-    const int hb = t % n_half, g = t / n_half;
-    const int blk = hb >> 1, h = hb & 1;
+    const int blk = t % nblk, g = t / nblk;
     int ba = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
     while (ba * (ba + 1) / 2 > blk) --ba;
     while ((ba + 1) * (ba + 2) / 2 <= blk) ++ba;
     const int bb = blk - ba * (ba + 1) / 2;
     const bool diag = ba == bb;
-    T acc[18], cmp[18];
+    T acc[36], cmp[36];
 #pragma unroll
-    for (int k = 0; k < 18; ++k) {
+    for (int k = 0; k < 36; ++k) {
       acc[k] = 0;
       cmp[k] = 0;
     }
@@ -1149,32 +1151,25 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
       }
       __syncthreads();
       if (working) {
-        T part[18];
+        T part[36];
 #pragma unroll
-        for (int k = 0; k < 18; ++k) part[k] = 0;
+        for (int k = 0; k < 36; ++k) part[k] = 0;
         for (int lr = g; lr < nc; lr += G) {
           const T* base = s_stg + lr * span * kStage;
           if (diag) {
             const T* st = base + ba * kStage;
-            if (h == 0) {
 #pragma unroll
-              for (int k = 0; k < 6; ++k) part[k] += st[48 + k];
+            for (int k = 0; k < 21; ++k) part[k] += st[48 + k];
 #pragma unroll
-              for (int k = 0; k < 3; ++k) part[6 + k] += st[69 + k];
-            } else {
-#pragma unroll
-              for (int k = 0; k < 15; ++k) part[k] += st[48 + 6 + k];
-#pragma unroll
-              for (int k = 0; k < 3; ++k) part[15 + k] += st[72 + k];
-            }
+            for (int r = 0; r < 6; ++r) part[21 + r] += st[69 + r];
           } else {
-            const T* Ya = base + ba * kStage + 12 * h;
+            const T* Ya = base + ba * kStage;
             const T* Wb = base + bb * kStage + 24;
             T w[18];
 #pragma unroll
             for (int c = 0; c < 6; ++c) load_row3<T>(Wb + 4 * c, w[3 * c], w[3 * c + 1], w[3 * c + 2]);
 #pragma unroll
-            for (int r = 0; r < 3; ++r) {
+            for (int r = 0; r < 6; ++r) {
               T y0, y1, y2;
               load_row3<T>(Ya + 4 * r, y0, y1, y2);
 #pragma unroll
@@ -1184,7 +1179,7 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
           }
         }
 #pragma unroll
-        for (int k = 0; k < 18; ++k) {
+        for (int k = 0; k < 36; ++k) {
           if (kKahan) {                              // acc - cmp is the running sum
             const T yk = part[k] - cmp[k];
             const T sm = acc[k] + yk;
@@ -1196,39 +1191,44 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
         }
       }
     }
+    // this item's block in the partial layout [half block][18]: off-diagonal rows 0-2 then
+    // rows 3-5 (6 columns each); diagonal: lower entries of rows 0-2 (6) and b rows 0-2, then
+    // lower entries of rows 3-5 (15) and b rows 3-5
+    auto slot = [&](int k) {
+      if (!diag) return k;                           // 36 values, both halves contiguous
+      if (k < 6) return k;
+      if (k < 21) return 18 + (k - 6);
+      return k < 24 ? 6 + (k - 21) : 18 + 15 + (k - 24);
+    };
+    const int nv = diag ? 27 : 36;
+    auto as_out = [&](int k) {
+      if constexpr (sizeof(T) == 4)
+        return DF{(float)acc[k], -(float)cmp[k]};
+      else
+        return (double)acc[k];
+    };
     if (G == 1) {
-      // one group: each item writes its 18 values, contiguous ([half block][18])
       if (working) {
 #pragma unroll
-        for (int k = 0; k < 18; ++k) {
-          if constexpr (sizeof(T) == 4)
-            out[hb * 18 + k] = DF{(float)acc[k], -(float)cmp[k]};
-          else
-            out[hb * 18 + k] = (double)acc[k];
-        }
+        for (int k = 0; k < 36; ++k)
+          if (k < nv) out[2 * blk * 18 + slot(k)] = as_out(k);
       }
     } else {
-      // several groups (single pass): every group's values in the staging area
-      // [group][half block][18], combined by a fixed pairwise tree (group g takes g + step),
-      // then group 0's written as it is
+      // several groups: every group's block in the staging area [group][block][36], combined
+      // by a fixed pairwise tree (group g takes g + step), then group 0's written
       Out* s_out = reinterpret_cast<Out*>(s_stg);
       __syncthreads();
       if (working) {
 #pragma unroll
-        for (int k = 0; k < 18; ++k) {
-          if constexpr (sizeof(T) == 4)
-            s_out[(g * n_half + hb) * 18 + k] = DF{(float)acc[k], -(float)cmp[k]};
-          else
-            s_out[(g * n_half + hb) * 18 + k] = (double)acc[k];
-        }
+        for (int k = 0; k < 36; ++k) s_out[(g * nblk + blk) * 36 + k] = as_out(k);
       }
       for (int step = 1; step < G; step *= 2) {
         __syncthreads();
         if (working && g % (2 * step) == 0 && g + step < G) {
-          Out* dst = s_out + (g * n_half + hb) * 18;
-          const Out* src = s_out + ((g + step) * n_half + hb) * 18;
+          Out* dst = s_out + (g * nblk + blk) * 36;
+          const Out* src = s_out + ((g + step) * nblk + blk) * 36;
 #pragma unroll
-          for (int k = 0; k < 18; ++k) {
+          for (int k = 0; k < 36; ++k) {
             if constexpr (sizeof(T) == 4)
               dst[k] = df_add(dst[k], src[k]);
             else
@@ -1237,17 +1237,20 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
         }
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < n_half * 18; e += blockDim.x) out[e] = s_out[e];
+      if (working && g == 0) {
+        const Out* src = s_out + blk * 36;
+        for (int k = 0; k < nv; ++k) out[2 * blk * 18 + slot(k)] = src[k];
+      }
     }
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS, sizeof(T) == 4 ? 2 : 1) k_schur_group(Dev d) { pdl_enter();
+__global__ void __launch_bounds__(SCHUR_THREADS, 1) k_schur_group(Dev d) { pdl_enter();
   k_schur_group_body<T>(d, blockIdx.x);
 }
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(SCHUR_THREADS, 1)
     k_schur_group_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
@@ -2380,7 +2383,7 @@ __global__ void __launch_bounds__(256) k_blk_syrk(Dev d, int p, int part) { pdl_
   Ctrl* ctrl = d.ctrl;
   if (ctrl->nonpd) return;
   const int npw = d.npw, o = p * kPW, o2 = o + kPW, tid = threadIdx.x;
-  const int blk = blockIdx.x, nt = (npw - o2) / 16;
+  const int blk = blockIdx.x, nt = (d.panel_end[p] - o2) / 16;   // tiles inside the envelope
   int ti, tj;
   if (part == 0) {
     ti = blk < nt ? blk : blk - nt + 1;
@@ -2910,8 +2913,9 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, con
       bool pending = false;
       for (int p = 0; p < npan; ++p) {
         if ((e = launch_ex(k_blk_panel, dim3(1), dim3(256), 0, s, 0, d, p)) != cudaSuccess) return e;
-        const int below = d.npw - kPW * (p + 1);
-        if (below == 0) break;
+        // rows below the panel inside the factor's envelope (the rest has zeros in its columns)
+        const int below = d.panel_end[p] - kPW * (p + 1);
+        if (below <= 0) continue;
         if ((e = launch_ex(k_blk_trsm, dim3(below / 8), dim3(256), 0, s, 0, d, p)) != cudaSuccess) return e;
         const int nt16 = below / 16, n_rest = (nt16 - 2) * (nt16 - 1) / 2;
         if (n_rest > 0 && overlap) {
@@ -2959,7 +2963,9 @@ int solve_kernels_per_iteration(const Dev& d) {
   int blocked = 0;
   if (chol_cluster_size(d.n_c) > 0 && d.chol_blocked) {
     blocked = 1 + d.npw / kPW;                     // load, panel factors
-    for (int below = d.npw - kPW; below > 0; below -= kPW) {
+    for (int p = 0; p < d.npw / kPW; ++p) {
+      const int below = d.panel_end[p] - kPW * (p + 1);
+      if (below <= 0) continue;
       const int nt16 = below / 16;
       blocked += 2 + ((nt16 - 2) * (nt16 - 1) / 2 > 0 ? 1 : 0);   // solve, update (two parts)
     }

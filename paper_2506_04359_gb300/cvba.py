@@ -110,6 +110,7 @@ def _load() -> C.CDLL:
         "cvba_batch_launch_count": (i, [vp, C.POINTER(cvba_opts), C.POINTER(C.c_int)]),
         "cvba_batch_set_chol_cluster": (i, [vp, i]),
         "cvba_batch_autotune": (i, [vp, C.POINTER(cvba_opts)] + [C.POINTER(C.c_int)] * 3),
+        "cvba_batch_autotune_clear": (None, []),
         "cvba_cost_workspace_bytes": (C.c_size_t, [i, i, i]),
         "cvba_cost_forward": (i, [i, i, i, i, i] + [vp] * 9 + [d, d, vp, vp, C.c_size_t, vp]),
         "cvba_cost_backward": (i, [i, i, i, i, i] + [vp] * 9 + [d, d, vp, vp, vp, vp, vp, vp, C.c_size_t, vp]),

@@ -1,5 +1,7 @@
 """Batched windows (one launch per LM phase for all windows, one Cholesky cluster per
 window, one graph per solve) against per-window solves and the oracle."""
+import time
+
 import numpy as np
 import pytest
 
@@ -61,8 +63,15 @@ def test_batch_mixed_rms_and_autotune(cvba, windows):
     iters = 10
     ctxs = [cvba.Context("mixed").load(p) for p in windows]
     batch = cvba.Batch(ctxs)
+    cvba.lib.cvba_batch_autotune_clear()
+    t0 = time.perf_counter()
     best = batch.cvba_batch_autotune(iters=2)
-    assert best["lin_tile_pairs"] in (64, 128, 256) and best["chol_cluster"] in (2, 4, 8)
+    t_tune = time.perf_counter() - t0
+    assert best["lin_tile_pairs"] in (32, 64, 128, 256) and best["chol_cluster"] in (2, 4, 8, 16)
+    assert best["schur_tile_landmarks"] in (8, 16, 32, 64, 128)
+    t0 = time.perf_counter()
+    again = batch.cvba_batch_autotune(iters=2)        # cached for this device and configuration
+    assert again == best and time.perf_counter() - t0 < 0.5 * t_tune
     for c, p in zip(ctxs, windows):                     # autotune restored the initial state
         np.testing.assert_array_equal(c.cvba_get_poses(), p.poses0)
     batch.cvba_batch_solve(iters)
