@@ -37,6 +37,7 @@ struct cvba_ctx {
   int chol_mode = 0;                            // 0 size-based, 1 cluster, 2 blocked
   std::vector<LinTile> lin_tiles;
   std::vector<SchurTile> schur_tiles, direct_tiles;
+  std::vector<int32_t> act_blk;                 // RCS blocks the reduction writes
 
   struct Slot {
     void* p;
@@ -335,6 +336,26 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
         for (int b = t.k_lo; b <= a; ++b) blk_tiles[fill[a * (a + 1) / 2 + b]++] = ti;
     }
   }
+  // blocks of the reduced camera system that any tile touches (and every diagonal block):
+  // the only ones the reduction writes; the others stay zero from the layout on
+  {
+    std::vector<char> act(n_blk, 0);
+    for (int i = 0; i < n_blk; ++i) act[i] = blk_tiles_off[i + 1] > blk_tiles_off[i];
+    for (int a = 0; a < nfb; ++a) act[a * (a + 1) / 2 + a] = 1;
+    std::vector<int> fb;
+    for (const auto& t : c->direct_tiles)
+      for (int j = t.l0; j < t.l1; ++j) {
+        fb.clear();
+        for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q)
+          if (kf_pb[pair_kf[q]] >= 0) fb.push_back(kf_pb[pair_kf[q]]);
+        for (int x : fb)
+          for (int y : fb)
+            if (x >= y) act[x * (x + 1) / 2 + y] = 1;
+      }
+    c->act_blk.clear();
+    for (int i = 0; i < n_blk; ++i)
+      if (act[i]) c->act_blk.push_back(i);
+  }
 
   // --- device buffers
   c->have_layout = false;
@@ -508,6 +529,11 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     d.blk_tiles_off = bto;
     d.blk_tiles = bt;
     d.n_blk = n_blk;
+    int32_t* ab;
+    CK(dalloc(c, &ab, c->act_blk.size()), "alloc");
+    CK(cudaMemcpy(ab, c->act_blk.data(), c->act_blk.size() * 4, cudaMemcpyHostToDevice), "upload");
+    d.act_blk = ab;
+    d.n_act = (int)c->act_blk.size();
   }
   CK(dalloc(c, &d.lin_part, (size_t)d.n_lin_tiles * 4), "alloc");
   CK(dalloc(c, &d.bs_part, (size_t)d.n_lin_tiles * 8), "alloc");
@@ -516,6 +542,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   CK(dalloc(c, &c->d_lm_order, M), "alloc");
   CK(cudaMemcpy(c->d_lm_order, c->lm_order.data(), (size_t)M * 4, cudaMemcpyHostToDevice), "upload");
   d.trace = c->d_trace;
+  CK(cudaMemset(d.S, 0, sizeof(double) * std::max<size_t>((size_t)n_c * n_c, 1)), "memset");
   CK(cudaMemset(d.dc, 0, sizeof(double) * std::max(n_c, 1)), "memset");
   CK(cudaMemset(d.dp, 0, sizeof(double) * (size_t)M * 3), "memset");
   CK(cudaMemset(d.lin_part, 0, sizeof(double) * (size_t)d.n_lin_tiles * 4), "memset");
@@ -1235,7 +1262,7 @@ cvba_status batch_prepare(cvba_batch* b, const cvba_opts* o) {
     for (int t = 0; t < d.n_lin_tiles; ++t) lin.push_back(make_int2(w, t));
     for (int a = 0; a < d.K; ++a) kf.push_back(make_int2(w, a));
     for (int t = 0; t < d.n_schur_tiles; ++t) sch.push_back(make_int2(w, t));
-    for (int t = 0; t < d.n_blk; ++t) blk.push_back(make_int2(w, t));
+    for (int32_t t : b->ctxs[w]->act_blk) blk.push_back(make_int2(w, t));
     for (int t = 0; t < d.n_direct_tiles; ++t) dir.push_back(make_int2(w, t));
     win.push_back(make_int2(w, 0));
   }

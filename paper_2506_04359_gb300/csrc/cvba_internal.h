@@ -149,6 +149,8 @@ struct Dev {
   const int32_t* blk_tiles_off;  // n_blk + 1, blocks (a >= b) of free keyframes
   const int32_t* blk_tiles;      // Schur tiles (non-direct) covering each block
   int n_blk;
+  const int32_t* act_blk;        // blocks some tile touches, plus the diagonal ones
+  int n_act;
   // partial sums per linearisation tile
   double* lin_part;           // n_lin_tiles * 4: cost, sum r^2, n_valid, n_inlier
   double* bs_part;            // n_lin_tiles * 4: candidate cost, pred_l, step2_l, unused

@@ -990,6 +990,11 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct_b(const Dev* __r
 // combined in a fixed order and the window is written as the tile's partial, summed over
 // tiles by k_rcs_reduce.  About 100 registers on the mixed path: two CTAs per SM.
 constexpr int kStage = 76;         // per (landmark, block): Y[6][4] W[6][4] Dg[21] bY[6] pad
+// Threads of a group Schur CTA: 512 on the mixed path, so that the 2 x 253 half-block items of
+// the widest window (22 keyframes) fit in one pass over its landmarks (each pass re-stages
+// them); 256 on the FP64 path, whose items need more registers.
+template <typename T>
+__host__ __device__ constexpr int group_threads() { return sizeof(T) == 4 ? 512 : 256; }
 template <typename T>
 struct GroupChunk {
   static constexpr int value = sizeof(T) == 4 ? 16 : 8;
@@ -1004,8 +1009,9 @@ constexpr size_t kGroupSlotBytes = K_MAX;
 size_t group_smem_bytes(int max_span, bool mixed) {
   const size_t t = mixed ? 4 : 8;
   const int ch = mixed ? 16 : 8;
-  // the staging area also holds the groups' partials for the combine: <= 256 items x 36 x 8 B
-  const size_t stage = std::max((size_t)ch * max_span * kStage * t, (size_t)SCHUR_THREADS * 36 * 8);
+  // the staging area also holds the groups' partials for the combine: <= 256 items x 18 x 8 B
+  const size_t stage = std::max((size_t)ch * max_span * kStage * t,
+                                (size_t)(mixed ? group_threads<float>() : group_threads<double>()) * 18 * 8);
   return sizeof(double) * 64 + t * (size_t)SCHUR_TILE_LMS * 9 + kGroupLpBytes + group_rot_bytes(t) +
          kGroupSlotBytes + stage;
 }
@@ -1072,26 +1078,25 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
     const int pbk = tile.k_lo + e / 9, a = pbk < d.fixed_kf ? pbk : pbk + 1;
     s_rot[e] = pose[a * POSE_STRIDE + e % 9];
   }
-  // One work item per window block (a >= b) and landmark group: a thread accumulates a whole
-  // 6 x 6 block (off-diagonal: -sum Y_a W_b^T, 108 FMAs per landmark from 12 vector loads;
-  // diagonal: the staged lower entries of U - Y_a W_a^T and Y_a g_l), so every tile takes
-  // one pass over its landmarks (nblk <= 253 <= the CTA's threads).
   const int nblk = span * (span + 1) / 2;            // <= 253 (span <= SPAN_MAX)
-  const int G = max(1, min(CH, SCHUR_THREADS / nblk));
-  const int n_items = nblk * G;
+  const int n_half = 2 * nblk;
+  constexpr int NT = group_threads<T>();
+  const int G = max(1, min(CH, NT / n_half));
+  const int n_items = n_half * G;                    // > NT only when G == 1
   Out* out = reinterpret_cast<Out*>(d.schur_part) + tile.part_off;
-  {
-    const int t = threadIdx.x;
+  for (int it0 = 0; it0 < n_items; it0 += NT) {     // passes
+    const int t = it0 + threadIdx.x;
     const bool working = t < n_items;
-    const int blk = t % nblk, g = t / nblk;
+    const int hb = t % n_half, g = t / n_half;
+    const int blk = hb >> 1, h = hb & 1;
     int ba = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
     while (ba * (ba + 1) / 2 > blk) --ba;
     while ((ba + 1) * (ba + 2) / 2 <= blk) ++ba;
     const int bb = blk - ba * (ba + 1) / 2;
     const bool diag = ba == bb;
-    T acc[36], cmp[36];
+    T acc[18], cmp[18];
 #pragma unroll
-    for (int k = 0; k < 36; ++k) {
+    for (int k = 0; k < 18; ++k) {
       acc[k] = 0;
       cmp[k] = 0;
     }
@@ -1151,25 +1156,32 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
       }
       __syncthreads();
       if (working) {
-        T part[36];
+        T part[18];
 #pragma unroll
-        for (int k = 0; k < 36; ++k) part[k] = 0;
+        for (int k = 0; k < 18; ++k) part[k] = 0;
         for (int lr = g; lr < nc; lr += G) {
           const T* base = s_stg + lr * span * kStage;
           if (diag) {
             const T* st = base + ba * kStage;
+            if (h == 0) {
 #pragma unroll
-            for (int k = 0; k < 21; ++k) part[k] += st[48 + k];
+              for (int k = 0; k < 6; ++k) part[k] += st[48 + k];
 #pragma unroll
-            for (int r = 0; r < 6; ++r) part[21 + r] += st[69 + r];
+              for (int k = 0; k < 3; ++k) part[6 + k] += st[69 + k];
+            } else {
+#pragma unroll
+              for (int k = 0; k < 15; ++k) part[k] += st[48 + 6 + k];
+#pragma unroll
+              for (int k = 0; k < 3; ++k) part[15 + k] += st[72 + k];
+            }
           } else {
-            const T* Ya = base + ba * kStage;
+            const T* Ya = base + ba * kStage + 12 * h;
             const T* Wb = base + bb * kStage + 24;
             T w[18];
 #pragma unroll
             for (int c = 0; c < 6; ++c) load_row3<T>(Wb + 4 * c, w[3 * c], w[3 * c + 1], w[3 * c + 2]);
 #pragma unroll
-            for (int r = 0; r < 6; ++r) {
+            for (int r = 0; r < 3; ++r) {
               T y0, y1, y2;
               load_row3<T>(Ya + 4 * r, y0, y1, y2);
 #pragma unroll
@@ -1179,7 +1191,7 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
           }
         }
 #pragma unroll
-        for (int k = 0; k < 36; ++k) {
+        for (int k = 0; k < 18; ++k) {
           if (kKahan) {                              // acc - cmp is the running sum
             const T yk = part[k] - cmp[k];
             const T sm = acc[k] + yk;
@@ -1191,44 +1203,39 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
         }
       }
     }
-    // this item's block in the partial layout [half block][18]: off-diagonal rows 0-2 then
-    // rows 3-5 (6 columns each); diagonal: lower entries of rows 0-2 (6) and b rows 0-2, then
-    // lower entries of rows 3-5 (15) and b rows 3-5
-    auto slot = [&](int k) {
-      if (!diag) return k;                           // 36 values, both halves contiguous
-      if (k < 6) return k;
-      if (k < 21) return 18 + (k - 6);
-      return k < 24 ? 6 + (k - 21) : 18 + 15 + (k - 24);
-    };
-    const int nv = diag ? 27 : 36;
-    auto as_out = [&](int k) {
-      if constexpr (sizeof(T) == 4)
-        return DF{(float)acc[k], -(float)cmp[k]};
-      else
-        return (double)acc[k];
-    };
     if (G == 1) {
+      // one group: each item writes its 18 values, contiguous ([half block][18])
       if (working) {
 #pragma unroll
-        for (int k = 0; k < 36; ++k)
-          if (k < nv) out[2 * blk * 18 + slot(k)] = as_out(k);
+        for (int k = 0; k < 18; ++k) {
+          if constexpr (sizeof(T) == 4)
+            out[hb * 18 + k] = DF{(float)acc[k], -(float)cmp[k]};
+          else
+            out[hb * 18 + k] = (double)acc[k];
+        }
       }
     } else {
-      // several groups: every group's block in the staging area [group][block][36], combined
-      // by a fixed pairwise tree (group g takes g + step), then group 0's written
+      // several groups (single pass): every group's values in the staging area
+      // [group][half block][18], combined by a fixed pairwise tree (group g takes g + step),
+      // then group 0's written as it is
       Out* s_out = reinterpret_cast<Out*>(s_stg);
       __syncthreads();
       if (working) {
 #pragma unroll
-        for (int k = 0; k < 36; ++k) s_out[(g * nblk + blk) * 36 + k] = as_out(k);
+        for (int k = 0; k < 18; ++k) {
+          if constexpr (sizeof(T) == 4)
+            s_out[(g * n_half + hb) * 18 + k] = DF{(float)acc[k], -(float)cmp[k]};
+          else
+            s_out[(g * n_half + hb) * 18 + k] = (double)acc[k];
+        }
       }
       for (int step = 1; step < G; step *= 2) {
         __syncthreads();
         if (working && g % (2 * step) == 0 && g + step < G) {
-          Out* dst = s_out + (g * nblk + blk) * 36;
-          const Out* src = s_out + ((g + step) * nblk + blk) * 36;
+          Out* dst = s_out + (g * n_half + hb) * 18;
+          const Out* src = s_out + ((g + step) * n_half + hb) * 18;
 #pragma unroll
-          for (int k = 0; k < 36; ++k) {
+          for (int k = 0; k < 18; ++k) {
             if constexpr (sizeof(T) == 4)
               dst[k] = df_add(dst[k], src[k]);
             else
@@ -1237,20 +1244,17 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
         }
       }
       __syncthreads();
-      if (working && g == 0) {
-        const Out* src = s_out + blk * 36;
-        for (int k = 0; k < nv; ++k) out[2 * blk * 18 + slot(k)] = src[k];
-      }
+      for (int e = threadIdx.x; e < n_half * 18; e += blockDim.x) out[e] = s_out[e];
     }
   }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS, 1) k_schur_group(Dev d) { pdl_enter();
+__global__ void __launch_bounds__(group_threads<T>(), 1) k_schur_group(Dev d) { pdl_enter();
   k_schur_group_body<T>(d, blockIdx.x);
 }
 template <typename T>
-__global__ void __launch_bounds__(SCHUR_THREADS, 1)
+__global__ void __launch_bounds__(group_threads<T>(), 1)
     k_schur_group_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
@@ -1359,7 +1363,7 @@ __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) { pdl_enter(); k_rcs_reduce_body(d, blockIdx.x); }
+__global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) { pdl_enter(); k_rcs_reduce_body(d, d.act_blk[blockIdx.x]); }
 __global__ void __launch_bounds__(256) k_rcs_reduce_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
@@ -2881,13 +2885,13 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, con
   if (d.n_schur_tiles > 0) {
     const size_t sm = group_smem_bytes(d.max_span, d.mixed != 0);
     if (d.mixed)
-      { if ((e = launch_ex(k_schur_group<float>, dim3(d.n_schur_tiles), dim3(SCHUR_THREADS), sm, s, 0, d)) != cudaSuccess) return e; }
+      { if ((e = launch_ex(k_schur_group<float>, dim3(d.n_schur_tiles), dim3(group_threads<float>()), sm, s, 0, d)) != cudaSuccess) return e; }
     else
-      { if ((e = launch_ex(k_schur_group<double>, dim3(d.n_schur_tiles), dim3(SCHUR_THREADS), sm, s, 0, d)) != cudaSuccess) return e; }
+      { if ((e = launch_ex(k_schur_group<double>, dim3(d.n_schur_tiles), dim3(group_threads<double>()), sm, s, 0, d)) != cudaSuccess) return e; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if ((e = mark(3)) != cudaSuccess) return e;
-  { if ((e = launch_ex(k_rcs_reduce, dim3(d.n_blk), dim3(256), 0, s, 0, d)) != cudaSuccess) return e; }
+  { if ((e = launch_ex(k_rcs_reduce, dim3(d.n_act), dim3(256), 0, s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(4)) != cudaSuccess) return e;
   if (d.n_direct_tiles > 0) {
@@ -3013,9 +3017,9 @@ cudaError_t enqueue_batch_iteration(const BatchLaunch& b, cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (b.n_schur > 0) {
     if (b.mixed)
-      { if ((e = launch_ex(k_schur_group_b<float>, dim3(b.n_schur), dim3(SCHUR_THREADS), b.group_smem, s, 0, b.wins, b.schur_items)) != cudaSuccess) return e; }
+      { if ((e = launch_ex(k_schur_group_b<float>, dim3(b.n_schur), dim3(group_threads<float>()), b.group_smem, s, 0, b.wins, b.schur_items)) != cudaSuccess) return e; }
     else
-      { if ((e = launch_ex(k_schur_group_b<double>, dim3(b.n_schur), dim3(SCHUR_THREADS), b.group_smem, s, 0, b.wins, b.schur_items)) != cudaSuccess) return e; }
+      { if ((e = launch_ex(k_schur_group_b<double>, dim3(b.n_schur), dim3(group_threads<double>()), b.group_smem, s, 0, b.wins, b.schur_items)) != cudaSuccess) return e; }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   { if ((e = launch_ex(k_rcs_reduce_b, dim3(b.n_blkit), dim3(256), 0, s, 0, b.wins, b.blk_items)) != cudaSuccess) return e; }
