@@ -990,11 +990,11 @@ __global__ void __launch_bounds__(SCHUR_THREADS) k_schur_direct_b(const Dev* __r
 // combined in a fixed order and the window is written as the tile's partial, summed over
 // tiles by k_rcs_reduce.  About 100 registers on the mixed path: two CTAs per SM.
 constexpr int kStage = 76;         // per (landmark, block): Y[6][4] W[6][4] Dg[21] bY[6] pad
-// Threads of a group Schur CTA: 512 on the mixed path, so that the 2 x 253 half-block items of
-// the widest window (22 keyframes) fit in one pass over its landmarks (each pass re-stages
-// them); 256 on the FP64 path, whose items need more registers.
+// Threads of a group Schur CTA.  512 threads on the mixed path (the 2 x 253 half-block items of
+// the widest window in one pass) capped the registers at 128 and ran slower at 100 keyframes
+// x 32 cameras (0.45 against 0.38 ms) than two 256-thread CTAs per SM with two passes.
 template <typename T>
-__host__ __device__ constexpr int group_threads() { return sizeof(T) == 4 ? 512 : 256; }
+__host__ __device__ constexpr int group_threads() { return 256; }
 template <typename T>
 struct GroupChunk {
   static constexpr int value = sizeof(T) == 4 ? 16 : 8;
@@ -1147,19 +1147,15 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
         atomicOr(&s_mask[l - c0], 1u << w);
       }
       __syncthreads();
-      // zero the records of keyframes of the window that a landmark does not observe
-      for (int i = threadIdx.x; i < nc * span; i += blockDim.x) {
-        const int l = i / span, sl = i % span;
-        if ((s_mask[l] >> sl) & 1u) continue;
-        float4* st = reinterpret_cast<float4*>(s_stg + (l * span + sl) * kStage);
-        for (int k = 0; k < kStage * (int)sizeof(T) / 16; ++k) st[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-      __syncthreads();
       if (working) {
         T part[18];
 #pragma unroll
         for (int k = 0; k < 18; ++k) part[k] = 0;
         for (int lr = g; lr < nc; lr += G) {
+          // a block takes a landmark's term only if it observes both keyframes (records of
+          // the others are never read, so they need no zeroing); a track covers consecutive
+          // keyframes, so a warp's items, which share ba, mostly skip together
+          if (!((s_mask[lr] >> ba) & (s_mask[lr] >> bb) & 1u)) continue;
           const T* base = s_stg + lr * span * kStage;
           if (diag) {
             const T* st = base + ba * kStage;
@@ -1250,11 +1246,11 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(group_threads<T>(), 1) k_schur_group(Dev d) { pdl_enter();
+__global__ void __launch_bounds__(group_threads<T>(), sizeof(T) == 4 ? 2 : 1) k_schur_group(Dev d) { pdl_enter();
   k_schur_group_body<T>(d, blockIdx.x);
 }
 template <typename T>
-__global__ void __launch_bounds__(group_threads<T>(), 1)
+__global__ void __launch_bounds__(group_threads<T>(), sizeof(T) == 4 ? 2 : 1)
     k_schur_group_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
@@ -1747,57 +1743,6 @@ __device__ __forceinline__ void chol_backward(const Dev& d, const CholSmem& Ls, 
 constexpr int kPW = 32;                            // panel width of the blocked factorisation
 constexpr int kPD = kPW + 1;                       // shared-memory row stride (no bank conflicts)
 
-// Backward substitution L^T x = y from the factor of the blocked form (global memory, row
-// stride npw), by 32-column panels from the last.  Panel p belongs to CTA p mod CS, which
-// keeps its entries of w (indexed by column, y on entry) up to date: it solves
-// L_pp^T x_p = w_p with one warp (column recursion, v_c = w_c - sum_{m>c} (L_mc / L_mm) v_m,
-// x = v / L_cc), writes x_p to d.dc and pushes it to every CTA (xb: two buffers of 32); after
-// a cluster barrier every CTA subtracts L_pq^T x_p from the panels q < p it owns.  scratch
-// holds 32 x 33 doubles.  Ends with a cluster barrier.
-__device__ __forceinline__ void chol_backward_panels(const Dev& d, int q, int CS, double* w, double* xb,
-                                                     double* scratch, cooperative_groups::cluster_group& cluster) {
-  const int n = d.n_c, npw = d.npw, npan = npw / kPW, tid = threadIdx.x, nt = blockDim.x;
-  for (int p = npan - 1; p >= 0; --p) {
-    const int o = p * kPW;
-    if (q == p % CS) {                             // uniform over the CTA
-      for (int e = tid; e < kPW * kPW; e += nt) {
-        const int m = e / kPW, c = e % kPW;
-        scratch[m * kPD + c] = m > c ? d.Lw[(size_t)(o + m) * npw + o + c] * d.Ldinv[o + m] : 0.0;
-      }
-      __syncthreads();
-      if (tid < kPW) {
-        double v = o + tid < n ? w[o + tid] : 0.0;
-#pragma unroll 4
-        for (int m = kPW - 1; m > 0; --m) {
-          const double x = __shfl_sync(0xffffffffu, v, m);
-          if (tid < m) v = fma(-scratch[m * kPD + tid], x, v);
-        }
-        const double xv = v * d.Ldinv[o + tid];
-        if (o + tid < n) d.dc[o + tid] = xv;
-        for (int dst = 0; dst < CS; ++dst) cluster.map_shared_rank(xb, dst)[(p & 1) * kPW + tid] = xv;
-      }
-    }
-    cluster.sync();
-    // own panels q' < p: w_q' -= L_pq'^T x_p (thread per column, four partial sums)
-    const double* xp = xb + (p & 1) * kPW;
-    const int n_own = p > q ? (p - 1 - q) / CS + 1 : 0;   // panels q, q + CS, ... below p
-    for (int e = tid; e < n_own * kPW; e += nt) {
-      const int oq = (q + (e / kPW) * CS) * kPW, c = oq + e % kPW;
-      if (c >= n) continue;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-#pragma unroll
-      for (int m = 0; m < kPW; m += 4) {
-        a0 = fma(d.Lw[(size_t)(o + m) * npw + c], xp[m], a0);
-        a1 = fma(d.Lw[(size_t)(o + m + 1) * npw + c], xp[m + 1], a1);
-        a2 = fma(d.Lw[(size_t)(o + m + 2) * npw + c], xp[m + 2], a2);
-        a3 = fma(d.Lw[(size_t)(o + m + 3) * npw + c], xp[m + 3], a3);
-      }
-      w[c] -= (a0 + a1) + (a2 + a3);
-    }
-  }
-  cluster.sync();                                  // dc complete
-}
-
 // |x| to FP32 with a relative error below 2^-20 using integer operations only (no FP64
 // pipe instruction): exponent rebiased, mantissa truncated; below the FP32 normal range
 // gives 0, above it +inf (NaN in gives +inf or NaN).
@@ -1885,24 +1830,30 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   const double floor_ = diag_floor(d, red);        // block-level, contains barriers
   auto rowp = [&](int lb) { return rows + Ls.row_off(q, lb); };
 
-  if (d.chol_blocked) {
-    // ---- the factor, the reciprocals of its diagonal and y = L^-1 rhs come from the blocked
-    // kernels (global memory): own block rows, every CTA a copy of y
-    for (int lb = 0; lb < Ls.nlb; ++lb) {
-      const int r = q + lb * CS;
-      if (r >= NB) break;
+  // inverses of own diagonal blocks (thread per (block, column))
+  auto own_block_inverses = [&]() {
+    for (int e = tid; e < Ls.nlb * kCB; e += nt) {
+      const int lb = e / kCB, j = e % kCB, r = q + lb * CS;
+      if (r >= NB) continue;
       const int W = Ls.row_width(q, lb);
-      double* R = rowp(lb);
-      for (int e = tid; e < kCB * W; e += nt) {
-        const int i = e / W, c = e % W, gi = kCB * r + i;
-        R[e] = c <= gi ? d.Lw[(size_t)gi * d.npw + c] : 0.0;
+      const double* D = rowp(lb) + kCB * r;
+      double z[kCB];
+#pragma unroll
+      for (int i = 0; i < kCB; ++i) {
+        double s = (i == j) ? 1.0 : 0.0;
+#pragma unroll
+        for (int m = 0; m < i; ++m) s = fma(-D[i * W + m], z[m], s);
+        z[i] = i < j ? 0.0 : s * rdiag[lb * kCB + i];
       }
-      if (tid < kCB) rdiag[lb * kCB + tid] = d.Ldinv[kCB * r + tid];
+#pragma unroll
+      for (int i = 0; i < kCB; ++i) linv[(lb * kCB + i) * kCB + j] = z[i];
     }
-    for (int c = tid; c < NP; c += nt) {
-      ybuf[c] = d.yw[c];
-      acc[c] = 0.0;
-    }
+  };
+
+  if (d.chol_blocked) {
+    // ---- the factor and the increment come from the blocked kernels (k_blk_back wrote dc).
+    // The factor's rows are loaded only if the refinement below applies a correction.
+    for (int c = tid; c < NP; c += nt) acc[c] = 0.0;
     for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
     if (tid == 0) *flag = 0;
     cluster.sync();
@@ -2048,52 +1999,36 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
     if (q == 0 && tid == 0) ctrl->nonpd = 1;
     return;
   }
-  // inverses of own diagonal blocks (thread per (block, column)), y to every CTA
-  for (int e = tid; e < Ls.nlb * kCB; e += nt) {
-    const int lb = e / kCB, j = e % kCB, r = q + lb * CS;
-    if (r >= NB) continue;
-    const int W = Ls.row_width(q, lb);
-    const double* D = rowp(lb) + kCB * r;
-    double z[kCB];
-#pragma unroll
-    for (int i = 0; i < kCB; ++i) {
-      double s = (i == j) ? 1.0 : 0.0;
-#pragma unroll
-      for (int m = 0; m < i; ++m) s = fma(-D[i * W + m], z[m], s);
-      z[i] = i < j ? 0.0 : s * rdiag[lb * kCB + i];
-    }
-#pragma unroll
-    for (int i = 0; i < kCB; ++i) linv[(lb * kCB + i) * kCB + j] = z[i];
-  }
-  if (Ls.gather) {
-    // small system: own block rows and their diagonal inverses to CTA 0, which runs the
-    // backward substitution alone (no cluster barrier per block)
-    __syncthreads();
-    double* gl = smem + Ls.gl_off();
-    double* glinv = smem + Ls.glinv_off();
-    for (int lb = 0; lb < Ls.nlb; ++lb) {
-      const int r = q + lb * CS;
-      if (r >= NB) break;
-      const double* R = rowp(lb);
-      double* dst = cluster.map_shared_rank(gl, 0) + (size_t)32 * r * (r + 1);
-      for (int e = tid; e < kCB * kCB * (r + 1); e += nt) dst[e] = R[e];
-      double* dli = cluster.map_shared_rank(glinv, 0) + (size_t)r * kCB * kCB;
-      for (int e = tid; e < kCB * kCB; e += nt) dli[e] = linv[lb * kCB * kCB + e];
-    }
-    cluster.sync();
-    if (q == 0) chol_backward_single(d, Ls, gl, glinv, ybuf, red);
-    cluster.sync();                                // dc visible everywhere
-  } else if (d.chol_blocked) {
-    chol_backward_panels(d, q, CS, ybuf, acc, panel0, cluster);   // acc, panels: free here
-  } else {
-    if (q == 0) {
-      for (int e = tid; e < CS * NP; e += nt) {
-        const int dst = e / NP, c = e % NP;
-        if (dst != 0) cluster.map_shared_rank(ybuf, dst)[c] = ybuf[c];
+  if (!d.chol_blocked) {                           // (blocked form: k_blk_back solved)
+    own_block_inverses();
+    if (Ls.gather) {
+      // small system: own block rows and their diagonal inverses to CTA 0, which runs the
+      // backward substitution alone (no cluster barrier per block)
+      __syncthreads();
+      double* gl = smem + Ls.gl_off();
+      double* glinv = smem + Ls.glinv_off();
+      for (int lb = 0; lb < Ls.nlb; ++lb) {
+        const int r = q + lb * CS;
+        if (r >= NB) break;
+        const double* R = rowp(lb);
+        double* dst = cluster.map_shared_rank(gl, 0) + (size_t)32 * r * (r + 1);
+        for (int e = tid; e < kCB * kCB * (r + 1); e += nt) dst[e] = R[e];
+        double* dli = cluster.map_shared_rank(glinv, 0) + (size_t)r * kCB * kCB;
+        for (int e = tid; e < kCB * kCB; e += nt) dli[e] = linv[lb * kCB * kCB + e];
       }
+      cluster.sync();
+      if (q == 0) chol_backward_single(d, Ls, gl, glinv, ybuf, red);
+      cluster.sync();                              // dc visible everywhere
+    } else {
+      if (q == 0) {
+        for (int e = tid; e < CS * NP; e += nt) {
+          const int dst = e / NP, c = e % NP;
+          if (dst != 0) cluster.map_shared_rank(ybuf, dst)[c] = ybuf[c];
+        }
+      }
+      cluster.sync();
+      chol_backward(d, Ls, q, rows, ybuf, acc, contrib, linv, red, false, cluster);
     }
-    cluster.sync();
-    chol_backward(d, Ls, q, rows, ybuf, acc, contrib, linv, red, false, cluster);
   }
 
   // ---- iterative refinement in FP64: r = rhs - A dc from the assembled S (global, lower
@@ -2160,6 +2095,23 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
     }
     if (it_r == 0 && q == 0 && tid == 0) ctrl->berr = (double)(rn / fmaxf(an * xn + bn, 1e-30f));
     if (rn <= an * xn * 0x1p-53f * sqrtf((float)n)) break;   // uniform over the cluster
+    if (d.chol_blocked && it_r == 0) {
+      // a correction: own block rows of the blocked form's factor and their inverses
+      for (int lb = 0; lb < Ls.nlb; ++lb) {
+        const int r = q + lb * CS;
+        if (r >= NB) break;
+        const int W = Ls.row_width(q, lb);
+        double* R = rowp(lb);
+        for (int e = tid; e < kCB * W; e += nt) {
+          const int i = e / W, c = e % W, gi = kCB * r + i;
+          R[e] = c <= gi ? d.Lw[(size_t)gi * d.npw + c] : 0.0;
+        }
+        if (tid < kCB) rdiag[lb * kCB + tid] = d.Ldinv[kCB * r + tid];
+      }
+      __syncthreads();
+      own_block_inverses();
+      __syncthreads();
+    }
     // forward sweep L y = r, right-looking: the owner of block k forms y_k = L_kk^-1 r_k
     // and pushes it to every CTA, which then updates its own rows below k
     for (int k = 0; k < NB; ++k) {
@@ -2279,10 +2231,15 @@ __global__ void __launch_bounds__(256) k_blk_load(Dev d) { pdl_enter();
     d.yw[i] = i < n ? rcs_rhs(d, i) : 0.0;
 }
 
+// The diagonal block is factored by 8-column sub-blocks with the right-hand side carried as
+// a 33rd row, so that the sub-block solves also form y_p = L_pp^-1 y_p.  Look-ahead: after the
+// solve of sub-block k, warp 0 updates the diagonal 8 x 8 block of sub-block k+1 and factors
+// it while the other warps update the rest of the trailing entries.
 __global__ void __launch_bounds__(256) k_blk_panel(Dev d, int p) { pdl_enter();
-  __shared__ double D[kPW * kPD];                  // the diagonal block
+  constexpr int kRows = kPW + 1;                   // the block's rows and the right-hand side
+  __shared__ double D[kRows * kPD];
   __shared__ __align__(16) double s_b8[kCB * (kCB - 1) / 2 + kCB];
-  __shared__ double s_dinv[kPW], s_y[kPW];
+  __shared__ double s_dinv[kPW];
   __shared__ int s_flag;
   Ctrl* ctrl = d.ctrl;
   if (ctrl->nonpd) return;
@@ -2291,72 +2248,80 @@ __global__ void __launch_bounds__(256) k_blk_panel(Dev d, int p) { pdl_enter();
     const int i = e / kPW, j = e % kPW;
     D[i * kPD + j] = j <= i ? d.Lw[(size_t)(o + i) * npw + o + j] : 0.0;
   }
-  if (tid < kPW) s_y[tid] = d.yw[o + tid];
+  if (tid < kPW) D[kPW * kPD + tid] = d.yw[o + tid];
   if (tid == 0) s_flag = 0;
+  __syncthreads();
+  factor8_warp(D, kPD, s_b8, &s_flag);
   __syncthreads();
   for (int kb = 0; kb < kPW / kCB; ++kb) {
     const int c0 = kb * kCB;
-    factor8_warp(D + c0 * kPD + c0, kPD, s_b8, &s_flag);
-    __syncthreads();
     if (tid < kCB) s_dinv[c0 + tid] = s_b8[kCB * (kCB - 1) / 2 + tid];
-    // sub-block rows below: t L_kk^T = a, 8 lanes per row (one column each)
+    // rows below the sub-block (and the right-hand side row): t L_kk^T = a, 8 lanes per row
     {
       const int row = c0 + kCB + tid / kCB, c = tid % kCB, base = (tid & 31) & ~(kCB - 1);
-      double t = row < kPW ? D[row * kPD + c0 + c] : 0.0;
+      double t = row < kRows ? D[row * kPD + c0 + c] : 0.0;
 #pragma unroll
       for (int m = 0; m < kCB - 1; ++m) {
         const double x = __shfl_sync(0xffffffffu, t, base + m);
         if (c > m) t = fma(-x, s_b8[pk_lower(c, m)], t);
       }
-      if (row < kPW) D[row * kPD + c0 + c] = t * s_b8[kCB * (kCB - 1) / 2 + c];
+      if (row < kRows) D[row * kPD + c0 + c] = t * s_b8[kCB * (kCB - 1) / 2 + c];
     }
     __syncthreads();
-    // trailing entries of the block: D_rc -= sum_m L_r,m L_c,m over this sub-block's columns
-    const int r0 = c0 + kCB, R = kPW - r0;
-    for (int e = tid; e < R * R; e += nt) {
-      const int r = r0 + e / R, c = r0 + e % R;
-      if (c > r) continue;
-      double acc = 0.0;
+    if (kb + 1 == kPW / kCB) break;
+    // trailing entries: D_rc -= sum_m L_r,m L_c,m over this sub-block's columns, c <= r
+    // (c < 32 for the right-hand side row)
+    const int r0 = c0 + kCB, c1 = r0 + kCB;
+    if (tid < 32) {
+      // the next diagonal block (36 entries), then its factor
+      for (int e = tid; e < kCB * (kCB + 1) / 2; e += 32) {
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= e) ++i;
+        const int r = r0 + i, c = r0 + e - i * (i + 1) / 2;
+        double acc = 0.0;
 #pragma unroll
-      for (int m = 0; m < kCB; ++m) acc = fma(D[r * kPD + c0 + m], D[c * kPD + c0 + m], acc);
-      D[r * kPD + c] -= acc;
+        for (int m = 0; m < kCB; ++m) acc = fma(D[r * kPD + c0 + m], D[c * kPD + c0 + m], acc);
+        D[r * kPD + c] -= acc;
+      }
+      __syncwarp();
+      factor8_warp(D + r0 * kPD + r0, kPD, s_b8, &s_flag);
+    } else {
+      const int R = kRows - r0;
+      for (int e = tid - 32; e < R * kPW; e += nt - 32) {
+        const int r = r0 + e / kPW, c = e % kPW;
+        if (c < r0 || c > r || (r < c1 && c < c1)) continue;   // outside, or the next diagonal block
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < kCB; ++m) acc = fma(D[r * kPD + c0 + m], D[c * kPD + c0 + m], acc);
+        D[r * kPD + c] -= acc;
+      }
     }
     __syncthreads();
   }
-  // y_p = L_pp^-1 y_p: v_c = y_c - sum_{m<c} (L_cm / L_mm) v_m, then y_c = v_c / L_cc
-  if (tid < 32) {
-    double v = s_y[tid];
-#pragma unroll 4
-    for (int m = 0; m < kPW - 1; ++m) {
-      const double mcm = tid > m ? D[tid * kPD + m] * s_dinv[m] : 0.0;
-      const double x = __shfl_sync(0xffffffffu, v, m);
-      if (tid > m) v = fma(-x, mcm, v);
-    }
-    s_y[tid] = v * s_dinv[tid];
-  }
-  __syncthreads();
   for (int e = tid; e < kPW * kPW; e += nt) {
     const int i = e / kPW, j = e % kPW;
     if (j <= i) d.Lw[(size_t)(o + i) * npw + o + j] = D[i * kPD + j];
   }
   if (tid < kPW) {
     d.Ldinv[o + tid] = s_dinv[tid];
-    d.yw[o + tid] = s_y[tid];
+    d.yw[o + tid] = D[kPW * kPD + tid];
   }
   if (tid == 0 && s_flag) ctrl->nonpd = 1;
 }
 
-// One warp per row below panel p (8 rows per CTA): L_ip = A_ip L_pp^-T by the same
-// column recursion as the cluster's panel solve, then y_i -= L_ip y_p.
-__global__ void __launch_bounds__(256) k_blk_trsm(Dev d, int p) { pdl_enter();
-  __shared__ double s_mt[kPW * kPW];               // s_mt[m * 32 + c] = L_cm / L_mm (c > m)
+// One warp per row below panel p (kTrsmRows rows per CTA: one warp per sub-partition, so that
+// the 31-step recursions of different rows do not queue on one FP64 pipe): L_ip = A_ip
+// L_pp^-T by the same column recursion as the cluster's panel solve, then y_i -= L_ip y_p.
+constexpr int kTrsmRows = 4;
+__global__ void __launch_bounds__(32 * kTrsmRows) k_blk_trsm(Dev d, int p) { pdl_enter();
+  __shared__ double s_mt[kPW * kPD];               // s_mt[m * kPD + c] = L_cm / L_mm (c > m)
   __shared__ double s_dv[kPW], s_yp[kPW];
   Ctrl* ctrl = d.ctrl;
   if (ctrl->nonpd) return;
   const int npw = d.npw, o = p * kPW, tid = threadIdx.x;
-  for (int e = tid; e < kPW * kPW; e += blockDim.x) {
-    const int m = e / kPW, c = e % kPW;
-    s_mt[e] = c > m ? d.Lw[(size_t)(o + c) * npw + o + m] * d.Ldinv[o + m] : 0.0;
+  for (int e = tid; e < kPW * kPW; e += blockDim.x) {   // row-major reads of L_pp
+    const int c = e / kPW, m = e % kPW;
+    s_mt[m * kPD + c] = c > m ? d.Lw[(size_t)(o + c) * npw + o + m] * d.Ldinv[o + m] : 0.0;
   }
   if (tid < kPW) {
     s_dv[tid] = d.Ldinv[o + tid];
@@ -2364,13 +2329,13 @@ __global__ void __launch_bounds__(256) k_blk_trsm(Dev d, int p) { pdl_enter();
   }
   __syncthreads();
   const int warp = tid >> 5, lane = tid & 31;
-  const int row = o + kPW + blockIdx.x * 8 + warp;
+  const int row = o + kPW + blockIdx.x * kTrsmRows + warp;
   double* a = d.Lw + (size_t)row * npw + o;
   double u = a[lane];
 #pragma unroll 4
   for (int m = 0; m < kPW - 1; ++m) {
     const double x = __shfl_sync(0xffffffffu, u, m);
-    if (lane > m) u = fma(-x, s_mt[m * kPW + lane], u);
+    if (lane > m) u = fma(-x, s_mt[m * kPD + lane], u);
   }
   const double t = u * s_dv[lane];
   a[lane] = t;
@@ -2381,13 +2346,15 @@ __global__ void __launch_bounds__(256) k_blk_trsm(Dev d, int p) { pdl_enter();
 // Trailing update after panel p: 16 x 16 tile (ti, tj), ti >= tj, of the rows and columns
 // below the panel: A_ij -= sum over the panel's 32 columns of L_i,m L_j,m.  part 0 takes the
 // tiles of the next panel's columns (tj < 2), which the next panel's factor and solve need;
-// part 1 the rest (tj >= 2), which can overlap them.
-__global__ void __launch_bounds__(256) k_blk_syrk(Dev d, int p, int part) { pdl_enter();
-  __shared__ double s_a[16 * kPD], s_b[16 * kPD];
+// part 1 the rest (tj >= 2), which can overlap them.  A CTA takes half a tile (8 rows): one
+// warp per sub-partition.
+__global__ void __launch_bounds__(128) k_blk_syrk(Dev d, int p, int part) { pdl_enter();
+  __shared__ double s_a[8 * kPD], s_b[16 * kPD];
   Ctrl* ctrl = d.ctrl;
   if (ctrl->nonpd) return;
   const int npw = d.npw, o = p * kPW, o2 = o + kPW, tid = threadIdx.x;
-  const int blk = blockIdx.x, nt = (d.panel_end[p] - o2) / 16;   // tiles inside the envelope
+  const int blk = blockIdx.x >> 1, half = blockIdx.x & 1;
+  const int nt = (d.panel_end[p] - o2) / 16;       // tiles inside the envelope
   int ti, tj;
   if (part == 0) {
     ti = blk < nt ? blk : blk - nt + 1;
@@ -2399,14 +2366,18 @@ __global__ void __launch_bounds__(256) k_blk_syrk(Dev d, int p, int part) { pdl_
     ti = t + 2;
     tj = blk - t * (t + 1) / 2 + 2;
   }
+  const int ra = o2 + 16 * ti + 8 * half, rb = o2 + 16 * tj;
+  for (int e = tid; e < 8 * kPW; e += blockDim.x) {
+    const int r = e / kPW, m = e % kPW;
+    s_a[r * kPD + m] = d.Lw[(size_t)(ra + r) * npw + o + m];
+  }
   for (int e = tid; e < 16 * kPW; e += blockDim.x) {
     const int r = e / kPW, m = e % kPW;
-    s_a[r * kPD + m] = d.Lw[(size_t)(o2 + 16 * ti + r) * npw + o + m];
-    s_b[r * kPD + m] = d.Lw[(size_t)(o2 + 16 * tj + r) * npw + o + m];
+    s_b[r * kPD + m] = d.Lw[(size_t)(rb + r) * npw + o + m];
   }
   __syncthreads();
   const int r = tid / 16, c = tid % 16;
-  const int gi = o2 + 16 * ti + r, gj = o2 + 16 * tj + c;
+  const int gi = ra + r, gj = rb + c;
   if (gj > gi) return;
   double acc0 = 0.0, acc1 = 0.0;
 #pragma unroll
@@ -2415,6 +2386,75 @@ __global__ void __launch_bounds__(256) k_blk_syrk(Dev d, int p, int part) { pdl_
     acc1 = fma(s_a[r * kPD + m + 1], s_b[c * kPD + m + 1], acc1);
   }
   d.Lw[(size_t)gi * npw + gj] -= acc0 + acc1;
+}
+
+// Backward substitution L^T x = y of the blocked form by one CTA, by 32-column panels from
+// the last: x_q solves L_qq^T x_q = w_q (one warp, column recursion v_c = w_c - sum_{m>c}
+// (L_mc / L_mm) v_m, x = v / L_cc), then the columns of the earlier panels inside the
+// envelope of panel q's rows take w_c -= sum_m L_{o+m, c} x_m (thread per column, fixed
+// order).  The diagonal block of the next panel is fetched during the update.
+constexpr int kBackThreads = 512;
+__global__ void __launch_bounds__(kBackThreads) k_blk_back(Dev d) { pdl_enter();
+  __shared__ double s_w[kMaxPanels * kPW];
+  __shared__ double s_m[2][kPW * kPD];             // s_m[.][m * kPD + c] = L_{o+m, o+c} / L_{o+m, o+m}, m > c
+  __shared__ double s_x[kPW];
+  Ctrl* ctrl = d.ctrl;
+  if (ctrl->nonpd) return;
+  const int n = d.n_c, npw = d.npw, npan = npw / kPW, tid = threadIdx.x, nt = blockDim.x;
+  auto mform = [&](int p, int e) {
+    const int m = e / kPW, c = e % kPW, o = p * kPW;
+    return m > c ? d.Lw[(size_t)(o + m) * npw + o + c] * d.Ldinv[o + m] : 0.0;
+  };
+  for (int i = tid; i < npw; i += nt) s_w[i] = d.yw[i];
+  for (int e = tid; e < kPW * kPW; e += nt) s_m[(npan - 1) & 1][(e / kPW) * kPD + e % kPW] = mform(npan - 1, e);
+  __syncthreads();
+  constexpr int kPre = (kPW * kPW + kBackThreads - 1) / kBackThreads;
+  for (int q = npan - 1; q >= 0; --q) {
+    const int o = q * kPW;
+    if (tid < kPW) {
+      const double* M = s_m[q & 1];
+      double v = o + tid < n ? s_w[o + tid] : 0.0;
+#pragma unroll 4
+      for (int m = kPW - 1; m > 0; --m) {
+        const double x = __shfl_sync(0xffffffffu, v, m);
+        if (tid < m) v = fma(-M[m * kPD + tid], x, v);
+      }
+      const double xv = v * d.Ldinv[o + tid];
+      s_x[tid] = xv;
+      if (o + tid < n) d.dc[o + tid] = xv;
+    }
+    double pre[kPre];
+    if (q > 0) {
+#pragma unroll
+      for (int k = 0; k < kPre; ++k) {
+        const int e = tid + k * nt;
+        pre[k] = e < kPW * kPW ? mform(q - 1, e) : 0.0;
+      }
+    }
+    __syncthreads();                               // x_q visible
+    int p_lo = q;                                  // panels whose envelope holds panel q's rows
+    while (p_lo > 0 && d.panel_end[p_lo - 1] > o) --p_lo;
+    for (int c = kPW * p_lo + tid; c < o; c += nt) {
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      const double* Lc = d.Lw + (size_t)o * npw + c;
+#pragma unroll
+      for (int m = 0; m < kPW; m += 4) {
+        a0 = fma(Lc[(size_t)m * npw], s_x[m], a0);
+        a1 = fma(Lc[(size_t)(m + 1) * npw], s_x[m + 1], a1);
+        a2 = fma(Lc[(size_t)(m + 2) * npw], s_x[m + 2], a2);
+        a3 = fma(Lc[(size_t)(m + 3) * npw], s_x[m + 3], a3);
+      }
+      s_w[c] -= (a0 + a1) + (a2 + a3);
+    }
+    if (q > 0) {
+#pragma unroll
+      for (int k = 0; k < kPre; ++k) {
+        const int e = tid + k * nt;
+        if (e < kPW * kPW) s_m[(q - 1) & 1][(e / kPW) * kPD + e % kPW] = pre[k];
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // --------------------------------------------------------------- k_backsub
@@ -2920,12 +2960,13 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, con
         // rows below the panel inside the factor's envelope (the rest has zeros in its columns)
         const int below = d.panel_end[p] - kPW * (p + 1);
         if (below <= 0) continue;
-        if ((e = launch_ex(k_blk_trsm, dim3(below / 8), dim3(256), 0, s, 0, d, p)) != cudaSuccess) return e;
+        if ((e = launch_ex(k_blk_trsm, dim3(below / kTrsmRows), dim3(32 * kTrsmRows), 0, s, 0, d, p)) != cudaSuccess)
+          return e;
         const int nt16 = below / 16, n_rest = (nt16 - 2) * (nt16 - 1) / 2;
         if (n_rest > 0 && overlap) {
           if ((e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
           if ((e = cudaStreamWaitEvent(side->s, side->fork, 0)) != cudaSuccess) return e;
-          k_blk_syrk<<<n_rest, 256, 0, side->s>>>(d, p, 1);
+          k_blk_syrk<<<2 * n_rest, 128, 0, side->s>>>(d, p, 1);
           if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
         if (pending) {
@@ -2936,11 +2977,12 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, con
           if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return e;
           pending = true;
         }
-        if ((e = launch_ex(k_blk_syrk, dim3(2 * nt16 - 1), dim3(256), 0, s, 0, d, p, 0)) != cudaSuccess) return e;
+        if ((e = launch_ex(k_blk_syrk, dim3(2 * (2 * nt16 - 1)), dim3(128), 0, s, 0, d, p, 0)) != cudaSuccess) return e;
         if (n_rest > 0 && !overlap)
-          if ((e = launch_ex(k_blk_syrk, dim3(n_rest), dim3(256), 0, s, 0, d, p, 1)) != cudaSuccess) return e;
+          if ((e = launch_ex(k_blk_syrk, dim3(2 * n_rest), dim3(128), 0, s, 0, d, p, 1)) != cudaSuccess) return e;
       }
       if (pending && (e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
+      if ((e = launch_ex(k_blk_back, dim3(1), dim3(kBackThreads), 0, s, 0, d)) != cudaSuccess) return e;
     }
     if ((e = launch_ex(k_chol_cluster, dim3(CS), dim3(256), chol_layout(d.n_c, CS).doubles() * sizeof(double), s, CS,
                        d)) != cudaSuccess)
@@ -2966,7 +3008,7 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, con
 int solve_kernels_per_iteration(const Dev& d) {
   int blocked = 0;
   if (chol_cluster_size(d.n_c) > 0 && d.chol_blocked) {
-    blocked = 1 + d.npw / kPW;                     // load, panel factors
+    blocked = 2 + d.npw / kPW;                     // load, panel factors, backward substitution
     for (int p = 0; p < d.npw / kPW; ++p) {
       const int below = d.panel_end[p] - kPW * (p + 1);
       if (below <= 0) continue;
