@@ -1084,6 +1084,21 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
   const int G = max(1, min(CH, NT / n_half));
   const int n_items = n_half * G;                    // > NT only when G == 1
   Out* out = reinterpret_cast<Out*>(d.schur_part) + tile.part_off;
+  // this thread's first pair of the next chunk, loaded while the current chunk's products run
+  int pf_a = 0, pf_l = 0;
+  T pf_v[PAIR_LIN];
+  auto prefetch = [&](int c0n) {
+    const int q = s_lp[c0n] + threadIdx.x;
+    if (q < s_lp[min(c0n + CH, nl)]) {
+      pf_a = d.pair_kf[q];
+      pf_l = d.pair_lm[q] - tile.l0;
+      const T* plq = reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN;
+#pragma unroll
+      for (int k = 0; k < PAIR_LIN; ++k) pf_v[k] = plq[k];
+    }
+  };
+  __syncthreads();                                   // s_lp complete
+  prefetch(0);
   for (int it0 = 0; it0 < n_items; it0 += NT) {     // passes
     const int t = it0 + threadIdx.x;
     const bool working = t < n_items;
@@ -1108,12 +1123,20 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
       // stage each pair's terms as one 76-value record (16-byte stores) and mark it present
       const int q0 = s_lp[c0], q1 = s_lp[c0 + nc];
       for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
-        const int a = d.pair_kf[q];
-        const int l = d.pair_lm[q] - tile.l0;        // index in the tile
-        const T* plq = reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN;
-        T pv[PAIR_LIN];                              // loaded before the slot test: no load chain
+        int a, l;                                    // keyframe, index of the landmark in the tile
+        T pv[PAIR_LIN];
+        if (q == q0 + (int)threadIdx.x) {            // prefetched
+          a = pf_a;
+          l = pf_l;
 #pragma unroll
-        for (int k = 0; k < PAIR_LIN; ++k) pv[k] = plq[k];
+          for (int k = 0; k < PAIR_LIN; ++k) pv[k] = pf_v[k];
+        } else {                                     // loaded before the slot test: no load chain
+          a = d.pair_kf[q];
+          l = d.pair_lm[q] - tile.l0;
+          const T* plq = reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN;
+#pragma unroll
+          for (int k = 0; k < PAIR_LIN; ++k) pv[k] = plq[k];
+        }
         const int w = s_slot[a];
         if (w < 0) continue;
         T W[18], Y[18], Dg[21], bY[6];
@@ -1145,6 +1168,10 @@ __device__ __forceinline__ void k_schur_group_body(const Dev& d, int item) {
           for (int r = 0; r < 6; ++r) st[69 + r] = bY[r];
         }
         atomicOr(&s_mask[l - c0], 1u << w);
+      }
+      {                                              // the next chunk (or the next pass's first)
+        const int cn = c0 + CH < nl ? c0 + CH : (it0 + NT < n_items ? 0 : -1);
+        if (cn >= 0) prefetch(cn);
       }
       __syncthreads();
       if (working) {
@@ -2388,72 +2415,102 @@ __global__ void __launch_bounds__(128) k_blk_syrk(Dev d, int p, int part) { pdl_
   d.Lw[(size_t)gi * npw + gj] -= acc0 + acc1;
 }
 
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // Backward substitution L^T x = y of the blocked form by one CTA, by 32-column panels from
-// the last: x_q solves L_qq^T x_q = w_q (one warp, column recursion v_c = w_c - sum_{m>c}
-// (L_mc / L_mm) v_m, x = v / L_cc), then the columns of the earlier panels inside the
-// envelope of panel q's rows take w_c -= sum_m L_{o+m, c} x_m (thread per column, fixed
-// order).  The diagonal block of the next panel is fetched during the update.
+// the last.  Panel q's rows are needed only over the columns [c_lo, o + 32) of its envelope
+// (c_lo: the first panel whose envelope holds the rows); that segment is copied to shared
+// memory asynchronously while the previous panel is solved (global memory is read directly
+// when it is wider than kBackWMax columns).  Per panel: x_q solves L_qq^T x_q = w_q (one
+// warp, column recursion v_c = w_c - sum_{m>c} (L_mc / L_mm) v_m, x = v / L_cc), then
+// w_c -= sum_m L_{o+m, c} x_m for the columns c in [c_lo, o) (two threads per column, the
+// halves added in a fixed order).
 constexpr int kBackThreads = 512;
+constexpr int kBackWMax = 256;                     // staged columns per row (doubles)
+
+size_t blk_back_smem(int npw) {
+  return sizeof(double) * (4 * (size_t)npw + 2 * (size_t)kPW * kBackWMax + kPW * kPD + kPW);
+}
+
 __global__ void __launch_bounds__(kBackThreads) k_blk_back(Dev d) { pdl_enter();
-  __shared__ double s_w[kMaxPanels * kPW];
-  __shared__ double s_m[2][kPW * kPD];             // s_m[.][m * kPD + c] = L_{o+m, o+c} / L_{o+m, o+m}, m > c
-  __shared__ double s_x[kPW];
+  extern __shared__ __align__(16) double smem[];
   Ctrl* ctrl = d.ctrl;
   if (ctrl->nonpd) return;
   const int n = d.n_c, npw = d.npw, npan = npw / kPW, tid = threadIdx.x, nt = blockDim.x;
-  auto mform = [&](int p, int e) {
-    const int m = e / kPW, c = e % kPW, o = p * kPW;
-    return m > c ? d.Lw[(size_t)(o + m) * npw + o + c] * d.Ldinv[o + m] : 0.0;
+  double* s_w = smem;                              // npw: y, then the running right-hand side
+  double* s_dv = s_w + npw;                        // npw: 1 / L_ii
+  double* s_part = s_dv + npw;                     // 2 x npw: the halves of a column's update
+  double* s_buf = s_part + 2 * npw;                // 2 x kPW x kBackWMax: staged row segments
+  double* s_m = s_buf + 2 * kPW * kBackWMax;       // kPW x kPD: L_{o+m, o+c} / L_{o+m, o+m}, m > c
+  double* s_x = s_m + kPW * kPD;                   // kPW
+  auto c_lo_of = [&](int q) {
+    int p = q;
+    while (p > 0 && d.panel_end[p - 1] > q * kPW) --p;
+    return p * kPW;
   };
-  for (int i = tid; i < npw; i += nt) s_w[i] = d.yw[i];
-  for (int e = tid; e < kPW * kPW; e += nt) s_m[(npan - 1) & 1][(e / kPW) * kPD + e % kPW] = mform(npan - 1, e);
-  __syncthreads();
-  constexpr int kPre = (kPW * kPW + kBackThreads - 1) / kBackThreads;
+  auto stage = [&](int q) {
+    const int o = q * kPW, c0 = c_lo_of(q), W = o + kPW - c0;
+    if (W > kBackWMax) return;
+    double* buf = s_buf + (q & 1) * kPW * kBackWMax;
+    const int nv = W / 2;                          // 16-byte pieces per row
+    for (int e = tid; e < kPW * nv; e += nt) {
+      const int r = e / nv, k = e % nv;
+      cp_async16(buf + r * kBackWMax + 2 * k, d.Lw + (size_t)(o + r) * npw + c0 + 2 * k);
+    }
+  };
+  for (int i = tid; i < npw; i += nt) {
+    s_w[i] = d.yw[i];
+    s_dv[i] = d.Ldinv[i];
+  }
+  stage(npan - 1);
+  cp_async_commit();
   for (int q = npan - 1; q >= 0; --q) {
-    const int o = q * kPW;
+    const int o = q * kPW, c0 = c_lo_of(q), W = o + kPW - c0;
+    const bool staged = W <= kBackWMax;
+    const double* buf = s_buf + (q & 1) * kPW * kBackWMax;
+    cp_async_wait_all();
+    __syncthreads();                               // panel q staged; the other buffer free
+    if (q > 0) stage(q - 1);
+    cp_async_commit();
+    auto Lat = [&](int m, int c) {                 // L_{o+m, c}, c in [c0, o + 32)
+      return staged ? buf[m * kBackWMax + (c - c0)] : d.Lw[(size_t)(o + m) * npw + c];
+    };
+    for (int e = tid; e < kPW * kPW; e += nt) {
+      const int m = e / kPW, c = e % kPW;
+      s_m[m * kPD + c] = m > c ? Lat(m, o + c) * s_dv[o + m] : 0.0;
+    }
+    __syncthreads();
     if (tid < kPW) {
-      const double* M = s_m[q & 1];
       double v = o + tid < n ? s_w[o + tid] : 0.0;
 #pragma unroll 4
       for (int m = kPW - 1; m > 0; --m) {
         const double x = __shfl_sync(0xffffffffu, v, m);
-        if (tid < m) v = fma(-M[m * kPD + tid], x, v);
+        if (tid < m) v = fma(-s_m[m * kPD + tid], x, v);
       }
-      const double xv = v * d.Ldinv[o + tid];
+      const double xv = v * s_dv[o + tid];
       s_x[tid] = xv;
       if (o + tid < n) d.dc[o + tid] = xv;
     }
-    double pre[kPre];
-    if (q > 0) {
-#pragma unroll
-      for (int k = 0; k < kPre; ++k) {
-        const int e = tid + k * nt;
-        pre[k] = e < kPW * kPW ? mform(q - 1, e) : 0.0;
-      }
-    }
     __syncthreads();                               // x_q visible
-    int p_lo = q;                                  // panels whose envelope holds panel q's rows
-    while (p_lo > 0 && d.panel_end[p_lo - 1] > o) --p_lo;
-    for (int c = kPW * p_lo + tid; c < o; c += nt) {
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      const double* Lc = d.Lw + (size_t)o * npw + c;
+    const int ncol = o - c0;                       // a multiple of 32
+    for (int e = tid; e < 2 * ncol; e += nt) {     // lanes l and l + 16 of a warp: one column's halves
+      const int l = e & 31, c = c0 + (e >> 5) * 16 + (l & 15), h = l >> 4;
+      double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-      for (int m = 0; m < kPW; m += 4) {
-        a0 = fma(Lc[(size_t)m * npw], s_x[m], a0);
-        a1 = fma(Lc[(size_t)(m + 1) * npw], s_x[m + 1], a1);
-        a2 = fma(Lc[(size_t)(m + 2) * npw], s_x[m + 2], a2);
-        a3 = fma(Lc[(size_t)(m + 3) * npw], s_x[m + 3], a3);
+      for (int m = 16 * h; m < 16 * h + 16; m += 2) {
+        a0 = fma(Lat(m, c), s_x[m], a0);
+        a1 = fma(Lat(m + 1, c), s_x[m + 1], a1);
       }
-      s_w[c] -= (a0 + a1) + (a2 + a3);
-    }
-    if (q > 0) {
-#pragma unroll
-      for (int k = 0; k < kPre; ++k) {
-        const int e = tid + k * nt;
-        if (e < kPW * kPW) s_m[(q - 1) & 1][(e / kPW) * kPD + e % kPW] = pre[k];
-      }
+      s_part[h * npw + c] = a0 + a1;
     }
     __syncthreads();
+    for (int c = c0 + tid; c < o; c += nt) s_w[c] -= s_part[c] + s_part[npw + c];
   }
 }
 
@@ -2858,6 +2915,7 @@ cudaError_t set_kernel_attributes() {
   if ((e = set_dyn_smem(k_schur_group<float>, group_smem_bytes(SPAN_MAX, true))) != cudaSuccess) return e;
   if ((e = set_dyn_smem(k_chol<true>, chol_smem(kCholSmemMaxN))) != cudaSuccess) return e;
   if ((e = set_dyn_smem(k_chol_cluster, kClusterSmemMax)) != cudaSuccess) return e;
+  if ((e = set_dyn_smem(k_blk_back, blk_back_smem(kMaxPanels * kPW))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
     return e;
   if ((e = set_dyn_smem(k_chol_cluster_b, kClusterSmemMax)) != cudaSuccess) return e;
@@ -2906,8 +2964,13 @@ cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double z
 
 // One part per kernel of the iteration (a part whose kernel is not launched for this
 // window's plan reads as zero).
-int profile_parts() { return 8; }
-const char* profile_names() { return "lin,kf_reduce,schur_group,rcs_reduce,schur_direct,chol,backsub,decide"; }
+// chol: the factorisation (blocked form: k_blk_load and the panel kernels; cluster form: the
+// cluster kernel), chol_back: the blocked form's backward substitution, chol_tail: the blocked
+// form's cluster kernel (refinement, epilogue, candidate poses).
+int profile_parts() { return 10; }
+const char* profile_names() {
+  return "lin,kf_reduce,schur_group,rcs_reduce,schur_direct,chol,chol_back,chol_tail,backsub,decide";
+}
 
 cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, const SideStream* side) {
   cudaError_t e;
@@ -2982,27 +3045,38 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, con
           if ((e = launch_ex(k_blk_syrk, dim3(2 * n_rest), dim3(128), 0, s, 0, d, p, 1)) != cudaSuccess) return e;
       }
       if (pending && (e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
-      if ((e = launch_ex(k_blk_back, dim3(1), dim3(kBackThreads), 0, s, 0, d)) != cudaSuccess) return e;
+      if ((e = mark(6)) != cudaSuccess) return e;
+      if ((e = launch_ex(k_blk_back, dim3(1), dim3(kBackThreads), blk_back_smem(d.npw), s, 0, d)) != cudaSuccess)
+        return e;
+      if ((e = mark(7)) != cudaSuccess) return e;
     }
     if ((e = launch_ex(k_chol_cluster, dim3(CS), dim3(256), chol_layout(d.n_c, CS).doubles() * sizeof(double), s, CS,
                        d)) != cudaSuccess)
       return e;
+    if (!d.chol_blocked) {
+      if ((e = mark(6)) != cudaSuccess) return e;
+      if ((e = mark(7)) != cudaSuccess) return e;
+    }
   } else if (d.n_c <= kCholSmemMaxN) {
     { if ((e = launch_ex(k_chol<true>, dim3(1), dim3(CHOL_THREADS), chol_smem(d.n_c), s, 0, d)) != cudaSuccess) return e; }
   } else {
     { if ((e = launch_ex(k_chol<false>, dim3(1), dim3(CHOL_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = mark(6)) != cudaSuccess) return e;
+  if (chol_cluster_size(d.n_c) <= 0) {
+    if ((e = mark(6)) != cudaSuccess) return e;
+    if ((e = mark(7)) != cudaSuccess) return e;
+  }
+  if ((e = mark(8)) != cudaSuccess) return e;
   if (d.mixed)
     { if ((e = launch_ex(k_backsub<float>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), backsub_smem(d), s, 0, d)) != cudaSuccess) return e; }
   else
     { if ((e = launch_ex(k_backsub<double>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), backsub_smem(d), s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = mark(7)) != cudaSuccess) return e;
+  if ((e = mark(9)) != cudaSuccess) return e;
   { if ((e = launch_ex(k_decide, dim3(1), dim3(DECIDE_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return mark(8);
+  return mark(10);
 }
 
 int solve_kernels_per_iteration(const Dev& d) {
