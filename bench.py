@@ -217,16 +217,6 @@ def traffic_of(kernel: str, workload: str):
     return rec.get("dram_bytes_per_launch")
 
 
-def whole_solve(prof: dict) -> dict:
-    """Profile parts with the reduced-system solve as one part: the factorisation, the blocked
-    form's backward substitution and its refinement / candidate-step kernel."""
-    out = dict(prof)
-    out["chol"] = sum(prof.get(k, 0.0) for k in ("chol", "chol_back", "chol_tail"))
-    out.pop("chol_back", None)
-    out.pop("chol_tail", None)
-    return out
-
-
 def chol_kernel_name(ctx_mode_blocked: bool) -> str:
     return "k_blk_* + k_chol_cluster" if ctx_mode_blocked else "k_chol_cluster"
 
@@ -550,7 +540,7 @@ def run_ours(args):
     wm = work_model(p, P, precision == "mixed")
     label = f"{args.workload} {precision}"
     blocked = 6 * (p.K - 1) >= 320
-    roofs = roofline(whole_solve(prof), wm, label, chol_name=chol_kernel_name(blocked))
+    roofs = roofline(prof, wm, label, chol_name=chol_kernel_name(blocked))
     dom = max(roofs, key=lambda k: roofs[k]["ms_per_launch"])
     roof = dict(roofs[dom])
     roof["workload"] = label
@@ -637,8 +627,7 @@ def run_ours(args):
             if prec == "mixed":
                 pq = cq.cvba_profile_iteration(10, huber_delta=q.huber_delta)
                 c1[prec]["parts_ms"] = pq
-                c1[prec]["roofline"] = roofline(whole_solve(pq), work_model(q, cq.cvba_get_sizes()["P"], True),
-                                                "c1 mixed")
+                c1[prec]["roofline"] = roofline(pq, work_model(q, cq.cvba_get_sizes()["P"], True), "c1 mixed")
             cq.close()
 
         wins = synth.make_batch(256)

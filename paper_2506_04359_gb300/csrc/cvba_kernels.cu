@@ -1830,6 +1830,315 @@ __device__ __forceinline__ double rcs_damp(const Dev& d, int i, double lam, doub
 __device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory"); }
 __device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory"); }
 
+// ------------------------------------------------- blocked Cholesky (large systems)
+// When the reduced camera system is large, its trailing updates exceed what the 8-row block
+// steps of the cluster form can hide, so the cluster factors A = L L^T right-looking by
+// 32-column panels held in global memory (Lw, L2-resident), only inside the factor's envelope
+// (rows [32 (p + 1), panel_end[p]) below panel p are the only ones with nonzeros in its
+// columns).  Per panel p, between cluster barriers:
+//   A  every warp of the cluster solves rows below the panel: L_ip = A_ip L_pp^-T and
+//      y_i -= L_ip y_p;
+//   B  16 x 16 tiles of the next panel's columns take A_ij -= L_ip L_jp^T (all CTAs);
+//   C  CTA 0 factors the next panel's diagonal block while the other CTAs update the rest of
+//      the trailing tiles (columns of the panels after the next).
+// k_blk_load first copies the damped system (padding rows: identity) and the right-hand side
+// to Lw and yw.  The right-hand side is carried as in the cluster form (y = L^-1 (b - g_p)
+// formed during the factorisation); CTA 0 then runs the backward substitution.  Data written
+// by other CTAs of the cluster is read through L2 (__ldcg) after the barrier that orders it.
+
+// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Shared-memory scratch of the blocked factorisation (doubles): the diagonal block with the
+// right-hand side as a 33rd row, the packed 8x8 factor, 1/L_ii, the M-form of the panel's
+// diagonal block, y_p, and two 16-row tile operands.
+constexpr int kBlkD = (kPW + 1) * kPD, kBlkB8 = 40, kBlkMs = kPW * kPD, kBlkTile = 16 * kPD;
+constexpr int kBlkScratch = kBlkD + kBlkB8 + kPW + kBlkMs + kPW + 2 * kBlkTile;
+
+// One CTA (>= 256 threads) factors the 32 x 32 diagonal block of panel p by 8-column
+// sub-blocks, the right-hand side rows riding along so that the sub-block solves also form
+// y_p = L_pp^-1 y_p.  Look-ahead: after the solve of sub-block k, warp 0 updates the diagonal
+// 8 x 8 block of sub-block k+1 and factors it while the other warps update the rest.  Writes
+// L_pp, 1/L_ii and y_p; a pivot that is not a positive normal number sets *flag.
+__device__ void blk_panel_factor(const Dev& d, int p, double* scr, int* flag) {
+  constexpr int kRows = kPW + 1;
+  double* D = scr;
+  double* s_b8 = scr + kBlkD;
+  double* s_dinv = s_b8 + kBlkB8;
+  const int npw = d.npw, o = p * kPW, tid = threadIdx.x, nt = blockDim.x;
+  for (int e = tid; e < kPW * kPW; e += nt) {
+    const int i = e / kPW, j = e % kPW;
+    D[i * kPD + j] = j <= i ? __ldcg(d.Lw + (size_t)(o + i) * npw + o + j) : 0.0;
+  }
+  if (tid < kPW) D[kPW * kPD + tid] = __ldcg(d.yw + o + tid);
+  __syncthreads();
+  factor8_warp(D, kPD, s_b8, flag);
+  __syncthreads();
+  for (int kb = 0; kb < kPW / kCB; ++kb) {
+    const int c0 = kb * kCB;
+    if (tid < kCB) s_dinv[c0 + tid] = s_b8[kCB * (kCB - 1) / 2 + tid];
+    // rows below the sub-block (and the right-hand side row): t L_kk^T = a, 8 lanes per row
+    {
+      const int row = c0 + kCB + tid / kCB, c = tid % kCB, base = (tid & 31) & ~(kCB - 1);
+      double t = row < kRows ? D[row * kPD + c0 + c] : 0.0;
+#pragma unroll
+      for (int m = 0; m < kCB - 1; ++m) {
+        const double x = __shfl_sync(0xffffffffu, t, base + m);
+        if (c > m) t = fma(-x, s_b8[pk_lower(c, m)], t);
+      }
+      if (row < kRows) D[row * kPD + c0 + c] = t * s_b8[kCB * (kCB - 1) / 2 + c];
+    }
+    __syncthreads();
+    if (kb + 1 == kPW / kCB) break;
+    // trailing entries: D_rc -= sum_m L_r,m L_c,m over this sub-block's columns, c <= r
+    // (c < 32 for the right-hand side row)
+    const int r0 = c0 + kCB, c1 = r0 + kCB;
+    if (tid < 32) {
+      for (int e = tid; e < kCB * (kCB + 1) / 2; e += 32) {   // the next diagonal block
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= e) ++i;
+        const int r = r0 + i, c = r0 + e - i * (i + 1) / 2;
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int m = 0; m < kCB; m += 2) {
+          a0 = fma(D[r * kPD + c0 + m], D[c * kPD + c0 + m], a0);
+          a1 = fma(D[r * kPD + c0 + m + 1], D[c * kPD + c0 + m + 1], a1);
+        }
+        D[r * kPD + c] -= a0 + a1;
+      }
+      __syncwarp();
+      factor8_warp(D + r0 * kPD + r0, kPD, s_b8, flag);
+    } else {
+      const int R = kRows - r0;
+      for (int e = tid - 32; e < R * kPW; e += nt - 32) {
+        const int r = r0 + e / kPW, c = e % kPW;
+        if (c < r0 || c > r || (r < c1 && c < c1)) continue;   // outside, or the next diagonal block
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int m = 0; m < kCB; m += 2) {
+          a0 = fma(D[r * kPD + c0 + m], D[c * kPD + c0 + m], a0);
+          a1 = fma(D[r * kPD + c0 + m + 1], D[c * kPD + c0 + m + 1], a1);
+        }
+        D[r * kPD + c] -= a0 + a1;
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < kPW * kPW; e += nt) {
+    const int i = e / kPW, j = e % kPW;
+    if (j <= i) d.Lw[(size_t)(o + i) * npw + o + j] = D[i * kPD + j];
+  }
+  if (tid < kPW) {
+    d.Ldinv[o + tid] = s_dinv[tid];
+    d.yw[o + tid] = D[kPW * kPD + tid];
+  }
+  __syncthreads();                                 // scratch free for the next use
+}
+
+// Phase A of panel p: warp gw of the cluster (CTA q, warp w: gw = 8 q + w) takes the rows
+// o + 32 + gw, + 8 CS, ... below the panel inside its envelope: L_ip = A_ip L_pp^-T by the
+// column recursion u_c = a_c - sum_{m<c} u_m M_cm (M_cm = L_cm / L_mm), t_c = u_c / L_cc, then
+// y_i -= L_ip y_p.
+__device__ void blk_trsm_rows(const Dev& d, int p, int q, int CS, double* scr) {
+  double* Ms = scr + kBlkD + kBlkB8 + kPW;         // Ms[m * kPD + c] = M_cm (c > m)
+  double* s_dv = Ms - kPW;
+  double* s_yp = Ms + kBlkMs;
+  const int npw = d.npw, o = p * kPW, end = d.panel_end[p], tid = threadIdx.x;
+  for (int e = tid; e < kPW * kPW; e += blockDim.x) {   // row-major reads of L_pp
+    const int c = e / kPW, m = e % kPW;
+    Ms[m * kPD + c] = c > m ? __ldcg(d.Lw + (size_t)(o + c) * npw + o + m) * __ldcg(d.Ldinv + o + m) : 0.0;
+  }
+  if (tid < kPW) {
+    s_dv[tid] = __ldcg(d.Ldinv + o + tid);
+    s_yp[tid] = __ldcg(d.yw + o + tid);
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int row = o + kPW + q * nw + warp; row < end; row += CS * nw) {
+    double* a = d.Lw + (size_t)row * npw + o;
+    double u = __ldcg(a + lane);
+#pragma unroll 4
+    for (int m = 0; m < kPW - 1; ++m) {
+      const double x = __shfl_sync(0xffffffffu, u, m);
+      if (lane > m) u = fma(-x, Ms[m * kPD + lane], u);
+    }
+    const double t = u * s_dv[lane];
+    a[lane] = t;
+    const double sy = warp_sum(t * s_yp[lane]);
+    if (lane == 0) d.yw[row] = __ldcg(d.yw + row) - sy;
+  }
+  __syncthreads();                                 // scratch free for the next use
+}
+
+// Tile (ti, tj), ti >= tj, of the trailing lower triangle after panel p (16 x 16, rows and
+// columns counted from the first row below the panel): A_ij -= sum over the panel's 32
+// columns of L_i,m L_j,m.  One entry per thread (256 threads).
+__device__ void blk_syrk_tile(const Dev& d, int p, int ti, int tj, double* scr) {
+  double* sa = scr + kBlkD + kBlkB8 + kPW + kBlkMs + kPW;
+  double* sb = sa + kBlkTile;
+  const int npw = d.npw, o = p * kPW, o2 = o + kPW, tid = threadIdx.x;
+  const int ra = o2 + 16 * ti, rb = o2 + 16 * tj;
+  for (int e = tid; e < 16 * kPW; e += blockDim.x) {
+    const int r = e / kPW, m = e % kPW;
+    sa[r * kPD + m] = __ldcg(d.Lw + (size_t)(ra + r) * npw + o + m);
+    sb[r * kPD + m] = __ldcg(d.Lw + (size_t)(rb + r) * npw + o + m);
+  }
+  __syncthreads();
+  if (tid < 256) {
+    const int r = tid / 16, c = tid % 16, gi = ra + r, gj = rb + c;
+    if (gj <= gi) {
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int m = 0; m < kPW; m += 2) {
+        a0 = fma(sa[r * kPD + m], sb[c * kPD + m], a0);
+        a1 = fma(sa[r * kPD + m + 1], sb[c * kPD + m + 1], a1);
+      }
+      double* x = d.Lw + (size_t)gi * npw + gj;
+      *x = __ldcg(x) - (a0 + a1);
+    }
+  }
+  __syncthreads();
+}
+
+// The blocked factorisation over the cluster (every CTA calls it; ends with a cluster
+// barrier).  A failed pivot sets *flag on every CTA and stops the loop uniformly.
+__device__ void blk_factor_cluster(const Dev& d, int q, int CS, double* scr, int* flag,
+                                   cooperative_groups::cluster_group& cluster) {
+  const int npan = d.npw / kPW, tid = threadIdx.x;
+  auto factor = [&](int p) {
+    blk_panel_factor(d, p, scr, flag);
+    if (*flag)
+      for (int r = tid; r < CS; r += blockDim.x) *cluster.map_shared_rank(flag, r) = 1;
+  };
+  auto rest_tile = [&](int p, int t) {             // triangle of the tiles ti >= tj >= 2
+    int k = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while (k * (k + 1) / 2 > t) --k;
+    while ((k + 1) * (k + 2) / 2 <= t) ++k;
+    blk_syrk_tile(d, p, k + 2, t - k * (k + 1) / 2 + 2, scr);
+  };
+  if (q == 0) factor(0);
+  cluster.sync();
+  for (int p = 0; p < npan && !*flag; ++p) {       // *flag is uniform after each barrier
+    const int below = d.panel_end[p] - kPW * (p + 1);
+    const int nt16 = below > 0 ? below / 16 : 0;
+    if (below > 0) {
+      blk_trsm_rows(d, p, q, CS, scr);             // A
+      cluster.sync();
+      for (int t = q; t < 2 * nt16 - 1; t += CS)   // B: tiles (ti, 0) then (ti >= 1, 1)
+        blk_syrk_tile(d, p, t < nt16 ? t : t - nt16 + 1, t < nt16 ? 0 : 1, scr);
+      cluster.sync();
+    }
+    if (p + 1 < npan) {                            // C
+      const int n_rest = nt16 >= 2 ? (nt16 - 2) * (nt16 - 1) / 2 : 0;
+      if (q == 0) {
+        if (CS == 1)
+          for (int t = 0; t < n_rest; ++t) rest_tile(p, t);
+        factor(p + 1);
+      } else {
+        for (int t = q - 1; t < n_rest; t += CS - 1) rest_tile(p, t);
+      }
+      cluster.sync();
+    }
+  }
+}
+
+// Backward substitution L^T x = y of the blocked form by one CTA (generic thread count, a
+// multiple of 32), by 32-column panels from the last; `smem` holds `avail` doubles.  Panel q's
+// rows are needed only over the columns [c_lo, o + 32) of its envelope (c_lo: the first panel
+// whose envelope holds the rows); that segment is copied to shared memory asynchronously while
+// the previous panel is solved (read from global memory when it is wider than the staging
+// buffer).  Per panel: x_q solves L_qq^T x_q = w_q (one warp, column recursion v_c = w_c -
+// sum_{m>c} (L_mc / L_mm) v_m, x = v / L_cc), then w_c -= sum_m L_{o+m, c} x_m for the columns
+// c in [c_lo, o) (two threads per column, the halves added in a fixed order).  Writes d.dc.
+__device__ void blk_backward_cta(const Dev& d, double* smem, size_t avail) {
+  const int n = d.n_c, npw = d.npw, npan = npw / kPW, tid = threadIdx.x, nt = blockDim.x;
+  double* s_w = smem;                              // npw: y, then the running right-hand side
+  double* s_dv = s_w + npw;                        // npw: 1 / L_ii
+  double* s_part = s_dv + npw;                     // 2 x npw: the halves of a column's update
+  double* s_m = s_part + 2 * npw;                  // kPW x kPD: L_{o+m, o+c} / L_{o+m, o+m}, m > c
+  double* s_x = s_m + kPW * kPD;                   // kPW
+  double* s_buf = s_x + kPW;                       // 2 x kPW x wmax: staged row segments
+  const size_t fixed = 4 * (size_t)npw + kPW * kPD + kPW;
+  const size_t room = avail > fixed ? (avail - fixed) / (2 * kPW) : 0;
+  const int wmax = (room < 256 ? (int)room : 256) & ~1;
+  auto c_lo_of = [&](int q) {
+    int p = q;
+    while (p > 0 && d.panel_end[p - 1] > q * kPW) --p;
+    return p * kPW;
+  };
+  auto stage = [&](int q) {
+    const int o = q * kPW, c0 = c_lo_of(q), W = o + kPW - c0;
+    if (W > wmax) return;
+    double* buf = s_buf + (q & 1) * kPW * wmax;
+    const int nv = W / 2;                          // 16-byte pieces per row
+    for (int e = tid; e < kPW * nv; e += nt) {
+      const int r = e / nv, k = e % nv;
+      cp_async16(buf + r * wmax + 2 * k, d.Lw + (size_t)(o + r) * npw + c0 + 2 * k);
+    }
+  };
+  for (int i = tid; i < npw; i += nt) {
+    s_w[i] = __ldcg(d.yw + i);
+    s_dv[i] = __ldcg(d.Ldinv + i);
+  }
+  stage(npan - 1);
+  cp_async_commit();
+  for (int q = npan - 1; q >= 0; --q) {
+    const int o = q * kPW, c0 = c_lo_of(q), W = o + kPW - c0;
+    const bool staged = W <= wmax;
+    const double* buf = s_buf + (q & 1) * kPW * wmax;
+    cp_async_wait_all();
+    __syncthreads();                               // panel q staged; the other buffer free
+    if (q > 0) stage(q - 1);
+    cp_async_commit();
+    auto Lat = [&](int m, int c) {                 // L_{o+m, c}, c in [c0, o + 32)
+      return staged ? buf[m * wmax + (c - c0)] : __ldcg(d.Lw + (size_t)(o + m) * npw + c);
+    };
+    for (int e = tid; e < kPW * kPW; e += nt) {
+      const int m = e / kPW, c = e % kPW;
+      s_m[m * kPD + c] = m > c ? Lat(m, o + c) * s_dv[o + m] : 0.0;
+    }
+    __syncthreads();
+    if (tid < kPW) {
+      double v = o + tid < n ? s_w[o + tid] : 0.0;
+#pragma unroll 4
+      for (int m = kPW - 1; m > 0; --m) {
+        const double x = __shfl_sync(0xffffffffu, v, m);
+        if (tid < m) v = fma(-s_m[m * kPD + tid], x, v);
+      }
+      const double xv = v * s_dv[o + tid];
+      s_x[tid] = xv;
+      if (o + tid < n) d.dc[o + tid] = xv;
+    }
+    __syncthreads();                               // x_q visible
+    const int ncol = o - c0;                       // a multiple of 32
+    for (int e = tid; e < 2 * ncol; e += nt) {     // lanes l and l + 16 of a warp: one column's halves
+      const int l = e & 31, c = c0 + (e >> 5) * 16 + (l & 15), h = l >> 4;
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int m = 16 * h; m < 16 * h + 16; m += 2) {
+        a0 = fma(Lat(m, c), s_x[m], a0);
+        a1 = fma(Lat(m + 1, c), s_x[m + 1], a1);
+      }
+      s_part[h * npw + c] = a0 + a1;
+    }
+    __syncthreads();
+    for (int c = c0 + tid; c < o; c += nt) s_w[c] -= s_part[c] + s_part[npw + c];
+  }
+  __syncthreads();
+}
+
+// Dynamic shared memory of the cluster kernel in the blocked form, besides its layout: the
+// factorisation scratch and the backward substitution's arrays with 256-column staging.
+size_t blk_cluster_smem(int npw) {
+  const size_t back = 4 * (size_t)npw + kPW * kPD + kPW + 2 * (size_t)kPW * 256;
+  return (std::max<size_t>(kBlkScratch, back) + 8) * sizeof(double);
+}
+
 __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   namespace cg = cooperative_groups;
   cg::cluster_group cluster = cg::this_cluster();
@@ -1851,7 +2160,12 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   double* rdiag = smem + Ls.rdiag_off();           // [lb][i] reciprocals of own diagonal entries
   double* nrm = smem + Ls.nrm_off();               // [CTA][4] refinement norms
   double* red = smem + Ls.red_off();
-  int* flag = reinterpret_cast<int*>(smem + Ls.flag_off());
+  // the blocked form uses all of shared memory below its last 8 doubles as scratch, with the
+  // flag there (its launch may ask for more than the layout)
+  unsigned dyn_bytes;
+  asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+  const size_t dyn_doubles = dyn_bytes / sizeof(double);
+  int* flag = reinterpret_cast<int*>(smem + (d.chol_blocked ? dyn_doubles - 8 : Ls.flag_off()));
   const int tid = threadIdx.x, nt = blockDim.x;
   const double lam = ctrl->lam;
   const double floor_ = diag_floor(d, red);        // block-level, contains barriers
@@ -1878,12 +2192,16 @@ __device__ __forceinline__ void chol_cluster_body(const Dev& d) {
   };
 
   if (d.chol_blocked) {
-    // ---- the factor and the increment come from the blocked kernels (k_blk_back wrote dc).
-    // The factor's rows are loaded only if the refinement below applies a correction.
-    for (int c = tid; c < NP; c += nt) acc[c] = 0.0;
-    for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
+    // ---- blocked factorisation over the cluster (Lw, yw loaded by k_blk_load), then the
+    // backward substitution on CTA 0; shared memory is scratch until then.  The factor's rows
+    // are loaded into their block rows only if the refinement below applies a correction.
     if (tid == 0) *flag = 0;
     cluster.sync();
+    blk_factor_cluster(d, q, CS, smem, flag, cluster);
+    if (!*flag && q == 0) blk_backward_cta(d, smem, dyn_doubles - 8);
+    for (int c = tid; c < NP; c += nt) acc[c] = 0.0;
+    for (int e = tid; e < Ls.nlb * CS * kCB; e += nt) contrib[e] = 0.0;
+    cluster.sync();                                // dc visible everywhere
   } else {
     // ---- load own block rows (damped, padded), rhs on CTA 0
     for (int lb = 0; lb < Ls.nlb; ++lb) {
@@ -2221,18 +2539,8 @@ __global__ void __launch_bounds__(256) k_chol_cluster_b(const Dev* __restrict__ 
   chol_cluster_body(sd);
 }
 
-// ------------------------------------------------- blocked Cholesky (large systems)
-// When the reduced camera system is large, the trailing updates of one cluster (16 SMs of
-// FP64) bound the factorisation, so A = L L^T is factored right-looking by 32-column
-// panels with the updates spread over the whole GPU.  Per panel p (columns [32p, 32p + 32)):
-//   k_blk_panel  one CTA factors the 32 x 32 diagonal block (8x8 sub-blocks: factor, panel
-//                solve and update inside the CTA) and forward-substitutes its part of y;
-//   k_blk_trsm   a warp per row below solves L_ip L_pp^T = A_ip and updates y_i -= L_ip y_p;
-//   k_blk_syrk   16 x 16 tiles of the trailing lower triangle take A_ij -= L_ip L_jp^T.
-// k_blk_load first copies the damped system (padding rows: identity) and the right-hand side
-// to the working arrays.  The cluster kernel then reads the factor back for the backward
-// substitution, the refinement and the epilogue.  The right-hand side is carried the same
-// way as in the cluster kernel (y = L^-1 (b - g_p) formed during the factorisation).
+// Copy of the damped reduced camera system (padding rows: identity) and of its right-hand
+// side to the blocked form's working arrays Lw and yw.
 __global__ void __launch_bounds__(256) k_blk_load(Dev d) { pdl_enter();
   __shared__ double s_red[64];
   Ctrl* ctrl = d.ctrl;
@@ -2256,262 +2564,6 @@ __global__ void __launch_bounds__(256) k_blk_load(Dev d) { pdl_enter();
   }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npw; i += gridDim.x * blockDim.x)
     d.yw[i] = i < n ? rcs_rhs(d, i) : 0.0;
-}
-
-// The diagonal block is factored by 8-column sub-blocks with the right-hand side carried as
-// a 33rd row, so that the sub-block solves also form y_p = L_pp^-1 y_p.  Look-ahead: after the
-// solve of sub-block k, warp 0 updates the diagonal 8 x 8 block of sub-block k+1 and factors
-// it while the other warps update the rest of the trailing entries.
-__global__ void __launch_bounds__(256) k_blk_panel(Dev d, int p) { pdl_enter();
-  constexpr int kRows = kPW + 1;                   // the block's rows and the right-hand side
-  __shared__ double D[kRows * kPD];
-  __shared__ __align__(16) double s_b8[kCB * (kCB - 1) / 2 + kCB];
-  __shared__ double s_dinv[kPW];
-  __shared__ int s_flag;
-  Ctrl* ctrl = d.ctrl;
-  if (ctrl->nonpd) return;
-  const int npw = d.npw, o = p * kPW, tid = threadIdx.x, nt = blockDim.x;
-  for (int e = tid; e < kPW * kPW; e += nt) {
-    const int i = e / kPW, j = e % kPW;
-    D[i * kPD + j] = j <= i ? d.Lw[(size_t)(o + i) * npw + o + j] : 0.0;
-  }
-  if (tid < kPW) D[kPW * kPD + tid] = d.yw[o + tid];
-  if (tid == 0) s_flag = 0;
-  __syncthreads();
-  factor8_warp(D, kPD, s_b8, &s_flag);
-  __syncthreads();
-  for (int kb = 0; kb < kPW / kCB; ++kb) {
-    const int c0 = kb * kCB;
-    if (tid < kCB) s_dinv[c0 + tid] = s_b8[kCB * (kCB - 1) / 2 + tid];
-    // rows below the sub-block (and the right-hand side row): t L_kk^T = a, 8 lanes per row
-    {
-      const int row = c0 + kCB + tid / kCB, c = tid % kCB, base = (tid & 31) & ~(kCB - 1);
-      double t = row < kRows ? D[row * kPD + c0 + c] : 0.0;
-#pragma unroll
-      for (int m = 0; m < kCB - 1; ++m) {
-        const double x = __shfl_sync(0xffffffffu, t, base + m);
-        if (c > m) t = fma(-x, s_b8[pk_lower(c, m)], t);
-      }
-      if (row < kRows) D[row * kPD + c0 + c] = t * s_b8[kCB * (kCB - 1) / 2 + c];
-    }
-    __syncthreads();
-    if (kb + 1 == kPW / kCB) break;
-    // trailing entries: D_rc -= sum_m L_r,m L_c,m over this sub-block's columns, c <= r
-    // (c < 32 for the right-hand side row)
-    const int r0 = c0 + kCB, c1 = r0 + kCB;
-    if (tid < 32) {
-      // the next diagonal block (36 entries), then its factor
-      for (int e = tid; e < kCB * (kCB + 1) / 2; e += 32) {
-        int i = 0;
-        while ((i + 1) * (i + 2) / 2 <= e) ++i;
-        const int r = r0 + i, c = r0 + e - i * (i + 1) / 2;
-        double acc = 0.0;
-#pragma unroll
-        for (int m = 0; m < kCB; ++m) acc = fma(D[r * kPD + c0 + m], D[c * kPD + c0 + m], acc);
-        D[r * kPD + c] -= acc;
-      }
-      __syncwarp();
-      factor8_warp(D + r0 * kPD + r0, kPD, s_b8, &s_flag);
-    } else {
-      const int R = kRows - r0;
-      for (int e = tid - 32; e < R * kPW; e += nt - 32) {
-        const int r = r0 + e / kPW, c = e % kPW;
-        if (c < r0 || c > r || (r < c1 && c < c1)) continue;   // outside, or the next diagonal block
-        double acc = 0.0;
-#pragma unroll
-        for (int m = 0; m < kCB; ++m) acc = fma(D[r * kPD + c0 + m], D[c * kPD + c0 + m], acc);
-        D[r * kPD + c] -= acc;
-      }
-    }
-    __syncthreads();
-  }
-  for (int e = tid; e < kPW * kPW; e += nt) {
-    const int i = e / kPW, j = e % kPW;
-    if (j <= i) d.Lw[(size_t)(o + i) * npw + o + j] = D[i * kPD + j];
-  }
-  if (tid < kPW) {
-    d.Ldinv[o + tid] = s_dinv[tid];
-    d.yw[o + tid] = D[kPW * kPD + tid];
-  }
-  if (tid == 0 && s_flag) ctrl->nonpd = 1;
-}
-
-// One warp per row below panel p (kTrsmRows rows per CTA: one warp per sub-partition, so that
-// the 31-step recursions of different rows do not queue on one FP64 pipe): L_ip = A_ip
-// L_pp^-T by the same column recursion as the cluster's panel solve, then y_i -= L_ip y_p.
-constexpr int kTrsmRows = 4;
-__global__ void __launch_bounds__(32 * kTrsmRows) k_blk_trsm(Dev d, int p) { pdl_enter();
-  __shared__ double s_mt[kPW * kPD];               // s_mt[m * kPD + c] = L_cm / L_mm (c > m)
-  __shared__ double s_dv[kPW], s_yp[kPW];
-  Ctrl* ctrl = d.ctrl;
-  if (ctrl->nonpd) return;
-  const int npw = d.npw, o = p * kPW, tid = threadIdx.x;
-  for (int e = tid; e < kPW * kPW; e += blockDim.x) {   // row-major reads of L_pp
-    const int c = e / kPW, m = e % kPW;
-    s_mt[m * kPD + c] = c > m ? d.Lw[(size_t)(o + c) * npw + o + m] * d.Ldinv[o + m] : 0.0;
-  }
-  if (tid < kPW) {
-    s_dv[tid] = d.Ldinv[o + tid];
-    s_yp[tid] = d.yw[o + tid];
-  }
-  __syncthreads();
-  const int warp = tid >> 5, lane = tid & 31;
-  const int row = o + kPW + blockIdx.x * kTrsmRows + warp;
-  double* a = d.Lw + (size_t)row * npw + o;
-  double u = a[lane];
-#pragma unroll 4
-  for (int m = 0; m < kPW - 1; ++m) {
-    const double x = __shfl_sync(0xffffffffu, u, m);
-    if (lane > m) u = fma(-x, s_mt[m * kPD + lane], u);
-  }
-  const double t = u * s_dv[lane];
-  a[lane] = t;
-  const double sy = warp_sum(t * s_yp[lane]);
-  if (lane == 0) d.yw[row] -= sy;
-}
-
-// Trailing update after panel p: 16 x 16 tile (ti, tj), ti >= tj, of the rows and columns
-// below the panel: A_ij -= sum over the panel's 32 columns of L_i,m L_j,m.  part 0 takes the
-// tiles of the next panel's columns (tj < 2), which the next panel's factor and solve need;
-// part 1 the rest (tj >= 2), which can overlap them.  A CTA takes half a tile (8 rows): one
-// warp per sub-partition.
-__global__ void __launch_bounds__(128) k_blk_syrk(Dev d, int p, int part) { pdl_enter();
-  __shared__ double s_a[8 * kPD], s_b[16 * kPD];
-  Ctrl* ctrl = d.ctrl;
-  if (ctrl->nonpd) return;
-  const int npw = d.npw, o = p * kPW, o2 = o + kPW, tid = threadIdx.x;
-  const int blk = blockIdx.x >> 1, half = blockIdx.x & 1;
-  const int nt = (d.panel_end[p] - o2) / 16;       // tiles inside the envelope
-  int ti, tj;
-  if (part == 0) {
-    ti = blk < nt ? blk : blk - nt + 1;
-    tj = blk < nt ? 0 : 1;
-  } else {                                         // triangle of the tiles ti >= tj >= 2
-    int t = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
-    while (t * (t + 1) / 2 > blk) --t;
-    while ((t + 1) * (t + 2) / 2 <= blk) ++t;
-    ti = t + 2;
-    tj = blk - t * (t + 1) / 2 + 2;
-  }
-  const int ra = o2 + 16 * ti + 8 * half, rb = o2 + 16 * tj;
-  for (int e = tid; e < 8 * kPW; e += blockDim.x) {
-    const int r = e / kPW, m = e % kPW;
-    s_a[r * kPD + m] = d.Lw[(size_t)(ra + r) * npw + o + m];
-  }
-  for (int e = tid; e < 16 * kPW; e += blockDim.x) {
-    const int r = e / kPW, m = e % kPW;
-    s_b[r * kPD + m] = d.Lw[(size_t)(rb + r) * npw + o + m];
-  }
-  __syncthreads();
-  const int r = tid / 16, c = tid % 16;
-  const int gi = ra + r, gj = rb + c;
-  if (gj > gi) return;
-  double acc0 = 0.0, acc1 = 0.0;
-#pragma unroll
-  for (int m = 0; m < kPW; m += 2) {
-    acc0 = fma(s_a[r * kPD + m], s_b[c * kPD + m], acc0);
-    acc1 = fma(s_a[r * kPD + m + 1], s_b[c * kPD + m + 1], acc1);
-  }
-  d.Lw[(size_t)gi * npw + gj] -= acc0 + acc1;
-}
-
-// 16-byte asynchronous copy global -> shared (both addresses 16-byte aligned).
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-// Backward substitution L^T x = y of the blocked form by one CTA, by 32-column panels from
-// the last.  Panel q's rows are needed only over the columns [c_lo, o + 32) of its envelope
-// (c_lo: the first panel whose envelope holds the rows); that segment is copied to shared
-// memory asynchronously while the previous panel is solved (global memory is read directly
-// when it is wider than kBackWMax columns).  Per panel: x_q solves L_qq^T x_q = w_q (one
-// warp, column recursion v_c = w_c - sum_{m>c} (L_mc / L_mm) v_m, x = v / L_cc), then
-// w_c -= sum_m L_{o+m, c} x_m for the columns c in [c_lo, o) (two threads per column, the
-// halves added in a fixed order).
-constexpr int kBackThreads = 512;
-constexpr int kBackWMax = 256;                     // staged columns per row (doubles)
-
-size_t blk_back_smem(int npw) {
-  return sizeof(double) * (4 * (size_t)npw + 2 * (size_t)kPW * kBackWMax + kPW * kPD + kPW);
-}
-
-__global__ void __launch_bounds__(kBackThreads) k_blk_back(Dev d) { pdl_enter();
-  extern __shared__ __align__(16) double smem[];
-  Ctrl* ctrl = d.ctrl;
-  if (ctrl->nonpd) return;
-  const int n = d.n_c, npw = d.npw, npan = npw / kPW, tid = threadIdx.x, nt = blockDim.x;
-  double* s_w = smem;                              // npw: y, then the running right-hand side
-  double* s_dv = s_w + npw;                        // npw: 1 / L_ii
-  double* s_part = s_dv + npw;                     // 2 x npw: the halves of a column's update
-  double* s_buf = s_part + 2 * npw;                // 2 x kPW x kBackWMax: staged row segments
-  double* s_m = s_buf + 2 * kPW * kBackWMax;       // kPW x kPD: L_{o+m, o+c} / L_{o+m, o+m}, m > c
-  double* s_x = s_m + kPW * kPD;                   // kPW
-  auto c_lo_of = [&](int q) {
-    int p = q;
-    while (p > 0 && d.panel_end[p - 1] > q * kPW) --p;
-    return p * kPW;
-  };
-  auto stage = [&](int q) {
-    const int o = q * kPW, c0 = c_lo_of(q), W = o + kPW - c0;
-    if (W > kBackWMax) return;
-    double* buf = s_buf + (q & 1) * kPW * kBackWMax;
-    const int nv = W / 2;                          // 16-byte pieces per row
-    for (int e = tid; e < kPW * nv; e += nt) {
-      const int r = e / nv, k = e % nv;
-      cp_async16(buf + r * kBackWMax + 2 * k, d.Lw + (size_t)(o + r) * npw + c0 + 2 * k);
-    }
-  };
-  for (int i = tid; i < npw; i += nt) {
-    s_w[i] = d.yw[i];
-    s_dv[i] = d.Ldinv[i];
-  }
-  stage(npan - 1);
-  cp_async_commit();
-  for (int q = npan - 1; q >= 0; --q) {
-    const int o = q * kPW, c0 = c_lo_of(q), W = o + kPW - c0;
-    const bool staged = W <= kBackWMax;
-    const double* buf = s_buf + (q & 1) * kPW * kBackWMax;
-    cp_async_wait_all();
-    __syncthreads();                               // panel q staged; the other buffer free
-    if (q > 0) stage(q - 1);
-    cp_async_commit();
-    auto Lat = [&](int m, int c) {                 // L_{o+m, c}, c in [c0, o + 32)
-      return staged ? buf[m * kBackWMax + (c - c0)] : d.Lw[(size_t)(o + m) * npw + c];
-    };
-    for (int e = tid; e < kPW * kPW; e += nt) {
-      const int m = e / kPW, c = e % kPW;
-      s_m[m * kPD + c] = m > c ? Lat(m, o + c) * s_dv[o + m] : 0.0;
-    }
-    __syncthreads();
-    if (tid < kPW) {
-      double v = o + tid < n ? s_w[o + tid] : 0.0;
-#pragma unroll 4
-      for (int m = kPW - 1; m > 0; --m) {
-        const double x = __shfl_sync(0xffffffffu, v, m);
-        if (tid < m) v = fma(-s_m[m * kPD + tid], x, v);
-      }
-      const double xv = v * s_dv[o + tid];
-      s_x[tid] = xv;
-      if (o + tid < n) d.dc[o + tid] = xv;
-    }
-    __syncthreads();                               // x_q visible
-    const int ncol = o - c0;                       // a multiple of 32
-    for (int e = tid; e < 2 * ncol; e += nt) {     // lanes l and l + 16 of a warp: one column's halves
-      const int l = e & 31, c = c0 + (e >> 5) * 16 + (l & 15), h = l >> 4;
-      double a0 = 0.0, a1 = 0.0;
-#pragma unroll
-      for (int m = 16 * h; m < 16 * h + 16; m += 2) {
-        a0 = fma(Lat(m, c), s_x[m], a0);
-        a1 = fma(Lat(m + 1, c), s_x[m + 1], a1);
-      }
-      s_part[h * npw + c] = a0 + a1;
-    }
-    __syncthreads();
-    for (int c = c0 + tid; c < o; c += nt) s_w[c] -= s_part[c] + s_part[npw + c];
-  }
 }
 
 // --------------------------------------------------------------- k_backsub
@@ -2915,7 +2967,6 @@ cudaError_t set_kernel_attributes() {
   if ((e = set_dyn_smem(k_schur_group<float>, group_smem_bytes(SPAN_MAX, true))) != cudaSuccess) return e;
   if ((e = set_dyn_smem(k_chol<true>, chol_smem(kCholSmemMaxN))) != cudaSuccess) return e;
   if ((e = set_dyn_smem(k_chol_cluster, kClusterSmemMax)) != cudaSuccess) return e;
-  if ((e = set_dyn_smem(k_blk_back, blk_back_smem(kMaxPanels * kPW))) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(k_chol_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) != cudaSuccess)
     return e;
   if ((e = set_dyn_smem(k_chol_cluster_b, kClusterSmemMax)) != cudaSuccess) return e;
@@ -2964,13 +3015,9 @@ cudaError_t enqueue_solve_init(const Dev& d, double lam0, double huber, double z
 
 // One part per kernel of the iteration (a part whose kernel is not launched for this
 // window's plan reads as zero).
-// chol: the factorisation (blocked form: k_blk_load and the panel kernels; cluster form: the
-// cluster kernel), chol_back: the blocked form's backward substitution, chol_tail: the blocked
-// form's cluster kernel (refinement, epilogue, candidate poses).
-int profile_parts() { return 10; }
-const char* profile_names() {
-  return "lin,kf_reduce,schur_group,rcs_reduce,schur_direct,chol,chol_back,chol_tail,backsub,decide";
-}
+// chol: the reduced-system solve (the cluster kernel, after k_blk_load in the blocked form).
+int profile_parts() { return 8; }
+const char* profile_names() { return "lin,kf_reduce,schur_group,rcs_reduce,schur_direct,chol,backsub,decide"; }
 
 cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, const SideStream* side) {
   cudaError_t e;
@@ -3008,88 +3055,35 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, con
   if ((e = mark(5)) != cudaSuccess) return e;
   if (chol_cluster_size(d.n_c) > 0) {
     const int CS = chol_cluster_size(d.n_c);
+    size_t smem = chol_layout(d.n_c, CS).doubles() * sizeof(double);
     if (d.chol_blocked) {
-      // blocked factorisation; the cluster kernel below then solves from the factor
-      const int npan = d.npw / kPW;
+      // the cluster kernel factors by panels from the working copy, then solves
       const size_t n_load = std::min(((size_t)d.npw * d.npw + 255) / 256, (size_t)152 * 8);
       if ((e = launch_ex(k_blk_load, dim3((unsigned)n_load), dim3(256), 0, s, 0, d)) != cudaSuccess) return e;
-      // The trailing update's tiles outside the next panel's columns run on the side stream
-      // (in order there, as every panel updates the same tiles), overlapping the next panel's
-      // factor and solve; the next panel's column update waits for them.
-      const bool overlap = side && side->s && side->fork && side->join;
-      bool pending = false;
-      for (int p = 0; p < npan; ++p) {
-        if ((e = launch_ex(k_blk_panel, dim3(1), dim3(256), 0, s, 0, d, p)) != cudaSuccess) return e;
-        // rows below the panel inside the factor's envelope (the rest has zeros in its columns)
-        const int below = d.panel_end[p] - kPW * (p + 1);
-        if (below <= 0) continue;
-        if ((e = launch_ex(k_blk_trsm, dim3(below / kTrsmRows), dim3(32 * kTrsmRows), 0, s, 0, d, p)) != cudaSuccess)
-          return e;
-        const int nt16 = below / 16, n_rest = (nt16 - 2) * (nt16 - 1) / 2;
-        if (n_rest > 0 && overlap) {
-          if ((e = cudaEventRecord(side->fork, s)) != cudaSuccess) return e;
-          if ((e = cudaStreamWaitEvent(side->s, side->fork, 0)) != cudaSuccess) return e;
-          k_blk_syrk<<<2 * n_rest, 128, 0, side->s>>>(d, p, 1);
-          if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
-        if (pending) {
-          if ((e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
-          pending = false;
-        }
-        if (n_rest > 0 && overlap) {
-          if ((e = cudaEventRecord(side->join, side->s)) != cudaSuccess) return e;
-          pending = true;
-        }
-        if ((e = launch_ex(k_blk_syrk, dim3(2 * (2 * nt16 - 1)), dim3(128), 0, s, 0, d, p, 0)) != cudaSuccess) return e;
-        if (n_rest > 0 && !overlap)
-          if ((e = launch_ex(k_blk_syrk, dim3(2 * n_rest), dim3(128), 0, s, 0, d, p, 1)) != cudaSuccess) return e;
-      }
-      if (pending && (e = cudaStreamWaitEvent(s, side->join, 0)) != cudaSuccess) return e;
-      if ((e = mark(6)) != cudaSuccess) return e;
-      if ((e = launch_ex(k_blk_back, dim3(1), dim3(kBackThreads), blk_back_smem(d.npw), s, 0, d)) != cudaSuccess)
-        return e;
-      if ((e = mark(7)) != cudaSuccess) return e;
+      smem = std::max(smem, blk_cluster_smem(d.npw));
     }
-    if ((e = launch_ex(k_chol_cluster, dim3(CS), dim3(256), chol_layout(d.n_c, CS).doubles() * sizeof(double), s, CS,
-                       d)) != cudaSuccess)
-      return e;
-    if (!d.chol_blocked) {
-      if ((e = mark(6)) != cudaSuccess) return e;
-      if ((e = mark(7)) != cudaSuccess) return e;
-    }
+    if ((e = launch_ex(k_chol_cluster, dim3(CS), dim3(256), smem, s, CS, d)) != cudaSuccess) return e;
   } else if (d.n_c <= kCholSmemMaxN) {
     { if ((e = launch_ex(k_chol<true>, dim3(1), dim3(CHOL_THREADS), chol_smem(d.n_c), s, 0, d)) != cudaSuccess) return e; }
   } else {
     { if ((e = launch_ex(k_chol<false>, dim3(1), dim3(CHOL_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (chol_cluster_size(d.n_c) <= 0) {
-    if ((e = mark(6)) != cudaSuccess) return e;
-    if ((e = mark(7)) != cudaSuccess) return e;
-  }
-  if ((e = mark(8)) != cudaSuccess) return e;
+  if ((e = mark(6)) != cudaSuccess) return e;
   if (d.mixed)
     { if ((e = launch_ex(k_backsub<float>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), backsub_smem(d), s, 0, d)) != cudaSuccess) return e; }
   else
     { if ((e = launch_ex(k_backsub<double>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), backsub_smem(d), s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = mark(9)) != cudaSuccess) return e;
+  if ((e = mark(7)) != cudaSuccess) return e;
   { if ((e = launch_ex(k_decide, dim3(1), dim3(DECIDE_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  return mark(10);
+  return mark(8);
 }
 
 int solve_kernels_per_iteration(const Dev& d) {
   int blocked = 0;
-  if (chol_cluster_size(d.n_c) > 0 && d.chol_blocked) {
-    blocked = 2 + d.npw / kPW;                     // load, panel factors, backward substitution
-    for (int p = 0; p < d.npw / kPW; ++p) {
-      const int below = d.panel_end[p] - kPW * (p + 1);
-      if (below <= 0) continue;
-      const int nt16 = below / 16;
-      blocked += 2 + ((nt16 - 2) * (nt16 - 1) / 2 > 0 ? 1 : 0);   // solve, update (two parts)
-    }
-  }
+  if (chol_cluster_size(d.n_c) > 0 && d.chol_blocked) blocked = 1;   // k_blk_load
   return 6 + (d.n_schur_tiles > 0 ? 1 : 0) + (d.n_direct_tiles > 0 ? 1 : 0) + blocked;
 }
 
