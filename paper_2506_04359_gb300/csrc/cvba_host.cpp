@@ -220,7 +220,9 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
         if (l1 > l0 && (np > target || l1 - l0 >= LIN_TILE_LMS)) break;
         ++l1;
       }
-      LinTile t{l0, l1, lm_pair[l0], lm_pair[l1], 0, 0, 0};
+      LinTile t{l0, l1, lm_pair[l0], lm_pair[l1], 0, 0, 0, 0, 0, 0, 0, 0};
+      t.o0 = pair_obs[t.p0];
+      t.o1 = pair_obs[t.p1];
       int lo = K, hi = -1;
       for (int q = t.p0; q < t.p1; ++q) {
         lo = std::min(lo, pair_kf[q]);
@@ -232,29 +234,27 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
       l0 = l1;
     }
   }
-  // offsets of the per-keyframe partials and, per keyframe, the tiles covering it
-  std::vector<int32_t> kf_tiles_off(K + 1, 0), kf_tiles;
+  // the per-keyframe partials, keyframe-major: keyframe a owns the slots [kf_tiles_off[a],
+  // kf_tiles_off[a + 1]) (12 values each), one per tile covering it, in tile order
+  std::vector<int32_t> kf_tiles_off(K + 1, 0);
   size_t kf_part_len = 0;
   {
     for (auto& t : c->lin_tiles) {
-      t.part_off = (int)kf_part_len;
+      t.part_off = -1;
       kf_part_len += (size_t)t.kf_n * 12;
       for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) kf_tiles_off[a + 1]++;
     }
     for (int a = 0; a < K; ++a) kf_tiles_off[a + 1] += kf_tiles_off[a];
-    kf_tiles.resize(kf_tiles_off[K]);
-    std::vector<int32_t> fill(kf_tiles_off.begin(), kf_tiles_off.end() - 1);
-    for (int ti = 0; ti < (int)c->lin_tiles.size(); ++ti) {
-      const auto& t = c->lin_tiles[ti];
-      for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) kf_tiles[fill[a]++] = ti;
-    }
   }
   // per tile and keyframe of its range: the tile-local indices of that keyframe's pairs
-  // (free keyframes only), in pair order
-  std::vector<int32_t> lin_kf_off, lin_kf_idx;
+  // (free keyframes only), in pair order, and the keyframe's partial slot for this tile
+  std::vector<int32_t> lin_kf_off, lin_kf_idx, lin_kf_slot;
   lin_kf_idx.reserve(P);
+  std::vector<int32_t> slot_fill(kf_tiles_off.begin(), kf_tiles_off.end() - 1);
   for (auto& t : c->lin_tiles) {
     t.kfl_off = (int)lin_kf_off.size();
+    for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) lin_kf_slot.push_back(slot_fill[a]++);
+    lin_kf_slot.push_back(0);                        // aligned with lin_kf_off (kf_n + 1 per tile)
     std::vector<int32_t> cnt((size_t)t.kf_n + 1, 0);
     for (int q = t.p0; q < t.p1; ++q)
       if (kf_pb[pair_kf[q]] >= 0) cnt[pair_kf[q] - t.kf_lo + 1]++;
@@ -262,6 +262,8 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     for (int k = 0; k < t.kf_n; ++k) cnt[k + 1] += cnt[k];
     for (int k = 0; k <= t.kf_n; ++k) lin_kf_off.push_back(base + cnt[k]);
     lin_kf_idx.resize((size_t)base + cnt[t.kf_n]);
+    t.kfi0 = base;
+    t.kfi_n = cnt[t.kf_n];
     for (int q = t.p0; q < t.p1; ++q)
       if (kf_pb[pair_kf[q]] >= 0) lin_kf_idx[base + cnt[pair_kf[q] - t.kf_lo]++] = q - t.p0;
   }
@@ -333,7 +335,10 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     for (int ti = 0; ti < (int)c->schur_tiles.size(); ++ti) {
       const auto& t = c->schur_tiles[ti];
       for (int a = t.k_lo; a < t.k_lo + t.span; ++a)
-        for (int b = t.k_lo; b <= a; ++b) blk_tiles[fill[a * (a + 1) / 2 + b]++] = ti;
+        for (int b = t.k_lo; b <= a; ++b) {
+          const int aa = a - t.k_lo, bb = b - t.k_lo;   // [half block][18] window layout
+          blk_tiles[fill[a * (a + 1) / 2 + b]++] = t.part_off + 2 * (aa * (aa + 1) / 2 + bb) * 18;
+        }
     }
   }
   // blocks of the reduced camera system that any tile touches (and every diagonal block):
@@ -504,12 +509,12 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     CK(dalloc(c, &kp, kf_part_len), "alloc");
     CK(dalloc(c, &sp, schur_part_len), "alloc");
     CK(dalloc(c, &kto, (size_t)K + 1), "alloc");
-    CK(dalloc(c, &kt, kf_tiles.size()), "alloc");
+    CK(dalloc(c, &kt, lin_kf_slot.size()), "alloc");
     CK(dalloc(c, &bto, (size_t)n_blk + 1), "alloc");
     CK(dalloc(c, &bt, blk_tiles.size()), "alloc");
     CK(cudaMemcpy(kto, kf_tiles_off.data(), kf_tiles_off.size() * 4, cudaMemcpyHostToDevice), "upload");
-    if (!kf_tiles.empty())
-      CK(cudaMemcpy(kt, kf_tiles.data(), kf_tiles.size() * 4, cudaMemcpyHostToDevice), "upload");
+    if (!lin_kf_slot.empty())
+      CK(cudaMemcpy(kt, lin_kf_slot.data(), lin_kf_slot.size() * 4, cudaMemcpyHostToDevice), "upload");
     CK(cudaMemcpy(bto, blk_tiles_off.data(), blk_tiles_off.size() * 4, cudaMemcpyHostToDevice), "upload");
     if (!blk_tiles.empty())
       CK(cudaMemcpy(bt, blk_tiles.data(), blk_tiles.size() * 4, cudaMemcpyHostToDevice), "upload");
@@ -525,9 +530,9 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     d.kf_part = kp;
     d.schur_part = sp;
     d.kf_tiles_off = kto;
-    d.kf_tiles = kt;
+    d.lin_kf_slot = kt;
     d.blk_tiles_off = bto;
-    d.blk_tiles = bt;
+    d.blk_part_at = bt;
     d.n_blk = n_blk;
     int32_t* ab;
     CK(dalloc(c, &ab, c->act_blk.size()), "alloc");

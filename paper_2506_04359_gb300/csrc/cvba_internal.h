@@ -23,8 +23,10 @@ constexpr int LIN_THREADS = 256;
 constexpr int SCHUR_THREADS = 256;
 constexpr int CHOL_THREADS = 1024;
 constexpr int DECIDE_THREADS = 256;
+constexpr int KDECIDE_THREADS = 1024;  // k_decide: many loads in flight over the tile partials
 constexpr int LIN_TILE_PAIRS = 256;     // pairs per linearisation / back-substitution tile
 constexpr int LIN_TILE_LMS = 256;       // landmarks per linearisation tile
+constexpr int LIN_TILE_OBS = 1024;      // observations a tile stages in shared memory (more: read in place)
 constexpr int SCHUR_TILE_PAIRS = 256;   // pairs staged in shared memory per Schur tile
 constexpr int SCHUR_TILE_LMS = 128;
 constexpr int SPAN_MAX = 22;            // free keyframes in one Schur tile's window (<= 253 blocks)
@@ -78,8 +80,10 @@ struct Ctrl {
 // back-substitution and evaluation.
 struct LinTile {
   int l0, l1, p0, p1;
-  int kf_lo, kf_n, part_off;   // keyframes [kf_lo, kf_lo + kf_n) touched; offset in kf_part
+  int kf_lo, kf_n, part_off;   // keyframes [kf_lo, kf_lo + kf_n) touched; part_off unused (-1)
   int kfl_off;                 // offset in lin_kf_off of this tile's kf_n + 1 list offsets
+  int o0, o1;                  // observations [o0, o1) of the tile's pairs
+  int kfi0, kfi_n;             // the tile's entries [kfi0, kfi0 + kfi_n) of lin_kf_idx
 };
 
 // Landmark range for the Schur kernel: pairs [p0, p1), off-diagonal block work items
@@ -140,14 +144,15 @@ struct Dev {
   // keyframe at or before the panel; the Cholesky fill stays inside this envelope)
   int16_t panel_end[kMaxPanels];
   // per-tile partials and the lists of tiles covering each keyframe / RCS block
-  double* kf_part;            // per lin tile: kf_n * 12 (g_p 6, diag Hpp 6); mixed: float (hi, lo) pairs
+  double* kf_part;            // keyframe-major slots of 12 (g_p 6, diag Hpp 6), one per covering lin
+                              // tile (kf_tiles_off); mixed: float (hi, lo) pairs
   const int32_t* lin_kf_off;  // per lin tile, per keyframe of its range: start in lin_kf_idx (kf_n + 1)
   const int32_t* lin_kf_idx;  // tile-local indices of each keyframe's free pairs, in pair order
+  const int32_t* lin_kf_slot; // per lin tile, per keyframe of its range: its slot in kf_part (kf_n + 1)
   double* schur_part;         // per Schur tile: window (rows (rows + 1) / 2) then b (rows)
-  const int32_t* kf_tiles_off;   // K + 1
-  const int32_t* kf_tiles;       // lin tiles covering each keyframe
+  const int32_t* kf_tiles_off;   // K + 1: each keyframe's slots in kf_part
   const int32_t* blk_tiles_off;  // n_blk + 1, blocks (a >= b) of free keyframes
-  const int32_t* blk_tiles;      // Schur tiles (non-direct) covering each block
+  const int32_t* blk_part_at;    // per block, per covering Schur tile: start of its 36 values in schur_part
   int n_blk;
   const int32_t* act_blk;        // blocks some tile touches, plus the diagonal ones
   int n_act;

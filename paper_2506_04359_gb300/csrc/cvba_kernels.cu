@@ -171,6 +171,31 @@ __device__ void block_sum_df(DF v[NV], double out[NV], float* red) {
   __syncthreads();
 }
 
+// As block_sum_df, but thread 0 gets the compensated (hi, lo) results themselves.
+template <int NV>
+__device__ void block_sum_df_pair(DF v[NV], DF out[NV], float* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum_df(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      red[(2 * k) * 32 + warp] = v[k].hi;
+      red[(2 * k + 1) * 32 + warp] = v[k].lo;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      DF x{lane < nw ? red[(2 * k) * 32 + lane] : 0.0f, lane < nw ? red[(2 * k + 1) * 32 + lane] : 0.0f};
+      out[k] = warp_sum_df(x);
+    }
+  }
+  __syncthreads();
+}
+
 // Fixed-order block sum of integer counts; thread 0 gets the result.  `red` >= 32 ints.
 __device__ int block_sum_i(int v, int* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -236,6 +261,37 @@ template <typename T> __device__ __forceinline__ const T* st_dc(const Dev& d);
 template <> __device__ __forceinline__ const double* st_dc<double>(const Dev& d) { return d.dc; }
 template <> __device__ __forceinline__ const float* st_dc<float>(const Dev& d) { return d.dc_f; }
 
+// A camera's rig record (fx fy cx cy | R_cb | t_cb) and a pose (R | t) by 16-byte loads
+// (records are 16-byte aligned in shared and global memory).
+__device__ __forceinline__ void load_rig16(const float* rg, float r[16]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 v = reinterpret_cast<const float4*>(rg)[k];
+    r[4 * k] = v.x; r[4 * k + 1] = v.y; r[4 * k + 2] = v.z; r[4 * k + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_rig16(const double* rg, double r[16]) {
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const double2 v = reinterpret_cast<const double2*>(rg)[k];
+    r[2 * k] = v.x; r[2 * k + 1] = v.y;
+  }
+}
+__device__ __forceinline__ void load_pose12(const float* P, float r[12]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 v = reinterpret_cast<const float4*>(P)[k];
+    r[4 * k] = v.x; r[4 * k + 1] = v.y; r[4 * k + 2] = v.z; r[4 * k + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_pose12(const double* P, double r[12]) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double2 v = reinterpret_cast<const double2*>(P)[k];
+    r[2 * k] = v.x; r[2 * k + 1] = v.y;
+  }
+}
+
 // Residuals of the observations [o0, o1) of one (landmark, keyframe) pair at pose P
 // and landmark pw; with JAC also the pair's camera-frame information M3 (sym 00 01 02 11
 // 12 22) and a3 = sum w A^T r, A = d pi(X_c) / d X_b = J_pi R_cb.
@@ -259,14 +315,13 @@ __device__ __forceinline__ void eval_pair(const T* __restrict__ P, const T* pw, 
     for (int k = 0; k < 3; ++k) a3[k] = 0;
   }
   for (int n = o0; n < o1; ++n) {
-    const T* rg = rig + obs_cam[n] * RIG_STRIDE;
-    const T fx = (T)rg[0], fy = (T)rg[1], cx = (T)rg[2], cy = (T)rg[3];
-    T Rc[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Rc[k] = (T)rg[4 + k];
-    const T xc = fma(Rc[0], X[0], fma(Rc[1], X[1], fma(Rc[2], X[2], (T)rg[13])));
-    const T yc = fma(Rc[3], X[0], fma(Rc[4], X[1], fma(Rc[5], X[2], (T)rg[14])));
-    const T zc = fma(Rc[6], X[0], fma(Rc[7], X[1], fma(Rc[8], X[2], (T)rg[15])));
+    T rg[16];
+    load_rig16(rig + obs_cam[n] * RIG_STRIDE, rg);
+    const T fx = rg[0], fy = rg[1], cx = rg[2], cy = rg[3];
+    const T* Rc = rg + 4;
+    const T xc = fma(Rc[0], X[0], fma(Rc[1], X[1], fma(Rc[2], X[2], rg[13])));
+    const T yc = fma(Rc[3], X[0], fma(Rc[4], X[1], fma(Rc[5], X[2], rg[14])));
+    const T zc = fma(Rc[6], X[0], fma(Rc[7], X[1], fma(Rc[8], X[2], rg[15])));
     if (!(zc > zmin)) continue;
     const T iz = (T)1 / zc;
     const T xn = xc * iz, yn = yc * iz;
@@ -500,11 +555,93 @@ __global__ void k_solve_init_b(const Dev* __restrict__ wins, double lam0, double
   solve_init_body(sd, lam0, huber, zmin, iters, reset, refine);
 }
 
+// ------------------------------------------------------------ tile staging
+// A linearisation tile's inputs are contiguous ranges (its pairs, their observations, its
+// landmarks' pair offsets), so a CTA copies them into shared memory with asynchronous copies
+// issued all at once: one memory latency per tile instead of a chain of dependent loads
+// (pair -> observation -> camera) per thread.  Tiles with more than LIN_TILE_OBS
+// observations read the observations in place.
+__device__ __forceinline__ void cpa4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cpa8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cpa16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cpa_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+// one element of T (4 or 8 bytes)
+template <typename T>
+__device__ __forceinline__ void cpa_t(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 4) cpa4(dst, src); else cpa8(dst, src);
+}
+
+// Staged tile inputs, at the start of the dynamic shared memory after 128 doubles of
+// reduction scratch: uv (2 LIN_TILE_OBS T), camera (LIN_TILE_OBS), pair keyframe and landmark
+// (LIN_TILE_PAIRS each), pair observation offsets (LIN_TILE_PAIRS + 1, absolute) and the
+// landmarks' pair offsets (LIN_TILE_LMS + 1, absolute).
+template <typename T>
+struct TileStage {
+  T* uv;
+  int *cam, *pkf, *plm, *pobs, *lmp;
+  char* end;                                   // first byte after the staging area (16-aligned)
+};
+template <typename T>
+__host__ __device__ constexpr size_t tile_stage_bytes() {
+  return sizeof(T) * 2 * LIN_TILE_OBS + sizeof(int) * (LIN_TILE_OBS + 2 * LIN_TILE_PAIRS + (LIN_TILE_PAIRS + 4) +
+                                                       (LIN_TILE_LMS + 4));
+}
+template <typename T>
+__device__ __forceinline__ TileStage<T> tile_stage(double* smem) {
+  TileStage<T> s;
+  s.uv = reinterpret_cast<T*>(smem + 128);
+  s.cam = reinterpret_cast<int*>(s.uv + 2 * LIN_TILE_OBS);
+  s.pkf = s.cam + LIN_TILE_OBS;
+  s.plm = s.pkf + LIN_TILE_PAIRS;
+  s.pobs = s.plm + LIN_TILE_PAIRS;
+  s.lmp = s.pobs + LIN_TILE_PAIRS + 4;
+  s.end = reinterpret_cast<char*>(s.lmp + LIN_TILE_LMS + 4);
+  return s;
+}
+// Issue the copies of the tile's pairs, landmark pair offsets and (if they fit) observations.
+template <typename T>
+__device__ __forceinline__ void stage_tile(const Dev& d, const LinTile& t, const TileStage<T>& s, bool obs) {
+  const int np = t.p1 - t.p0, nl = t.l1 - t.l0, no = t.o1 - t.o0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) {
+    cpa4(s.pkf + i, d.pair_kf + t.p0 + i);
+    cpa4(s.plm + i, d.pair_lm + t.p0 + i);
+  }
+  for (int i = threadIdx.x; i <= np; i += blockDim.x) cpa4(s.pobs + i, d.pair_obs + t.p0 + i);
+  for (int i = threadIdx.x; i <= nl; i += blockDim.x) cpa4(s.lmp + i, d.lm_pair + t.l0 + i);
+  if (obs) {
+    const T* uv = reinterpret_cast<const T*>(d.obs_uv);
+    for (int i = threadIdx.x; i < no; i += blockDim.x) {
+      cpa4(s.cam + i, d.obs_cam + t.o0 + i);
+      if constexpr (sizeof(T) == 4) cpa8(s.uv + 2 * i, uv + 2 * (size_t)(t.o0 + i));
+      else cpa16(s.uv + 2 * i, uv + 2 * (size_t)(t.o0 + i));
+    }
+  }
+}
+
 // ----------------------------------------------------------------- k_lin
 // Thread per (landmark, keyframe) pair; each pair writes its contributions to its own
 // shared-memory slot, then owner threads sum them in pair order (per landmark: its
 // contiguous pairs; per keyframe and component: the tile's pairs of that keyframe), so
-// there are no atomics and the sums are reproducible.
+// there are no atomics and the sums are reproducible.  The pair summaries leave through
+// shared memory as one contiguous store.
+template <typename T>
+__host__ __device__ constexpr size_t lin_smem_bytes(int C) {
+  return sizeof(double) * 128 + tile_stage_bytes<T>() +
+         sizeof(T) * ((size_t)C * RIG_STRIDE + LIN_TILE_PAIRS * (21 + PAIR_LIN) + LIN_TILE_LMS * 3) +
+         sizeof(int) * (2 * (K_MAX + 4) + LIN_TILE_PAIRS);
+}
 template <typename T>
 __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
   Ctrl* ctrl = d.ctrl;
@@ -512,33 +649,51 @@ __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
   extern __shared__ __align__(16) double smem[];
   const LinTile tile = d.lin_tiles[item];
   const int nl = tile.l1 - tile.l0, np = tile.p1 - tile.p0;
+  const bool obs_s = tile.o1 - tile.o0 <= LIN_TILE_OBS;
   double* s_red = smem;                                // 128
-  T* s_rig = reinterpret_cast<T*>(s_red + 128);        // C * 16
+  const TileStage<T> sg = tile_stage<T>(smem);
+  T* s_rig = reinterpret_cast<T*>(sg.end);             // C * 16
   T* s_pair = s_rig + d.C * RIG_STRIDE;                // LIN_TILE_PAIRS * 21
-  const T* rig = st_rig<T>(d);
-  for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = rig[i];
-  __syncthreads();
-
+  T* s_plin = s_pair + LIN_TILE_PAIRS * 21;            // LIN_TILE_PAIRS * PAIR_LIN
+  T* s_lm = s_plin + LIN_TILE_PAIRS * PAIR_LIN;        // LIN_TILE_LMS * 3
+  int* s_kfo = reinterpret_cast<int*>(s_lm + LIN_TILE_LMS * 3);   // kf_n + 1 (absolute)
+  int* s_kfs = s_kfo + K_MAX + 4;                      // kf_n: each keyframe's slot in kf_part
+  int* s_kfi = s_kfs + K_MAX + 4;                      // kfi_n
   const int cur = ctrl->cur;
   const T* pose = st_pose<T>(d, cur);
   const T* lmp = st_lm<T>(d, cur);
+  stage_tile<T>(d, tile, sg, obs_s);
+  for (int i = threadIdx.x; i < 3 * nl; i += blockDim.x) cpa_t<T>(s_lm + i, lmp + 3 * (size_t)tile.l0 + i);
+  for (int i = threadIdx.x; i <= tile.kf_n; i += blockDim.x) {
+    cpa4(s_kfo + i, d.lin_kf_off + tile.kfl_off + i);
+    cpa4(s_kfs + i, d.lin_kf_slot + tile.kfl_off + i);
+  }
+  for (int i = threadIdx.x; i < tile.kfi_n; i += blockDim.x) cpa4(s_kfi + i, d.lin_kf_idx + tile.kfi0 + i);
+  const T* rig = st_rig<T>(d);
+  for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = rig[i];
+  cpa_wait_all();
+  __syncthreads();
+
   const T hub = (T)ctrl->huber, zmin = (T)ctrl->zmin;
   PairStats<T> st;
   for (int qi = threadIdx.x; qi < np; qi += blockDim.x) {
-    const int q = tile.p0 + qi;
-    const int a = d.pair_kf[q], j = d.pair_lm[q];
-    T X[3], M3[6], a3[3];
-    eval_pair<T, true>(pose + a * POSE_STRIDE, lmp + 3 * j, d.pair_obs[q], d.pair_obs[q + 1], d.obs_cam,
-                       reinterpret_cast<const T*>(d.obs_uv), s_rig, hub, zmin, X, M3, a3, st);
-    T* pl = reinterpret_cast<T*>(d.pair_lin) + (size_t)q * PAIR_LIN;
+    const int a = sg.pkf[qi], jl = sg.plm[qi] - tile.l0;
+    T X[3], M3[6], a3[3], Pv[12];
+    load_pose12(pose + a * POSE_STRIDE, Pv);
+    if (obs_s)
+      eval_pair<T, true>(Pv, s_lm + 3 * jl, sg.pobs[qi] - tile.o0, sg.pobs[qi + 1] - tile.o0,
+                         sg.cam, sg.uv, s_rig, hub, zmin, X, M3, a3, st);
+    else
+      eval_pair<T, true>(Pv, s_lm + 3 * jl, sg.pobs[qi], sg.pobs[qi + 1], d.obs_cam,
+                         reinterpret_cast<const T*>(d.obs_uv), s_rig, hub, zmin, X, M3, a3, st);
+    T* pl = s_plin + qi * PAIR_LIN;
 #pragma unroll
     for (int k = 0; k < 6; ++k) pl[k] = M3[k];
 #pragma unroll
     for (int k = 0; k < 3; ++k) pl[6 + k] = X[k];
     // landmark block: J_lm = A R  ->  Hll += R^T M3 R, g_l += R^T a3
-    T R[9], M[9], G[9];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) R[k] = pose[a * POSE_STRIDE + k];
+    T M[9], G[9];
+    const T* R = Pv;
     sym3_full(M3, M);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
@@ -567,17 +722,16 @@ __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
     sl[19] = M3[0] * X[2] * X[2] - 2 * M3[2] * X[0] * X[2] + M3[5] * X[0] * X[0];
     sl[20] = M3[0] * X[1] * X[1] - 2 * M3[1] * X[0] * X[1] + M3[3] * X[0] * X[0];
   }
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {                  // mixed: (hi, lo) float pairs, summed by k_decide
     DF v[2] = {st.cost.df(), st.sq.df()};
-    double o[2];
-    block_sum_df<2>(v, o, reinterpret_cast<float*>(s_red));   // contains barriers: slots complete
+    DF o[2];
+    block_sum_df_pair<2>(v, o, reinterpret_cast<float*>(s_red));   // contains barriers: slots complete
     const int nv = block_sum_i(st.nv, reinterpret_cast<int*>(s_red));
     const int ni = block_sum_i(st.ni, reinterpret_cast<int*>(s_red));
     if (threadIdx.x == 0) {
-      d.lin_part[item * 4 + 0] = o[0];
-      d.lin_part[item * 4 + 1] = o[1];
-      d.lin_part[item * 4 + 2] = (double)nv;
-      d.lin_part[item * 4 + 3] = (double)ni;
+      float4* lp = reinterpret_cast<float4*>(d.lin_part + item * 4);
+      lp[0] = make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo);
+      lp[1] = make_float4((float)nv, 0.0f, (float)ni, 0.0f);
     }
   } else {
     double v[4] = {st.cost.value(), st.sq.value(), (double)st.nv, (double)st.ni};
@@ -587,39 +741,40 @@ __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
       for (int k = 0; k < 4; ++k) d.lin_part[item * 4 + k] = v[k];
     }
   }
-  // per landmark: sum of its pairs (contiguous, in order)
+  {                                                  // pair summaries: one contiguous store
+    T* out = reinterpret_cast<T*>(d.pair_lin) + (size_t)tile.p0 * PAIR_LIN;
+    for (int e = threadIdx.x; e < np * PAIR_LIN; e += blockDim.x) out[e] = s_plin[e];
+  }
+  // per landmark and value (Hll 6, g_l 3): sum of its pairs (contiguous, in order); one
+  // thread per (landmark, value), so the FP64 stores (and, on the mixed path, the FP32 -> FP64
+  // conversions, each a full FP64-pipe slot) spread over the CTA's warps
   T mx = 0;
-  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
-    const int j = tile.l0 + l;
-    Acc<T> h[9];
-    for (int q = d.lm_pair[j]; q < d.lm_pair[j + 1]; ++q)
-#pragma unroll
-      for (int k = 0; k < 9; ++k) h[k].add(s_pair[(q - tile.p0) * 21 + k]);
+  for (int e = threadIdx.x; e < nl * 9; e += blockDim.x) {
+    const int l = e / 9, k = e - 9 * l, j = tile.l0 + l;
+    Acc<T> h;
+    for (int q = sg.lmp[l]; q < sg.lmp[l + 1]; ++q) h.add(s_pair[(q - tile.p0) * 21 + k]);
+    const bool dg = k == 0 || k == 3 || k == 5;
     if constexpr (sizeof(T) == 4) {                  // FP32 inputs of the landmark blocks
-#pragma unroll
-      for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = (double)h[k].rounded();
-#pragma unroll
-      for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = (double)h[6 + k].rounded();
-      mx = fmaxf(mx, fmaxf(h[0].rounded(), fmaxf(h[3].rounded(), h[5].rounded())));
+      const float r = h.rounded();
+      if (k < 6) d.lm_H[j * 6 + k] = (double)r; else d.lm_g[j * 3 + k - 6] = (double)r;
+      if (dg) mx = fmaxf(mx, r);
     } else {
-#pragma unroll
-      for (int k = 0; k < 6; ++k) d.lm_H[j * 6 + k] = h[k].value();
-#pragma unroll
-      for (int k = 0; k < 3; ++k) d.lm_g[j * 3 + k] = h[6 + k].value();
-      mx = fmax(mx, fmax(h[0].value(), fmax(h[3].value(), h[5].value())));
+      const double r = h.value();
+      if (k < 6) d.lm_H[j * 6 + k] = r; else d.lm_g[j * 3 + k - 6] = r;
+      if (dg) mx = fmax(mx, r);
     }
   }
   // per keyframe and component: sum over this tile's pairs of that keyframe, in pair
   // order (the tile's pairs of each keyframe are listed in lin_kf_idx)
-  const int* koff = d.lin_kf_off + tile.kfl_off;
   for (int e = threadIdx.x; e < tile.kf_n * 12; e += blockDim.x) {
     const int ka = e / 12, comp = e % 12;
     Acc<T> sum;
-    for (int i = koff[ka]; i < koff[ka + 1]; ++i) sum.add(s_pair[d.lin_kf_idx[i] * 21 + 9 + comp]);
+    for (int i = s_kfo[ka]; i < s_kfo[ka + 1]; ++i) sum.add(s_pair[s_kfi[i - tile.kfi0] * 21 + 9 + comp]);
+    const size_t at = (size_t)s_kfs[ka] * 12 + comp;   // keyframe-major slot
     if constexpr (sizeof(T) == 4)
-      reinterpret_cast<float2*>(d.kf_part)[tile.part_off + e] = make_float2(sum.s, -sum.c);
+      reinterpret_cast<float2*>(d.kf_part)[at] = make_float2(sum.s, -sum.c);
     else
-      d.kf_part[tile.part_off + e] = sum.value();
+      d.kf_part[at] = sum.value();
   }
   double mxd;
   if constexpr (sizeof(T) == 4)
@@ -631,9 +786,8 @@ __device__ __forceinline__ void k_lin_body(const Dev& d, int item) {
 }
 
 template <typename T>
-// Mixed path: five CTAs per SM (48 registers, a few spilled) hide more of the per-pair
-// global-load latency than three without spills (about 20 % faster on a 4M-observation window).
-__global__ void __launch_bounds__(LIN_THREADS, sizeof(T) == 4 ? 5 : 1) k_lin(Dev d) { pdl_enter(); k_lin_body<T>(d, blockIdx.x); }
+// Mixed path: four CTAs per SM (the staged tile takes ~55 KB of shared memory at 32 cameras).
+__global__ void __launch_bounds__(LIN_THREADS, sizeof(T) == 4 ? 4 : 2) k_lin(Dev d) { pdl_enter(); k_lin_body<T>(d, blockIdx.x); }
 template <typename T>
 __global__ void __launch_bounds__(LIN_THREADS) k_lin_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
@@ -642,39 +796,62 @@ __global__ void __launch_bounds__(LIN_THREADS) k_lin_b(const Dev* __restrict__ w
   k_lin_body<T>(sd, it.y);
 }
 
-// g_p and diag(Hpp) of keyframe blockIdx.x: fixed-order sum of the covering tiles'
-// partials (lane l takes tiles l, l+32, ...; then a butterfly over the warp).
+// g_p and diag(Hpp) of keyframe `item`: fixed-order sum of the covering tiles' partials,
+// which are contiguous (keyframe-major slots of 12 values).  Thread t reads the values t + 384 i
+// (coalesced; its component is t mod 12, its slots t / 12 + 32 i) in eight interleaved sums
+// (i mod 8, combined pairwise); warp c then adds component c's 32 thread sums by a butterfly.
 __device__ __forceinline__ void k_kf_reduce_body(const Dev& d, int item) {
-  __shared__ int s_off[384];
-  const int a = item;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;   // warp = component (12)
-  const int t0 = d.kf_tiles_off[a], t1 = d.kf_tiles_off[a + 1];
-  double v = 0.0;
-  DF vf{0.0f, 0.0f};                                 // mixed: tile partials are (hi, lo) floats
+  __shared__ double s_v[384];
+  __shared__ DF s_vf[384];
+  const int a = item, tid = threadIdx.x;
+  const int n = (d.kf_tiles_off[a + 1] - d.kf_tiles_off[a]) * 12;
+  const size_t base = (size_t)d.kf_tiles_off[a] * 12;
   const bool mixed = d.mixed != 0;
-  for (int c0 = t0; c0 < t1; c0 += 384) {            // stage offsets of a chunk of tiles
-    const int nc = min(384, t1 - c0);
-    __syncthreads();
-    if (threadIdx.x < nc) {
-      const LinTile tl = d.lin_tiles[d.kf_tiles[c0 + threadIdx.x]];
-      s_off[threadIdx.x] = tl.part_off + (a - tl.kf_lo) * 12;
+  if (mixed) {                                       // tile partials are (hi, lo) floats
+    const float2* kp = reinterpret_cast<const float2*>(d.kf_part) + base;
+    DF s8[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s8[u] = DF{0.0f, 0.0f};
+    int t = tid;
+    for (; t + 7 * 384 < n; t += 8 * 384) {
+      float2 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = kp[t + 384 * u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s8[u] = df_add(s8[u], DF{x[u].x, x[u].y});
     }
-    __syncthreads();
-    if (mixed) {
-      const float2* kp = reinterpret_cast<const float2*>(d.kf_part);
-      for (int t = lane; t < nc; t += 32) {
-        const float2 x = kp[s_off[t] + warp];
-        vf = df_add(vf, DF{x.x, x.y});
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (t + 384 * u < n) {
+        const float2 x = kp[t + 384 * u];
+        s8[u] = df_add(s8[u], DF{x.x, x.y});
       }
-    } else {
-      for (int t = lane; t < nc; t += 32) v += d.kf_part[s_off[t] + warp];
-    }
-  }
-  if (mixed) {
-    vf = warp_sum_df(vf);
-    v = (double)vf.hi + (double)vf.lo;
+    s_vf[(tid % 12) * 32 + tid / 12] = df_add(df_add(df_add(s8[0], s8[1]), df_add(s8[2], s8[3])),
+                                              df_add(df_add(s8[4], s8[5]), df_add(s8[6], s8[7])));
   } else {
-    v = warp_sum(v);
+    const double* kp = d.kf_part + base;
+    double s8[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    int t = tid;
+    for (; t + 7 * 384 < n; t += 8 * 384) {
+      double x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = kp[t + 384 * u];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s8[u] += x[u];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (t + 384 * u < n) s8[u] += kp[t + 384 * u];
+    s_v[(tid % 12) * 32 + tid / 12] = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+  }
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31;        // warp = component (12)
+  double v;
+  if (mixed) {
+    const DF x = warp_sum_df(s_vf[warp * 32 + lane]);
+    v = (double)x.hi + (double)x.lo;
+  } else {
+    v = warp_sum(s_v[warp * 32 + lane]);
   }
   if (lane == 0) {
     if (warp < 6) {
@@ -1289,101 +1466,95 @@ __global__ void __launch_bounds__(group_threads<T>(), sizeof(T) == 4 ? 2 : 1)
 // of the window partials of the Schur tiles covering it, assigned (zero when no tile covers
 // it); the direct tiles' atomics are added after this kernel.
 __device__ __forceinline__ void k_rcs_reduce_body(const Dev& d, int item) {
-  __shared__ int s_off[256], s_klo[256];
+  // A covering tile's partial of block (a, b) is 36 consecutive values (two half blocks of
+  // 18, k_schur_group's layout) starting at blk_part_at[i].  Thread (g, e), g < 7, e < 36,
+  // sums value e over the covering tiles g, g + 7, ... (four interleaved sums, combined
+  // pairwise); the seven group sums are then added in order g = 0..6.
+  __shared__ double s_sum[7 * 36];
+  __shared__ DF s_sumf[7 * 36];
   const int blk = item;
   const int t0 = d.blk_tiles_off[blk], t1 = d.blk_tiles_off[blk + 1];
   int a = (int)((sqrtf(8.0f * (float)blk + 1.0f) - 1.0f) * 0.5f);
   while (a * (a + 1) / 2 > blk) --a;
   while ((a + 1) * (a + 2) / 2 <= blk) ++a;
   const int b = blk - a * (a + 1) / 2;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int n_ent = a == b ? 27 : 36;              // 21 lower entries + 6 of b, or 36
-  constexpr int kPer = 5;                          // entries per warp (8 warps x 5 >= 36)
-  double v[kPer] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  DF vf[kPer];                                       // mixed: partials are (hi, lo) floats
-#pragma unroll
-  for (int k = 0; k < kPer; ++k) vf[k] = DF{0.0f, 0.0f};
   const bool mixed = d.mixed != 0;
-  for (int c0 = t0; c0 < t1; c0 += 256) {          // stage a chunk of covering tiles
-    const int nc = min(256, t1 - c0);
-    __syncthreads();
-    if (threadIdx.x < nc) {
-      const SchurTile st = d.schur_tiles[d.blk_tiles[c0 + threadIdx.x]];
-      s_off[threadIdx.x] = st.part_off;
-      s_klo[threadIdx.x] = st.k_lo;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      const int e = warp + k * nw;
-      if (e >= n_ent) break;
-      int r, c;
-      bool is_b = false;
-      if (a != b) {
-        r = e / 6;
-        c = e % 6;
-      } else if (e < 21) {
-        r = 0;
-        while ((r + 1) * (r + 2) / 2 <= e) ++r;
-        c = e - r * (r + 1) / 2;
-      } else {
-        r = e - 21;
-        c = 0;
-        is_b = true;
-      }
-      for (int t = lane; t < nc; t += 32) {
-        // tile partial layout: [half block][18], half blocks 2 blk + h of the window's
-        // lower blocks (aa, bb) in row-major order (k_schur_group)
-        const int aa = a - s_klo[t], bb = b - s_klo[t];
-        const int hb0 = 2 * (aa * (aa + 1) / 2 + bb);
-        int idx;
-        if (is_b) {
-          idx = r < 3 ? hb0 * 18 + 6 + r : (hb0 + 1) * 18 + 15 + (r - 3);
-        } else if (a != b) {
-          idx = (hb0 + r / 3) * 18 + (r % 3) * 6 + c;
-        } else {
-          const int il = r * (r + 1) / 2 + c;
-          idx = il < 6 ? hb0 * 18 + il : (hb0 + 1) * 18 + (il - 6);
-        }
-        if (mixed) {
-          const DF x = reinterpret_cast<const DF*>(d.schur_part)[s_off[t] + idx];
-          vf[k] = df_add(vf[k], x);
-        } else {
-          v[k] += d.schur_part[s_off[t] + idx];
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < kPer; ++k) {
-    const int e = warp + k * nw;
-    if (e >= n_ent) break;
-    double sum;
+  const int g = threadIdx.x / 36, e = threadIdx.x % 36;
+  const int* at = d.blk_part_at;
+  if (g < 7) {
     if (mixed) {
-      const DF x = warp_sum_df(vf[k]);
-      sum = (double)x.hi + (double)x.lo;
-    } else {
-      sum = warp_sum(v[k]);
-    }
-    if (lane == 0) {
-      if (a == b && e >= 21) {
-        d.bS[6 * a + (e - 21)] = sum;
-      } else {
-        int r, c;
-        if (a != b) {
-          r = e / 6;
-          c = e % 6;
-        } else {
-          r = 0;
-          while ((r + 1) * (r + 2) / 2 <= e) ++r;
-          c = e - r * (r + 1) / 2;
-        }
-        const int gr = 6 * a + r, gc = 6 * b + c;  // both triangles: rows read contiguously
-        d.S[(size_t)gr * d.n_c + gc] = sum;
-        if (gr != gc) d.S[(size_t)gc * d.n_c + gr] = sum;
+      const DF* sp = reinterpret_cast<const DF*>(d.schur_part);
+      DF s4[4] = {DF{0.0f, 0.0f}, DF{0.0f, 0.0f}, DF{0.0f, 0.0f}, DF{0.0f, 0.0f}};
+      int t = t0 + g;
+      for (; t + 3 * 7 < t1; t += 4 * 7) {
+        DF x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = sp[at[t + 7 * u] + e];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s4[u] = df_add(s4[u], x[u]);
       }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (t + 7 * u < t1) s4[u] = df_add(s4[u], sp[at[t + 7 * u] + e]);
+      s_sumf[g * 36 + e] = df_add(df_add(s4[0], s4[1]), df_add(s4[2], s4[3]));
+    } else {
+      double s4[4] = {0.0, 0.0, 0.0, 0.0};
+      int t = t0 + g;
+      for (; t + 3 * 7 < t1; t += 4 * 7) {
+        double x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[u] = d.schur_part[at[t + 7 * u] + e];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s4[u] += x[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (t + 7 * u < t1) s4[u] += d.schur_part[at[t + 7 * u] + e];
+      s_sum[g * 36 + e] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
   }
+  __syncthreads();
+  if (threadIdx.x >= 36) return;
+  double sum;
+  if (mixed) {
+    DF x = s_sumf[e];
+#pragma unroll
+    for (int k = 1; k < 7; ++k) x = df_add(x, s_sumf[k * 36 + e]);
+    sum = (double)x.hi + (double)x.lo;
+  } else {
+    sum = s_sum[e];
+#pragma unroll
+    for (int k = 1; k < 7; ++k) sum += s_sum[k * 36 + e];
+  }
+  // value e -> entry: off-diagonal blocks row-major (r = e / 6, c = e % 6); diagonal blocks
+  // [lower entries of rows 0-2 (6), b rows 0-2 (3), unused (9) | lower entries of rows 3-5
+  // (15), b rows 3-5 (3)], lower entry il = r (r + 1) / 2 + c
+  int r, c;
+  if (a != b) {
+    r = e / 6;
+    c = e % 6;
+  } else {
+    int il;
+    if (e < 6) {
+      il = e;
+    } else if (e < 9) {
+      d.bS[6 * a + (e - 6)] = sum;
+      return;
+    } else if (e < 18) {
+      return;
+    } else if (e < 33) {
+      il = 6 + (e - 18);
+    } else {
+      d.bS[6 * a + 3 + (e - 33)] = sum;
+      return;
+    }
+    r = 0;
+    while ((r + 1) * (r + 2) / 2 <= il) ++r;
+    c = il - r * (r + 1) / 2;
+  }
+  const int gr = 6 * a + r, gc = 6 * b + c;          // both triangles: rows read contiguously
+  d.S[(size_t)gr * d.n_c + gc] = sum;
+  if (gr != gc) d.S[(size_t)gc * d.n_c + gr] = sum;
 }
 
 __global__ void __launch_bounds__(256) k_rcs_reduce(Dev d) { pdl_enter(); k_rcs_reduce_body(d, d.act_blk[blockIdx.x]); }
@@ -2568,6 +2739,11 @@ __global__ void __launch_bounds__(256) k_blk_load(Dev d) { pdl_enter();
 
 // --------------------------------------------------------------- k_backsub
 template <typename T>
+__host__ __device__ constexpr size_t backsub_smem_bytes(int C) {
+  return sizeof(double) * 128 + tile_stage_bytes<T>() +
+         sizeof(T) * ((size_t)C * RIG_STRIDE + LIN_TILE_PAIRS * (3 + PAIR_LIN) + LIN_TILE_LMS * 3);
+}
+template <typename T>
 __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
   extern __shared__ __align__(16) double smem[];
   Ctrl* ctrl = d.ctrl;
@@ -2576,28 +2752,37 @@ __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
     if (threadIdx.x < 4) d.bs_part[item * 4 + threadIdx.x] = 0.0;
     return;
   }
-  const int nl = tile.l1 - tile.l0;
+  const int nl = tile.l1 - tile.l0, np = tile.p1 - tile.p0;
+  const bool obs_s = tile.o1 - tile.o0 <= LIN_TILE_OBS;
   double* s_red = smem;                              // 128
-  T* s_rig = reinterpret_cast<T*>(s_red + 128);      // C * 16
+  const TileStage<T> sg = tile_stage<T>(smem);
+  T* s_rig = reinterpret_cast<T*>(sg.end);           // C * 16
   T* s_acc = s_rig + d.C * RIG_STRIDE;               // LIN_TILE_PAIRS * 3 (per pair slots)
-  T* s_new = s_acc + LIN_TILE_PAIRS * 3;             // LIN_TILE_LMS * 3
+  T* s_plin = s_acc + LIN_TILE_PAIRS * 3;            // LIN_TILE_PAIRS * PAIR_LIN
+  T* s_new = s_plin + LIN_TILE_PAIRS * PAIR_LIN;     // LIN_TILE_LMS * 3
+  stage_tile<T>(d, tile, sg, obs_s);
+  {
+    const T* pl = reinterpret_cast<const T*>(d.pair_lin) + (size_t)tile.p0 * PAIR_LIN;
+    for (int e = threadIdx.x; e < np * PAIR_LIN; e += blockDim.x) cpa_t<T>(s_plin + e, pl + e);
+  }
   const T* rig = st_rig<T>(d);
   for (int i = threadIdx.x; i < d.C * RIG_STRIDE; i += blockDim.x) s_rig[i] = rig[i];
+  cpa_wait_all();
   const double lam = ctrl->lam;
   const double floor_ = diag_floor(d, s_red);   // contains __syncthreads
   const int cur = ctrl->cur;
   const T* pose = st_pose<T>(d, cur);
   const T* dcT = st_dc<T>(d);
   // phase 1: W_ja^T dc_a = R_a^T M3 (rho + phi x X) accumulated per landmark
-  for (int q = tile.p0 + threadIdx.x; q < tile.p1; q += blockDim.x) {
-    const int a = d.pair_kf[q];
+  for (int qi = threadIdx.x; qi < np; qi += blockDim.x) {
+    const int a = sg.pkf[qi];
     const int pb = d.kf_pb[a];
-    T* acc = s_acc + (q - tile.p0) * 3;
+    T* acc = s_acc + qi * 3;
     if (pb < 0) {
       acc[0] = acc[1] = acc[2] = 0;
       continue;
     }
-    const T* pl = reinterpret_cast<const T*>(d.pair_lin) + (size_t)q * PAIR_LIN;
+    const T* pl = s_plin + qi * PAIR_LIN;
     const T* xi = dcT + 6 * pb;
     T X[3] = {pl[6], pl[7], pl[8]};
     T u[3];
@@ -2614,110 +2799,102 @@ __device__ __forceinline__ void k_backsub_body(const Dev& d, int item) {
     T w3[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) w3[r] = M[r * 3] * u[0] + M[r * 3 + 1] * u[1] + M[r * 3 + 2] * u[2];
-    const T* R = pose + a * POSE_STRIDE;
+    T R[12];
+    load_pose12(pose + a * POSE_STRIDE, R);
 #pragma unroll
     for (int c = 0; c < 3; ++c) acc[c] = R[c] * w3[0] + R[3 + c] * w3[1] + R[6 + c] * w3[2];
   }
   __syncthreads();
   // phase 2: dp_j = -V_j^-1 (g_l + acc); candidate landmark; predicted-reduction part
   // (FP64 path: in FP64; mixed path: in FP32 with compensated sums, the new landmark
-  // position in FP64)
+  // position in FP64).  Thread per (landmark, component c): each forms the three sums
+  // g_l + acc, then its row of V_j^-1 and its components of dp_j, the candidate and the
+  // predicted reduction (spreading the FP64 work over the CTA's warps).
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   Acc<float> lp_f, st2_f;
-  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
-    const int j = tile.l0 + l;
+  for (int e = threadIdx.x; e < nl * 3; e += blockDim.x) {
+    const int l = e / 3, c = e - 3 * l, j = tile.l0 + l;
     Acc<T> w0, w1, w2;
-    for (int q = d.lm_pair[j]; q < d.lm_pair[j + 1]; ++q) {
+    for (int q = sg.lmp[l]; q < sg.lmp[l + 1]; ++q) {
       const T* acc = s_acc + (q - tile.p0) * 3;
       w0.add(acc[0]);
       w1.add(acc[1]);
       w2.add(acc[2]);
     }
-    const double* p = d.lm[cur] + 3 * j;
-    double* pn = d.lm[cur ^ 1] + 3 * j;
-    double n0, n1, n2;
+    // row c of the symmetric V^-1 (00 01 02 11 12 22)
+    const int i0 = c == 0 ? 0 : (c == 1 ? 1 : 2), i1 = c == 0 ? 1 : (c == 1 ? 3 : 4), i2 = c == 0 ? 2 : (c == 1 ? 4 : 5);
+    const int hd = c == 0 ? 0 : (c == 1 ? 3 : 5);
+    double ec;
     if constexpr (sizeof(T) == 4) {
       const float* Vi = reinterpret_cast<const float*>(d.lm_Vinv) + VINV_STRIDE * j;
       const float tau = Vi[6];
       const float g0 = (float)d.lm_g[3 * j], g1 = (float)d.lm_g[3 * j + 1], g2 = (float)d.lm_g[3 * j + 2];
       const float t0 = g0 + w0.rounded(), t1 = g1 + w1.rounded(), t2 = g2 + w2.rounded();
-      const float dp0 = -(Vi[0] * t0 + Vi[1] * t1 + Vi[2] * t2);
-      const float dp1 = -(Vi[1] * t0 + Vi[3] * t1 + Vi[4] * t2);
-      const float dp2 = -(Vi[2] * t0 + Vi[4] * t1 + Vi[5] * t2);
-      const double* H = d.lm_H + 6 * j;
+      const float dpc = -(Vi[i0] * t0 + Vi[i1] * t1 + Vi[i2] * t2);
+      const float gc = c == 0 ? g0 : (c == 1 ? g1 : g2);
       const float lamf = (float)lam, fl = (float)floor_;
-      const float D0 = fmaxf((float)H[0], fl), D1 = fmaxf((float)H[3], fl), D2 = fmaxf((float)H[5], fl);
-      lp_f.add(dp0 * ((lamf * D0 + tau) * dp0 - g0) + dp1 * ((lamf * D1 + tau) * dp1 - g1) +
-               dp2 * ((lamf * D2 + tau) * dp2 - g2));
-      st2_f.add(dp0 * dp0 + dp1 * dp1 + dp2 * dp2);
-      const double e0 = dp0, e1 = dp1, e2 = dp2;
-      d.dp[j * 3] = e0;
-      d.dp[j * 3 + 1] = e1;
-      d.dp[j * 3 + 2] = e2;
-      n0 = p[0] + e0;
-      n1 = p[1] + e1;
-      n2 = p[2] + e2;
+      const float Dc = fmaxf((float)d.lm_H[6 * j + hd], fl);
+      lp_f.add(dpc * ((lamf * Dc + tau) * dpc - gc));
+      st2_f.add(dpc * dpc);
+      ec = dpc;
     } else {
       const double* Vi = d.lm_Vinv + VINV_STRIDE * j;
       const double tau = Vi[6];
       const double* g = d.lm_g + 3 * j;
       const double t0 = g[0] + w0.value(), t1 = g[1] + w1.value(), t2 = g[2] + w2.value();
-      const double dp0 = -(Vi[0] * t0 + Vi[1] * t1 + Vi[2] * t2);
-      const double dp1 = -(Vi[1] * t0 + Vi[3] * t1 + Vi[4] * t2);
-      const double dp2 = -(Vi[2] * t0 + Vi[4] * t1 + Vi[5] * t2);
-      const double* H = d.lm_H + 6 * j;
-      const double D0 = fmax(H[0], floor_), D1 = fmax(H[3], floor_), D2 = fmax(H[5], floor_);
-      v[1] += dp0 * ((lam * D0 + tau) * dp0 - g[0]) + dp1 * ((lam * D1 + tau) * dp1 - g[1]) +
-              dp2 * ((lam * D2 + tau) * dp2 - g[2]);
-      v[2] += dp0 * dp0 + dp1 * dp1 + dp2 * dp2;
-      d.dp[j * 3] = dp0;
-      d.dp[j * 3 + 1] = dp1;
-      d.dp[j * 3 + 2] = dp2;
-      n0 = p[0] + dp0;
-      n1 = p[1] + dp1;
-      n2 = p[2] + dp2;
+      const double dpc = -(Vi[i0] * t0 + Vi[i1] * t1 + Vi[i2] * t2);
+      const double Dc = fmax(d.lm_H[6 * j + hd], floor_);
+      v[1] += dpc * ((lam * Dc + tau) * dpc - g[c]);
+      v[2] += dpc * dpc;
+      ec = dpc;
     }
-    pn[0] = n0; pn[1] = n1; pn[2] = n2;
-    const T m0 = (T)n0, m1 = (T)n1, m2 = (T)n2;
-    s_new[l * 3] = m0; s_new[l * 3 + 1] = m1; s_new[l * 3 + 2] = m2;
-    if constexpr (sizeof(T) == 4) {
-      float* pf = d.lm_f[cur ^ 1] + 3 * j;
-      pf[0] = m0; pf[1] = m1; pf[2] = m2;
-    }
+    d.dp[j * 3 + c] = ec;
+    const double nc = d.lm[cur][3 * j + c] + ec;
+    d.lm[cur ^ 1][3 * j + c] = nc;
+    const T mc = (T)nc;
+    s_new[l * 3 + c] = mc;
+    if constexpr (sizeof(T) == 4) d.lm_f[cur ^ 1][3 * j + c] = mc;
   }
   __syncthreads();
   // phase 3: candidate cost, same arithmetic and order as k_lin's cost
   const T* pnew = st_pose<T>(d, cur ^ 1);
   const T hub = (T)ctrl->huber, zmin = (T)ctrl->zmin;
   PairStats<T> st;
-  for (int q = tile.p0 + threadIdx.x; q < tile.p1; q += blockDim.x) {
-    const int a = d.pair_kf[q], j = d.pair_lm[q];
-    T X[3];
-    eval_pair<T, false>(pnew + a * POSE_STRIDE, s_new + 3 * (j - tile.l0), d.pair_obs[q], d.pair_obs[q + 1],
-                        d.obs_cam, reinterpret_cast<const T*>(d.obs_uv), s_rig, hub, zmin, X, nullptr, nullptr, st);
+  for (int qi = threadIdx.x; qi < np; qi += blockDim.x) {
+    const int a = sg.pkf[qi], jl = sg.plm[qi] - tile.l0;
+    T X[3], Pv[12];
+    load_pose12(pnew + a * POSE_STRIDE, Pv);
+    if (obs_s)
+      eval_pair<T, false>(Pv, s_new + 3 * jl, sg.pobs[qi] - tile.o0, sg.pobs[qi + 1] - tile.o0,
+                          sg.cam, sg.uv, s_rig, hub, zmin, X, nullptr, nullptr, st);
+    else
+      eval_pair<T, false>(Pv, s_new + 3 * jl, sg.pobs[qi], sg.pobs[qi + 1], d.obs_cam,
+                          reinterpret_cast<const T*>(d.obs_uv), s_rig, hub, zmin, X, nullptr, nullptr, st);
   }
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {                  // mixed: (hi, lo) float pairs, summed by k_decide
     DF f[3] = {st.cost.df(), lp_f.df(), st2_f.df()};
-    double o[3];
-    block_sum_df<3>(f, o, reinterpret_cast<float*>(s_red));
-    v[0] = o[0];
-    v[1] = o[1];
-    v[2] = o[2];
+    DF o[3];
+    block_sum_df_pair<3>(f, o, reinterpret_cast<float*>(s_red));
+    if (threadIdx.x == 0) {
+      float4* bp = reinterpret_cast<float4*>(d.bs_part + item * 4);
+      bp[0] = make_float4(o[0].hi, o[0].lo, o[1].hi, o[1].lo);
+      bp[1] = make_float4(o[2].hi, o[2].lo, 0.0f, 0.0f);
+    }
   } else {
     v[0] = st.cost.value();
     block_sum4(v, s_red);
-  }
-  if (threadIdx.x == 0) {
-    d.bs_part[item * 4 + 0] = v[0];
-    d.bs_part[item * 4 + 1] = v[1];
-    d.bs_part[item * 4 + 2] = v[2];
-    d.bs_part[item * 4 + 3] = 0.0;
+    if (threadIdx.x == 0) {
+      d.bs_part[item * 4 + 0] = v[0];
+      d.bs_part[item * 4 + 1] = v[1];
+      d.bs_part[item * 4 + 2] = v[2];
+      d.bs_part[item * 4 + 3] = 0.0;
+    }
   }
 }
 
 template <typename T>
-// Mixed path: seven CTAs per SM (32 registers), likewise latency-bound (about 12 % faster).
-__global__ void __launch_bounds__(LIN_THREADS, sizeof(T) == 4 ? 7 : 1) k_backsub(Dev d) { pdl_enter(); k_backsub_body<T>(d, blockIdx.x); }
+// Mixed path: six CTAs per SM (the staged tile takes ~34 KB of shared memory at 32 cameras).
+__global__ void __launch_bounds__(LIN_THREADS, sizeof(T) == 4 ? 6 : 1) k_backsub(Dev d) { pdl_enter(); k_backsub_body<T>(d, blockIdx.x); }
 template <typename T>
 __global__ void __launch_bounds__(LIN_THREADS) k_backsub_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
@@ -2742,18 +2919,85 @@ __device__ void reduce_parts(const double* part, int n_tiles, double out[4], dou
 
 __device__ __forceinline__ void k_decide_body(const Dev& d, int item) {
   __shared__ double s_red[128];
+  __shared__ double s_sum[8 * 256];
+  __shared__ DF s_sumf[8 * 256];
   Ctrl* ctrl = d.ctrl;
-  // fixed-order sums of the tile partials: warp w < 7 takes value w (lin: cost, sum r^2,
-  // n_valid, n_inlier; candidate: cost, L part, |dp|^2), lane l the tiles l, l + 32, ...
-  // then a butterfly; the warps run on all four sub-partitions at once
+  // fixed-order sums of the tile partials.  A tile's four partials are two 16-byte halves
+  // (lin: (cost, sum r^2), (n_valid, n_inlier); candidate: (cost, L part), (|dp|^2, 0)).
+  // Thread t (1024) takes array t / 512 and half t % 2 of the tiles (t % 512) / 2 + 256 i,
+  // loading them coalesced, eight at a time, into four interleaved sums per value (combined
+  // pairwise); warp w < 8 then adds the 256 thread sums of value w in a fixed order.  The
+  // mixed path's partials are (hi, lo) float pairs summed as such: on GB300 an FP64 add holds
+  // a sub-partition's FP64 pipe for ~64 cycles per warp instruction.
   {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < 7) {
-      const double* part = warp < 4 ? d.lin_part : d.bs_part;
-      const int k = warp < 4 ? warp : warp - 4;
-      double v = 0.0;
-      for (int t = lane; t < d.n_lin_tiles; t += 32) v += part[t * 4 + k];
-      v = warp_sum(v);
+    const int tid = threadIdx.x, arr = tid >> 9, u = tid & 511, half = u & 1, r0 = u >> 1;
+    const int n = d.n_lin_tiles;
+    const int slot = (arr * 2 + half) * 2;           // values slot, slot + 1 of s_sum*
+    if (d.mixed) {
+      const float4* part = reinterpret_cast<const float4*>(arr == 0 ? d.lin_part : d.bs_part);
+      DF a0[4], a1[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) a0[k] = a1[k] = DF{0.0f, 0.0f};
+      int r = r0;
+      for (; r + 7 * 256 < n; r += 8 * 256) {
+        float4 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = part[(r + 256 * k) * 2 + half];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          a0[k & 3] = df_add(a0[k & 3], DF{x[k].x, x[k].y});
+          a1[k & 3] = df_add(a1[k & 3], DF{x[k].z, x[k].w});
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (r + 256 * k < n) {
+          const float4 x = part[(r + 256 * k) * 2 + half];
+          a0[k & 3] = df_add(a0[k & 3], DF{x.x, x.y});
+          a1[k & 3] = df_add(a1[k & 3], DF{x.z, x.w});
+        }
+      s_sumf[slot * 256 + r0] = df_add(df_add(a0[0], a0[1]), df_add(a0[2], a0[3]));
+      s_sumf[(slot + 1) * 256 + r0] = df_add(df_add(a1[0], a1[1]), df_add(a1[2], a1[3]));
+    } else {
+      const double2* part = reinterpret_cast<const double2*>(arr == 0 ? d.lin_part : d.bs_part);
+      double a0[4] = {0.0, 0.0, 0.0, 0.0}, a1[4] = {0.0, 0.0, 0.0, 0.0};
+      int r = r0;
+      for (; r + 7 * 256 < n; r += 8 * 256) {
+        double2 x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = part[(r + 256 * k) * 2 + half];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          a0[k & 3] += x[k].x;
+          a1[k & 3] += x[k].y;
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (r + 256 * k < n) {
+          const double2 x = part[(r + 256 * k) * 2 + half];
+          a0[k & 3] += x.x;
+          a1[k & 3] += x.y;
+        }
+      s_sum[slot * 256 + r0] = (a0[0] + a0[1]) + (a0[2] + a0[3]);
+      s_sum[(slot + 1) * 256 + r0] = (a1[0] + a1[1]) + (a1[2] + a1[3]);
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    if (warp < 8) {                                  // value warp: lin 0-3, candidate 4-7
+      double v;
+      if (d.mixed) {
+        DF x = s_sumf[warp * 256 + lane];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) x = df_add(x, s_sumf[warp * 256 + lane + 32 * k]);
+        x = warp_sum_df(x);
+        v = (double)x.hi + (double)x.lo;
+      } else {
+        double x = s_sum[warp * 256 + lane];
+#pragma unroll
+        for (int k = 1; k < 8; ++k) x += s_sum[warp * 256 + lane + 32 * k];
+        v = warp_sum(x);
+      }
       if (lane == 0) s_red[warp] = v;
     }
   }
@@ -2816,8 +3060,8 @@ __device__ __forceinline__ void k_decide_body(const Dev& d, int item) {
   }
 }
 
-__global__ void __launch_bounds__(DECIDE_THREADS) k_decide(Dev d) { pdl_enter(); k_decide_body(d, blockIdx.x); }
-__global__ void __launch_bounds__(DECIDE_THREADS) k_decide_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
+__global__ void __launch_bounds__(KDECIDE_THREADS) k_decide(Dev d) { pdl_enter(); k_decide_body(d, blockIdx.x); }
+__global__ void __launch_bounds__(KDECIDE_THREADS) k_decide_b(const Dev* __restrict__ wins, const int2* __restrict__ items) { pdl_enter();
   __shared__ Dev sd;
   const int2 it = items[blockIdx.x];
   load_dev(sd, wins + it.x);
@@ -2888,12 +3132,8 @@ __global__ void k_state_io(Dev d, int mode, double* user, const int32_t* lm_orde
 }
 
 size_t tsize(const Dev& d) { return d.mixed ? sizeof(float) : sizeof(double); }
-size_t lin_smem(const Dev& d) {
-  return sizeof(double) * 128 + tsize(d) * (d.C * RIG_STRIDE + LIN_TILE_PAIRS * 21) + sizeof(int) * LIN_TILE_PAIRS;
-}
-size_t backsub_smem(const Dev& d) {
-  return sizeof(double) * 128 + tsize(d) * (d.C * RIG_STRIDE + LIN_TILE_PAIRS * 3 + LIN_TILE_LMS * 3);
-}
+size_t lin_smem(const Dev& d) { return d.mixed ? lin_smem_bytes<float>(d.C) : lin_smem_bytes<double>(d.C); }
+size_t backsub_smem(const Dev& d) { return d.mixed ? backsub_smem_bytes<float>(d.C) : backsub_smem_bytes<double>(d.C); }
 size_t eval_smem(const Dev& d) { return sizeof(double) * 128 + tsize(d) * d.C * RIG_STRIDE; }
 constexpr int kCholSmemMaxN = 160;
 size_t chol_smem(int n) { return sizeof(double) * ((size_t)n * n + n); }
@@ -3076,7 +3316,7 @@ cudaError_t enqueue_iteration(const Dev& d, cudaStream_t s, cudaEvent_t* ev, con
     { if ((e = launch_ex(k_backsub<double>, dim3(d.n_lin_tiles), dim3(LIN_THREADS), backsub_smem(d), s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = mark(7)) != cudaSuccess) return e;
-  { if ((e = launch_ex(k_decide, dim3(1), dim3(DECIDE_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
+  { if ((e = launch_ex(k_decide, dim3(1), dim3(KDECIDE_THREADS), 0, s, 0, d)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return mark(8);
 }
@@ -3159,7 +3399,7 @@ cudaError_t enqueue_batch_iteration(const BatchLaunch& b, cudaStream_t s) {
   else
     { if ((e = launch_ex(k_backsub_b<double>, dim3(b.n_lin), dim3(LIN_THREADS), b.backsub_smem, s, 0, b.wins, b.lin_items)) != cudaSuccess) return e; }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  { if ((e = launch_ex(k_decide_b, dim3(b.n_win), dim3(DECIDE_THREADS), 0, s, 0, b.wins, b.win_items)) != cudaSuccess) return e; }
+  { if ((e = launch_ex(k_decide_b, dim3(b.n_win), dim3(KDECIDE_THREADS), 0, s, 0, b.wins, b.win_items)) != cudaSuccess) return e; }
   return cudaGetLastError();
 }
 
