@@ -274,8 +274,10 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   c->direct_tiles.clear();
   int max_span = 1;
   {
+    // default: at most 96 landmarks per tile (at 100 keyframes x 32 cameras, 96 against 128:
+    // group Schur 367 against 381 us, reduction 25 against 22 us)
     const int target = c->tune_schur_lms > 0 ? std::min(SCHUR_TILE_LMS, c->tune_schur_lms)
-                                             : std::max(8, std::min(SCHUR_TILE_LMS, (M + n_sm - 1) / n_sm));
+                                             : std::max(8, std::min(96, (M + n_sm - 1) / n_sm));
     std::vector<int> lo(M, INT32_MAX), hi(M, -1);
     for (int j = 0; j < M; ++j)
       for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
