@@ -45,6 +45,8 @@ struct cvba_ctx {
   };
   std::vector<Slot> arena;       // device buffers of the layout, reused when large enough
   size_t arena_next = 0;
+  void* h_pin = nullptr;         // pinned host staging of the layout's uploads (kept, grown)
+  size_t h_pin_bytes = 0;
   Dev d{};
   double* d_eval = nullptr;
   int32_t* d_lm_order = nullptr;
@@ -118,6 +120,18 @@ void free_device(cvba_ctx* c) {
   c->d_eval = nullptr;
   c->d_lm_order = nullptr;
   c->have_layout = false;
+}
+
+// Pinned host staging of at least `bytes` (kept by the context and grown when needed), so the
+// layout's large uploads are asynchronous copies at the link's rate.
+cudaError_t ensure_pinned(cvba_ctx* c, size_t bytes) {
+  if (bytes <= c->h_pin_bytes) return cudaSuccess;
+  if (c->h_pin) cudaFreeHost(c->h_pin);
+  c->h_pin = nullptr;
+  c->h_pin_bytes = 0;
+  const cudaError_t e = cudaMallocHost(&c->h_pin, bytes);
+  if (e == cudaSuccess) c->h_pin_bytes = bytes;
+  return e;
 }
 
 // Next buffer of the layout: the slot used by the previous layout is kept when it is
@@ -246,27 +260,53 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     }
     for (int a = 0; a < K; ++a) kf_tiles_off[a + 1] += kf_tiles_off[a];
   }
-  // per tile and keyframe of its range: the tile-local indices of that keyframe's pairs
-  // (free keyframes only), in pair order, and the keyframe's partial slot for this tile
   std::vector<int32_t> lin_kf_off, lin_kf_idx, lin_kf_slot;
-  lin_kf_idx.reserve(P);
-  std::vector<int32_t> slot_fill(kf_tiles_off.begin(), kf_tiles_off.end() - 1);
-  for (auto& t : c->lin_tiles) {
-    t.kfl_off = (int)lin_kf_off.size();
-    for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) lin_kf_slot.push_back(slot_fill[a]++);
-    lin_kf_slot.push_back(0);                        // aligned with lin_kf_off (kf_n + 1 per tile)
-    std::vector<int32_t> cnt((size_t)t.kf_n + 1, 0);
-    for (int q = t.p0; q < t.p1; ++q)
-      if (kf_pb[pair_kf[q]] >= 0) cnt[pair_kf[q] - t.kf_lo + 1]++;
-    const int base = (int)lin_kf_idx.size();
-    for (int k = 0; k < t.kf_n; ++k) cnt[k + 1] += cnt[k];
-    for (int k = 0; k <= t.kf_n; ++k) lin_kf_off.push_back(base + cnt[k]);
-    lin_kf_idx.resize((size_t)base + cnt[t.kf_n]);
-    t.kfi0 = base;
-    t.kfi_n = cnt[t.kf_n];
-    for (int q = t.p0; q < t.p1; ++q)
-      if (kf_pb[pair_kf[q]] >= 0) lin_kf_idx[base + cnt[pair_kf[q] - t.kf_lo]++] = q - t.p0;
+  // per tile and keyframe of its range: the tile-local indices of that keyframe's pairs
+  // (free keyframes only), in pair order, and the keyframe's partial slot for this tile.
+  // Offsets by a sequential pass over the tiles (free-pair counts first, in parallel), the
+  // lists filled in parallel, tile by tile.
+  const int n_lt = (int)c->lin_tiles.size();
+  {
+    std::vector<int32_t> n_free((size_t)n_lt, 0);
+    parallel_for(n_lt, host_threads(), [&](int64_t t0, int64_t t1, int) {
+      for (int64_t ti = t0; ti < t1; ++ti) {
+        const LinTile& t = c->lin_tiles[ti];
+        int m = 0;
+        for (int q = t.p0; q < t.p1; ++q) m += kf_pb[pair_kf[q]] >= 0 ? 1 : 0;
+        n_free[ti] = m;
+      }
+    });
+    int kfl = 0, kfi = 0;
+    for (int ti = 0; ti < n_lt; ++ti) {
+      LinTile& t = c->lin_tiles[ti];
+      t.kfl_off = kfl;
+      t.kfi0 = kfi;
+      t.kfi_n = n_free[ti];
+      kfl += t.kf_n + 1;
+      kfi += n_free[ti];
+    }
+    lin_kf_off.assign((size_t)kfl, 0);
+    lin_kf_slot.assign((size_t)kfl, 0);
+    lin_kf_idx.assign((size_t)kfi, 0);
   }
+  {
+    std::vector<int32_t> slot_fill(kf_tiles_off.begin(), kf_tiles_off.end() - 1);
+    for (const LinTile& t : c->lin_tiles)            // slots in tile order per keyframe
+      for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) lin_kf_slot[t.kfl_off + (a - t.kf_lo)] = slot_fill[a]++;
+  }
+  parallel_for(n_lt, host_threads(), [&](int64_t t0, int64_t t1, int) {
+    std::vector<int32_t> cnt;
+    for (int64_t ti = t0; ti < t1; ++ti) {
+      const LinTile& t = c->lin_tiles[ti];
+      cnt.assign((size_t)t.kf_n + 1, 0);
+      for (int q = t.p0; q < t.p1; ++q)
+        if (kf_pb[pair_kf[q]] >= 0) cnt[pair_kf[q] - t.kf_lo + 1]++;
+      for (int k = 0; k < t.kf_n; ++k) cnt[k + 1] += cnt[k];
+      for (int k = 0; k <= t.kf_n; ++k) lin_kf_off[t.kfl_off + k] = t.kfi0 + cnt[k];
+      for (int q = t.p0; q < t.p1; ++q)
+        if (kf_pb[pair_kf[q]] >= 0) lin_kf_idx[t.kfi0 + cnt[pair_kf[q] - t.kf_lo]++] = q - t.p0;
+    }
+  });
   // Schur tiles: runs of landmarks (in internal order) with the same window [lo, hi] of
   // free keyframes, at most `target` landmarks; landmarks spanning more than SPAN_MAX free
   // keyframes go to direct tiles (<= SCHUR_TILE_PAIRS pairs, <= SCHUR_TILE_LMS landmarks).
@@ -279,13 +319,15 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     const int target = c->tune_schur_lms > 0 ? std::min(SCHUR_TILE_LMS, c->tune_schur_lms)
                                              : std::max(8, std::min(96, (M + n_sm - 1) / n_sm));
     std::vector<int> lo(M, INT32_MAX), hi(M, -1);
-    for (int j = 0; j < M; ++j)
-      for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
-        const int pb = kf_pb[pair_kf[q]];
-        if (pb < 0) continue;
-        lo[j] = std::min(lo[j], pb);
-        hi[j] = std::max(hi[j], pb);
-      }
+    parallel_for(M, host_threads(), [&](int64_t j0, int64_t j1, int) {
+      for (int64_t j = j0; j < j1; ++j)
+        for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
+          const int pb = kf_pb[pair_kf[q]];
+          if (pb < 0) continue;
+          lo[j] = std::min(lo[j], pb);
+          hi[j] = std::max(hi[j], pb);
+        }
+    });
     auto wide = [&](int j) { return hi[j] >= 0 && hi[j] - lo[j] + 1 > SPAN_MAX; };
     int l0 = 0;
     while (l0 < M) {
@@ -433,17 +475,38 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   d.kf_pb = kpb;
   d.lin_tiles = lt;
   d.schur_tiles = st;
+  // the observation pixels (in slot order, FP32 on the mixed path) and the large index arrays
+  // go through the context's pinned staging by asynchronous copies on the library's stream,
+  // waited for once at the end of the layout
+  const size_t uv_bytes = (size_t)N * 2 * (mixed ? sizeof(float) : sizeof(double));
+  const size_t idx_bytes = ((size_t)N + 3 * (size_t)P + 1 + 2 * ((size_t)M + 1)) * sizeof(int32_t);
+  CK(cudaStreamSynchronize(c->stream), "sync");     // no copy of an earlier layout still reads the staging
+  CK(ensure_pinned(c, uv_bytes + idx_bytes + 16 * 256), "pinned staging");
+  char* const pin = static_cast<char*>(c->h_pin);
+  size_t pin_off = 0;
+  auto pin_take = [&](size_t bytes) {
+    char* h = pin + pin_off;
+    pin_off += (bytes + 255) / 256 * 256;
+    return h;
+  };
+  auto stage = [&](void* dst, const void* src, size_t bytes) {
+    char* h = pin_take(bytes);
+    parallel_for((int64_t)bytes, host_threads(), [&](int64_t b0, int64_t b1, int) {
+      std::memcpy(h + b0, static_cast<const char*>(src) + b0, (size_t)(b1 - b0));
+    });
+    return cudaMemcpyAsync(dst, h, bytes, cudaMemcpyHostToDevice, c->stream);
+  };
   if (mixed) {
     float* uvf;
     CK(dalloc(c, &uvf, (size_t)N * 2), "alloc obs");
-    std::vector<float> h(2 * (size_t)N);
+    float* h = reinterpret_cast<float*>(pin_take(uv_bytes));
     parallel_for(N, host_threads(), [&](int64_t s0, int64_t s1, int) {
       for (int64_t s = s0; s < s1; ++s) {
         h[2 * s] = (float)uv[2 * (size_t)c->obs_order[s]];
         h[2 * s + 1] = (float)uv[2 * (size_t)c->obs_order[s] + 1];
       }
     });
-    CK(cudaMemcpy(uvf, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice), "upload obs");
+    CK(cudaMemcpyAsync(uvf, h, uv_bytes, cudaMemcpyHostToDevice, c->stream), "upload obs");
     d.obs_uv = uvf;
     float* pl;
     CK(dalloc(c, &pl, (size_t)P * PAIR_LIN), "alloc pair lin");
@@ -451,14 +514,14 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   } else {
     double* uvd;
     CK(dalloc(c, &uvd, (size_t)N * 2), "alloc obs");
-    std::vector<double> h(2 * (size_t)N);
+    double* h = reinterpret_cast<double*>(pin_take(uv_bytes));
     parallel_for(N, host_threads(), [&](int64_t s0, int64_t s1, int) {
       for (int64_t s = s0; s < s1; ++s) {
         h[2 * s] = uv[2 * (size_t)c->obs_order[s]];
         h[2 * s + 1] = uv[2 * (size_t)c->obs_order[s] + 1];
       }
     });
-    CK(cudaMemcpy(uvd, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice), "upload obs");
+    CK(cudaMemcpyAsync(uvd, h, uv_bytes, cudaMemcpyHostToDevice, c->stream), "upload obs");
     d.obs_uv = uvd;
     double* pl;
     CK(dalloc(c, &pl, (size_t)P * PAIR_LIN), "alloc pair lin");
@@ -480,14 +543,23 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     // factor envelope: first free keyframe coupled with each free keyframe (through a shared
     // landmark), then per panel the last row whose first coupled column falls in or before it
     std::vector<int> first_blk(K, INT32_MAX);
-    for (int j = 0; j < M; ++j) {
-      int lo = INT32_MAX;
-      for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q)
-        if (kf_pb[pair_kf[q]] >= 0) lo = std::min(lo, kf_pb[pair_kf[q]]);
-      for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
-        const int pb = kf_pb[pair_kf[q]];
-        if (pb >= 0) first_blk[pb] = std::min(first_blk[pb], lo);
-      }
+    {
+      const int T = host_threads();
+      std::vector<int> part((size_t)T * K, INT32_MAX);   // per thread, merged by min
+      parallel_for(M, T, [&](int64_t j0, int64_t j1, int t) {
+        int* fb = part.data() + (size_t)t * K;
+        for (int64_t j = j0; j < j1; ++j) {
+          int lo = INT32_MAX;
+          for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q)
+            if (kf_pb[pair_kf[q]] >= 0) lo = std::min(lo, kf_pb[pair_kf[q]]);
+          for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
+            const int pb = kf_pb[pair_kf[q]];
+            if (pb >= 0) fb[pb] = std::min(fb[pb], lo);
+          }
+        }
+      });
+      for (int t = 0; t < T; ++t)
+        for (int a = 0; a < K; ++a) first_blk[a] = std::min(first_blk[a], part[(size_t)t * K + a]);
     }
     const int npan = d.npw / 32;
     for (int pn = 0; pn < kMaxPanels; ++pn) d.panel_end[pn] = 0;
@@ -586,12 +658,12 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     CK(upload_f32(c, d.pose_f[0], poseh.data(), poseh.size()), "upload mirrors");
     CK(upload_f32(c, d.lm_f[0], lmh.data(), lmh.size()), "upload mirrors");
   }
-  CK(cudaMemcpy(ocam, obs_cam.data(), (size_t)N * 4, cudaMemcpyHostToDevice), "upload");
-  CK(cudaMemcpy(pkf, pair_kf.data(), (size_t)P * 4, cudaMemcpyHostToDevice), "upload");
-  CK(cudaMemcpy(plm, pair_lm.data(), (size_t)P * 4, cudaMemcpyHostToDevice), "upload");
-  CK(cudaMemcpy(pobs, pair_obs.data(), ((size_t)P + 1) * 4, cudaMemcpyHostToDevice), "upload");
-  CK(cudaMemcpy(lpair, lm_pair.data(), ((size_t)M + 1) * 4, cudaMemcpyHostToDevice), "upload");
-  CK(cudaMemcpy(lblk, lm_blk.data(), ((size_t)M + 1) * 4, cudaMemcpyHostToDevice), "upload");
+  CK(stage(ocam, obs_cam.data(), (size_t)N * 4), "upload");
+  CK(stage(pkf, pair_kf.data(), (size_t)P * 4), "upload");
+  CK(stage(plm, pair_lm.data(), (size_t)P * 4), "upload");
+  CK(stage(pobs, pair_obs.data(), ((size_t)P + 1) * 4), "upload");
+  CK(stage(lpair, lm_pair.data(), ((size_t)M + 1) * 4), "upload");
+  CK(stage(lblk, lm_blk.data(), ((size_t)M + 1) * 4), "upload");
   CK(cudaMemcpy(kpb, kf_pb.data(), (size_t)K * 4, cudaMemcpyHostToDevice), "upload");
   CK(cudaMemcpy(lt, c->lin_tiles.data(), c->lin_tiles.size() * sizeof(LinTile), cudaMemcpyHostToDevice), "upload");
   if (!c->schur_tiles.empty())
@@ -600,6 +672,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   if (!c->direct_tiles.empty())
     CK(cudaMemcpy(dtl, c->direct_tiles.data(), c->direct_tiles.size() * sizeof(SchurTile), cudaMemcpyHostToDevice),
        "upload");
+  CK(cudaStreamSynchronize(c->stream), "upload");   // the staging is free again
   c->have_layout = true;
   return CVBA_OK;
 }
@@ -694,6 +767,9 @@ void cvba_destroy(cvba_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->side.s) cudaStreamSynchronize(c->side.s);
     free_device(c);
+    if (c->h_pin) cudaFreeHost(c->h_pin);
+    c->h_pin = nullptr;
+    c->h_pin_bytes = 0;
     if (c->side.join) cudaEventDestroy(c->side.join);
     if (c->side.fork) cudaEventDestroy(c->side.fork);
     if (c->side.s) cudaStreamDestroy(c->side.s);

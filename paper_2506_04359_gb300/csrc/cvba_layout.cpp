@@ -16,6 +16,8 @@
 // by group from the keys, with no gather of the caller's arrays.  Every step is
 // deterministic and independent of the thread count.
 #include <algorithm>
+#include <condition_variable>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -29,11 +31,99 @@ int host_threads() {
   return (int)std::max(1u, std::min(h == 0 ? 1u : h, 32u));
 }
 
+namespace {
+
+// Worker threads kept for the library's lifetime, so a parallel section costs a wake-up
+// rather than thread creation (a layout runs about ten sections).  One section runs on the
+// pool at a time; a section started while another holds the pool, or from inside a task,
+// runs on threads of its own (the previous scheme), so nesting and concurrent contexts cannot
+// deadlock.  Workers are detached and never joined: they sleep on the condition variable.
+thread_local bool tl_pool_worker = false;
+
+class Pool {
+ public:
+  static Pool& get() {
+    static Pool* p = new Pool();                    // never destroyed (detached workers)
+    return *p;
+  }
+  // Runs fn(0..n-1); false (nothing run) if the pool is busy or the caller is a worker.
+  bool run(int n, const std::function<void(int)>& fn) {
+    if (tl_pool_worker) return false;
+    std::unique_lock<std::mutex> section(run_mu_, std::try_to_lock);
+    if (!section.owns_lock()) return false;
+    uint64_t g;
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      while ((int)n_workers_ < n - 1) {
+        std::thread(&Pool::worker, this).detach();
+        ++n_workers_;
+      }
+      fn_ = &fn;
+      n_ = n;
+      next_ = 1;
+      remaining_ = n - 1;
+      g = ++gen_;
+    }
+    cv_.notify_all();
+    fn(0);
+    help(g);
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return remaining_ == 0; });
+    fn_ = nullptr;
+    return true;
+  }
+
+ private:
+  // Take tasks of generation g until none is left; a task index is handed out under the
+  // lock together with the generation check, so a late worker never runs a task of a
+  // section that has ended, and the section's caller waits until every taken task is done.
+  void help(uint64_t g) {
+    for (;;) {
+      const std::function<void(int)>* f;
+      int t;
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (gen_ != g || fn_ == nullptr || next_ >= n_) return;
+        f = fn_;
+        t = next_++;
+      }
+      (*f)(t);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--remaining_ == 0) done_cv_.notify_all();
+    }
+  }
+  void worker() {
+    tl_pool_worker = true;
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+      }
+      help(seen);
+    }
+  }
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)>* fn_ = nullptr;
+  int n_ = 0, next_ = 0, remaining_ = 0;
+  unsigned n_workers_ = 0;
+  uint64_t gen_ = 0;
+};
+
+}  // namespace
+
 void parallel_tasks(int n, const std::function<void(int)>& fn) {
+  if (n <= 1) {
+    if (n == 1) fn(0);
+    return;
+  }
+  if (Pool::get().run(n, fn)) return;
   std::vector<std::thread> pool;
-  pool.reserve(n > 0 ? n - 1 : 0);
+  pool.reserve(n - 1);
   for (int t = 1; t < n; ++t) pool.emplace_back(fn, t);
-  if (n > 0) fn(0);
+  fn(0);
   for (auto& th : pool) th.join();
 }
 
@@ -43,11 +133,7 @@ void parallel_for(int64_t n, int threads, const std::function<void(int64_t, int6
     fn(0, n, 0);
     return;
   }
-  std::vector<std::thread> pool;
-  pool.reserve(threads - 1);
-  for (int t = 1; t < threads; ++t) pool.emplace_back(fn, n * t / threads, n * (t + 1) / threads, t);
-  fn(0, n / threads, 0);
-  for (auto& th : pool) th.join();
+  parallel_tasks(threads, [&](int t) { fn(n * t / threads, n * (t + 1) / threads, t); });
 }
 
 namespace {
