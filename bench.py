@@ -218,7 +218,7 @@ def traffic_of(kernel: str, workload: str):
 
 
 def chol_kernel_name(ctx_mode_blocked: bool) -> str:
-    return "k_blk_* + k_chol_cluster" if ctx_mode_blocked else "k_chol_cluster"
+    return "k_blk_load + k_chol_cluster" if ctx_mode_blocked else "k_chol_cluster"
 
 
 def roofline(prof: dict, wm: dict, workload: str, only_hbm: bool = False, chol_name: str = "k_chol_cluster") -> dict:

@@ -223,7 +223,7 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
   goff[M] = N;
   // --- per landmark: sort its keys (stable order is kept by the caller index in the key),
   //     first / last keyframe
-  std::vector<int32_t> first((size_t)M), last((size_t)M);
+  std::vector<int32_t> first((size_t)M), last((size_t)M), npair_of((size_t)M);
   parallel_for(M, T, [&](int64_t j0, int64_t j1, int) {
     for (int64_t j = j0; j < j1; ++j) {
       uint64_t* g = grp.data() + goff[j];
@@ -239,6 +239,10 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
       }
       first[j] = m > 0 ? (int32_t)((g[0] >> 32) / C) : K;
       last[j] = m > 0 ? (int32_t)((g[m - 1] >> 32) / C) : -1;
+      int np = 0;                                  // distinct keyframes: the landmark's pairs
+      for (int64_t a = 0; a < m; ++a)
+        if (a == 0 || (uint32_t)(g[a] >> 32) / C != (uint32_t)(g[a - 1] >> 32) / C) ++np;
+      npair_of[j] = np;
     }
   });
   for (int j = 0; j < M; ++j)
@@ -261,33 +265,29 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
   counting_sort(L.lm_order, first, K);
   L.lm_rank.resize(M);
   for (int i = 0; i < M; ++i) L.lm_rank[L.lm_order[i]] = i;
-  // --- slots: groups in internal order; distinct keyframe runs are the pairs
+  // --- slots: groups in internal order; distinct keyframe runs are the pairs.  Offsets by
+  //     prefix sums over the internal order, then one pass fills slots and pairs together.
   L.lm_off.resize((size_t)M + 1);
-  L.lm_off[0] = 0;
-  for (int i = 0; i < M; ++i) L.lm_off[i + 1] = L.lm_off[i] + (int32_t)(goff[L.lm_order[i] + 1] - goff[L.lm_order[i]]);
-  std::vector<int32_t> npair((size_t)M, 0);
+  L.lm_pair.resize((size_t)M + 1);
+  {
+    std::vector<int32_t> sz((size_t)M), np((size_t)M);
+    parallel_for(M, T, [&](int64_t i0, int64_t i1, int) {
+      for (int64_t i = i0; i < i1; ++i) {
+        const int j = L.lm_order[i];
+        sz[i] = (int32_t)(goff[j + 1] - goff[j]);
+        np[i] = npair_of[j];
+      }
+    });
+    L.lm_off[0] = 0;
+    L.lm_pair[0] = 0;
+    for (int i = 0; i < M; ++i) {
+      L.lm_off[i + 1] = L.lm_off[i] + sz[i];
+      L.lm_pair[i + 1] = L.lm_pair[i] + np[i];
+    }
+  }
+  const int P = L.lm_pair[M];
   L.obs_order.resize(N);
   L.obs_cam.resize(N);
-  parallel_for(M, T, [&](int64_t i0, int64_t i1, int) {
-    for (int64_t i = i0; i < i1; ++i) {
-      const int j = L.lm_order[i];
-      const uint64_t* g = grp.data() + goff[j];
-      const int64_t m = goff[j + 1] - goff[j];
-      const int64_t s0 = L.lm_off[i];
-      int np = 0;
-      for (int64_t a = 0; a < m; ++a) {
-        const uint32_t kc = (uint32_t)(g[a] >> 32);
-        L.obs_order[s0 + a] = (int32_t)(uint32_t)g[a];
-        L.obs_cam[s0 + a] = (int32_t)(kc % C);
-        if (a == 0 || kc / C != (uint32_t)(g[a - 1] >> 32) / C) ++np;
-      }
-      npair[i] = np;
-    }
-  });
-  L.lm_pair.resize((size_t)M + 1);
-  L.lm_pair[0] = 0;
-  for (int i = 0; i < M; ++i) L.lm_pair[i + 1] = L.lm_pair[i] + npair[i];
-  const int P = L.lm_pair[M];
   L.pair_kf.resize(P);
   L.pair_lm.resize(P);
   L.pair_obs.resize((size_t)P + 1);
@@ -295,13 +295,16 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
     for (int64_t i = i0; i < i1; ++i) {
       const uint64_t* g = grp.data() + goff[L.lm_order[i]];
       const int64_t m = L.lm_off[i + 1] - L.lm_off[i];
+      const int64_t s0 = L.lm_off[i];
       int q = L.lm_pair[i];
       for (int64_t a = 0; a < m; ++a) {
-        const uint32_t k = (uint32_t)(g[a] >> 32) / C;
-        if (a == 0 || k != (uint32_t)(g[a - 1] >> 32) / C) {
-          L.pair_kf[q] = (int32_t)k;
+        const uint32_t kc = (uint32_t)(g[a] >> 32);
+        L.obs_order[s0 + a] = (int32_t)(uint32_t)g[a];
+        L.obs_cam[s0 + a] = (int32_t)(kc % C);
+        if (a == 0 || kc / C != (uint32_t)(g[a - 1] >> 32) / C) {
+          L.pair_kf[q] = (int32_t)(kc / C);
           L.pair_lm[q] = (int32_t)i;
-          L.pair_obs[q] = L.lm_off[i] + (int32_t)a;
+          L.pair_obs[q] = (int32_t)(s0 + a);
           ++q;
         }
       }
