@@ -19,9 +19,11 @@
 //   k_pgo_load      the dense lower triangle of A = H + lambda D (zero outside the blocks);
 //   k_pgo_potrf / k_pgo_trsm / k_pgo_syrk   right-looking Cholesky by 32-column panels: the
 //                   diagonal block on one CTA, the panel's rows one warp each, the trailing
-//                   update in 16 x 16 tiles over the GPU;
-//   k_pgo_solve     one CTA: L y = -g and L^T delta = y by 32-row panels, the predicted
-//                   reduction and the step norm;
+//                   update in 16 x 16 tiles over the GPU, each panel only over its envelope
+//                   (the rows whose first coupled pose lies in or before the panel: the fill
+//                   stays inside this profile);
+//   k_pgo_solve     one CTA: L y = -g and L^T delta = y by 32-row panels over the same
+//                   envelopes, the predicted reduction and the step norm;
 //   k_pgo_candidate thread per pose: Exp(delta_i) T_i;  k_pgo_cost: thread per edge at the
 //                   candidate;  k_pgo_decide: one CTA: fixed-order cost sums, gain, accept,
 //                   damping, state swap, iteration record.
@@ -68,6 +70,8 @@ struct Pgo {
   const int32_t* p_ab;       // n_pair x 2: (a, b) free poses, a > b, by column
   const int32_t* p_off;      // n_pair + 1
   const int32_t* p_list;     // edges of each pair, with side of a in bit 0 (2 * edge + (a is j))
+  const int32_t* pend;       // npw / 32: end of each panel's envelope (rows [32 (p + 1), pend[p])
+                             // are the only ones with nonzeros in panel p's columns)
   PgoCtrl* ctrl;
   cvba_lm_record* trace;
 };
@@ -467,8 +471,9 @@ __global__ void __launch_bounds__(1024) k_pgo_solve(Pgo p) {
   for (int i = tid; i < npw; i += blockDim.x) x[i] = i < p.n ? -p.g[i] : 0.0;
   __syncthreads();
   const int npan = npw / kPW;
+  __shared__ double s_part[1024];
   for (int pan = 0; pan < npan; ++pan) {
-    const int o = pan * kPW;
+    const int o = pan * kPW, end = p.pend[pan];
     if (tid < 32) {
       double v = x[o + lane];
       for (int m = 0; m < kPW; ++m) {
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(1024) k_pgo_solve(Pgo p) {
       x[o + lane] = v;
     }
     __syncthreads();
-    for (int i = o + kPW + tid; i < npw; i += blockDim.x) {
+    for (int i = o + kPW + tid; i < end; i += blockDim.x) {   // rows of the panel's envelope
       double s = 0.0;
       for (int m = 0; m < kPW; ++m) s += p.Lw[(size_t)i * npw + o + m] * x[o + m];
       x[i] -= s;
@@ -487,11 +492,20 @@ __global__ void __launch_bounds__(1024) k_pgo_solve(Pgo p) {
     __syncthreads();
   }
   for (int pan = npan - 1; pan >= 0; --pan) {
-    const int o = pan * kPW;
-    // x_p -= L_{below, p}^T x_below
+    const int o = pan * kPW, end = p.pend[pan];
+    // x_p -= L_{below, p}^T x_below over the panel's envelope: thread (g, c) sums column c over
+    // the rows o + 32 + g + 32 k (a warp reads whole row segments), then the 32 partials of
+    // each column are added in order g = 0..31
+    {
+      const int c = tid & 31, g = tid >> 5;
+      double s = 0.0;
+      for (int i = o + kPW + g; i < end; i += 32) s += p.Lw[(size_t)i * npw + o + c] * x[i];
+      s_part[g * 32 + c] = s;
+    }
+    __syncthreads();
     if (tid < kPW) {
       double s = 0.0;
-      for (int i = o + kPW; i < npw; ++i) s += p.Lw[(size_t)i * npw + o + tid] * x[i];
+      for (int g = 0; g < 32; ++g) s += s_part[g * 32 + tid];
       x[o + tid] -= s;
     }
     __syncthreads();
@@ -618,7 +632,8 @@ __global__ void k_pgo_store(Pgo p, double* user) {
 // ------------------------------------------------------------------ host side
 
 struct Layout {
-  size_t ctrl, pose0, pose1, er, eJ, ecost, ccost, Hd, Ho, g, D, Lw, x, col, d_off, d_list, p_ab, p_off, p_list, total;
+  size_t ctrl, pose0, pose1, er, eJ, ecost, ccost, Hd, Ho, g, D, Lw, x, col, d_off, d_list, p_ab, p_off, p_list, pend,
+      total;
 };
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -651,6 +666,7 @@ Layout plan(int K, int E, int n_pair) {
   L.p_ab = take(sizeof(int32_t) * 2 * (size_t)std::max(n_pair, 1));
   L.p_off = take(sizeof(int32_t) * (size_t)(n_pair + 1));
   L.p_list = take(sizeof(int32_t) * (size_t)std::max(E, 1));
+  L.pend = take(sizeof(int32_t) * (size_t)(npw / kPW));
   L.total = o;
   return L;
 }
@@ -723,6 +739,24 @@ extern "C" cvba_status cvba_pgo_solve(int n_poses, int n_edges, const int32_t* e
     }
   }
   const int n_pair = (int)p_off.size() - 1;
+  // envelope of the factor by 32-column panel: the first column of each row is that of its
+  // pose's first coupled pose (the Cholesky fill stays inside this profile), so the rows below
+  // panel p with nonzeros in its columns end at the last row whose first column is in or
+  // before the panel
+  const int n_c = 6 * nfree, npw_h = (n_c + kPW - 1) / kPW * kPW, npan_h = npw_h / kPW;
+  std::vector<int32_t> pend(npan_h);
+  {
+    std::vector<int> first(nfree);
+    for (int a = 0; a < nfree; ++a) first[a] = a;
+    for (int q = 0; q < n_pair; ++q) first[p_ab[2 * q]] = std::min(first[p_ab[2 * q]], p_ab[2 * q + 1]);
+    for (int pn = 0; pn < npan_h; ++pn) {
+      const int end_col = kPW * pn + kPW - 1;
+      int last = kPW * (pn + 1) - 1;
+      for (int r = kPW * (pn + 1); r < n_c; ++r)
+        if (6 * first[r / 6] <= end_col) last = r;
+      pend[pn] = std::min(npw_h, (last + 1 + kPW - 1) / kPW * kPW);
+    }
+  }
   const Layout L = plan(K, E, n_pair);
   unsigned char* w = static_cast<unsigned char*>(work);
   Pgo p{};
@@ -747,6 +781,7 @@ extern "C" cvba_status cvba_pgo_solve(int n_poses, int n_edges, const int32_t* e
   p.p_ab = reinterpret_cast<const int32_t*>(w + L.p_ab);
   p.p_off = reinterpret_cast<const int32_t*>(w + L.p_off);
   p.p_list = reinterpret_cast<const int32_t*>(w + L.p_list);
+  p.pend = reinterpret_cast<const int32_t*>(w + L.pend);
   p.ctrl = reinterpret_cast<PgoCtrl*>(w + L.ctrl);
   p.trace = trace;
   auto up = [&](size_t off, const std::vector<int32_t>& v) {
@@ -759,6 +794,7 @@ extern "C" cvba_status cvba_pgo_solve(int n_poses, int n_edges, const int32_t* e
   if (e == cudaSuccess) e = up(L.p_ab, p_ab);
   if (e == cudaSuccess) e = up(L.p_off, p_off);
   if (e == cudaSuccess) e = up(L.p_list, p_list);
+  if (e == cudaSuccess) e = up(L.pend, pend);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);     // the host lists go out of scope
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -775,8 +811,8 @@ extern "C" cvba_status cvba_pgo_solve(int n_poses, int n_edges, const int32_t* e
     if (n_pair > 0) k_pgo_load_pairs<<<n_pair, 64, 0, s>>>(p);
     for (int pan = 0; pan < npan; ++pan) {
       k_pgo_potrf<<<1, 256, 0, s>>>(p, pan);
-      const int below = p.npw - kPW * (pan + 1);
-      if (below == 0) break;
+      const int below = pend[pan] - kPW * (pan + 1);   // rows of the panel's envelope
+      if (below == 0) continue;
       k_pgo_trsm<<<below / 8, 256, 0, s>>>(p, pan);
       const int nt = below / 16;
       k_pgo_syrk<<<nt * (nt + 1) / 2, 256, 0, s>>>(p, pan);
