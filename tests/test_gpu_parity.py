@@ -68,12 +68,14 @@ def rounding_floor(w, poses, lms, lam, draws=6, seed=0):
     return np.sqrt(acc / draws) / float(np.linalg.norm(delta))
 
 
-def lockstep(cvba, p, iters, precision="fp64", lam0=1e-4):
+def lockstep(cvba, p, iters, precision="fp64", lam0=1e-4, lin_tile_pairs=0):
     """Drive GPU and oracle from the same state each iteration; return per-iteration
     (relative increment difference, allowed difference, gpu record, oracle record).
     Allowed: 1e-9 relative plus four times the residual-rounding floor."""
     w = ba.Window.from_problem(p)
     ctx = cvba.Context(precision).load(p)
+    if lin_tile_pairs:
+        ctx.cvba_set_tuning(lin_tile_pairs, 0)
     poses, lms, lam, nu = p.poses0.copy(), p.lm0.copy(), lam0, 2.0
     out = []
     for _ in range(iters):
@@ -163,6 +165,28 @@ def test_fp64_lockstep_wide_landmarks(cvba):
     for d, tol, g, o in lockstep(cvba, p, 3):
         assert d <= tol, (d, tol)
         assert g["accepted"] == int(o.accepted)
+
+
+def test_fp64_lockstep_tiles_beyond_the_staged_observations(cvba):
+    """Every observation of the 5-keyframe stereo window repeated eight times (a valid
+    window: the same objective with each term weighted eight-fold), so a (landmark,
+    keyframe) pair holds 16 observations, and tiles of 256 pairs hold more than the 1024
+    observations a linearisation or back-substitution tile stages in shared memory: those
+    tiles read their observations in place.  Increments, costs and decisions as the
+    oracle's."""
+    base = synth.make_problem("c0", M=200, seed=5)
+    p = base.copy()
+    p.obs_kf = np.repeat(base.obs_kf, 8)
+    p.obs_cam = np.repeat(base.obs_cam, 8)
+    p.obs_lm = np.repeat(base.obs_lm, 8)
+    p.obs_uv = np.repeat(base.obs_uv, 8, axis=0)
+    p.outlier = np.repeat(base.outlier, 8)
+    n_pairs = np.unique(p.obs_lm.astype(np.int64) * p.K + p.obs_kf).size
+    assert 256 * p.N / n_pairs > 2 * 1024
+    for d, tol, g, o in lockstep(cvba, p, 3, lin_tile_pairs=256):
+        assert d <= tol, (d, tol)
+        assert g["accepted"] == int(o.accepted)
+        assert abs(g["cost0"] - o.cost0) <= 1e-9 * o.cost0
 
 
 @pytest.fixture(scope="module")
