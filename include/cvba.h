@@ -120,10 +120,13 @@ cvba_status cvba_set_rig(cvba_ctx* ctx, int n_cams, const double* intr, const do
  * Any pointer may be NULL. */
 cvba_status cvba_get_rig(cvba_ctx* ctx, double* intr, double* T_cb, int32_t* wh);
 
-/* n_kf >= 2 keyframe poses T_bw[n_kf*12]; keyframe `fixed_kf` is held constant. */
+/* n_kf >= 2 keyframe poses T_bw[n_kf*12]; keyframe `fixed_kf` is held constant.  Once a
+ * layout exists (cvba_set_observations), the poses of the current state are replaced and the
+ * landmarks keep their current values. */
 cvba_status cvba_set_poses(cvba_ctx* ctx, int n_kf, const double* T_bw, int fixed_kf);
 
-/* n_lm >= 1 landmarks p_w[n_lm*3] in world coordinates. */
+/* n_lm >= 1 landmarks p_w[n_lm*3] in world coordinates.  Once a layout exists, the
+ * landmarks of the current state are replaced and the poses keep their current values. */
 cvba_status cvba_set_landmarks(cvba_ctx* ctx, int n_lm, const double* p_w);
 
 /* n_obs observations: keyframe kf[n], camera cam[n], landmark lm[n] and pixel uv[2n..2n+1].

@@ -677,24 +677,51 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   return CVBA_OK;
 }
 
-cvba_status upload_state(cvba_ctx* c) {
-  // poses / landmarks replaced after the layout exists: write into the current buffer
-  const int cur = read_cur(c);
+// Poses and / or landmarks replaced after the layout exists: written into the current state
+// buffer (FP64, and the FP32 mirrors on the mixed path) from the context's pinned staging, by
+// asynchronous copies waited for once.  Only what was replaced is written.
+cvba_status upload_state(cvba_ctx* c, bool poses, bool lms) {
+  const int cur = read_cur(c);                     // (waits for the stream: the staging is free)
   const int K = c->K, M = c->M;
-  std::vector<double> poseh((size_t)K * POSE_STRIDE);
-  for (int a = 0; a < K; ++a)
-    for (int r = 0; r < 3; ++r) {
-      for (int q = 0; q < 3; ++q) poseh[a * POSE_STRIDE + r * 3 + q] = c->poses[a * 12 + r * 4 + q];
-      poseh[a * POSE_STRIDE + 9 + r] = c->poses[a * 12 + r * 4 + 3];
+  const size_t need = (poses ? (size_t)K * POSE_STRIDE * 12 : 0) + (lms ? (size_t)M * 3 * 12 : 0) + 4 * 256;
+  CK(ensure_pinned(c, need), "pinned staging");
+  char* const pin = static_cast<char*>(c->h_pin);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* h = pin + off;
+    off += (bytes + 255) / 256 * 256;
+    return h;
+  };
+  if (poses) {
+    double* ph = reinterpret_cast<double*>(take((size_t)K * POSE_STRIDE * 8));
+    for (int a = 0; a < K; ++a)
+      for (int r = 0; r < 3; ++r) {
+        for (int q = 0; q < 3; ++q) ph[a * POSE_STRIDE + r * 3 + q] = c->poses[a * 12 + r * 4 + q];
+        ph[a * POSE_STRIDE + 9 + r] = c->poses[a * 12 + r * 4 + 3];
+      }
+    CK(cudaMemcpyAsync(c->d.pose[cur], ph, (size_t)K * POSE_STRIDE * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+    if (c->d.pose_f[cur]) {
+      float* pf = reinterpret_cast<float*>(take((size_t)K * POSE_STRIDE * 4));
+      for (int e = 0; e < K * POSE_STRIDE; ++e) pf[e] = (float)ph[e];
+      CK(cudaMemcpyAsync(c->d.pose_f[cur], pf, (size_t)K * POSE_STRIDE * 4, cudaMemcpyHostToDevice, c->stream),
+         "upload mirrors");
     }
-  std::vector<double> lmh((size_t)M * 3);
-  for (int i = 0; i < M; ++i)
-    for (int k = 0; k < 3; ++k) lmh[(size_t)i * 3 + k] = c->lms[(size_t)c->lm_order[i] * 3 + k];
-  CK(cudaMemcpyAsync(c->d.pose[cur], poseh.data(), poseh.size() * 8, cudaMemcpyHostToDevice, c->stream), "upload");
-  CK(cudaMemcpyAsync(c->d.lm[cur], lmh.data(), lmh.size() * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+  }
+  if (lms) {
+    double* lh = reinterpret_cast<double*>(take((size_t)M * 3 * 8));
+    float* lf = c->d.lm_f[cur] ? reinterpret_cast<float*>(take((size_t)M * 3 * 4)) : nullptr;
+    parallel_for(M, host_threads(), [&](int64_t i0, int64_t i1, int) {
+      for (int64_t i = i0; i < i1; ++i)
+        for (int k = 0; k < 3; ++k) {
+          const double v = c->lms[(size_t)c->lm_order[i] * 3 + k];
+          lh[i * 3 + k] = v;
+          if (lf) lf[i * 3 + k] = (float)v;
+        }
+    });
+    CK(cudaMemcpyAsync(c->d.lm[cur], lh, (size_t)M * 3 * 8, cudaMemcpyHostToDevice, c->stream), "upload");
+    if (lf) CK(cudaMemcpyAsync(c->d.lm_f[cur], lf, (size_t)M * 3 * 4, cudaMemcpyHostToDevice, c->stream), "upload mirrors");
+  }
   CK(cudaStreamSynchronize(c->stream), "sync");
-  CK(upload_f32(c, c->d.pose_f[cur], poseh.data(), poseh.size()), "upload mirrors");
-  CK(upload_f32(c, c->d.lm_f[cur], lmh.data(), lmh.size()), "upload mirrors");
   return CVBA_OK;
 }
 
@@ -833,7 +860,7 @@ cvba_status cvba_set_poses(cvba_ctx* c, int n_kf, const double* T_bw, int fixed_
   c->fixed_kf = fixed_kf;
   c->poses.assign(T_bw, T_bw + (size_t)n_kf * 12);
   c->have_poses = true;
-  if (c->have_layout) return upload_state(c);
+  if (c->have_layout) return upload_state(c, true, false);
   return CVBA_OK;
 }
 
@@ -846,7 +873,7 @@ cvba_status cvba_set_landmarks(cvba_ctx* c, int n_lm, const double* p_w) {
   c->M = n_lm;
   c->lms.assign(p_w, p_w + (size_t)n_lm * 3);
   c->have_lms = true;
-  if (c->have_layout) return upload_state(c);
+  if (c->have_layout) return upload_state(c, false, true);
   return CVBA_OK;
 }
 
