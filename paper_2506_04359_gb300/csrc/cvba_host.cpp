@@ -480,8 +480,11 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   // waited for once at the end of the layout
   const size_t uv_bytes = (size_t)N * 2 * (mixed ? sizeof(float) : sizeof(double));
   const size_t idx_bytes = ((size_t)N + 3 * (size_t)P + 1 + 2 * ((size_t)M + 1)) * sizeof(int32_t);
+  const size_t state_bytes = ((size_t)C * RIG_STRIDE + (size_t)K * POSE_STRIDE + (size_t)M * 3) * (mixed ? 12 : 8);
+  const size_t table_bytes = (size_t)M * 4 + (size_t)K * 4 + sizeof(Ctrl) + c->lin_tiles.size() * sizeof(LinTile) +
+                             (c->schur_tiles.size() + c->direct_tiles.size()) * sizeof(SchurTile);
   CK(cudaStreamSynchronize(c->stream), "sync");     // no copy of an earlier layout still reads the staging
-  CK(ensure_pinned(c, uv_bytes + idx_bytes + 16 * 256), "pinned staging");
+  CK(ensure_pinned(c, uv_bytes + idx_bytes + state_bytes + table_bytes + 32 * 256), "pinned staging");
   char* const pin = static_cast<char*>(c->h_pin);
   size_t pin_off = 0;
   auto pin_take = [&](size_t bytes) {
@@ -619,21 +622,23 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   CK(dalloc(c, &d.ctrl, 1), "alloc");
   CK(dalloc(c, &c->d_eval, 4), "alloc");
   CK(dalloc(c, &c->d_lm_order, M), "alloc");
-  CK(cudaMemcpy(c->d_lm_order, c->lm_order.data(), (size_t)M * 4, cudaMemcpyHostToDevice), "upload");
+  CK(stage(c->d_lm_order, c->lm_order.data(), (size_t)M * 4), "upload");
   d.trace = c->d_trace;
-  CK(cudaMemset(d.S, 0, sizeof(double) * std::max<size_t>((size_t)n_c * n_c, 1)), "memset");
-  CK(cudaMemset(d.dc, 0, sizeof(double) * std::max(n_c, 1)), "memset");
-  CK(cudaMemset(d.dp, 0, sizeof(double) * (size_t)M * 3), "memset");
-  CK(cudaMemset(d.lin_part, 0, sizeof(double) * (size_t)d.n_lin_tiles * 4), "memset");
-  CK(cudaMemset(d.bs_part, 0, sizeof(double) * (size_t)d.n_lin_tiles * 8), "memset");
+  // zero fills on the library's stream, ordered with the copies below and the solve
+  CK(cudaMemsetAsync(d.S, 0, sizeof(double) * std::max<size_t>((size_t)n_c * n_c, 1), c->stream), "memset");
+  CK(cudaMemsetAsync(d.dc, 0, sizeof(double) * std::max(n_c, 1), c->stream), "memset");
+  CK(cudaMemsetAsync(d.dp, 0, sizeof(double) * (size_t)M * 3, c->stream), "memset");
+  CK(cudaMemsetAsync(d.lin_part, 0, sizeof(double) * (size_t)d.n_lin_tiles * 4, c->stream), "memset");
+  CK(cudaMemsetAsync(d.bs_part, 0, sizeof(double) * (size_t)d.n_lin_tiles * 8, c->stream), "memset");
   {
     Ctrl h{};
     h.cur = 0;
     h.lam = 1e-4;
     h.nu = 2.0;
-    CK(cudaMemcpy(d.ctrl, &h, sizeof(Ctrl), cudaMemcpyHostToDevice), "upload ctrl");
+    CK(stage(d.ctrl, &h, sizeof(Ctrl)), "upload ctrl");
   }
-  std::vector<double> righ((size_t)C * RIG_STRIDE);
+  // rig, poses and landmarks (internal order), and their FP32 mirrors, assembled in the staging
+  double* righ = reinterpret_cast<double*>(pin_take((size_t)C * RIG_STRIDE * 8));
   for (int k = 0; k < C; ++k) {
     for (int i = 0; i < 4; ++i) righ[k * RIG_STRIDE + i] = c->intr[k * 4 + i];
     for (int r = 0; r < 3; ++r) {
@@ -641,22 +646,31 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
       righ[k * RIG_STRIDE + 13 + r] = c->T_cb[k * 12 + r * 4 + 3];
     }
   }
-  std::vector<double> poseh((size_t)K * POSE_STRIDE);
+  double* poseh = reinterpret_cast<double*>(pin_take((size_t)K * POSE_STRIDE * 8));
   for (int a = 0; a < K; ++a)
     for (int r = 0; r < 3; ++r) {
       for (int q = 0; q < 3; ++q) poseh[a * POSE_STRIDE + r * 3 + q] = c->poses[a * 12 + r * 4 + q];
       poseh[a * POSE_STRIDE + 9 + r] = c->poses[a * 12 + r * 4 + 3];
     }
-  std::vector<double> lmh((size_t)M * 3);
-  for (int i = 0; i < M; ++i)
-    for (int k = 0; k < 3; ++k) lmh[(size_t)i * 3 + k] = c->lms[(size_t)c->lm_order[i] * 3 + k];
-  CK(cudaMemcpy(rig, righ.data(), righ.size() * 8, cudaMemcpyHostToDevice), "upload rig");
-  CK(cudaMemcpy(pose0, poseh.data(), poseh.size() * 8, cudaMemcpyHostToDevice), "upload poses");
-  CK(cudaMemcpy(lm0, lmh.data(), lmh.size() * 8, cudaMemcpyHostToDevice), "upload landmarks");
+  double* lmh = reinterpret_cast<double*>(pin_take((size_t)M * 3 * 8));
+  parallel_for(M, host_threads(), [&](int64_t i0, int64_t i1, int) {
+    for (int64_t i = i0; i < i1; ++i)
+      for (int k = 0; k < 3; ++k) lmh[i * 3 + k] = c->lms[(size_t)c->lm_order[i] * 3 + k];
+  });
+  CK(cudaMemcpyAsync(rig, righ, (size_t)C * RIG_STRIDE * 8, cudaMemcpyHostToDevice, c->stream), "upload rig");
+  CK(cudaMemcpyAsync(pose0, poseh, (size_t)K * POSE_STRIDE * 8, cudaMemcpyHostToDevice, c->stream), "upload poses");
+  CK(cudaMemcpyAsync(lm0, lmh, (size_t)M * 3 * 8, cudaMemcpyHostToDevice, c->stream), "upload landmarks");
   if (mixed) {
-    CK(upload_f32(c, const_cast<float*>(d.rig_f), righ.data(), righ.size()), "upload mirrors");
-    CK(upload_f32(c, d.pose_f[0], poseh.data(), poseh.size()), "upload mirrors");
-    CK(upload_f32(c, d.lm_f[0], lmh.data(), lmh.size()), "upload mirrors");
+    auto mirror = [&](float* dst, const double* src, size_t n) {
+      float* h = reinterpret_cast<float*>(pin_take(n * 4));
+      parallel_for((int64_t)n, host_threads(), [&](int64_t e0, int64_t e1, int) {
+        for (int64_t e = e0; e < e1; ++e) h[e] = (float)src[e];
+      });
+      return cudaMemcpyAsync(dst, h, n * 4, cudaMemcpyHostToDevice, c->stream);
+    };
+    CK(mirror(const_cast<float*>(d.rig_f), righ, (size_t)C * RIG_STRIDE), "upload mirrors");
+    CK(mirror(d.pose_f[0], poseh, (size_t)K * POSE_STRIDE), "upload mirrors");
+    CK(mirror(d.lm_f[0], lmh, (size_t)M * 3), "upload mirrors");
   }
   CK(stage(ocam, obs_cam.data(), (size_t)N * 4), "upload");
   CK(stage(pkf, pair_kf.data(), (size_t)P * 4), "upload");
@@ -664,14 +678,11 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   CK(stage(pobs, pair_obs.data(), ((size_t)P + 1) * 4), "upload");
   CK(stage(lpair, lm_pair.data(), ((size_t)M + 1) * 4), "upload");
   CK(stage(lblk, lm_blk.data(), ((size_t)M + 1) * 4), "upload");
-  CK(cudaMemcpy(kpb, kf_pb.data(), (size_t)K * 4, cudaMemcpyHostToDevice), "upload");
-  CK(cudaMemcpy(lt, c->lin_tiles.data(), c->lin_tiles.size() * sizeof(LinTile), cudaMemcpyHostToDevice), "upload");
-  if (!c->schur_tiles.empty())
-    CK(cudaMemcpy(st, c->schur_tiles.data(), c->schur_tiles.size() * sizeof(SchurTile), cudaMemcpyHostToDevice),
-       "upload");
+  CK(stage(kpb, kf_pb.data(), (size_t)K * 4), "upload");
+  CK(stage(lt, c->lin_tiles.data(), c->lin_tiles.size() * sizeof(LinTile)), "upload");
+  if (!c->schur_tiles.empty()) CK(stage(st, c->schur_tiles.data(), c->schur_tiles.size() * sizeof(SchurTile)), "upload");
   if (!c->direct_tiles.empty())
-    CK(cudaMemcpy(dtl, c->direct_tiles.data(), c->direct_tiles.size() * sizeof(SchurTile), cudaMemcpyHostToDevice),
-       "upload");
+    CK(stage(dtl, c->direct_tiles.data(), c->direct_tiles.size() * sizeof(SchurTile)), "upload");
   CK(cudaStreamSynchronize(c->stream), "upload");   // the staging is free again
   c->have_layout = true;
   return CVBA_OK;
