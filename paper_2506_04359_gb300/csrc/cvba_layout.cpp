@@ -39,6 +39,7 @@ namespace {
 // runs on threads of its own (the previous scheme), so nesting and concurrent contexts cannot
 // deadlock.  Workers are detached and never joined: they sleep on the condition variable.
 thread_local bool tl_pool_worker = false;
+thread_local bool tl_in_section = false;             // this thread runs a pool section's task 0
 
 class Pool {
  public:
@@ -48,7 +49,7 @@ class Pool {
   }
   // Runs fn(0..n-1); false (nothing run) if the pool is busy or the caller is a worker.
   bool run(int n, const std::function<void(int)>& fn) {
-    if (tl_pool_worker) return false;
+    if (tl_pool_worker || tl_in_section) return false;   // nested: never re-lock run_mu_
     std::unique_lock<std::mutex> section(run_mu_, std::try_to_lock);
     if (!section.owns_lock()) return false;
     uint64_t g;
@@ -65,8 +66,10 @@ class Pool {
       g = ++gen_;
     }
     cv_.notify_all();
+    tl_in_section = true;
     fn(0);
     help(g);
+    tl_in_section = false;
     std::unique_lock<std::mutex> lk(mu_);
     done_cv_.wait(lk, [&] { return remaining_ == 0; });
     fn_ = nullptr;
