@@ -46,7 +46,6 @@ struct HostLayout {
   std::vector<int32_t> lm_order, lm_rank, obs_order, lm_off, obs_cam;
   std::vector<int32_t> pair_kf, pair_lm, pair_obs, lm_pair;
   // work arrays, kept for the next layout of the same context
-  std::vector<int32_t> rec_lm;
   std::vector<uint64_t> rec_key, grp;
   std::vector<int64_t> goff;
 };

@@ -7,15 +7,17 @@
 //  - observation slots are ordered by (internal landmark, keyframe, camera, caller index);
 //  - pairs are the distinct (internal landmark, keyframe) runs of the slots, in slot order.
 //
-// Algorithm: every observation becomes a 64-bit key (keyframe * C + camera, caller index);
-// the keys are grouped by the caller's landmark index with a parallel two-level counting
-// sort (a radix pass into one landmark range per thread, then a counting sort inside each
-// range); each landmark's keys are sorted in place (insertion sort: groups hold a few to a
-// few tens of observations), which orders them by (keyframe, camera, caller index); the
-// landmarks are ordered by two stable counting sorts; and the slots and pairs are filled group
-// by group from the keys, with no gather of the caller's arrays.  Every step is
-// deterministic and independent of the thread count.
+// Algorithm: the caller's landmarks are cut into buckets of 2^s consecutive indices (about
+// 16k observations a bucket); every observation becomes a 64-bit key (landmark within its
+// bucket, keyframe, camera, caller index); a parallel counting pass and stable scatter group
+// the keys by bucket; each bucket, in a core's cache, is then put in order by two stable
+// counting sorts, by (keyframe, camera) and then by landmark, which leaves every landmark's
+// keys in (keyframe, camera, caller index) order; the landmarks are ordered by one stable
+// counting sort on (first, last); and the slots and pairs are filled group by group from the
+// keys, with no gather of the caller's arrays.  Every step is deterministic and independent
+// of the thread count and of which thread takes which bucket.
 #include <algorithm>
+#include <atomic>
 #include <condition_variable>
 #include <mutex>
 #include <string>
@@ -139,115 +141,105 @@ void parallel_for(int64_t n, int threads, const std::function<void(int64_t, int6
   parallel_tasks(threads, [&](int t) { fn(n * t / threads, n * (t + 1) / threads, t); });
 }
 
-namespace {
-
-// Stable counting sort of idx by key[idx] in [0, n_keys).
-void counting_sort(std::vector<int32_t>& idx, const std::vector<int32_t>& key, int n_keys) {
-  std::vector<int64_t> cnt((size_t)n_keys + 1, 0);
-  for (int32_t i : idx) cnt[(size_t)key[i] + 1]++;
-  for (int k = 0; k < n_keys; ++k) cnt[k + 1] += cnt[k];
-  std::vector<int32_t> out(idx.size());
-  for (int32_t i : idx) out[cnt[key[i]]++] = i;
-  idx.swap(out);
-}
-
-}  // namespace
-
 bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t* kf, const int32_t* cam,
                          const int32_t* lm, HostLayout& L, std::string& err) {
+  static_assert(K_MAX <= 256 && C_MAX <= 256, "keyframe and camera take 8 bits of a sort key");
   const int T = host_threads();
   // work arrays live in L (kept between calls, so a window of the same size reuses them
   // without new pages)
-  std::vector<int32_t>& rec_lm = L.rec_lm;
-  std::vector<uint64_t>& rec_key = L.rec_key;
+  std::vector<uint64_t>& rec = L.rec_key;
   std::vector<uint64_t>& grp = L.grp;
   std::vector<int64_t>& goff = L.goff;
-  // Every observation as a 64-bit sort key: (keyframe * C + camera) above, caller index
-  // below, so ordering the keys orders by (keyframe, camera, caller index), and the
-  // keyframe and camera come back out of the key without a gather.
-  auto key_of = [&](int64_t n) { return ((uint64_t)(uint32_t)(kf[n] * C + cam[n]) << 32) | (uint32_t)n; };
-  // --- group by caller landmark: parallel radix pass (T landmark ranges), then a counting
-  //     sort inside each range
-  std::vector<int32_t> bucket_lo((size_t)T + 1);
-  for (int b = 0; b <= T; ++b) bucket_lo[b] = (int32_t)((int64_t)M * b / T);
-  std::vector<uint8_t> bucket_of((size_t)M);
-  for (int b = 0; b < T; ++b)
-    for (int j = bucket_lo[b]; j < bucket_lo[b + 1]; ++j) bucket_of[j] = (uint8_t)b;
-  std::vector<int64_t> cnt((size_t)T * T, 0);          // [chunk][bucket]
+  // Landmark buckets: 2^sh consecutive caller landmarks each, sized so that a bucket holds
+  // about 16k observations (its keys and a copy stay in a core's cache) and at most 2^16
+  // landmarks.
+  int sh = 0;
+  while (sh < 16 && ((int64_t)N << (sh + 1)) <= (int64_t)16384 * std::max(M, 1)) ++sh;
+  const int W = 1 << sh;
+  const int B = std::max(1, (int)(((int64_t)M + W - 1) >> sh));
+  // Every observation as a 64-bit sort key: its landmark's index within the bucket in bits
+  // 48..63, keyframe in 40..47, camera in 32..39, caller index below.  Ordering a bucket's
+  // keys orders it by (landmark, keyframe, camera, caller index), and keyframe, camera and
+  // caller index come back out of the key by shifts, without a gather.
+  auto key_of = [&](int64_t n) {
+    return ((uint64_t)(uint32_t)(lm[n] & (W - 1)) << 48) | ((uint64_t)(uint32_t)kf[n] << 40) |
+           ((uint64_t)(uint32_t)cam[n] << 32) | (uint32_t)n;
+  };
+  auto kf_of = [](uint64_t key) { return (int32_t)((key >> 40) & 0xff); };
+  auto cam_of = [](uint64_t key) { return (int32_t)((key >> 32) & 0xff); };
+  // --- group by bucket: parallel counting pass and stable scatter (chunks of the caller's
+  //     order, so each bucket receives its keys in caller order)
+  std::vector<int64_t> cnt((size_t)T * B, 0);          // [chunk][bucket]
   std::vector<int64_t> kf_cnt((size_t)T * K, 0);       // [chunk][keyframe]
   parallel_tasks(T, [&](int c) {
     const int64_t n0 = (int64_t)N * c / T, n1 = (int64_t)N * (c + 1) / T;
-    int64_t* cc = cnt.data() + (size_t)c * T;
+    int64_t* cc = cnt.data() + (size_t)c * B;
     int64_t* kc = kf_cnt.data() + (size_t)c * K;
     for (int64_t n = n0; n < n1; ++n) {
-      cc[bucket_of[lm[n]]]++;
+      cc[lm[n] >> sh]++;
       kc[kf[n]]++;
     }
   });
-  std::vector<int64_t> pos((size_t)T * T), boff((size_t)T + 1, 0);
+  std::vector<int64_t> boff((size_t)B + 1, 0);
   {
-    int64_t acc = 0;
-    for (int b = 0; b < T; ++b) {
+    int64_t acc = 0;                                   // cnt becomes each chunk's write position
+    for (int b = 0; b < B; ++b) {
       boff[b] = acc;
       for (int c = 0; c < T; ++c) {
-        pos[(size_t)c * T + b] = acc;
-        acc += cnt[(size_t)c * T + b];
+        const int64_t m = cnt[(size_t)c * B + b];
+        cnt[(size_t)c * B + b] = acc;
+        acc += m;
       }
     }
-    boff[T] = acc;
+    boff[B] = acc;
   }
-  rec_lm.resize((size_t)N);
-  rec_key.resize((size_t)N);
+  rec.resize((size_t)N);
   parallel_tasks(T, [&](int c) {
     const int64_t n0 = (int64_t)N * c / T, n1 = (int64_t)N * (c + 1) / T;
-    int64_t* p = pos.data() + (size_t)c * T;
-    for (int64_t n = n0; n < n1; ++n) {
-      const int b = bucket_of[lm[n]];
-      const int64_t q = p[b]++;
-      rec_lm[q] = lm[n];
-      rec_key[q] = key_of(n);
-    }
+    int64_t* p = cnt.data() + (size_t)c * B;
+    for (int64_t n = n0; n < n1; ++n) rec[p[lm[n] >> sh]++] = key_of(n);
   });
+  // --- per bucket, in cache: a stable counting sort by (keyframe, camera), then a stable
+  //     one by landmark, which leaves each landmark's keys in (keyframe, camera, caller
+  //     index) order; then each landmark's first and last keyframe and its pair count
   goff.resize((size_t)M + 1);
   grp.resize((size_t)N);
-  parallel_tasks(T, [&](int b) {
-    const int lo = bucket_lo[b], hi = bucket_lo[b + 1];
-    std::vector<int64_t> fill((size_t)(hi - lo), 0);
-    for (int64_t q = boff[b]; q < boff[b + 1]; ++q) fill[rec_lm[q] - lo]++;
-    int64_t acc = boff[b];
-    for (int j = lo; j < hi; ++j) {       // goff[j] for the range's own landmarks only
-      const int64_t m = fill[j - lo];
-      goff[j] = acc;
-      fill[j - lo] = acc;
-      acc += m;
-    }
-    for (int64_t q = boff[b]; q < boff[b + 1]; ++q) grp[fill[rec_lm[q] - lo]++] = rec_key[q];
-  });
-  goff[M] = N;
-  // --- per landmark: sort its keys (stable order is kept by the caller index in the key),
-  //     first / last keyframe
   std::vector<int32_t> first((size_t)M), last((size_t)M), npair_of((size_t)M);
-  parallel_for(M, T, [&](int64_t j0, int64_t j1, int) {
-    for (int64_t j = j0; j < j1; ++j) {
-      uint64_t* g = grp.data() + goff[j];
-      const int64_t m = goff[j + 1] - goff[j];
-      for (int64_t a = 1; a < m; ++a) {
-        const uint64_t v = g[a];
-        int64_t b = a - 1;
-        while (b >= 0 && g[b] > v) {
-          g[b + 1] = g[b];
-          --b;
+  {
+    const int KC = K * C;
+    std::atomic<int> next_bucket{0};
+    parallel_tasks(T, [&](int) {
+      std::vector<uint64_t> tmp;
+      std::vector<int64_t> h((size_t)std::max(KC, W) + 1);
+      for (int b; (b = next_bucket.fetch_add(1)) < B;) {
+        const int64_t e0 = boff[b], E = boff[b + 1] - e0;
+        const int lo = b << sh, nl = std::min(M - lo, W);
+        const uint64_t* src = rec.data() + e0;
+        if ((int64_t)tmp.size() < E) tmp.resize((size_t)E);
+        std::fill(h.begin(), h.begin() + KC + 1, 0);
+        for (int64_t a = 0; a < E; ++a) h[(size_t)kf_of(src[a]) * C + cam_of(src[a]) + 1]++;
+        for (int d = 0; d < KC; ++d) h[d + 1] += h[d];
+        for (int64_t a = 0; a < E; ++a) tmp[h[(size_t)kf_of(src[a]) * C + cam_of(src[a])]++] = src[a];
+        std::fill(h.begin(), h.begin() + nl + 1, 0);
+        for (int64_t a = 0; a < E; ++a) h[(tmp[a] >> 48) + 1]++;
+        for (int j = 0; j < nl; ++j) h[j + 1] += h[j];
+        for (int j = 0; j < nl; ++j) goff[lo + j] = e0 + h[j];
+        uint64_t* dst = grp.data() + e0;
+        for (int64_t a = 0; a < E; ++a) dst[h[tmp[a] >> 48]++] = tmp[a];
+        for (int j = 0; j < nl; ++j) {                 // h[j] is now the end of landmark lo + j
+          const int64_t g0 = j == 0 ? 0 : h[j - 1], m = h[j] - g0;
+          const uint64_t* g = dst + g0;
+          first[lo + j] = m > 0 ? kf_of(g[0]) : K;
+          last[lo + j] = m > 0 ? kf_of(g[m - 1]) : -1;
+          int np = 0;                                  // distinct keyframes: the landmark's pairs
+          for (int64_t q = 0; q < m; ++q)
+            if (q == 0 || kf_of(g[q]) != kf_of(g[q - 1])) ++np;
+          npair_of[lo + j] = np;
         }
-        g[b + 1] = v;
       }
-      first[j] = m > 0 ? (int32_t)((g[0] >> 32) / C) : K;
-      last[j] = m > 0 ? (int32_t)((g[m - 1] >> 32) / C) : -1;
-      int np = 0;                                  // distinct keyframes: the landmark's pairs
-      for (int64_t a = 0; a < m; ++a)
-        if (a == 0 || (uint32_t)(g[a] >> 32) / C != (uint32_t)(g[a - 1] >> 32) / C) ++np;
-      npair_of[j] = np;
-    }
-  });
+    });
+  }
+  goff[M] = N;
   for (int j = 0; j < M; ++j)
     if (goff[j + 1] - goff[j] < 2) {
       err = "landmark " + std::to_string(j) + " has fewer than 2 observations";
@@ -261,33 +253,89 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
       return false;
     }
   }
-  // --- landmark order: (first, last, caller index)
+  // --- landmark order (first, last, caller index): a parallel stable counting sort by first
+  //     keyframe (every landmark has an observation, so first and last are keyframes), then
+  //     per first keyframe a stable counting sort by last; each landmark's slot and pair
+  //     counts are placed at its rank on the way, and summed into offsets after
   L.lm_order.resize(M);
-  for (int j = 0; j < M; ++j) L.lm_order[j] = j;
-  counting_sort(L.lm_order, last, K);
-  counting_sort(L.lm_order, first, K);
   L.lm_rank.resize(M);
-  for (int i = 0; i < M; ++i) L.lm_rank[L.lm_order[i]] = i;
-  // --- slots: groups in internal order; distinct keyframe runs are the pairs.  Offsets by
-  //     prefix sums over the internal order, then one pass fills slots and pairs together.
   L.lm_off.resize((size_t)M + 1);
   L.lm_pair.resize((size_t)M + 1);
   {
-    std::vector<int32_t> sz((size_t)M), np((size_t)M);
-    parallel_for(M, T, [&](int64_t i0, int64_t i1, int) {
-      for (int64_t i = i0; i < i1; ++i) {
-        const int j = L.lm_order[i];
-        sz[i] = (int32_t)(goff[j + 1] - goff[j]);
-        np[i] = npair_of[j];
+    std::vector<int64_t> fpos((size_t)T * K, 0);       // [chunk][first]
+    std::vector<int64_t> foff((size_t)K + 1, 0);
+    std::vector<int32_t> by_first((size_t)M);
+    parallel_tasks(T, [&](int c) {
+      const int64_t j0 = (int64_t)M * c / T, j1 = (int64_t)M * (c + 1) / T;
+      int64_t* fc = fpos.data() + (size_t)c * K;
+      for (int64_t j = j0; j < j1; ++j) fc[first[j]]++;
+    });
+    {
+      int64_t acc = 0;
+      for (int f = 0; f < K; ++f) {
+        foff[f] = acc;
+        for (int c = 0; c < T; ++c) {
+          const int64_t m = fpos[(size_t)c * K + f];
+          fpos[(size_t)c * K + f] = acc;
+          acc += m;
+        }
+      }
+      foff[K] = acc;
+    }
+    parallel_tasks(T, [&](int c) {
+      const int64_t j0 = (int64_t)M * c / T, j1 = (int64_t)M * (c + 1) / T;
+      int64_t* fc = fpos.data() + (size_t)c * K;
+      for (int64_t j = j0; j < j1; ++j) by_first[fc[first[j]]++] = (int32_t)j;
+    });
+    std::atomic<int> next_first{0};
+    parallel_tasks(T, [&](int) {
+      std::vector<int64_t> h((size_t)K + 1);
+      for (int f; (f = next_first.fetch_add(1)) < K;) {
+        const int64_t i0 = foff[f], i1 = foff[f + 1];
+        std::fill(h.begin(), h.end(), 0);
+        for (int64_t i = i0; i < i1; ++i) h[last[by_first[i]] + 1]++;
+        h[0] = i0;
+        for (int k = 0; k < K; ++k) h[k + 1] += h[k];
+        for (int64_t i = i0; i < i1; ++i) {
+          const int j = by_first[i];
+          const int64_t r = h[last[j]]++;
+          L.lm_order[r] = j;
+          L.lm_rank[j] = (int32_t)r;
+          L.lm_off[r + 1] = (int32_t)(goff[j + 1] - goff[j]);
+          L.lm_pair[r + 1] = npair_of[j];
+        }
       }
     });
+    // offsets: per-chunk sums, then each chunk's running sums from its base
+    std::vector<int64_t> so((size_t)T + 1, 0), sp((size_t)T + 1, 0);
+    parallel_tasks(T, [&](int c) {
+      const int64_t i0 = (int64_t)M * c / T, i1 = (int64_t)M * (c + 1) / T;
+      int64_t a = 0, q = 0;
+      for (int64_t i = i0; i < i1; ++i) {
+        a += L.lm_off[i + 1];
+        q += L.lm_pair[i + 1];
+      }
+      so[c + 1] = a;
+      sp[c + 1] = q;
+    });
+    for (int c = 0; c < T; ++c) {
+      so[c + 1] += so[c];
+      sp[c + 1] += sp[c];
+    }
     L.lm_off[0] = 0;
     L.lm_pair[0] = 0;
-    for (int i = 0; i < M; ++i) {
-      L.lm_off[i + 1] = L.lm_off[i] + sz[i];
-      L.lm_pair[i + 1] = L.lm_pair[i] + np[i];
-    }
+    parallel_tasks(T, [&](int c) {
+      const int64_t i0 = (int64_t)M * c / T, i1 = (int64_t)M * (c + 1) / T;
+      int64_t a = so[c], q = sp[c];
+      for (int64_t i = i0; i < i1; ++i) {
+        a += L.lm_off[i + 1];
+        q += L.lm_pair[i + 1];
+        L.lm_off[i + 1] = (int32_t)a;
+        L.lm_pair[i + 1] = (int32_t)q;
+      }
+    });
   }
+  // --- slots: groups in internal order; distinct keyframe runs are the pairs
   const int P = L.lm_pair[M];
   L.obs_order.resize(N);
   L.obs_cam.resize(N);
@@ -296,16 +344,17 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
   L.pair_obs.resize((size_t)P + 1);
   parallel_for(M, T, [&](int64_t i0, int64_t i1, int) {
     for (int64_t i = i0; i < i1; ++i) {
+      if (i + 8 < i1) __builtin_prefetch(grp.data() + goff[L.lm_order[i + 8]]);   // groups are met in rank order
       const uint64_t* g = grp.data() + goff[L.lm_order[i]];
       const int64_t m = L.lm_off[i + 1] - L.lm_off[i];
       const int64_t s0 = L.lm_off[i];
       int q = L.lm_pair[i];
       for (int64_t a = 0; a < m; ++a) {
-        const uint32_t kc = (uint32_t)(g[a] >> 32);
+        const int32_t k = kf_of(g[a]);
         L.obs_order[s0 + a] = (int32_t)(uint32_t)g[a];
-        L.obs_cam[s0 + a] = (int32_t)(kc % C);
-        if (a == 0 || kc / C != (uint32_t)(g[a - 1] >> 32) / C) {
-          L.pair_kf[q] = (int32_t)(kc / C);
+        L.obs_cam[s0 + a] = cam_of(g[a]);
+        if (a == 0 || k != kf_of(g[a - 1])) {
+          L.pair_kf[q] = k;
           L.pair_lm[q] = (int32_t)i;
           L.pair_obs[q] = (int32_t)(s0 + a);
           ++q;

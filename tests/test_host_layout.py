@@ -83,6 +83,30 @@ def test_host_layout_matches_the_definition(driver, tmp_path, name, seed):
     assert np.array_equal(out["lm_pair"], lp)
 
 
+@pytest.mark.parametrize("K,C,M,per_lm", [(256, 64, 3000, (2, 60)), (2, 1, 70000, (2, 3)), (40, 3, 1, (200, 201))])
+def test_host_layout_matches_the_definition_at_the_limits(driver, tmp_path, K, C, M, per_lm):
+    """The largest keyframe and camera counts the library accepts (both go into 8 bits of a
+    sort key), many landmarks with two or three observations each (buckets of many
+    landmarks), and a single landmark seen 200 times (one bucket, one group)."""
+    rng = np.random.default_rng(K * 1000 + C)
+    cnt = rng.integers(per_lm[0], per_lm[1], size=M)
+    lm = np.repeat(np.arange(M), cnt)
+    kf = rng.integers(0, K, size=len(lm))
+    kf[:K] = np.arange(K) if len(lm) >= K else kf[:K]      # every keyframe observed
+    cam = rng.integers(0, C, size=len(lm))
+    perm = rng.permutation(len(lm))
+    kf, cam, lm = kf[perm], cam[perm], lm[perm]
+    out = run_layout(driver, str(tmp_path), K, C, M, kf, cam, lm, 0)
+    assert not isinstance(out, str), out
+    lo, oo, off = ba.device_layout(kf, cam, lm, M)
+    assert np.array_equal(out["lm_order"], lo)
+    assert np.array_equal(out["obs_order"], oo)
+    assert np.array_equal(out["lm_off"], off)
+    pk, pl, po, lp = expected_pairs(kf, lm, lo, oo, M)
+    assert np.array_equal(out["pair_kf"], pk) and np.array_equal(out["pair_lm"], pl)
+    assert np.array_equal(out["pair_obs"][:-1], po) and np.array_equal(out["lm_pair"], lp)
+
+
 def test_host_layout_rejections(driver, tmp_path):
     kf = [0, 1, 0, 1, 0]                     # landmark 2 has one observation
     cam = [0, 0, 1, 1, 0]
