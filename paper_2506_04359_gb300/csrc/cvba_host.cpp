@@ -237,16 +237,22 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
       LinTile t{l0, l1, lm_pair[l0], lm_pair[l1], 0, 0, 0, 0, 0, 0, 0, 0};
       t.o0 = pair_obs[t.p0];
       t.o1 = pair_obs[t.p1];
-      int lo = K, hi = -1;
-      for (int q = t.p0; q < t.p1; ++q) {
-        lo = std::min(lo, pair_kf[q]);
-        hi = std::max(hi, pair_kf[q]);
-      }
-      t.kf_lo = hi >= 0 ? lo : 0;
-      t.kf_n = hi >= 0 ? hi - lo + 1 : 0;
       c->lin_tiles.push_back(t);
       l0 = l1;
     }
+    // each tile's keyframe range, from its pairs
+    parallel_ranges((int64_t)c->lin_tiles.size(), [&](int64_t t0, int64_t t1, int) {
+      for (int64_t ti = t0; ti < t1; ++ti) {
+        LinTile& t = c->lin_tiles[ti];
+        int lo = K, hi = -1;
+        for (int q = t.p0; q < t.p1; ++q) {
+          lo = std::min(lo, pair_kf[q]);
+          hi = std::max(hi, pair_kf[q]);
+        }
+        t.kf_lo = hi >= 0 ? lo : 0;
+        t.kf_n = hi >= 0 ? hi - lo + 1 : 0;
+      }
+    });
   }
   // the per-keyframe partials, keyframe-major: keyframe a owns the slots [kf_tiles_off[a],
   // kf_tiles_off[a + 1]) (12 values each), one per tile covering it, in tile order
@@ -268,7 +274,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   const int n_lt = (int)c->lin_tiles.size();
   {
     std::vector<int32_t> n_free((size_t)n_lt, 0);
-    parallel_for(n_lt, host_threads(), [&](int64_t t0, int64_t t1, int) {
+    parallel_ranges(n_lt, [&](int64_t t0, int64_t t1, int) {
       for (int64_t ti = t0; ti < t1; ++ti) {
         const LinTile& t = c->lin_tiles[ti];
         int m = 0;
@@ -294,7 +300,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     for (const LinTile& t : c->lin_tiles)            // slots in tile order per keyframe
       for (int a = t.kf_lo; a < t.kf_lo + t.kf_n; ++a) lin_kf_slot[t.kfl_off + (a - t.kf_lo)] = slot_fill[a]++;
   }
-  parallel_for(n_lt, host_threads(), [&](int64_t t0, int64_t t1, int) {
+  parallel_ranges(n_lt, [&](int64_t t0, int64_t t1, int) {
     std::vector<int32_t> cnt;
     for (int64_t ti = t0; ti < t1; ++ti) {
       const LinTile& t = c->lin_tiles[ti];
@@ -483,8 +489,11 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   const size_t state_bytes = ((size_t)C * RIG_STRIDE + (size_t)K * POSE_STRIDE + (size_t)M * 3) * (mixed ? 12 : 8);
   const size_t table_bytes = (size_t)M * 4 + (size_t)K * 4 + sizeof(Ctrl) + c->lin_tiles.size() * sizeof(LinTile) +
                              (c->schur_tiles.size() + c->direct_tiles.size()) * sizeof(SchurTile);
+  const size_t list_bytes = (kf_tiles_off.size() + lin_kf_slot.size() + blk_tiles_off.size() + blk_tiles.size() +
+                             lin_kf_off.size() + lin_kf_idx.size() + c->act_blk.size()) * sizeof(int32_t);
   CK(cudaStreamSynchronize(c->stream), "sync");     // no copy of an earlier layout still reads the staging
-  CK(ensure_pinned(c, uv_bytes + idx_bytes + state_bytes + table_bytes + 32 * 256), "pinned staging");
+  // (fewer than 40 buffers are taken from the staging, each rounded up to 256 bytes)
+  CK(ensure_pinned(c, uv_bytes + idx_bytes + state_bytes + table_bytes + list_bytes + 40 * 256), "pinned staging");
   char* const pin = static_cast<char*>(c->h_pin);
   size_t pin_off = 0;
   auto pin_take = [&](size_t bytes) {
@@ -589,19 +598,15 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     CK(dalloc(c, &kt, lin_kf_slot.size()), "alloc");
     CK(dalloc(c, &bto, (size_t)n_blk + 1), "alloc");
     CK(dalloc(c, &bt, blk_tiles.size()), "alloc");
-    CK(cudaMemcpy(kto, kf_tiles_off.data(), kf_tiles_off.size() * 4, cudaMemcpyHostToDevice), "upload");
-    if (!lin_kf_slot.empty())
-      CK(cudaMemcpy(kt, lin_kf_slot.data(), lin_kf_slot.size() * 4, cudaMemcpyHostToDevice), "upload");
-    CK(cudaMemcpy(bto, blk_tiles_off.data(), blk_tiles_off.size() * 4, cudaMemcpyHostToDevice), "upload");
-    if (!blk_tiles.empty())
-      CK(cudaMemcpy(bt, blk_tiles.data(), blk_tiles.size() * 4, cudaMemcpyHostToDevice), "upload");
+    CK(stage(kto, kf_tiles_off.data(), kf_tiles_off.size() * 4), "upload");
+    if (!lin_kf_slot.empty()) CK(stage(kt, lin_kf_slot.data(), lin_kf_slot.size() * 4), "upload");
+    CK(stage(bto, blk_tiles_off.data(), blk_tiles_off.size() * 4), "upload");
+    if (!blk_tiles.empty()) CK(stage(bt, blk_tiles.data(), blk_tiles.size() * 4), "upload");
     int32_t *lko, *lki;
     CK(dalloc(c, &lko, lin_kf_off.size()), "alloc");
     CK(dalloc(c, &lki, std::max<size_t>(1, lin_kf_idx.size())), "alloc");
-    if (!lin_kf_off.empty())
-      CK(cudaMemcpy(lko, lin_kf_off.data(), lin_kf_off.size() * 4, cudaMemcpyHostToDevice), "upload");
-    if (!lin_kf_idx.empty())
-      CK(cudaMemcpy(lki, lin_kf_idx.data(), lin_kf_idx.size() * 4, cudaMemcpyHostToDevice), "upload");
+    if (!lin_kf_off.empty()) CK(stage(lko, lin_kf_off.data(), lin_kf_off.size() * 4), "upload");
+    if (!lin_kf_idx.empty()) CK(stage(lki, lin_kf_idx.data(), lin_kf_idx.size() * 4), "upload");
     d.lin_kf_off = lko;
     d.lin_kf_idx = lki;
     d.kf_part = kp;
@@ -613,7 +618,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     d.n_blk = n_blk;
     int32_t* ab;
     CK(dalloc(c, &ab, c->act_blk.size()), "alloc");
-    CK(cudaMemcpy(ab, c->act_blk.data(), c->act_blk.size() * 4, cudaMemcpyHostToDevice), "upload");
+    CK(stage(ab, c->act_blk.data(), c->act_blk.size() * 4), "upload");
     d.act_blk = ab;
     d.n_act = (int)c->act_blk.size();
   }
@@ -1174,11 +1179,15 @@ cvba_status cvba_get_landmarks(cvba_ctx* c, double* p_w) {
     return CVBA_OK;
   }
   DeviceGuard g(c->device);
-  const int cur = read_cur(c);
-  std::vector<double> h((size_t)c->M * 3);
-  CK(d2h(c, h.data(), c->d.lm[cur], h.size() * 8), "copy landmarks");
-  for (int i = 0; i < c->M; ++i)
-    for (int k = 0; k < 3; ++k) p_w[(size_t)c->lm_order[i] * 3 + k] = h[(size_t)i * 3 + k];
+  const int cur = read_cur(c);                     // (waits for the stream: the staging is free)
+  const size_t bytes = (size_t)c->M * 3 * 8;
+  CK(ensure_pinned(c, bytes), "pinned staging");
+  CK(d2h(c, c->h_pin, c->d.lm[cur], bytes), "copy landmarks");
+  const double* h = static_cast<const double*>(c->h_pin);
+  parallel_for(c->M, host_threads(), [&](int64_t i0, int64_t i1, int) {
+    for (int64_t i = i0; i < i1; ++i)
+      for (int k = 0; k < 3; ++k) p_w[(size_t)c->lm_order[i] * 3 + k] = h[(size_t)i * 3 + k];
+  });
   return CVBA_OK;
 }
 

@@ -34,10 +34,13 @@ constexpr int kCholBlockedMinN = 320;   // RCS size from which the blocked facto
 constexpr int kMaxPanels = (6 * (K_MAX - 1) + 31) / 32;   // 32-column panels of the largest system
 
 // Host threads (cvba_layout.cpp): fn(t) for t in [0, n) on n threads; fn(begin, end, thread)
-// over [0, n) split in contiguous ranges over up to `threads` threads.
+// over [0, n) split in contiguous ranges over up to `threads` threads (one thread per 4096
+// items at most); parallel_ranges splits [0, n) over up to all host threads whatever n is,
+// for loops whose items are each large (tiles of many pairs).
 int host_threads();
 void parallel_tasks(int n, const std::function<void(int)>& fn);
 void parallel_for(int64_t n, int threads, const std::function<void(int64_t, int64_t, int)>& fn);
+void parallel_ranges(int64_t n, const std::function<void(int64_t, int64_t, int)>& fn);
 
 // Host part of a window's layout (cvba_layout.cpp): landmark order and rank, observation
 // slots (caller index per slot, camera per slot), landmark slot offsets, and the (landmark,

@@ -141,6 +141,15 @@ void parallel_for(int64_t n, int threads, const std::function<void(int64_t, int6
   parallel_tasks(threads, [&](int t) { fn(n * t / threads, n * (t + 1) / threads, t); });
 }
 
+void parallel_ranges(int64_t n, const std::function<void(int64_t, int64_t, int)>& fn) {
+  const int threads = (int)std::max<int64_t>(1, std::min<int64_t>(host_threads(), n));
+  if (threads == 1) {
+    fn(0, n, 0);
+    return;
+  }
+  parallel_tasks(threads, [&](int t) { fn(n * t / threads, n * (t + 1) / threads, t); });
+}
+
 bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t* kf, const int32_t* cam,
                          const int32_t* lm, HostLayout& L, std::string& err) {
   static_assert(K_MAX <= 256 && C_MAX <= 256, "keyframe and camera take 8 bits of a sort key");

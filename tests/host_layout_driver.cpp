@@ -6,8 +6,8 @@
 //                                     (int32); writes out.bin (lm_order, lm_rank, obs_order,
 //                                     lm_off, obs_cam, pair_kf, pair_lm, pair_obs, lm_pair) and
 //                                     sizes.txt (P), or err.txt if the layout is rejected
-//   host_layout_driver pool           nested and concurrent sections; exit status 0 if every
-//                                     task ran exactly once
+//   host_layout_driver pool           nested and concurrent sections, and ranges over few
+//                                     large items; exit status 0 if every task ran exactly once
 #include <atomic>
 #include <cstdio>
 #include <fstream>
@@ -66,6 +66,14 @@ static int run_pool() {
     });
   for (auto& th : callers) th.join();
   want += 4L * 100 * 100000;
+  for (int64_t n : {0, 1, 3, 300, 100000}) {                              // every item exactly once
+    std::vector<std::atomic<int>> seen((size_t)n);
+    parallel_ranges(n, [&](int64_t a, int64_t b, int) {
+      for (int64_t i = a; i < b; ++i) seen[i]++;
+    });
+    for (auto& s : seen) sum += s.load();
+    want += n;
+  }
   std::printf("%ld %ld\n", sum.load(), want);
   return sum.load() == want ? 0 : 1;
 }
