@@ -7,14 +7,15 @@
 //  - observation slots are ordered by (internal landmark, keyframe, camera, caller index);
 //  - pairs are the distinct (internal landmark, keyframe) runs of the slots, in slot order.
 //
-// Algorithm: the caller's landmarks are cut into buckets of 2^s consecutive indices (about
-// 16k observations a bucket); every observation becomes a 64-bit key (landmark within its
-// bucket, keyframe, camera, caller index); a parallel counting pass and stable scatter group
-// the keys by bucket; each bucket, in a core's cache, is then put in order by two stable
-// counting sorts, by (keyframe, camera) and then by landmark, which leaves every landmark's
-// keys in (keyframe, camera, caller index) order; the landmarks are ordered by one stable
-// counting sort on (first, last); and the slots and pairs are filled group by group from the
-// keys, with no gather of the caller's arrays.  Every step is deterministic and independent
+// Algorithm: the caller's landmarks are cut into buckets of 2^s consecutive indices (8k to
+// 16k observations a bucket on average); every observation becomes a 64-bit key (landmark
+// within its bucket, keyframe, camera, caller index); a parallel counting pass and stable
+// scatter group the keys by bucket; each bucket, in a core's cache, is then put in order by
+// two stable counting sorts, by (keyframe, camera) and then by landmark, which leaves every
+// landmark's keys in (keyframe, camera, caller index) order; the landmarks are ordered by a
+// stable counting sort on the first keyframe and, within each first keyframe, one on the
+// last; and the slots and pairs are filled group by group from the keys, with no gather of
+// the caller's arrays.  Every step is deterministic and independent
 // of the thread count and of which thread takes which bucket.
 #include <algorithm>
 #include <atomic>
