@@ -514,6 +514,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     float* h = reinterpret_cast<float*>(pin_take(uv_bytes));
     parallel_for(N, host_threads(), [&](int64_t s0, int64_t s1, int) {
       for (int64_t s = s0; s < s1; ++s) {
+        if (s + 16 < s1) __builtin_prefetch(uv + 2 * (size_t)c->obs_order[s + 16]);   // a random gather
         h[2 * s] = (float)uv[2 * (size_t)c->obs_order[s]];
         h[2 * s + 1] = (float)uv[2 * (size_t)c->obs_order[s] + 1];
       }
@@ -529,6 +530,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     double* h = reinterpret_cast<double*>(pin_take(uv_bytes));
     parallel_for(N, host_threads(), [&](int64_t s0, int64_t s1, int) {
       for (int64_t s = s0; s < s1; ++s) {
+        if (s + 16 < s1) __builtin_prefetch(uv + 2 * (size_t)c->obs_order[s + 16]);   // a random gather
         h[2 * s] = uv[2 * (size_t)c->obs_order[s]];
         h[2 * s + 1] = uv[2 * (size_t)c->obs_order[s] + 1];
       }
