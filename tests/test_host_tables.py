@@ -107,6 +107,23 @@ def wide_window(seed=0):
                   seed)
 
 
+def small_window(K, C, M, fixed, seed=0):
+    """A small random window: every landmark seen from 2 to 4 random (keyframe, camera) views,
+    every keyframe observed."""
+    rng = np.random.default_rng(seed)
+    kf, cam, lm = [], [], []
+    for j in range(M):
+        for _ in range(rng.integers(2, 5)):
+            kf.append(rng.integers(0, K)), cam.append(rng.integers(0, C)), lm.append(j)
+    kf[:K] = list(range(K))
+    N = len(kf)
+    intr = np.tile([300.0, 310.0, 160.0, 120.0], (C, 1))
+    T_cb = np.tile(np.hstack([np.eye(3), np.ones((3, 1))]), (C, 1, 1))
+    poses = np.tile(np.hstack([np.eye(3), np.zeros((3, 1))]), (K, 1, 1))
+    return Window(K, C, M, fixed, kf, cam, lm, rng.normal(100, 10, (N, 2)), intr, T_cb, poses,
+                  rng.normal(0, 3, (M, 3)), seed)
+
+
 def run(driver, d, w, prec, lin_pairs=0, schur_lms=0, chol_mode=0):
     w.write(d)
     r = subprocess.run([driver, d, prec, str(lin_pairs), str(schur_lms), str(chol_mode)], capture_output=True,
@@ -303,9 +320,18 @@ def check_tables(w, sz, t, prec, lin_pairs, schur_lms, chol_mode):
     ("c2", "mixed", 0, 0, 0),
     ("wide", "mixed", 0, 0, 0),
     ("wide", "fp64", 32, 8, 1),
+    ("two_keyframes", "fp64", 0, 0, 0),
+    ("fixed_last", "mixed", 0, 0, 2),
+    ("fixed_first_one_camera", "fp64", 32, 8, 0),
 ])
 def test_host_tables_match_their_definitions(driver, tmp_path, name, prec, lin_pairs, schur_lms, chol_mode):
-    w = wide_window() if name == "wide" else Window.from_problem(synth.make_problem(name, 0))
+    small = {"two_keyframes": (2, 1, 3, 0), "fixed_last": (8, 3, 60, 7), "fixed_first_one_camera": (6, 1, 500, 0)}
+    if name == "wide":
+        w = wide_window()
+    elif name in small:
+        w = small_window(*small[name])
+    else:
+        w = Window.from_problem(synth.make_problem(name, 0))
     sz, t = run(driver, str(tmp_path), w, prec, lin_pairs, schur_lms, chol_mode)
     if name == "wide":
         assert len(t("direct_tiles")) > 0     # the window exercises direct tiles
