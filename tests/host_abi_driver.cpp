@@ -133,6 +133,36 @@ int main(int argc, char** argv) {
     b.z_min = nan;
     rec("solve_nonfinite_zmin", cvba_solve(c, &b, nullptr), c);
   }
+  // the captured solve graph: kept while the options and the device view are unchanged
+  // (new state values change neither), rebuilt when either changes
+  {
+    const int g0 = g_instantiate_count;
+    cvba_solve(c, &o, nullptr);
+    cvba_solve(c, &o, nullptr);
+    out << "graphs_same " << g_instantiate_count - g0 << "\n";
+    cvba_opts o3 = o;
+    o3.iters = 3;
+    cvba_solve(c, &o3, nullptr);
+    out << "graphs_iters " << g_instantiate_count - g0 << "\n";
+    cvba_set_landmarks(c, M, lms.data());
+    cvba_set_poses(c, K, poses.data(), fixed);
+    cvba_solve(c, &o3, nullptr);
+    out << "graphs_new_state " << g_instantiate_count - g0 << "\n";
+    cvba_set_observations(c, N, kf.data(), cam.data(), lm.data(), uv.data());
+    cvba_solve(c, &o3, nullptr);
+    out << "graphs_same_window_again " << g_instantiate_count - g0 << "\n";
+    cvba_set_tuning(c, 32, 8);                     // the sizes the window had already: same view
+    cvba_solve(c, &o3, nullptr);
+    out << "graphs_same_tuning " << g_instantiate_count - g0 << "\n";
+    cvba_set_tuning(c, 64, 16);
+    cvba_solve(c, &o3, nullptr);
+    out << "graphs_tuning " << g_instantiate_count - g0 << "\n";
+    rec("chol_mode_2", cvba_set_chol_mode(c, 2), c);
+    rec("solve_blocked", cvba_solve(c, &o3, nullptr), c);
+    out << "graphs_chol_mode " << g_instantiate_count - g0 << "\n";
+    cvba_set_tuning(c, 0, 0);
+    cvba_set_chol_mode(c, 0);
+  }
   rec("chol_mode_3", cvba_set_chol_mode(c, 3), c);
   rec("tuning_negative", cvba_set_tuning(c, -1, 0), c);
   rec("damping_set", cvba_set_damping(c, 0.5, 3.0), c);

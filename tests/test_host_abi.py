@@ -5,7 +5,8 @@ sizes and options (CVBA_ERR_INVALID_ARG), indices out of range (CVBA_ERR_INDEX, 
 first bad observation), non-finite values (CVBA_ERR_NONFINITE), a landmark left with one
 observation, and the checkpoint: its size query, a round trip into a fresh context holding
 another state of the same problem (poses, landmarks and damping restored), and the refusal
-of a truncated buffer, a corrupted header and another problem's context."""
+of a truncated buffer, a corrupted header and another problem's context; and when the captured
+solve graph is reused or rebuilt."""
 import os
 import shutil
 import subprocess
@@ -36,7 +37,7 @@ EXPECTED = {
     "observations_single_view_landmark": INVALID, "observations_none": INVALID, "observations": OK,
     "solve_negative_huber": INVALID, "solve_refine_9": INVALID, "solve_negative_iters": INVALID,
     "solve_nonfinite_zmin": INVALID, "chol_mode_3": INVALID, "tuning_negative": INVALID, "damping_set": OK,
-    "state_size": OK, "state_get": OK, "state_truncated": INVALID, "state_garbage": INVALID, "state_set": OK,
+    "chol_mode_2": OK, "solve_blocked": OK, "state_size": OK, "state_get": OK, "state_truncated": INVALID, "state_garbage": INVALID, "state_set": OK,
     "other_problem_layout": OK, "state_other_problem": INVALID,
 }
 
@@ -64,7 +65,7 @@ def test_abi_statuses_and_checkpoint(driver, tmp_path):
     status, msg, extra = {}, {}, {}
     for line in open(tmp_path / "status.txt"):
         name, rest = line.rstrip("\n").split(" ", 1)
-        if name in ("done", "state_bytes", "state_restored"):
+        if name in ("done", "state_bytes", "state_restored") or name.startswith("graphs_"):
             extra[name] = rest.split()
             continue
         code, _, text = rest.partition(" ")
@@ -81,3 +82,9 @@ def test_abi_statuses_and_checkpoint(driver, tmp_path):
     assert n_query == n_got and n_query > 8 * (12 * p.K + 3 * p.M)
     flag, lam, nu = extra["state_restored"]
     assert flag == "1" and float(lam) == 0.5 and float(nu) == 3.0
+    # the solve graph: reused for the same options and device view (new state values, the same
+    # window loaded again into the same buffers, a tiling equal to the window's default sizes),
+    # rebuilt for new options, another tiling or another factorisation
+    graphs = {k: int(v[0]) for k, v in extra.items() if k.startswith("graphs_")}
+    assert graphs == {"graphs_same": 1, "graphs_iters": 2, "graphs_new_state": 2, "graphs_same_window_again": 2,
+                      "graphs_same_tuning": 2, "graphs_tuning": 3, "graphs_chol_mode": 4}
