@@ -161,8 +161,8 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
   std::vector<uint64_t>& grp = L.grp;
   std::vector<int64_t>& goff = L.goff;
   // Landmark buckets: 2^sh consecutive caller landmarks each, sized so that a bucket holds
-  // about 16k observations (its keys and a copy stay in a core's cache) and at most 2^16
-  // landmarks.
+  // 8k to 16k observations on average (its keys and a copy stay in a core's cache) and at most
+  // 2^16 landmarks.
   int sh = 0;
   while (sh < 16 && ((int64_t)N << (sh + 1)) <= (int64_t)16384 * std::max(M, 1)) ++sh;
   const int W = 1 << sh;
