@@ -95,9 +95,16 @@ cvba_status cuda_fail(cvba_ctx* c, cudaError_t e, const char* what) {
   } while (0)
 
 bool all_finite(const double* p, size_t n) {
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(p[i])) return false;
-  return true;
+  const int T = host_threads();
+  std::vector<char> ok((size_t)T, 1);              // per thread: no non-finite value seen
+  parallel_for((int64_t)n, T, [&](int64_t i0, int64_t i1, int t) {
+    for (int64_t i = i0; i < i1; ++i)
+      if (!std::isfinite(p[i])) {
+        ok[t] = 0;
+        break;
+      }
+  });
+  return std::all_of(ok.begin(), ok.end(), [](char v) { return v != 0; });
 }
 
 void drop_graph(cvba_ctx* c) {
@@ -889,7 +896,10 @@ cvba_status cvba_set_landmarks(cvba_ctx* c, int n_lm, const double* p_w) {
   DeviceGuard g(c->device);
   if (c->have_layout && n_lm != c->M) c->have_layout = false;
   c->M = n_lm;
-  c->lms.assign(p_w, p_w + (size_t)n_lm * 3);
+  c->lms.resize((size_t)n_lm * 3);
+  parallel_for((int64_t)n_lm * 3, host_threads(), [&](int64_t e0, int64_t e1, int) {
+    std::copy(p_w + e0, p_w + e1, c->lms.begin() + e0);
+  });
   c->have_lms = true;
   if (c->have_layout) return upload_state(c, false, true);
   return CVBA_OK;

@@ -8,6 +8,7 @@
 //     writes  <dir>/status.txt
 #include <cstdlib>
 #include <fstream>
+#include <limits>
 
 #include "cvba_host.cpp"
 #include "cuda_standin.h"
@@ -86,6 +87,16 @@ int main(int argc, char** argv) {
     auto l2 = lms;
     l2[4] = nan;
     rec("landmarks_nonfinite", cvba_set_landmarks(c, M, l2.data()), c);
+  }
+  {
+    // a large array (checked over several threads): one non-finite value near the end
+    cvba_ctx* big = nullptr;
+    cvba_create(&big, 0, nullptr, CVBA_FP64);
+    std::vector<double> many((size_t)3 * 50000, 1.0);
+    rec("landmarks_many", cvba_set_landmarks(big, 50000, many.data()), big);
+    many[many.size() - 2] = std::numeric_limits<double>::infinity();
+    rec("landmarks_many_nonfinite", cvba_set_landmarks(big, 50000, many.data()), big);
+    cvba_destroy(big);
   }
   rec("landmarks", cvba_set_landmarks(c, M, lms.data()), c);
   // observations

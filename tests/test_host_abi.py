@@ -31,7 +31,8 @@ EXPECTED = {
     "rig_zero_image_size": INVALID, "rig": OK,
     "poses_one_keyframe": INVALID, "poses_257_keyframes": INVALID, "poses_fixed_out_of_range": INDEX,
     "poses_nonfinite": NONFINITE, "poses": OK,
-    "landmarks_none": INVALID, "landmarks_nonfinite": NONFINITE, "landmarks": OK,
+    "landmarks_none": INVALID, "landmarks_nonfinite": NONFINITE, "landmarks_many": OK,
+    "landmarks_many_nonfinite": NONFINITE, "landmarks": OK,
     "observations_camera_out_of_range": INDEX, "observations_landmark_negative": INDEX,
     "observations_keyframe_out_of_range": INDEX, "observations_nonfinite": NONFINITE,
     "observations_single_view_landmark": INVALID, "observations_none": INVALID, "observations": OK,
