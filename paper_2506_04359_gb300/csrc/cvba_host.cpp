@@ -38,6 +38,11 @@ struct cvba_ctx {
   std::vector<LinTile> lin_tiles;
   std::vector<SchurTile> schur_tiles, direct_tiles;
   std::vector<int32_t> act_blk;                 // RCS blocks the reduction writes
+  struct Tables {                               // host tables of the layout, kept so that a window
+    std::vector<int32_t> lm_blk, kf_tiles_off;  // of the same shape reuses their storage
+    std::vector<int32_t> lin_kf_off, lin_kf_idx, lin_kf_slot, blk_tiles_off, blk_tiles;
+    std::vector<int> win_lo, win_hi;
+  } tb;
 
   struct Slot {
     void* p;
@@ -213,7 +218,8 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   std::vector<int32_t>& lm_pair = HL.lm_pair;
   std::vector<int32_t>& obs_cam = HL.obs_cam;
   const int P = (int)pair_kf.size();
-  std::vector<int32_t> lm_blk(M + 1, 0);
+  std::vector<int32_t>& lm_blk = c->tb.lm_blk;
+  lm_blk.assign((size_t)M + 1, 0);
   {
     int64_t acc = 0;
     for (int j = 0; j < M; ++j) {
@@ -263,7 +269,8 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   }
   // the per-keyframe partials, keyframe-major: keyframe a owns the slots [kf_tiles_off[a],
   // kf_tiles_off[a + 1]) (12 values each), one per tile covering it, in tile order
-  std::vector<int32_t> kf_tiles_off(K + 1, 0);
+  std::vector<int32_t>& kf_tiles_off = c->tb.kf_tiles_off;
+  kf_tiles_off.assign((size_t)K + 1, 0);
   size_t kf_part_len = 0;
   {
     for (auto& t : c->lin_tiles) {
@@ -273,7 +280,9 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     }
     for (int a = 0; a < K; ++a) kf_tiles_off[a + 1] += kf_tiles_off[a];
   }
-  std::vector<int32_t> lin_kf_off, lin_kf_idx, lin_kf_slot;
+  std::vector<int32_t>& lin_kf_off = c->tb.lin_kf_off;
+  std::vector<int32_t>& lin_kf_idx = c->tb.lin_kf_idx;
+  std::vector<int32_t>& lin_kf_slot = c->tb.lin_kf_slot;
   // per tile and keyframe of its range: the tile-local indices of that keyframe's pairs
   // (free keyframes only), in pair order, and the keyframe's partial slot for this tile.
   // Offsets by a sequential pass over the tiles (free-pair counts first, in parallel), the
@@ -300,7 +309,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     }
     lin_kf_off.assign((size_t)kfl, 0);
     lin_kf_slot.assign((size_t)kfl, 0);
-    lin_kf_idx.assign((size_t)kfi, 0);
+    lin_kf_idx.resize((size_t)kfi);                // every entry is written below
   }
   {
     std::vector<int32_t> slot_fill(kf_tiles_off.begin(), kf_tiles_off.end() - 1);
@@ -331,7 +340,10 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
     // group Schur 367 against 381 us, reduction 25 against 22 us)
     const int target = c->tune_schur_lms > 0 ? std::min(SCHUR_TILE_LMS, c->tune_schur_lms)
                                              : std::max(8, std::min(96, (M + n_sm - 1) / n_sm));
-    std::vector<int> lo(M, INT32_MAX), hi(M, -1);
+    std::vector<int>& lo = c->tb.win_lo;
+    std::vector<int>& hi = c->tb.win_hi;
+    lo.assign((size_t)M, INT32_MAX);
+    hi.assign((size_t)M, -1);
     parallel_for(M, host_threads(), [&](int64_t j0, int64_t j1, int) {
       for (int64_t j = j0; j < j1; ++j)
         for (int q = lm_pair[j]; q < lm_pair[j + 1]; ++q) {
@@ -374,7 +386,9 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
   // window partial offsets and, per block (a >= b) of free keyframes, the covering tiles
   const int nfb = K - 1;
   const int n_blk = nfb * (nfb + 1) / 2;
-  std::vector<int32_t> blk_tiles_off(n_blk + 1, 0), blk_tiles;
+  std::vector<int32_t>& blk_tiles_off = c->tb.blk_tiles_off;
+  std::vector<int32_t>& blk_tiles = c->tb.blk_tiles;
+  blk_tiles_off.assign((size_t)n_blk + 1, 0);
   size_t schur_part_len = 0;
   {
     for (auto& t : c->schur_tiles) {
@@ -387,7 +401,7 @@ cvba_status build_layout(cvba_ctx* c, const int32_t* kf, const int32_t* cam, con
         for (int b = t.k_lo; b <= a; ++b) blk_tiles_off[a * (a + 1) / 2 + b + 1]++;
     }
     for (int i = 0; i < n_blk; ++i) blk_tiles_off[i + 1] += blk_tiles_off[i];
-    blk_tiles.resize(blk_tiles_off[n_blk]);
+    blk_tiles.resize(blk_tiles_off[n_blk]);         // every entry is written below
     std::vector<int32_t> fill(blk_tiles_off.begin(), blk_tiles_off.end() - 1);
     for (int ti = 0; ti < (int)c->schur_tiles.size(); ++ti) {
       const auto& t = c->schur_tiles[ti];

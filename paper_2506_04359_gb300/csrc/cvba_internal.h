@@ -51,6 +51,7 @@ struct HostLayout {
   // work arrays, kept for the next layout of the same context
   std::vector<uint64_t> rec_key, grp;
   std::vector<int64_t> goff;
+  std::vector<int32_t> first, last, npair_of, by_first;
 };
 // False (with a message) if a landmark has fewer than 2 observations or a free keyframe has
 // none.  Indices must be valid.

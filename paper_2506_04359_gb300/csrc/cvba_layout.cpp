@@ -214,7 +214,12 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
   //     index) order; then each landmark's first and last keyframe and its pair count
   goff.resize((size_t)M + 1);
   grp.resize((size_t)N);
-  std::vector<int32_t> first((size_t)M), last((size_t)M), npair_of((size_t)M);
+  std::vector<int32_t>& first = L.first;           // every entry is written below
+  std::vector<int32_t>& last = L.last;
+  std::vector<int32_t>& npair_of = L.npair_of;
+  first.resize((size_t)M);
+  last.resize((size_t)M);
+  npair_of.resize((size_t)M);
   {
     const int KC = K * C;
     std::atomic<int> next_bucket{0};
@@ -274,7 +279,8 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
   {
     std::vector<int64_t> fpos((size_t)T * K, 0);       // [chunk][first]
     std::vector<int64_t> foff((size_t)K + 1, 0);
-    std::vector<int32_t> by_first((size_t)M);
+    std::vector<int32_t>& by_first = L.by_first;    // every entry is written below
+    by_first.resize((size_t)M);
     parallel_tasks(T, [&](int c) {
       const int64_t j0 = (int64_t)M * c / T, j1 = (int64_t)M * (c + 1) / T;
       int64_t* fc = fpos.data() + (size_t)c * K;
