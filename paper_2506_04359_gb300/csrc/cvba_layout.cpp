@@ -224,8 +224,9 @@ bool compute_host_layout(int K, int C, int M, int N, int fixed_kf, const int32_t
     const int KC = K * C;
     std::atomic<int> next_bucket{0};
     parallel_tasks(T, [&](int) {
-      std::vector<uint64_t> tmp;
-      std::vector<int64_t> h((size_t)std::max(KC, W) + 1);
+      thread_local std::vector<uint64_t> tmp;      // per thread, kept by the pool's workers
+      thread_local std::vector<int64_t> h;
+      if (h.size() < (size_t)std::max(KC, W) + 1) h.resize((size_t)std::max(KC, W) + 1);
       for (int b; (b = next_bucket.fetch_add(1)) < B;) {
         const int64_t e0 = boff[b], E = boff[b + 1] - e0;
         const int lo = b << sh, nl = std::min(M - lo, W);
