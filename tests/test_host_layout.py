@@ -107,6 +107,43 @@ def test_host_layout_matches_the_definition_at_the_limits(driver, tmp_path, K, C
     assert np.array_equal(out["pair_obs"][:-1], po) and np.array_equal(out["lm_pair"], lp)
 
 
+def test_host_layout_on_many_random_small_windows(driver, tmp_path):
+    """120 seeded random windows (2 to 12 keyframes, 1 to 4 cameras, 1 to 300 landmarks with
+    2 to 7 views each, now and then one with a single view, repeated (keyframe, camera) views,
+    a random fixed keyframe, shuffled order): each layout equals the definition, and each
+    refusal is one the definition calls for (a landmark with fewer than two observations, or a
+    free keyframe with none)."""
+    rng = np.random.default_rng(2024)
+    n_rejected = 0
+    for _ in range(120):
+        K, C, M = int(rng.integers(2, 13)), int(rng.integers(1, 5)), int(rng.integers(1, 301))
+        cnt = rng.integers(2, 8, size=M)
+        if rng.random() < 0.15:                  # now and then a landmark seen once
+            cnt[rng.integers(0, M)] = 1
+        lm = np.repeat(np.arange(M), cnt)
+        kf = rng.integers(0, K, size=len(lm))
+        cam = rng.integers(0, C, size=len(lm))
+        perm = rng.permutation(len(lm))
+        kf, cam, lm = kf[perm], cam[perm], lm[perm]
+        fixed = int(rng.integers(0, K))
+        out = run_layout(driver, str(tmp_path), K, C, M, kf, cam, lm, fixed)
+        counts = np.bincount(lm, minlength=M)
+        seen = np.bincount(kf, minlength=K)
+        should_reject = bool(np.any(counts < 2) or np.any((seen == 0) & (np.arange(K) != fixed)))
+        if isinstance(out, str):
+            assert should_reject, out
+            n_rejected += 1
+            continue
+        assert not should_reject
+        lo, oo, off = ba.device_layout(kf, cam, lm, M)
+        assert np.array_equal(out["lm_order"], lo) and np.array_equal(out["obs_order"], oo)
+        assert np.array_equal(out["lm_off"], off)
+        pk, pl, po, lp = expected_pairs(kf, lm, lo, oo, M)
+        assert np.array_equal(out["pair_kf"], pk) and np.array_equal(out["pair_lm"], pl)
+        assert np.array_equal(out["pair_obs"][:-1], po) and np.array_equal(out["lm_pair"], lp)
+    assert 0 < n_rejected < 120                  # both outcomes occur
+
+
 def test_host_layout_rejections(driver, tmp_path):
     kf = [0, 1, 0, 1, 0]                     # landmark 2 has one observation
     cam = [0, 0, 1, 1, 0]
