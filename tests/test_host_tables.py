@@ -336,3 +336,47 @@ def test_host_tables_match_their_definitions(driver, tmp_path, name, prec, lin_p
     if name == "wide":
         assert len(t("direct_tiles")) > 0     # the window exercises direct tiles
     check_tables(w, sz, t, prec, lin_pairs, schur_lms, chol_mode)
+
+
+def random_window(rng):
+    """A random window: 2 to 40 keyframes, 1 to 4 cameras, 1 to 800 landmarks, most seen from a
+    few nearby keyframes, some from keyframes spread over the window; every keyframe observed."""
+    K, C, M = int(rng.integers(2, 41)), int(rng.integers(1, 5)), int(rng.integers(1, 801))
+    kf, cam, lm = [], [], []
+    for j in range(M):
+        if rng.random() < 0.08:
+            ks = rng.choice(K, size=int(rng.integers(min(2, K), K + 1)), replace=False)
+        else:
+            a = int(rng.integers(0, K))
+            ks = np.clip(a + np.arange(int(rng.integers(1, 5))), 0, K - 1)
+        views = [(int(k), int(rng.integers(0, C))) for k in ks for _ in range(int(rng.integers(1, 3)))]
+        if len(views) < 2:
+            views.append((int(ks[0]), int(rng.integers(0, C))))
+        for k, c in views:
+            kf.append(k), cam.append(c), lm.append(j)
+    kf += list(range(K))                         # every keyframe observed, by landmark 0
+    cam += [0] * K
+    lm += [0] * K
+    perm = rng.permutation(len(kf))
+    kf, cam, lm = (np.asarray(a)[perm] for a in (kf, cam, lm))
+    N = len(kf)
+    intr = np.tile([350.0, 350.0, 200.0, 150.0], (C, 1))
+    T_cb = np.tile(np.hstack([np.eye(3), np.zeros((3, 1))]), (C, 1, 1))
+    poses = np.tile(np.hstack([np.eye(3), np.zeros((3, 1))]), (K, 1, 1))
+    return Window(K, C, M, int(rng.integers(0, K)), kf, cam, lm, rng.normal(200, 30, (N, 2)), intr, T_cb, poses,
+                  rng.normal(0, 4, (M, 3)), int(rng.integers(0, 1000)))
+
+
+def test_host_tables_on_random_windows(driver, tmp_path):
+    """24 seeded random windows, each with a random precision, tiling and factorisation mode."""
+    rng = np.random.default_rng(77)
+    for i in range(24):
+        w = random_window(rng)
+        prec = "mixed" if rng.random() < 0.5 else "fp64"
+        lin = int(rng.choice([0, 32, 64, 128, 256]))
+        schur = int(rng.choice([0, 8, 16, 32, 64, 128]))
+        mode = int(rng.integers(0, 3))
+        d = tmp_path / f"r{i}"
+        d.mkdir()
+        sz, t = run(driver, str(d), w, prec, lin, schur, mode)
+        check_tables(w, sz, t, prec, lin, schur, mode)
